@@ -1,0 +1,156 @@
+"""CPU oracle of the approximate-region hot path (TEST INFRASTRUCTURE ONLY).
+
+Only the tests, ``__graft_entry__.smoke()`` and the benchmark's CPU-baseline leg
+import this package. The product path (the CUDA library and its binding) never
+does, and the two share no code: the oracle is plain C in this directory,
+loaded through ctypes, restating each technique of HPAC-Offload (arXiv
+2308.16877) step by step on the logical grid-stride schedule of Section 3.1.3.
+
+Constants mirror the C enums in ``hpac_oracle.c`` (written independently of the
+library's header).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+
+import numpy as np
+
+from . import build as _build
+
+BLACKSCHOLES, EOS, IDENTITY = 0, 1, 3
+F32, F64 = 0, 1
+THREAD, WARP, BLOCK = 0, 1, 2
+SMALL, LARGE, INI, FINI, RANDOM = 0, 1, 2, 3, 4
+EXACT, APPROX, SKIPPED = 0, 1, 2
+MAPE, RMSE, MCR = 0, 1, 2
+
+
+class Region(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("dtype", C.c_int32), ("n", C.c_int64),
+                ("n_in", C.c_int32), ("n_out", C.c_int32), ("in_stride", C.c_int64),
+                ("out_stride", C.c_int64), ("threads", C.c_int64), ("block", C.c_int32),
+                ("param", C.c_double)]
+
+
+_lib = None
+
+
+def lib() -> C.CDLL:
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = C.CDLL(path)
+        P, I64, I32, D = C.c_void_p, C.c_int64, C.c_int32, C.c_double
+        RP = C.POINTER(Region)
+        L.orc_run_exact.argtypes = [RP, P, P]
+        L.orc_run_perfo.argtypes = [RP, P, I32, I32, D, C.c_uint64, I32, P, P, P]
+        L.orc_run_taf.argtypes = [RP, P, I32, I32, D, I32, P, P, P, P]
+        L.orc_run_iact.argtypes = [RP, P, I32, I32, D, I32, P, P, P, P, P]
+        L.orc_quality.argtypes = [I64, P, P, I32, P, P]
+        L.orc_num_threads.restype = C.c_int
+        for f in ("orc_run_exact", "orc_run_perfo", "orc_run_taf", "orc_run_iact", "orc_quality"):
+            getattr(L, f).restype = C.c_int
+        _hydro_bind(L)
+        _lib = L
+    return _lib
+
+
+def _hydro_bind(L):
+    if not hasattr(L, "orc_hydro_init"):
+        return
+    P, I32, D = C.c_void_p, C.c_int32, C.c_double
+    L.orc_hydro_init.argtypes = [I32, P, P, P, P, P, P, P]
+    L.orc_hydro_step.argtypes = [I32, D, D, P, P, P, P, P, P, P, P, P, P, P, P, P, I32, P, P, P]
+    L.orc_hex_volume.argtypes = [P, P, P]
+    L.orc_hex_volume.restype = D
+    L.orc_hex_volume_grad.argtypes = [P, P, P, P, P, P]
+    for f in ("orc_hydro_init", "orc_hydro_step"):
+        getattr(L, f).restype = C.c_int
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def num_threads() -> int:
+    return int(lib().orc_num_threads())
+
+
+def _region(kind, x, n, param, threads, block):
+    x = np.ascontiguousarray(x)
+    dtype = F32 if x.dtype == np.float32 else F64
+    if x.dtype not in (np.float32, np.float64):
+        raise TypeError(x.dtype)
+    d, stride = x.shape
+    n = stride if n is None else n
+    r = Region(kind, dtype, n, d, 1, stride, n, threads, block, float(param))
+    return r, x, n
+
+
+def _out(x, n, out):
+    if out is None:
+        return np.zeros(n, dtype=x.dtype)
+    return out
+
+
+def run_exact(kind, x, param=0.0, n=None):
+    r, x, n = _region(kind, x, n, param, 0, 32)
+    out = np.zeros(n, dtype=x.dtype)
+    if lib().orc_run_exact(C.byref(r), _ptr(x), _ptr(out)):
+        raise ValueError("oracle rejected the region")
+    return out
+
+
+def run_perfo(kind, x, param, pkind, m=0, rate=0.0, seed=0, herded=1, threads=0, block=256,
+              n=None, out=None):
+    r, x, n = _region(kind, x, n, param, threads, block)
+    out = _out(x, n, out)
+    mask = np.full(n, 255, dtype=np.uint8)
+    cnt = np.zeros(4, dtype=np.int64)
+    if lib().orc_run_perfo(C.byref(r), _ptr(x), pkind, m, rate, seed, herded, _ptr(out),
+                           _ptr(mask), _ptr(cnt)):
+        raise ValueError("oracle rejected perforation arguments")
+    return out, mask, cnt
+
+
+def run_taf(kind, x, param, hsize, psize, thresh, level=THREAD, threads=0, block=256, n=None):
+    r, x, n = _region(kind, x, n, param, threads, block)
+    out = np.zeros(n, dtype=x.dtype)
+    stat = np.zeros(n, dtype=x.dtype)
+    mask = np.full(n, 255, dtype=np.uint8)
+    cnt = np.zeros(4, dtype=np.int64)
+    if lib().orc_run_taf(C.byref(r), _ptr(x), hsize, psize, thresh, level, _ptr(out), _ptr(mask),
+                         _ptr(stat), _ptr(cnt)):
+        raise ValueError("oracle rejected TAF arguments")
+    return out, mask, stat, cnt
+
+
+def run_iact(kind, x, param, tsize, tperwarp, thresh, level=THREAD, in_scale=None, threads=0,
+             block=256, n=None):
+    r, x, n = _region(kind, x, n, param, threads, block)
+    out = np.zeros(n, dtype=x.dtype)
+    stat = np.zeros(n, dtype=x.dtype)
+    mask = np.full(n, 255, dtype=np.uint8)
+    cnt = np.zeros(4, dtype=np.int64)
+    sc = None if in_scale is None else np.ascontiguousarray(in_scale, dtype=np.float64)
+    if lib().orc_run_iact(C.byref(r), _ptr(x), tsize, tperwarp, thresh, level, _ptr(sc),
+                          _ptr(out), _ptr(mask), _ptr(stat), _ptr(cnt)):
+        raise ValueError("oracle rejected iACT arguments")
+    return out, mask, stat, cnt
+
+
+def quality(a, b, metric):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    if a.shape != b.shape:
+        raise ValueError("shape mismatch")
+    res = np.zeros(2, dtype=np.float64)
+    aux = np.zeros(2, dtype=np.int64)
+    if lib().orc_quality(a.size, _ptr(a), _ptr(b), metric, _ptr(res), _ptr(aux)):
+        raise ValueError("bad metric")
+    return float(res[0]), dict(zero_max_abs=float(res[1]), zeros=int(aux[0]),
+                               zeros_mismatch=int(aux[1]))
+
+
+__all__ = [k for k in dir() if not k.startswith("_")] + ["math"]

@@ -1,0 +1,28 @@
+"""Element-wise tolerances derived from the arithmetic of each region.
+
+Black-Scholes in single precision: the call C = S N(d1) - K e^{-rT} N(d2) is a
+difference of two non-negative terms, the larger being S N(d1), so rounding in
+the final combination is bounded relative to S N(d1) (the 1e-5 relative bar of
+the parity criterion). The rounding error of the argument d1 (a log, a sum and
+a division, each a few units of single-precision roundoff eps32) moves the
+price by dC/dd1 * delta_d1 with dC/dd1 = S phi(d1) (the K e^{-rT} phi(d2) term
+is equal to it), and delta_d1 <= 16 eps32 (1 + |d1| + |ln(S/K)| / (sigma sqrt T)).
+Results below 1e-30 are subnormal in single precision and keep fewer bits.
+"""
+import numpy as np
+from scipy import special
+
+EPS32 = float(np.finfo(np.float32).eps)
+BS_RTOL = 1e-5          # relative bar for single-precision outputs
+F64_RTOL = 1e-12        # relative bar for double-precision outputs
+
+
+def blackscholes_tol(x, r):
+    S, K, T, sig = (np.asarray(c, dtype=np.float64) for c in x)
+    sst = sig * np.sqrt(T)
+    lnsk = np.log(S / K)
+    d1 = (lnsk + (r + 0.5 * sig * sig) * T) / sst
+    big = S * special.ndtr(d1)
+    dd = 16.0 * EPS32 * (1.0 + np.abs(d1) + np.abs(lnsk) / sst)
+    sens = S * np.exp(-0.5 * d1 * d1) / np.sqrt(2.0 * np.pi)
+    return BS_RTOL * big + sens * dd + 1e-30
