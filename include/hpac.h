@@ -1,0 +1,233 @@
+/*
+ * hpac.h - C ABI of a GB300 (sm_103a) library that runs an annotated,
+ * data-parallel loop region under the software approximation techniques of
+ * HPAC-Offload (Fink, Parasyris, Georgakoudis, Menon, arXiv 2308.16877):
+ * loop perforation, TAF temporal output memoization and iACT approximate input
+ * memoization, with thread-, warp- or block-level (majority-rules) decisions.
+ *
+ * Conventions shared by every call:
+ *  - Pointers named d_* are CUDA device pointers owned by the caller; h_* are
+ *    host pointers owned by the caller. The library owns region handles and the
+ *    small device buffers it allocates for them.
+ *  - Region inputs are a column-major (structure-of-arrays) matrix: element d
+ *    of invocation i is at d_in[d * in_stride + i] (the strided array section
+ *    in(input[i*D:D:N]) of the paper's programming model, Section 3.2). The
+ *    single output of invocation i is d_out[i].
+ *  - Work is enqueued on the region's CUDA stream and returns without waiting,
+ *    except calls given a non-NULL h_stats / h_result, which wait for their own
+ *    work to finish before returning.
+ *  - Every call returns an hpac_status; on anything but HPAC_OK,
+ *    hpac_last_error() returns a message for the calling host thread. No call
+ *    aborts the process or traps on the device.
+ *  - The logical schedule is part of the semantics (Section 3.1.3, Figure 3(d)):
+ *    logical thread t (0 <= t < T) performs invocations i = t + k*T,
+ *    k = 0, 1, ..., i < N; warps are 32 consecutive logical threads and blocks
+ *    block_threads consecutive logical threads. Decisions and memoization
+ *    state follow this schedule exactly, whatever the physical launch.
+ *  - Approximation state (TAF windows, iACT tables) lives for one call only, as
+ *    in the paper's shared-memory AC state scoped to one kernel (Section 3.1.1).
+ */
+#ifndef HPAC_H_
+#define HPAC_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  HPAC_OK = 0,
+  HPAC_EINVAL = 1,        /* bad argument: descriptor, knob, pointer or size   */
+  HPAC_ENOMEM = 2,        /* a device or host allocation failed                */
+  HPAC_ECUDA = 3,         /* a CUDA runtime call failed (message says which)   */
+  HPAC_ETIMEOUT = 4,      /* reserved: a bounded device-side wait gave up      */
+  HPAC_EUNSUPPORTED = 5   /* valid request this build does not implement       */
+} hpac_status;
+
+typedef enum { HPAC_F32 = 0, HPAC_F64 = 1 } hpac_dtype;
+
+/* Decision hierarchy, the level(thread|warp|team) clause of Section 3.2. At
+ * warp and block level the group approximates iff strictly more than half of
+ * its deciding lanes meet their criterion (Section 3.3, majority rules). */
+typedef enum { HPAC_LEVEL_THREAD = 0, HPAC_LEVEL_WARP = 1, HPAC_LEVEL_BLOCK = 2 } hpac_level;
+
+/* Built-in regions.
+ *  BLACKSCHOLES: European call (Table 1, Black-Scholes). D = 4 inputs
+ *    (spot S, strike K, expiry T in years, volatility sigma), param = rate r.
+ *    F32 or F64. C = S N(d1) - K e^{-rT} N(d2).
+ *  EOS: ideal-gas pressure with an implicit trapezoid energy update. D = 4
+ *    inputs (e_n, v_{n+1}, dv, q_{n+1}), param = gamma. F64 only.
+ *    p = (gamma-1) e_{n+1} / v_{n+1}, e_{n+1} = (e_n - dv (p_n + 2q)/2) /
+ *    (1 + (gamma-1) dv / (2 v_{n+1})) clamped at 0, p_n = (gamma-1) e_n / (v_{n+1} - dv).
+ *  IDENTITY: output = first input; 1 <= D <= 8; F32 or F64. A region without
+ *    arithmetic, for measuring a technique's own cost and for bit-exact tests. */
+typedef enum {
+  HPAC_REGION_BLACKSCHOLES = 0,
+  HPAC_REGION_EOS = 1,
+  HPAC_REGION_IDENTITY = 3
+} hpac_region_kind;
+
+/* Perforation patterns (Section 2.3; the runtime encounter counter of Section
+ * 3.3). With k the invocation's step within its logical thread and
+ * key = k when herded (Section 3.1.5: every thread drops the same steps) or
+ * key = i otherwise:
+ *  SMALL:M   drop when key mod M == M-1 (skip one of every M)
+ *  LARGE:M   drop when key mod M != 0   (execute one of every M)
+ *  INI:P     drop i <  floor(N P / 100) (first P percent of the loop)
+ *  FINI:P    drop i >= N - floor(N P / 100) (last P percent)
+ *  RANDOM:r  drop when (splitmix64(seed ^ key) >> 40) < floor(r * 2^24)
+ *            (SplitMix64 of Steele, Lea and Flood 2014; not in the paper) */
+typedef enum {
+  HPAC_PERFO_SMALL = 0,
+  HPAC_PERFO_LARGE = 1,
+  HPAC_PERFO_INI = 2,
+  HPAC_PERFO_FINI = 3,
+  HPAC_PERFO_RANDOM = 4
+} hpac_perfo_kind;
+
+/* Per-invocation mask values written to d_mask (one byte per invocation). */
+enum { HPAC_MASK_EXACT = 0, HPAC_MASK_APPROX = 1, HPAC_MASK_SKIPPED = 2 };
+
+typedef enum { HPAC_METRIC_MAPE = 0, HPAC_METRIC_RMSE = 1, HPAC_METRIC_MCR = 2 } hpac_metric;
+
+/* One annotated loop region. */
+typedef struct {
+  int32_t kind;             /* hpac_region_kind                                  */
+  int32_t dtype;            /* hpac_dtype of inputs, output and statistic        */
+  int64_t n;                /* trip count N >= 0                                 */
+  int32_t n_in;             /* D, checked against kind                           */
+  int32_t n_out;            /* must be 1                                         */
+  int64_t in_stride;        /* >= n; column stride of d_in, in elements          */
+  int64_t out_stride;       /* >= n; reserved for multi-output regions           */
+  int64_t logical_threads;  /* T >= 0; 0 means N (one invocation per thread)     */
+  int32_t block_threads;    /* B: multiple of 32, 32..1024                       */
+  int32_t reserved0;        /* must be 0                                         */
+  double param;             /* r (BLACKSCHOLES), gamma (EOS), unused (IDENTITY)  */
+} hpac_region_desc;
+
+/* perfo(kind:arg) clause (Section 3.2, Table 2). m_or_percent is M for
+ * SMALL/LARGE (>= 1) and P for INI/FINI (0..100); rate in [0, 1] and seed are
+ * used by RANDOM; herded selects the step-uniform pattern (default 1). */
+typedef struct {
+  int32_t kind;
+  int32_t m_or_percent;
+  double rate;
+  uint64_t seed;
+  int32_t herded;
+  int32_t reserved0;
+} hpac_perfo_knobs;
+
+/* memo(out:hsize:psize:thresh) clause (Sections 2.3, 3.2). hsize in 1..64,
+ * psize >= 0, thresh >= 0 (a plain ratio; +inf always predicts once the window
+ * is full), level is an hpac_level. */
+typedef struct {
+  int32_t hsize;
+  int32_t psize;
+  double thresh;
+  int32_t level;
+  int32_t reserved0;
+} hpac_taf_knobs;
+
+/* memo(in:tsize:thresh:tperwarp) clause (Sections 2.3, 3.1.4, 3.2). tsize in
+ * 1..64 slots per table, tperwarp in {1,2,4,8,16,32} tables per warp (32 gives
+ * one private table per lane), thresh >= 0 on the Euclidean distance of scaled
+ * inputs z_d = in_scale[d] * x_d (single precision), level an hpac_level.
+ * in_scale: host array of D doubles, or NULL for all ones. */
+typedef struct {
+  int32_t tsize;
+  int32_t tperwarp;
+  double thresh;
+  int32_t level;
+  int32_t reserved0;
+  const double *in_scale;
+} hpac_iact_knobs;
+
+/* Counts for one call. borderline counts decisions whose statistic lies
+ * within 1e-6 relative of the threshold. */
+typedef struct {
+  int64_t invocations;
+  int64_t approximated;
+  int64_t skipped;
+  int64_t borderline;
+} hpac_stats;
+
+/* Result of hpac_quality. For MAPE the terms with exact value 0 are set
+ * aside: zeros counts them, zeros_mismatch those whose approximation is not
+ * 0, zero_max_abs the largest |approx| among them. used = terms averaged. */
+typedef struct {
+  double value;
+  double zero_max_abs;
+  int64_t used;
+  int64_t zeros;
+  int64_t zeros_mismatch;
+} hpac_quality_result;
+
+typedef struct hpac_region hpac_region;
+
+/* Create a region handle on the current CUDA device. desc is copied;
+ * cuda_stream is a cudaStream_t (NULL = legacy default stream) used by every
+ * later call on the handle. Allocates a few hundred bytes of device memory for
+ * counters. Errors: HPAC_EINVAL (descriptor), HPAC_ECUDA, HPAC_ENOMEM. */
+hpac_status hpac_region_create(const hpac_region_desc *desc, void *cuda_stream,
+                               hpac_region **out);
+
+/* Destroy a handle (NULL is accepted). Waits for the handle's stream. */
+hpac_status hpac_region_destroy(hpac_region *region);
+
+/* Change the stream later calls on the handle are enqueued on. */
+hpac_status hpac_region_set_stream(hpac_region *region, void *cuda_stream);
+
+/* Accurate execution path: d_out[i] = region(d_in[:, i]) for all i < N
+ * (the non-approximated region the paper's speedups are measured against). */
+hpac_status hpac_run_exact(hpac_region *region, const void *d_in, void *d_out);
+
+/* Loop perforation (Sections 2.3, 3.1.5, 3.3). Dropped invocations read no
+ * input and leave d_out[i] untouched. d_mask (nullable, N bytes) receives
+ * HPAC_MASK_EXACT / HPAC_MASK_SKIPPED. h_stats (nullable) makes the call
+ * synchronous and returns the counts. */
+hpac_status hpac_run_perfo(hpac_region *region, const hpac_perfo_knobs *knobs, const void *d_in,
+                           void *d_out, uint8_t *d_mask, hpac_stats *h_stats);
+
+/* TAF (Section 2.3; GPU algorithm Section 3.1.3; runtime Section 3.3). Per
+ * logical thread, a window of the last hsize accurate outputs; when full, the
+ * relative standard deviation RSD = sigma/|mu| (population moments, 0/0 := 0)
+ * is compared with thresh and, if lower, the next psize invocations output the
+ * newest window value without reading their inputs. The window is kept across
+ * a prediction run. d_mask (nullable) gets EXACT/APPROX; d_stat (nullable, N
+ * values of the region dtype) gets the RSD of every accurate invocation with a
+ * full window, NaN elsewhere. */
+hpac_status hpac_run_taf(hpac_region *region, const hpac_taf_knobs *knobs, const void *d_in,
+                         void *d_out, uint8_t *d_mask, void *d_stat, hpac_stats *h_stats);
+
+/* iACT (Section 2.3; table sharing Section 3.1.4; read/write phases Section
+ * 3.3). Read phase: each lane finds the nearest valid slot of its table
+ * (ties to the lowest slot) and wants to approximate iff its distance is below
+ * thresh. Approximated invocations output that slot's value; at warp/block
+ * level a majority forces every lane holding a valid slot. Write phase: per
+ * table, the exactly computing lane farthest from the table (ties to the
+ * lowest lane) stores its (scaled input, output) in the round-robin slot.
+ * d_stat (nullable) gets the nearest distance (+inf for an empty table). */
+hpac_status hpac_run_iact(hpac_region *region, const hpac_iact_knobs *knobs, const void *d_in,
+                          void *d_out, uint8_t *d_mask, void *d_stat, hpac_stats *h_stats);
+
+/* Quality loss of an approximated output against an exact reference (Section
+ * 4): MAPE (Eq. 1), RMSE, or MCR (Eq. 2), accumulated in double precision on
+ * the device. d_exact: n doubles; d_approx: n values of approx_dtype. The call
+ * waits for the result. Uses a device buffer the library allocates once per
+ * device on first use. */
+hpac_status hpac_quality(int32_t approx_dtype, int64_t n, const double *d_exact,
+                         const void *d_approx, int32_t metric, hpac_quality_result *h_result,
+                         void *cuda_stream);
+
+/* Message for the last non-OK status returned on the calling host thread. */
+const char *hpac_last_error(void);
+
+/* Library version string. */
+const char *hpac_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HPAC_H_ */

@@ -1,0 +1,228 @@
+// C ABI of libhpac: argument checking, region handles, statistics readback.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include "hpac_internal.cuh"
+
+namespace hpac {
+
+static thread_local char g_err[512] = "";
+
+hpac_status set_error(hpac_status s, const char *fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+  return s;
+}
+
+hpac_status cuda_error(cudaError_t e, const char *what) {
+  return set_error(HPAC_ECUDA, "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+int max_dyn_smem(int device) {
+  static int cached[64] = {0};
+  if (device < 0 || device >= 64) return 48 * 1024;
+  if (!cached[device]) {
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) != cudaSuccess ||
+        v <= 0)
+      v = 48 * 1024;
+    cached[device] = v - 1024;  // headroom for the kernels' static shared memory
+  }
+  return cached[device];
+}
+
+static hpac_status check_desc(const hpac_region_desc *d) {
+  if (!d) return set_error(HPAC_EINVAL, "descriptor is NULL");
+  if (d->n < 0) return set_error(HPAC_EINVAL, "n = %lld < 0", (long long)d->n);
+  if (d->n_out != 1) return set_error(HPAC_EINVAL, "n_out = %d, must be 1", d->n_out);
+  if (d->n_in < 1 || d->n_in > kMaxIn) return set_error(HPAC_EINVAL, "n_in = %d not in 1..8", d->n_in);
+  if (d->in_stride < d->n || d->out_stride < d->n)
+    return set_error(HPAC_EINVAL, "stride smaller than n");
+  if (d->logical_threads < 0) return set_error(HPAC_EINVAL, "logical_threads < 0");
+  if (d->block_threads < 32 || d->block_threads > 1024 || d->block_threads % 32)
+    return set_error(HPAC_EINVAL, "block_threads = %d, must be a multiple of 32 in 32..1024",
+                     d->block_threads);
+  if (d->dtype != HPAC_F32 && d->dtype != HPAC_F64) return set_error(HPAC_EINVAL, "dtype %d", d->dtype);
+  if (d->reserved0 != 0) return set_error(HPAC_EINVAL, "reserved field not zero");
+  if (!isfinite(d->param)) return set_error(HPAC_EINVAL, "param is not finite");
+  switch (d->kind) {
+    case HPAC_REGION_BLACKSCHOLES:
+      if (d->n_in != 4) return set_error(HPAC_EINVAL, "Black-Scholes takes 4 inputs");
+      break;
+    case HPAC_REGION_EOS:
+      if (d->n_in != 4) return set_error(HPAC_EINVAL, "EOS takes 4 inputs");
+      if (d->dtype != HPAC_F64) return set_error(HPAC_EUNSUPPORTED, "EOS is double precision only");
+      break;
+    case HPAC_REGION_IDENTITY:
+      break;
+    default:
+      return set_error(HPAC_EINVAL, "unknown region kind %d", d->kind);
+  }
+  return HPAC_OK;
+}
+
+static hpac_status check_call(hpac_region *r, const void *in, const void *out) {
+  if (!r) return set_error(HPAC_EINVAL, "region is NULL");
+  if (r->d.n > 0 && (!in || !out)) return set_error(HPAC_EINVAL, "input or output pointer is NULL");
+  int dev = -1;
+  HPAC_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev != r->device)
+    return set_error(HPAC_EINVAL, "current device %d differs from the region's device %d", dev,
+                     r->device);
+  return HPAC_OK;
+}
+
+static hpac_status begin_counters(hpac_region *r, const void *h_stats) {
+  if (!h_stats) return HPAC_OK;
+  HPAC_CUDA_TRY(cudaMemsetAsync(r->d_counters, 0, 2 * sizeof(unsigned long long), r->stream));
+  return HPAC_OK;
+}
+
+static hpac_status end_counters(hpac_region *r, hpac_stats *h, int64_t skipped_known) {
+  if (!h) return HPAC_OK;
+  unsigned long long c[2] = {0, 0};
+  HPAC_CUDA_TRY(cudaMemcpyAsync(c, r->d_counters, sizeof(c), cudaMemcpyDeviceToHost, r->stream));
+  HPAC_CUDA_TRY(cudaStreamSynchronize(r->stream));
+  h->invocations = r->d.n;
+  h->approximated = (int64_t)c[0];
+  h->skipped = skipped_known;
+  h->borderline = (int64_t)c[1];
+  return HPAC_OK;
+}
+
+}  // namespace hpac
+
+using namespace hpac;
+
+extern "C" {
+
+const char *hpac_last_error(void) { return g_err; }
+
+const char *hpac_version(void) { return "hpac-gb300 0.1 (sm_103a)"; }
+
+hpac_status hpac_region_create(const hpac_region_desc *desc, void *cuda_stream, hpac_region **out) {
+  if (!out) return set_error(HPAC_EINVAL, "out is NULL");
+  *out = nullptr;
+  hpac_status s = check_desc(desc);
+  if (s != HPAC_OK) return s;
+  hpac_region *r = (hpac_region *)calloc(1, sizeof(hpac_region));
+  if (!r) return set_error(HPAC_ENOMEM, "host allocation of the region handle failed");
+  r->d = *desc;
+  r->stream = (cudaStream_t)cuda_stream;
+  cudaError_t e = cudaGetDevice(&r->device);
+  if (e == cudaSuccess) e = cudaMalloc(&r->d_counters, 4 * sizeof(unsigned long long));
+  if (e != cudaSuccess) {
+    free(r);
+    return cuda_error(e, "hpac_region_create");
+  }
+  *out = r;
+  return HPAC_OK;
+}
+
+hpac_status hpac_region_destroy(hpac_region *r) {
+  if (!r) return HPAC_OK;
+  cudaError_t e = cudaStreamSynchronize(r->stream);
+  cudaError_t f = cudaFree(r->d_counters);
+  free(r);
+  if (e != cudaSuccess) return cuda_error(e, "hpac_region_destroy: stream");
+  if (f != cudaSuccess) return cuda_error(f, "hpac_region_destroy: free");
+  return HPAC_OK;
+}
+
+hpac_status hpac_region_set_stream(hpac_region *r, void *cuda_stream) {
+  if (!r) return set_error(HPAC_EINVAL, "region is NULL");
+  r->stream = (cudaStream_t)cuda_stream;
+  return HPAC_OK;
+}
+
+hpac_status hpac_run_exact(hpac_region *r, const void *d_in, void *d_out) {
+  hpac_status s = check_call(r, d_in, d_out);
+  if (s != HPAC_OK) return s;
+  return launch_exact(r, d_in, d_out);
+}
+
+hpac_status hpac_run_perfo(hpac_region *r, const hpac_perfo_knobs *k, const void *d_in, void *d_out,
+                           uint8_t *d_mask, hpac_stats *h_stats) {
+  hpac_status s = check_call(r, d_in, d_out);
+  if (s != HPAC_OK) return s;
+  if (!k) return set_error(HPAC_EINVAL, "knobs are NULL");
+  switch (k->kind) {
+    case HPAC_PERFO_SMALL:
+    case HPAC_PERFO_LARGE:
+      if (k->m_or_percent < 1) return set_error(HPAC_EINVAL, "perforation M = %d < 1", k->m_or_percent);
+      break;
+    case HPAC_PERFO_INI:
+    case HPAC_PERFO_FINI:
+      if (k->m_or_percent < 0 || k->m_or_percent > 100)
+        return set_error(HPAC_EINVAL, "perforation percent %d not in 0..100", k->m_or_percent);
+      break;
+    case HPAC_PERFO_RANDOM:
+      if (!(k->rate >= 0.0 && k->rate <= 1.0))
+        return set_error(HPAC_EINVAL, "perforation rate %g not in [0, 1]", k->rate);
+      break;
+    default:
+      return set_error(HPAC_EINVAL, "unknown perforation kind %d", k->kind);
+  }
+  if (k->reserved0 != 0) return set_error(HPAC_EINVAL, "reserved field not zero");
+  s = begin_counters(r, h_stats);
+  if (s != HPAC_OK) return s;
+  s = launch_perfo(r, k, d_in, d_out, d_mask, h_stats ? r->d_counters : nullptr);
+  if (s != HPAC_OK) return s;
+  s = end_counters(r, h_stats, 0);
+  if (s == HPAC_OK && h_stats) {
+    // the perforation kernel counts dropped invocations in the first counter
+    h_stats->skipped = h_stats->approximated;
+    h_stats->approximated = 0;
+    h_stats->borderline = 0;
+  }
+  return s;
+}
+
+hpac_status hpac_run_taf(hpac_region *r, const hpac_taf_knobs *k, const void *d_in, void *d_out,
+                         uint8_t *d_mask, void *d_stat, hpac_stats *h_stats) {
+  hpac_status s = check_call(r, d_in, d_out);
+  if (s != HPAC_OK) return s;
+  if (!k) return set_error(HPAC_EINVAL, "knobs are NULL");
+  if (k->hsize < 1 || k->hsize > kMaxHsize)
+    return set_error(HPAC_EINVAL, "hsize %d not in 1..%d", k->hsize, kMaxHsize);
+  if (k->psize < 0) return set_error(HPAC_EINVAL, "psize %d < 0", k->psize);
+  if (!(k->thresh >= 0.0)) return set_error(HPAC_EINVAL, "threshold must be >= 0 (got %g)", k->thresh);
+  if (k->level < HPAC_LEVEL_THREAD || k->level > HPAC_LEVEL_BLOCK)
+    return set_error(HPAC_EINVAL, "level %d", k->level);
+  if (k->reserved0 != 0) return set_error(HPAC_EINVAL, "reserved field not zero");
+  s = begin_counters(r, h_stats);
+  if (s != HPAC_OK) return s;
+  s = launch_taf(r, k, d_in, d_out, d_mask, d_stat, h_stats ? r->d_counters : nullptr);
+  if (s != HPAC_OK) return s;
+  return end_counters(r, h_stats, 0);
+}
+
+hpac_status hpac_run_iact(hpac_region *r, const hpac_iact_knobs *k, const void *d_in, void *d_out,
+                          uint8_t *d_mask, void *d_stat, hpac_stats *h_stats) {
+  hpac_status s = check_call(r, d_in, d_out);
+  if (s != HPAC_OK) return s;
+  if (!k) return set_error(HPAC_EINVAL, "knobs are NULL");
+  if (k->tsize < 1 || k->tsize > kMaxTsize)
+    return set_error(HPAC_EINVAL, "tsize %d not in 1..%d", k->tsize, kMaxTsize);
+  if (k->tperwarp < 1 || k->tperwarp > 32 || (32 % k->tperwarp) != 0)
+    return set_error(HPAC_EINVAL, "tperwarp %d must divide 32", k->tperwarp);
+  if (!(k->thresh >= 0.0)) return set_error(HPAC_EINVAL, "threshold must be >= 0 (got %g)", k->thresh);
+  if (k->level < HPAC_LEVEL_THREAD || k->level > HPAC_LEVEL_BLOCK)
+    return set_error(HPAC_EINVAL, "level %d", k->level);
+  if (k->reserved0 != 0) return set_error(HPAC_EINVAL, "reserved field not zero");
+  if (k->in_scale)
+    for (int j = 0; j < r->d.n_in; ++j)
+      if (!isfinite(k->in_scale[j])) return set_error(HPAC_EINVAL, "in_scale[%d] is not finite", j);
+  s = begin_counters(r, h_stats);
+  if (s != HPAC_OK) return s;
+  s = launch_iact(r, k, d_in, d_out, d_mask, d_stat, h_stats ? r->d_counters : nullptr);
+  if (s != HPAC_OK) return s;
+  return end_counters(r, h_stats, 0);
+}
+
+}  // extern "C"

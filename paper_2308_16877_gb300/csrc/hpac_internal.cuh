@@ -1,0 +1,51 @@
+// Internal declarations shared by the translation units of libhpac.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "hpac.h"
+
+struct hpac_region {
+  hpac_region_desc d;
+  cudaStream_t stream;
+  int device;
+  unsigned long long *d_counters;  // [0] approximated, [1] borderline
+};
+
+namespace hpac {
+
+constexpr int kWarp = 32;
+constexpr int kMaxIn = 8;
+constexpr int kMaxHsize = 64;
+constexpr int kMaxTsize = 64;
+constexpr double kBorderRel = 1e-6;
+
+// Thread-local error reporting (hpac_last_error).
+hpac_status set_error(hpac_status s, const char *fmt, ...);
+hpac_status cuda_error(cudaError_t e, const char *what);
+
+inline int64_t logical_threads(const hpac_region_desc &d) {
+  return d.logical_threads > 0 ? d.logical_threads : (d.n > 0 ? d.n : 1);
+}
+
+// Launchers (one translation unit each). All validate nothing: the C ABI layer
+// has checked the descriptor and knobs before calling them.
+hpac_status launch_exact(const hpac_region *r, const void *in, void *out);
+hpac_status launch_perfo(const hpac_region *r, const hpac_perfo_knobs *k, const void *in, void *out,
+                         uint8_t *mask, unsigned long long *counters);
+hpac_status launch_taf(const hpac_region *r, const hpac_taf_knobs *k, const void *in, void *out,
+                       uint8_t *mask, void *stat, unsigned long long *counters);
+hpac_status launch_iact(const hpac_region *r, const hpac_iact_knobs *k, const void *in, void *out,
+                        uint8_t *mask, void *stat, unsigned long long *counters);
+
+// Largest dynamic shared memory a block of this device may use.
+int max_dyn_smem(int device);
+
+}  // namespace hpac
+
+#define HPAC_CUDA_TRY(call)                                   \
+  do {                                                        \
+    cudaError_t e_ = (call);                                  \
+    if (e_ != cudaSuccess) return hpac::cuda_error(e_, #call); \
+  } while (0)

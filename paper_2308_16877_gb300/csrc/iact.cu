@@ -1,0 +1,271 @@
+// iACT: approximate input memoization with tables shared within a warp
+// (Sections 2.3 and 3.1.4; read/write phases, farthest-lane writer and
+// round-robin replacement, Section 3.3).
+//
+// Each warp owns tperwarp tables in shared memory; lanes [j*L, (j+1)*L),
+// L = 32/tperwarp, share table j. Layout puts the table index innermost,
+//   z[slot][d][table] (float, scaled inputs), y[slot][table] (region type),
+// so at a given (slot, d) the lanes of a warp read consecutive words, and the
+// lanes that share a table read one word (a broadcast): no bank conflicts.
+// Valid slots always form a prefix [0, filled) because replacement is
+// round-robin from slot 0.
+//
+// A step is: read phase (every active lane scans its table), decision
+// (per lane, or ballot/popcount majority per warp, or a shared tally per
+// block), execution (table value or exact region), __syncwarp, write phase
+// (segmented arg-max of the distance over each table's exactly computing
+// lanes with shuffles; the winner writes its slot), __syncwarp.
+#include "hpac_internal.cuh"
+#include "regions.cuh"
+
+namespace hpac {
+namespace {
+
+struct IactParams {
+  float scale_f[kMaxIn];   // per-dimension scale, single precision
+  double scale_d[kMaxIn];  // per-dimension scale, double precision
+  int D;
+  int tsize;
+  int g;                   // tables per warp
+  int L;                   // lanes per table
+  float thr;
+  double thr_d;
+};
+
+template <typename V>
+struct WarpTables {
+  float *z;     // [tsize][D][g]
+  V *y;         // [tsize][g]
+  int *filled;  // [g]
+  int *rr;      // [g]
+};
+
+template <typename V>
+__host__ __device__ inline size_t warp_table_bytes(int tsize, int D, int g) {
+  size_t zb = (size_t)tsize * D * g * sizeof(float);
+  zb = (zb + 7) & ~(size_t)7;
+  return zb + (size_t)tsize * g * sizeof(V) + 2 * (size_t)g * sizeof(int);
+}
+
+template <class R, int LEVEL>
+__global__ void __launch_bounds__(1024) iact_kernel(R reg, const typename R::T *__restrict__ in,
+                                                    int64_t stride, typename R::T *__restrict__ out,
+                                                    uint8_t *__restrict__ mask,
+                                                    typename R::T *__restrict__ stat, int64_t n,
+                                                    int64_t T, IactParams P,
+                                                    unsigned long long *__restrict__ counters) {
+  using V = typename R::T;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ unsigned long long s_cnt[2];
+  __shared__ int s_tally[3];
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  const int D = P.D, tsize = P.tsize, g = P.g, L = P.L;
+  const int tab = lane / L;
+  const size_t wbytes = warp_table_bytes<V>(tsize, D, g);
+  unsigned char *base = smem_raw + (size_t)warp * wbytes;
+  WarpTables<V> W;
+  W.z = reinterpret_cast<float *>(base);
+  size_t zb = ((size_t)tsize * D * g * sizeof(float) + 7) & ~(size_t)7;
+  W.y = reinterpret_cast<V *>(base + zb);
+  W.filled = reinterpret_cast<int *>(base + zb + (size_t)tsize * g * sizeof(V));
+  W.rr = W.filled + g;
+  if (lane < g) {
+    W.filled[lane] = 0;
+    W.rr[lane] = 0;
+  }
+  if (threadIdx.x < 2) s_cnt[threadIdx.x] = 0;
+  if (LEVEL == HPAC_LEVEL_BLOCK && threadIdx.x == 0) s_tally[0] = s_tally[1] = s_tally[2] = 0;
+  __syncthreads();
+
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t t_lead = LEVEL == HPAC_LEVEL_BLOCK ? (int64_t)blockIdx.x * blockDim.x : t - lane;
+  unsigned long long n_apx = 0, n_border = 0;
+
+  if (t_lead < T) {
+    int k3 = 0;
+    for (int64_t i = t; t_lead + (i - t) < n; i += T) {
+      const bool act = (t < T) && (i < n);
+      // ---- read phase
+      float z[kMaxIn];
+      V x[kMaxIn];
+      bool has = false;
+      float best = INFINITY;
+      int near = 0;
+      if (act) {
+#pragma unroll
+        for (int d = 0; d < kMaxIn; ++d) {
+          if (d < D) {
+            x[d] = in[d * stride + i];
+            if (sizeof(V) == 4)
+              z[d] = __fmul_rn(P.scale_f[d], (float)x[d]);
+            else
+              z[d] = __double2float_rn(__dmul_rn(P.scale_d[d], (double)x[d]));
+          }
+        }
+        const int filled = W.filled[tab];
+        for (int j = 0; j < filled; ++j) {
+          float acc = 0.0f;
+          const float *zs = W.z + (size_t)j * D * g + tab;
+#pragma unroll
+          for (int d = 0; d < kMaxIn; ++d) {
+            if (d < D) {
+              const float df = __fsub_rn(z[d], zs[d * g]);
+              acc = __fadd_rn(acc, __fmul_rn(df, df));
+            }
+          }
+          if (!has || acc < best) {
+            best = acc;
+            near = j;
+          }
+          has = true;
+        }
+      }
+      const float dmin = has ? __fsqrt_rn(best) : INFINITY;
+      const bool wants = act && has && dmin < P.thr;
+      // ---- decision
+      bool apx;
+      if (LEVEL == HPAC_LEVEL_THREAD) {
+        apx = wants;
+      } else if (LEVEL == HPAC_LEVEL_WARP) {
+        const unsigned na = __ballot_sync(0xffffffffu, act);
+        const unsigned nw = __ballot_sync(0xffffffffu, wants);
+        apx = (2 * __popc(nw) > __popc(na)) && act && has;
+      } else {
+        const unsigned na = __ballot_sync(0xffffffffu, act);
+        const unsigned nw = __ballot_sync(0xffffffffu, wants);
+        if (threadIdx.x == 0) s_tally[k3 == 2 ? 0 : k3 + 1] = 0;
+        if (lane == 0) atomicAdd(&s_tally[k3], (__popc(nw) << 16) | __popc(na));
+        __syncthreads();
+        const int tally = s_tally[k3];
+        apx = (2 * (tally >> 16) > (tally & 0xffff)) && act && has;
+        k3 = k3 == 2 ? 0 : k3 + 1;
+      }
+      // ---- execute
+      V y = (V)0;
+      if (act) {
+        if (apx) {
+          y = W.y[(size_t)near * g + tab];
+          if (mask) mask[i] = HPAC_MASK_APPROX;
+          ++n_apx;
+        } else {
+          y = reg(x);
+          if (mask) mask[i] = HPAC_MASK_EXACT;
+        }
+        out[i] = y;
+        if (stat) stat[i] = (V)dmin;
+        if (has && borderline((double)dmin, P.thr_d)) ++n_border;
+      }
+      __syncwarp();
+      // ---- write phase: per table, the farthest exactly computing lane
+      float key = (act && !apx) ? dmin : -1.0f;
+      int who = lane;
+      for (int off = 1; off < L; off <<= 1) {
+        const float ok = __shfl_xor_sync(0xffffffffu, key, off);
+        const int ow = __shfl_xor_sync(0xffffffffu, who, off);
+        if (ok > key || (ok == key && ow < who)) {
+          key = ok;
+          who = ow;
+        }
+      }
+      if (who == lane && key >= 0.0f) {
+        const int slot = W.rr[tab];
+#pragma unroll
+        for (int d = 0; d < kMaxIn; ++d)
+          if (d < D) W.z[((size_t)slot * D + d) * g + tab] = z[d];
+        W.y[(size_t)slot * g + tab] = y;
+        W.rr[tab] = slot + 1 == tsize ? 0 : slot + 1;
+        if (W.filled[tab] < tsize) W.filled[tab] += 1;
+      }
+      __syncwarp();
+    }
+  }
+  warp_count(s_cnt, n_apx, n_border);
+  __syncthreads();
+  if (counters && threadIdx.x == 0) {
+    if (s_cnt[0]) atomicAdd(&counters[0], s_cnt[0]);
+    if (s_cnt[1]) atomicAdd(&counters[1], s_cnt[1]);
+  }
+}
+
+template <class R>
+hpac_status launch(const hpac_region *r, R reg, const hpac_iact_knobs *k, const void *in, void *out,
+                   uint8_t *mask, void *stat, unsigned long long *counters) {
+  using V = typename R::T;
+  const hpac_region_desc &d = r->d;
+  if (d.n == 0) return HPAC_OK;
+  IactParams P{};
+  P.D = d.n_in;
+  P.tsize = k->tsize;
+  P.g = k->tperwarp;
+  P.L = 32 / k->tperwarp;
+  P.thr = (float)k->thresh;
+  P.thr_d = k->thresh;
+  for (int j = 0; j < kMaxIn; ++j) {
+    const double s = (k->in_scale && j < d.n_in) ? k->in_scale[j] : 1.0;
+    P.scale_d[j] = s;
+    P.scale_f[j] = (float)s;
+  }
+  const int64_t T = logical_threads(d);
+  const size_t wbytes = warp_table_bytes<V>(P.tsize, P.D, P.g);
+  const int limit = max_dyn_smem(r->device);
+  // At thread and warp level only the warp is semantic, so the physical block
+  // may shrink to fit the tables; at block level B is part of the semantics.
+  int B = d.block_threads;
+  if (k->level != HPAC_LEVEL_BLOCK) {
+    while (B > 32 && (size_t)(B / 32) * wbytes > (size_t)limit) B -= 32;
+  }
+  const size_t smem = (size_t)(B / 32) * wbytes;
+  if (smem > (size_t)limit)
+    return set_error(HPAC_EUNSUPPORTED, "iACT tables of %zu bytes per block exceed %d", smem, limit);
+  const int64_t blocks = (T + B - 1) / B;
+  if (blocks > 0x7fffffffLL) return set_error(HPAC_EINVAL, "too many logical threads");
+  V *o = static_cast<V *>(out);
+  V *st = static_cast<V *>(stat);
+  const V *x = static_cast<const V *>(in);
+  switch (k->level) {
+    case HPAC_LEVEL_THREAD: {
+      auto fn = iact_kernel<R, HPAC_LEVEL_THREAD>;
+      HPAC_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      fn<<<(unsigned)blocks, B, smem, r->stream>>>(reg, x, d.in_stride, o, mask, st, d.n, T, P, counters);
+      break;
+    }
+    case HPAC_LEVEL_WARP: {
+      auto fn = iact_kernel<R, HPAC_LEVEL_WARP>;
+      HPAC_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      fn<<<(unsigned)blocks, B, smem, r->stream>>>(reg, x, d.in_stride, o, mask, st, d.n, T, P, counters);
+      break;
+    }
+    default: {
+      auto fn = iact_kernel<R, HPAC_LEVEL_BLOCK>;
+      HPAC_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      fn<<<(unsigned)blocks, B, smem, r->stream>>>(reg, x, d.in_stride, o, mask, st, d.n, T, P, counters);
+      break;
+    }
+  }
+  HPAC_CUDA_TRY(cudaGetLastError());
+  return HPAC_OK;
+}
+
+// Identity reads only its first input for the exact value, but iACT needs all
+// D inputs for the distance; the kernel loads them regardless of kReads.
+}  // namespace
+
+hpac_status launch_iact(const hpac_region *r, const hpac_iact_knobs *k, const void *in, void *out,
+                        uint8_t *mask, void *stat, unsigned long long *counters) {
+  const hpac_region_desc &d = r->d;
+  switch (d.kind) {
+    case HPAC_REGION_BLACKSCHOLES:
+      if (d.dtype == HPAC_F32)
+        return launch(r, BlackScholes32{(float)d.param}, k, in, out, mask, stat, counters);
+      return launch(r, BlackScholes64{d.param}, k, in, out, mask, stat, counters);
+    case HPAC_REGION_EOS:
+      return launch(r, Eos64{d.param}, k, in, out, mask, stat, counters);
+    case HPAC_REGION_IDENTITY:
+      if (d.dtype == HPAC_F32) return launch(r, Identity<float>{}, k, in, out, mask, stat, counters);
+      return launch(r, Identity<double>{}, k, in, out, mask, stat, counters);
+  }
+  return set_error(HPAC_EUNSUPPORTED, "region kind %d", d.kind);
+}
+
+}  // namespace hpac

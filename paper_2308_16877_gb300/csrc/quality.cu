@@ -1,0 +1,169 @@
+// Quality loss against an exact reference (Section 4): MAPE (Eq. 1), RMSE and
+// the misclassification rate MCR (Eq. 2), accumulated in double precision.
+//
+// Two deterministic passes: a fixed grid of kBlocks blocks reduces grid-stride
+// slices to per-block partials (a tree inside each block), then one block
+// reduces the partials in index order. The partials live in a device buffer
+// allocated once per device and kept for the life of the process; a host
+// mutex serializes calls, which wait for their result before returning.
+#include <math.h>
+#include <mutex>
+
+#include "hpac_internal.cuh"
+
+namespace hpac {
+namespace {
+
+constexpr int kBlocks = 1216;  // 8 x 152 SMs
+constexpr int kThreads = 256;
+
+struct Partial {
+  double sum;
+  double zmax;
+  unsigned long long used;
+  unsigned long long zeros;
+  unsigned long long zbad;
+};
+
+template <typename B>
+__global__ void __launch_bounds__(kThreads) quality_partial(const double *__restrict__ a,
+                                                            const B *__restrict__ b, int64_t n,
+                                                            int metric, Partial *__restrict__ part) {
+  __shared__ double s_sum[kThreads];
+  __shared__ double s_zmax[kThreads];
+  __shared__ unsigned long long s_used[kThreads], s_zeros[kThreads], s_zbad[kThreads];
+  double sum = 0.0, zmax = 0.0;
+  unsigned long long used = 0, zeros = 0, zbad = 0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const double ai = __ldcs(a + i);
+    const double bi = (double)__ldcs(b + i);
+    if (metric == HPAC_METRIC_MAPE) {
+      if (ai == 0.0) {
+        ++zeros;
+        if (bi != 0.0) ++zbad;
+        zmax = fmax(zmax, fabs(bi));
+        continue;
+      }
+      sum += fabs(ai - bi) / fabs(ai);
+    } else if (metric == HPAC_METRIC_RMSE) {
+      const double d = ai - bi;
+      sum += d * d;
+    } else {
+      sum += (ai != bi) ? 1.0 : 0.0;
+    }
+    ++used;
+  }
+  s_sum[threadIdx.x] = sum;
+  s_zmax[threadIdx.x] = zmax;
+  s_used[threadIdx.x] = used;
+  s_zeros[threadIdx.x] = zeros;
+  s_zbad[threadIdx.x] = zbad;
+  __syncthreads();
+  for (int w = kThreads / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) {
+      s_sum[threadIdx.x] += s_sum[threadIdx.x + w];
+      s_zmax[threadIdx.x] = fmax(s_zmax[threadIdx.x], s_zmax[threadIdx.x + w]);
+      s_used[threadIdx.x] += s_used[threadIdx.x + w];
+      s_zeros[threadIdx.x] += s_zeros[threadIdx.x + w];
+      s_zbad[threadIdx.x] += s_zbad[threadIdx.x + w];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    part[blockIdx.x] = Partial{s_sum[0], s_zmax[0], s_used[0], s_zeros[0], s_zbad[0]};
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) quality_final(const Partial *__restrict__ part, int np,
+                                                          Partial *__restrict__ res) {
+  __shared__ Partial s[kThreads];
+  Partial acc{0.0, 0.0, 0, 0, 0};
+  for (int j = threadIdx.x; j < np; j += blockDim.x) {
+    const Partial p = part[j];
+    acc.sum += p.sum;
+    acc.zmax = fmax(acc.zmax, p.zmax);
+    acc.used += p.used;
+    acc.zeros += p.zeros;
+    acc.zbad += p.zbad;
+  }
+  s[threadIdx.x] = acc;
+  __syncthreads();
+  for (int w = kThreads / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) {
+      s[threadIdx.x].sum += s[threadIdx.x + w].sum;
+      s[threadIdx.x].zmax = fmax(s[threadIdx.x].zmax, s[threadIdx.x + w].zmax);
+      s[threadIdx.x].used += s[threadIdx.x + w].used;
+      s[threadIdx.x].zeros += s[threadIdx.x + w].zeros;
+      s[threadIdx.x].zbad += s[threadIdx.x + w].zbad;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *res = s[0];
+}
+
+// Per-device scratch: kBlocks partials + 1 result.
+Partial *g_scratch[64] = {nullptr};
+std::mutex g_mu;
+
+// Callers hold g_mu for the whole call: the scratch is shared by every call
+// on the device and the call waits for its result before releasing it.
+hpac_status scratch_for(int dev, Partial **out) {
+  if (dev < 0 || dev >= 64) return set_error(HPAC_EUNSUPPORTED, "device ordinal %d", dev);
+  if (!g_scratch[dev]) {
+    Partial *p = nullptr;
+    cudaError_t e = cudaMalloc(&p, (kBlocks + 1) * sizeof(Partial));
+    if (e != cudaSuccess) return cuda_error(e, "hpac_quality scratch");
+    g_scratch[dev] = p;
+  }
+  *out = g_scratch[dev];
+  return HPAC_OK;
+}
+
+}  // namespace
+}  // namespace hpac
+
+using namespace hpac;
+
+extern "C" hpac_status hpac_quality(int32_t approx_dtype, int64_t n, const double *d_exact,
+                                    const void *d_approx, int32_t metric,
+                                    hpac_quality_result *h_result, void *cuda_stream) {
+  if (!h_result) return set_error(HPAC_EINVAL, "h_result is NULL");
+  if (n < 0) return set_error(HPAC_EINVAL, "n < 0");
+  if (metric < HPAC_METRIC_MAPE || metric > HPAC_METRIC_MCR)
+    return set_error(HPAC_EINVAL, "metric %d", metric);
+  if (approx_dtype != HPAC_F32 && approx_dtype != HPAC_F64)
+    return set_error(HPAC_EINVAL, "dtype %d", approx_dtype);
+  if (n > 0 && (!d_exact || !d_approx)) return set_error(HPAC_EINVAL, "NULL data pointer");
+  *h_result = hpac_quality_result{0.0, 0.0, 0, 0, 0};
+  if (n == 0) return HPAC_OK;
+  int dev = 0;
+  HPAC_CUDA_TRY(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(g_mu);
+  Partial *scr = nullptr;
+  hpac_status s = scratch_for(dev, &scr);
+  if (s != HPAC_OK) return s;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  int64_t blocks = (n + kThreads - 1) / kThreads;
+  blocks = blocks > kBlocks ? kBlocks : blocks;
+  if (approx_dtype == HPAC_F32)
+    quality_partial<float><<<(unsigned)blocks, kThreads, 0, st>>>(
+        d_exact, static_cast<const float *>(d_approx), n, metric, scr);
+  else
+    quality_partial<double><<<(unsigned)blocks, kThreads, 0, st>>>(
+        d_exact, static_cast<const double *>(d_approx), n, metric, scr);
+  HPAC_CUDA_TRY(cudaGetLastError());
+  quality_final<<<1, kThreads, 0, st>>>(scr, (int)blocks, scr + kBlocks);
+  HPAC_CUDA_TRY(cudaGetLastError());
+  Partial res;
+  HPAC_CUDA_TRY(cudaMemcpyAsync(&res, scr + kBlocks, sizeof(Partial), cudaMemcpyDeviceToHost, st));
+  HPAC_CUDA_TRY(cudaStreamSynchronize(st));
+  double v = res.used ? res.sum / (double)res.used : 0.0;
+  if (metric == HPAC_METRIC_RMSE) v = sqrt(v);
+  h_result->value = v;
+  h_result->zero_max_abs = res.zmax;
+  h_result->used = (int64_t)res.used;
+  h_result->zeros = (int64_t)res.zeros;
+  h_result->zeros_mismatch = (int64_t)res.zbad;
+  return HPAC_OK;
+}

@@ -1,0 +1,138 @@
+// Device-side regions and the IEEE-rounded decision statistics.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+namespace hpac {
+
+// ---------------------------------------------------------------------------
+// Regions. Each has the value type T, the number of inputs its exact
+// evaluation reads (kReads) and operator() over those inputs.
+// ---------------------------------------------------------------------------
+
+// European call (Table 1, Black-Scholes): C = S N(d1) - K e^{-rT} N(d2),
+// d1 = (ln(S/K) + (r + sigma^2/2) T) / (sigma sqrt T), d2 = d1 - sigma sqrt T,
+// N(x) = erfc(-x / sqrt 2) / 2.
+struct BlackScholes32 {
+  using T = float;
+  static constexpr int kReads = 4;
+  float r;
+  __device__ __forceinline__ float operator()(const float *x) const {
+    const float S = x[0], K = x[1], Tm = x[2], sig = x[3];
+    const float sst = sig * sqrtf(Tm);
+    const float d1 = (logf(S / K) + (r + 0.5f * sig * sig) * Tm) / sst;
+    const float d2 = d1 - sst;
+    const float n1 = 0.5f * erfcf(-0.70710678118654752440f * d1);
+    const float n2 = 0.5f * erfcf(-0.70710678118654752440f * d2);
+    return S * n1 - K * expf(-r * Tm) * n2;
+  }
+};
+
+struct BlackScholes64 {
+  using T = double;
+  static constexpr int kReads = 4;
+  double r;
+  __device__ __forceinline__ double operator()(const double *x) const {
+    const double S = x[0], K = x[1], Tm = x[2], sig = x[3];
+    const double sst = sig * sqrt(Tm);
+    const double d1 = (log(S / K) + (r + 0.5 * sig * sig) * Tm) / sst;
+    const double d2 = d1 - sst;
+    const double n1 = 0.5 * erfc(-0.70710678118654752440 * d1);
+    const double n2 = 0.5 * erfc(-0.70710678118654752440 * d2);
+    return S * n1 - K * exp(-r * Tm) * n2;
+  }
+};
+
+// Ideal-gas EOS with the implicit trapezoid energy update solved in closed
+// form: e1 = (e - dv (p0 + 2q)/2) / (1 + (g-1) dv / (2 v1)), clamped at 0,
+// p0 = (g-1) e / (v1 - dv), output p1 = (g-1) e1 / v1.
+struct Eos64 {
+  using T = double;
+  static constexpr int kReads = 4;
+  double gamma;
+  __device__ __forceinline__ double operator()(const double *x) const {
+    const double e = x[0], v1 = x[1], dv = x[2], q = x[3];
+    const double gm1 = gamma - 1.0;
+    const double p0 = gm1 * e / (v1 - dv);
+    double e1 = (e - 0.5 * dv * (p0 + 2.0 * q)) / (1.0 + 0.5 * gm1 * dv / v1);
+    e1 = e1 < 0.0 ? 0.0 : e1;
+    return gm1 * e1 / v1;
+  }
+};
+
+template <typename T_>
+struct Identity {
+  using T = T_;
+  static constexpr int kReads = 1;
+  __device__ __forceinline__ T operator()(const T *x) const { return x[0]; }
+};
+
+// ---------------------------------------------------------------------------
+// IEEE-rounded arithmetic (no contraction), one overload set per precision, so
+// that the decision statistics are bit-reproducible.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float sub_rn(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float div_rn(float a, float b) { return __fdiv_rn(a, b); }
+__device__ __forceinline__ float sqrt_rn(float a) { return __fsqrt_rn(a); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double sub_rn(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double div_rn(double a, double b) { return __ddiv_rn(a, b); }
+__device__ __forceinline__ double sqrt_rn(double a) { return __dsqrt_rn(a); }
+
+template <typename T>
+__device__ __forceinline__ T inf_v() { return (T)INFINITY; }
+template <typename T>
+__device__ __forceinline__ T nan_v() { return (T)NAN; }
+
+// Relative standard deviation of the h window values held in shared memory
+// at win[slot * ld] (slot order oldest .. newest starting at `oldest`,
+// wrapping at h): two passes, population moments, RSD = sigma / |mu|;
+// 0/0 reads as 0 and sigma/0 (sigma > 0) as +inf.
+template <typename T>
+__device__ __forceinline__ T window_rsd(const T *win, int ld, int oldest, int h) {
+  T sum = (T)0;
+  int s = oldest;
+  for (int j = 0; j < h; ++j) {
+    sum = add_rn(sum, win[s * ld]);
+    s = (s + 1 == h) ? 0 : s + 1;
+  }
+  const T mu = div_rn(sum, (T)h);
+  T acc = (T)0;
+  s = oldest;
+  for (int j = 0; j < h; ++j) {
+    const T d = sub_rn(win[s * ld], mu);
+    acc = add_rn(acc, mul_rn(d, d));
+    s = (s + 1 == h) ? 0 : s + 1;
+  }
+  const T var = div_rn(acc, (T)h);
+  const T sd = sqrt_rn(var);
+  const T amu = mu < (T)0 ? -mu : mu;
+  if (amu == (T)0) return var == (T)0 ? (T)0 : inf_v<T>();
+  return div_rn(sd, amu);
+}
+
+__device__ __forceinline__ bool borderline(double s, double thr) {
+  if (isinf(thr) || isnan(s)) return false;
+  return fabs(s - thr) <= 1e-6 * thr;
+}
+
+// Warp-aggregated add of two per-thread counts into a block-wide shared pair,
+// then (by the caller, after a barrier) one global add per block.
+__device__ __forceinline__ void warp_count(unsigned long long *sm, unsigned long long a,
+                                           unsigned long long b) {
+  for (int off = 16; off > 0; off >>= 1) {
+    a += __shfl_down_sync(0xffffffffu, a, off);
+    b += __shfl_down_sync(0xffffffffu, b, off);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (a) atomicAdd(&sm[0], a);
+    if (b) atomicAdd(&sm[1], b);
+  }
+}
+
+}  // namespace hpac

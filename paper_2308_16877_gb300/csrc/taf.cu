@@ -1,0 +1,179 @@
+// TAF: temporal approximate function memoization, HPAC-Offload GPU algorithm
+// (Section 3.1.3, Figure 3(d); runtime Section 3.3; majority rules Section 3.3).
+//
+// One physical thread per logical thread t, walking its grid-stride sequence
+// i = t + k*T. Its window of the last hsize accurate outputs lives in shared
+// memory (Section 3.1.1), column-major so that the lanes of a warp touch
+// consecutive words: win[slot * blockDim.x + threadIdx.x]. A predicting
+// thread stores the newest window value and issues no input load, so
+// prediction removes the region's input bytes and arithmetic. At warp level the
+// decision is a ballot + popcount over the lanes that computed this step; at
+// block level each warp's count goes to a shared tally read after a barrier.
+// Every lane of a group keeps looping until the group's first lane is done, so
+// barriers and ballots are always reached by the whole group.
+#include "hpac_internal.cuh"
+#include "regions.cuh"
+
+namespace hpac {
+namespace {
+
+template <class R, int LEVEL>
+__global__ void __launch_bounds__(1024) taf_kernel(R reg, const typename R::T *__restrict__ in,
+                                                   int64_t stride, typename R::T *__restrict__ out,
+                                                   uint8_t *__restrict__ mask,
+                                                   typename R::T *__restrict__ stat, int64_t n,
+                                                   int64_t T, int h, int p,
+                                                   typename R::T thr, int thr_inf, double thr_d,
+                                                   unsigned long long *__restrict__ counters) {
+  using V = typename R::T;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ unsigned long long s_cnt[2];
+  __shared__ int s_tally[3];
+  V *win = reinterpret_cast<V *>(smem_raw);
+  const int ld = blockDim.x;
+  const int lane = threadIdx.x & 31;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  // first logical thread whose activity bounds this thread's loop
+  const int64_t t_lead = LEVEL == HPAC_LEVEL_THREAD ? t
+                         : LEVEL == HPAC_LEVEL_WARP ? t - lane
+                                                    : (int64_t)blockIdx.x * blockDim.x;
+  if (threadIdx.x < 2) s_cnt[threadIdx.x] = 0;
+  if (LEVEL == HPAC_LEVEL_BLOCK && threadIdx.x == 0) s_tally[0] = s_tally[1] = s_tally[2] = 0;
+  __syncthreads();
+
+  int pos = 0;   // next slot to write
+  int cnt = 0;   // filled slots
+  int pred = 0;  // predictions still owed
+  unsigned long long n_apx = 0, n_border = 0;
+
+  if (t_lead < T) {
+    int k3 = 0;  // step index mod 3 (block-level tally buffer)
+    for (int64_t i = t; t_lead + (i - t) < n; i += T) {
+      const bool act = (t < T) && (i < n);
+      bool decided = false, wants = false;
+      if (act) {
+        if (pred > 0) {
+          const int newest = pos == 0 ? h - 1 : pos - 1;
+          out[i] = win[newest * ld + threadIdx.x];
+          if (mask) mask[i] = HPAC_MASK_APPROX;
+          if (stat) stat[i] = nan_v<V>();
+          --pred;
+          ++n_apx;
+        } else {
+          V x[R::kReads];
+#pragma unroll
+          for (int d = 0; d < R::kReads; ++d) x[d] = in[d * stride + i];
+          const V y = reg(x);
+          out[i] = y;
+          if (mask) mask[i] = HPAC_MASK_EXACT;
+          win[pos * ld + threadIdx.x] = y;
+          pos = (pos + 1 == h) ? 0 : pos + 1;
+          cnt = cnt < h ? cnt + 1 : h;
+          decided = true;
+          if (cnt == h) {
+            const V s = window_rsd<V>(win + threadIdx.x, ld, pos, h);
+            if (stat) stat[i] = s;
+            n_border += borderline((double)s, thr_d) ? 1 : 0;
+            wants = thr_inf || s < thr;
+          } else if (stat) {
+            stat[i] = nan_v<V>();
+          }
+        }
+      }
+      if (LEVEL == HPAC_LEVEL_THREAD) {
+        if (decided && wants) pred = p;
+      } else if (LEVEL == HPAC_LEVEL_WARP) {
+        const unsigned dec = __ballot_sync(0xffffffffu, decided);
+        const unsigned wan = __ballot_sync(0xffffffffu, decided && wants);
+        if (2 * __popc(wan) > __popc(dec) && decided && cnt == h) pred = p;
+      } else {
+        const unsigned dec = __ballot_sync(0xffffffffu, decided);
+        const unsigned wan = __ballot_sync(0xffffffffu, decided && wants);
+        // Three tally buffers: step k adds into buffer k%3 and thread 0 clears
+        // buffer (k+1)%3 before the barrier; that buffer was last read at step
+        // k-2, before the barrier of step k-1, and is next written at step k+1,
+        // after the barrier of step k.
+        if (threadIdx.x == 0) s_tally[k3 == 2 ? 0 : k3 + 1] = 0;
+        if (lane == 0) atomicAdd(&s_tally[k3], (__popc(wan) << 16) | __popc(dec));
+        __syncthreads();
+        const int tally = s_tally[k3];
+        const int nw = tally >> 16, nd = tally & 0xffff;
+        if (2 * nw > nd && decided && cnt == h) pred = p;
+        k3 = k3 == 2 ? 0 : k3 + 1;
+      }
+    }
+  }
+  warp_count(s_cnt, n_apx, n_border);
+  __syncthreads();
+  if (counters && threadIdx.x == 0) {
+    if (s_cnt[0]) atomicAdd(&counters[0], s_cnt[0]);
+    if (s_cnt[1]) atomicAdd(&counters[1], s_cnt[1]);
+  }
+}
+
+template <class R>
+hpac_status launch(const hpac_region *r, R reg, const hpac_taf_knobs *k, const void *in, void *out,
+                   uint8_t *mask, void *stat, unsigned long long *counters) {
+  using V = typename R::T;
+  const hpac_region_desc &d = r->d;
+  if (d.n == 0) return HPAC_OK;
+  const int64_t T = logical_threads(d);
+  const int B = d.block_threads;
+  const size_t smem = (size_t)k->hsize * B * sizeof(V);
+  const int limit = max_dyn_smem(r->device);
+  if ((int64_t)smem > limit)
+    return set_error(HPAC_EUNSUPPORTED, "TAF window of %zu bytes per block exceeds %d", smem, limit);
+  const int64_t blocks = (T + B - 1) / B;
+  if (blocks > 0x7fffffffLL) return set_error(HPAC_EINVAL, "too many logical threads");
+  const V thr = (V)k->thresh;
+  const int thr_inf = isinf(k->thresh) ? 1 : 0;
+  V *o = static_cast<V *>(out);
+  V *st = static_cast<V *>(stat);
+  const V *x = static_cast<const V *>(in);
+  switch (k->level) {
+    case HPAC_LEVEL_THREAD: {
+      auto fn = taf_kernel<R, HPAC_LEVEL_THREAD>;
+      HPAC_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      fn<<<(unsigned)blocks, B, smem, r->stream>>>(reg, x, d.in_stride, o, mask, st, d.n, T, k->hsize,
+                                                   k->psize, thr, thr_inf, k->thresh, counters);
+      break;
+    }
+    case HPAC_LEVEL_WARP: {
+      auto fn = taf_kernel<R, HPAC_LEVEL_WARP>;
+      HPAC_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      fn<<<(unsigned)blocks, B, smem, r->stream>>>(reg, x, d.in_stride, o, mask, st, d.n, T, k->hsize,
+                                                   k->psize, thr, thr_inf, k->thresh, counters);
+      break;
+    }
+    default: {
+      auto fn = taf_kernel<R, HPAC_LEVEL_BLOCK>;
+      HPAC_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      fn<<<(unsigned)blocks, B, smem, r->stream>>>(reg, x, d.in_stride, o, mask, st, d.n, T, k->hsize,
+                                                   k->psize, thr, thr_inf, k->thresh, counters);
+      break;
+    }
+  }
+  HPAC_CUDA_TRY(cudaGetLastError());
+  return HPAC_OK;
+}
+
+}  // namespace
+
+hpac_status launch_taf(const hpac_region *r, const hpac_taf_knobs *k, const void *in, void *out,
+                       uint8_t *mask, void *stat, unsigned long long *counters) {
+  const hpac_region_desc &d = r->d;
+  switch (d.kind) {
+    case HPAC_REGION_BLACKSCHOLES:
+      if (d.dtype == HPAC_F32)
+        return launch(r, BlackScholes32{(float)d.param}, k, in, out, mask, stat, counters);
+      return launch(r, BlackScholes64{d.param}, k, in, out, mask, stat, counters);
+    case HPAC_REGION_EOS:
+      return launch(r, Eos64{d.param}, k, in, out, mask, stat, counters);
+    case HPAC_REGION_IDENTITY:
+      if (d.dtype == HPAC_F32) return launch(r, Identity<float>{}, k, in, out, mask, stat, counters);
+      return launch(r, Identity<double>{}, k, in, out, mask, stat, counters);
+  }
+  return set_error(HPAC_EUNSUPPORTED, "region kind %d", d.kind);
+}
+
+}  // namespace hpac

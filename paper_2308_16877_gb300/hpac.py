@@ -1,0 +1,287 @@
+"""Python binding of libhpac: the C ABI declared in include/hpac.h, same names.
+
+Argument marshalling only: every step of a call runs in the library's CUDA
+kernels. Tensors are torch CUDA tensors (device memory and streams are
+PyTorch's; the arithmetic is not). If the shared library is missing it is built
+from the in-tree sources with nvcc; if that is impossible the import of the
+library raises, there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+HPAC_OK, HPAC_EINVAL, HPAC_ENOMEM, HPAC_ECUDA, HPAC_ETIMEOUT, HPAC_EUNSUPPORTED = range(6)
+HPAC_F32, HPAC_F64 = 0, 1
+HPAC_LEVEL_THREAD, HPAC_LEVEL_WARP, HPAC_LEVEL_BLOCK = 0, 1, 2
+HPAC_REGION_BLACKSCHOLES, HPAC_REGION_EOS, HPAC_REGION_IDENTITY = 0, 1, 3
+HPAC_PERFO_SMALL, HPAC_PERFO_LARGE, HPAC_PERFO_INI, HPAC_PERFO_FINI, HPAC_PERFO_RANDOM = range(5)
+HPAC_MASK_EXACT, HPAC_MASK_APPROX, HPAC_MASK_SKIPPED = 0, 1, 2
+HPAC_METRIC_MAPE, HPAC_METRIC_RMSE, HPAC_METRIC_MCR = 0, 1, 2
+
+
+class hpac_region_desc(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("dtype", C.c_int32), ("n", C.c_int64), ("n_in", C.c_int32),
+                ("n_out", C.c_int32), ("in_stride", C.c_int64), ("out_stride", C.c_int64),
+                ("logical_threads", C.c_int64), ("block_threads", C.c_int32),
+                ("reserved0", C.c_int32), ("param", C.c_double)]
+
+
+class hpac_perfo_knobs(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("m_or_percent", C.c_int32), ("rate", C.c_double),
+                ("seed", C.c_uint64), ("herded", C.c_int32), ("reserved0", C.c_int32)]
+
+
+class hpac_taf_knobs(C.Structure):
+    _fields_ = [("hsize", C.c_int32), ("psize", C.c_int32), ("thresh", C.c_double),
+                ("level", C.c_int32), ("reserved0", C.c_int32)]
+
+
+class hpac_iact_knobs(C.Structure):
+    _fields_ = [("tsize", C.c_int32), ("tperwarp", C.c_int32), ("thresh", C.c_double),
+                ("level", C.c_int32), ("reserved0", C.c_int32), ("in_scale", C.POINTER(C.c_double))]
+
+
+class hpac_stats(C.Structure):
+    _fields_ = [("invocations", C.c_int64), ("approximated", C.c_int64), ("skipped", C.c_int64),
+                ("borderline", C.c_int64)]
+
+    def as_dict(self):
+        return {f: int(getattr(self, f)) for f, _ in self._fields_}
+
+
+class hpac_quality_result(C.Structure):
+    _fields_ = [("value", C.c_double), ("zero_max_abs", C.c_double), ("used", C.c_int64),
+                ("zeros", C.c_int64), ("zeros_mismatch", C.c_int64)]
+
+    def as_dict(self):
+        return {f: (float if t is C.c_double else int)(getattr(self, f)) for f, t in self._fields_}
+
+
+# Every symbol include/hpac.h declares, with its ctypes signature.
+_P = C.c_void_p
+SIGNATURES = {
+    "hpac_region_create": (C.c_int, [C.POINTER(hpac_region_desc), _P, C.POINTER(_P)]),
+    "hpac_region_destroy": (C.c_int, [_P]),
+    "hpac_region_set_stream": (C.c_int, [_P, _P]),
+    "hpac_run_exact": (C.c_int, [_P, _P, _P]),
+    "hpac_run_perfo": (C.c_int, [_P, C.POINTER(hpac_perfo_knobs), _P, _P, _P, C.POINTER(hpac_stats)]),
+    "hpac_run_taf": (C.c_int, [_P, C.POINTER(hpac_taf_knobs), _P, _P, _P, _P, C.POINTER(hpac_stats)]),
+    "hpac_run_iact": (C.c_int, [_P, C.POINTER(hpac_iact_knobs), _P, _P, _P, _P, C.POINTER(hpac_stats)]),
+    "hpac_quality": (C.c_int, [C.c_int32, C.c_int64, _P, _P, C.c_int32,
+                               C.POINTER(hpac_quality_result), _P]),
+    "hpac_last_error": (C.c_char_p, []),
+    "hpac_version": (C.c_char_p, []),
+}
+
+_lib = None
+_lock = threading.Lock()
+
+
+def library_path() -> str:
+    from . import build as _b
+    return _b.LIB
+
+
+def load(build_if_missing: bool = True) -> C.CDLL:
+    """Load libhpac.so (building it from source first if it is absent)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = library_path()
+        if not os.path.exists(path):
+            if not build_if_missing:
+                raise RuntimeError(f"libhpac is not built ({path} missing)")
+            from . import build as _b
+            _b.build()
+        lib = C.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+        return lib
+
+
+class HpacError(RuntimeError):
+    def __init__(self, status, where):
+        msg = load().hpac_last_error().decode(errors="replace")
+        super().__init__(f"{where}: status {status}: {msg}")
+        self.status = status
+
+
+def _check(status, where):
+    if status != HPAC_OK:
+        raise HpacError(status, where)
+
+
+# --------------------------------------------------------------------------
+# thin wrappers with the C names
+# --------------------------------------------------------------------------
+
+def hpac_region_create(desc: hpac_region_desc, stream: int | None):
+    h = _P()
+    _check(load().hpac_region_create(C.byref(desc), stream or None, C.byref(h)), "hpac_region_create")
+    return h
+
+
+def hpac_region_destroy(h):
+    _check(load().hpac_region_destroy(h), "hpac_region_destroy")
+
+
+def hpac_region_set_stream(h, stream):
+    _check(load().hpac_region_set_stream(h, stream or None), "hpac_region_set_stream")
+
+
+def hpac_run_exact(h, d_in: int, d_out: int):
+    _check(load().hpac_run_exact(h, d_in, d_out), "hpac_run_exact")
+
+
+def hpac_run_perfo(h, knobs, d_in, d_out, d_mask=None, want_stats=False):
+    st = hpac_stats() if want_stats else None
+    _check(load().hpac_run_perfo(h, C.byref(knobs), d_in, d_out, d_mask,
+                                 C.byref(st) if st is not None else None), "hpac_run_perfo")
+    return st
+
+
+def hpac_run_taf(h, knobs, d_in, d_out, d_mask=None, d_stat=None, want_stats=False):
+    st = hpac_stats() if want_stats else None
+    _check(load().hpac_run_taf(h, C.byref(knobs), d_in, d_out, d_mask, d_stat,
+                               C.byref(st) if st is not None else None), "hpac_run_taf")
+    return st
+
+
+def hpac_run_iact(h, knobs, d_in, d_out, d_mask=None, d_stat=None, want_stats=False):
+    st = hpac_stats() if want_stats else None
+    _check(load().hpac_run_iact(h, C.byref(knobs), d_in, d_out, d_mask, d_stat,
+                                C.byref(st) if st is not None else None), "hpac_run_iact")
+    return st
+
+
+def hpac_quality(dtype, n, d_exact, d_approx, metric, stream=None):
+    res = hpac_quality_result()
+    _check(load().hpac_quality(dtype, n, d_exact, d_approx, metric, C.byref(res), stream or None),
+           "hpac_quality")
+    return res
+
+
+def hpac_last_error() -> str:
+    return load().hpac_last_error().decode(errors="replace")
+
+
+def hpac_version() -> str:
+    return load().hpac_version().decode()
+
+
+# --------------------------------------------------------------------------
+# tensor-level convenience layer
+# --------------------------------------------------------------------------
+
+def _dtype_code(t):
+    import torch
+    if t.dtype == torch.float32:
+        return HPAC_F32
+    if t.dtype == torch.float64:
+        return HPAC_F64
+    raise TypeError(f"unsupported dtype {t.dtype}")
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream_handle(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+class Region:
+    """An annotated loop region over a (D, stride) CUDA tensor of inputs."""
+
+    def __init__(self, kind: int, x, n: int | None = None, param: float = 0.0,
+                 logical_threads: int = 0, block_threads: int = 256, stream=None):
+        if not x.is_cuda or x.dim() != 2 or not x.is_contiguous():
+            raise ValueError("inputs must be a contiguous 2-D CUDA tensor (D, stride)")
+        self.kind = kind
+        self.dtype = x.dtype
+        self.d_in, stride = x.shape
+        self.n = stride if n is None else n
+        self.desc = hpac_region_desc(kind, _dtype_code(x), self.n, self.d_in, 1, stride, self.n,
+                                     logical_threads, block_threads, 0, float(param))
+        self._h = hpac_region_create(self.desc, _stream_handle(stream))
+
+    def close(self):
+        if self._h:
+            hpac_region_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def set_stream(self, stream):
+        hpac_region_set_stream(self._h, _stream_handle(stream))
+
+    def _check_io(self, x, out, mask=None, stat=None):
+        if x.dtype != self.dtype or out.dtype != self.dtype:
+            raise TypeError("dtype mismatch")
+        if out.numel() < self.n:
+            raise ValueError("output too small")
+        if mask is not None and mask.numel() < self.n:
+            raise ValueError("mask too small")
+        if stat is not None and (stat.numel() < self.n or stat.dtype != self.dtype):
+            raise ValueError("stat too small or wrong dtype")
+
+    def run_exact(self, x, out):
+        self._check_io(x, out)
+        hpac_run_exact(self._h, _ptr(x), _ptr(out))
+        return out
+
+    def run_perfo(self, x, out, kind, m_or_percent=0, rate=0.0, seed=0, herded=True, mask=None,
+                  stats=False):
+        self._check_io(x, out, mask)
+        k = hpac_perfo_knobs(kind, int(m_or_percent), float(rate), int(seed), 1 if herded else 0, 0)
+        st = hpac_run_perfo(self._h, k, _ptr(x), _ptr(out), _ptr(mask), stats)
+        return st.as_dict() if st is not None else None
+
+    def run_taf(self, x, out, hsize, psize, thresh, level=HPAC_LEVEL_THREAD, mask=None, stat=None,
+                stats=False):
+        self._check_io(x, out, mask, stat)
+        k = hpac_taf_knobs(int(hsize), int(psize), float(thresh), int(level), 0)
+        st = hpac_run_taf(self._h, k, _ptr(x), _ptr(out), _ptr(mask), _ptr(stat), stats)
+        return st.as_dict() if st is not None else None
+
+    def run_iact(self, x, out, tsize, tperwarp, thresh, level=HPAC_LEVEL_THREAD, in_scale=None,
+                 mask=None, stat=None, stats=False):
+        self._check_io(x, out, mask, stat)
+        sc = None
+        if in_scale is not None:
+            vals = [float(v) for v in in_scale]
+            if len(vals) != self.d_in:
+                raise ValueError("in_scale needs one value per input")
+            sc = (C.c_double * len(vals))(*vals)
+        k = hpac_iact_knobs(int(tsize), int(tperwarp), float(thresh), int(level), 0,
+                            C.cast(sc, C.POINTER(C.c_double)) if sc is not None else None)
+        st = hpac_run_iact(self._h, k, _ptr(x), _ptr(out), _ptr(mask), _ptr(stat), stats)
+        return st.as_dict() if st is not None else None
+
+
+def quality(exact, approx, metric, stream=None):
+    """MAPE / RMSE / MCR of approx against exact (float64 CUDA tensor)."""
+    import torch
+    if exact.dtype != torch.float64 or exact.numel() != approx.numel():
+        raise ValueError("exact must be float64 with as many elements as approx")
+    r = hpac_quality(_dtype_code(approx), exact.numel(), _ptr(exact), _ptr(approx), metric,
+                     _stream_handle(stream))
+    return r.as_dict()

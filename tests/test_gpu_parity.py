@@ -1,0 +1,270 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle, element by
+element, on seeded inputs spanning several tiles with ragged tails, plus the
+edge cases: empty and one-element regions, logical threads not a multiple of
+the warp, blocks of 32 and 1024, strided and misaligned inputs."""
+import numpy as np
+import pytest
+
+from paper_2308_16877_gb300 import workloads as W
+from parity import source_index, taf_compare
+from tolerances import EPS32, EPS64, output_tol
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+GAMMA = 5.0 / 3.0
+
+
+@pytest.fixture(scope="module")
+def H():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2308_16877_gb300 import hpac
+    hpac.load()
+    return hpac
+
+
+def inputs(kind, n, dtype=np.float32, seed=2308, stride=None, d=2, ikind="walk"):
+    if kind == 0:
+        x = W.blackscholes_inputs(n, seed=seed, stride=stride)
+        return x.astype(dtype), W.BS_RATE
+    if kind == 1:
+        return W.eos_inputs(n, seed=seed, stride=stride), GAMMA
+    return W.identity_inputs(n, d=d, seed=seed, dtype=dtype, kind=ikind, stride=stride), 0.0
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+# ---------------------------------------------------------------- exact
+
+@pytest.mark.parametrize("kind,dt", [(0, np.float32), (0, np.float64), (1, np.float64),
+                                     (3, np.float32), (3, np.float64)])
+@pytest.mark.parametrize("n", [0, 1, 3, 31, 33, 1000, 65536, 65539])
+def test_exact(H, orc, kind, dt, n):
+    x, param = inputs(kind, n, dt)
+    out = torch.full((n,), float("nan"), dtype=torch.float32 if dt == np.float32 else torch.float64,
+                     device="cuda")
+    with H.Region(kind, dev(x), param=param) as R:
+        R.run_exact(dev(x), out)
+    g = host(out)
+    x64 = x.astype(np.float64)
+    ref = orc.run_exact(kind, x64 if kind != 3 else x, param)
+    tol = output_tol(kind, x64, param, dt)
+    if kind == 3:
+        assert np.array_equal(g, ref)
+    else:
+        assert np.all(np.abs(g.astype(np.float64) - ref.astype(np.float64)) <= tol)
+
+
+def test_exact_strided_and_misaligned(H, orc):
+    n, stride = 1001, 1030
+    x, r = inputs(0, n, np.float32, stride=stride)
+    xd = dev(x)
+    out = torch.empty(n + 1, dtype=torch.float32, device="cuda")
+    with H.Region(0, xd, n=n, param=r) as R:
+        R.run_exact(xd, out[1:])           # output misaligned by 4 bytes: scalar path
+    g = host(out)[1:]
+    ref = orc.run_exact(0, x[:, :n].astype(np.float64), r)
+    assert np.all(np.abs(g - ref) <= output_tol(0, x[:, :n], r, np.float32))
+
+
+def test_exact_sampled_full_size(H, orc):
+    """2^24 options (256 MB of inputs, the HBM-scale launch): sampled outputs
+    against the oracle evaluated on just those options."""
+    n = 1 << 24
+    x, r = inputs(0, n, np.float32, seed=99)
+    xd = dev(x)
+    out = torch.empty(n, dtype=torch.float32, device="cuda")
+    with H.Region(0, xd, param=r) as R:
+        R.run_exact(xd, out)
+    idx = np.random.default_rng(0).choice(n, 20000, replace=False)
+    idx = np.concatenate([idx, [0, 1, n - 2, n - 1]])
+    g = host(out)[idx]
+    xs = x[:, idx]
+    ref = orc.run_exact(0, xs.astype(np.float64), r)
+    assert np.all(np.abs(g - ref) <= output_tol(0, xs, r, np.float32))
+
+
+# ---------------------------------------------------------------- perforation
+
+PERFO = [(0, 4, 0.0), (0, 2, 0.0), (1, 3, 0.0), (2, 10, 0.0), (2, 100, 0.0), (3, 37, 0.0),
+         (4, 0, 0.3), (4, 0, 1.0), (0, 1, 0.0)]
+
+
+@pytest.mark.parametrize("kind,dt", [(0, np.float32), (1, np.float64), (3, np.float64)])
+@pytest.mark.parametrize("pk,m,rate", PERFO)
+@pytest.mark.parametrize("herded", [1, 0])
+@pytest.mark.parametrize("n,T", [(65536, 8192), (5003, 77), (1, 0)])
+def test_perforation(H, orc, kind, dt, pk, m, rate, herded, n, T):
+    x, param = inputs(kind, n, dt)
+    tdt = torch.float32 if dt == np.float32 else torch.float64
+    out = torch.full((n,), float("nan"), dtype=tdt, device="cuda")
+    mask = torch.full((n,), 255, dtype=torch.uint8, device="cuda")
+    with H.Region(kind, dev(x), param=param, logical_threads=T) as R:
+        st = R.run_perfo(dev(x), out, pk, m, rate, seed=77, herded=bool(herded), mask=mask, stats=True)
+    g, gm = host(out), host(mask)
+    ref = np.full(n, np.nan, dtype=dt)
+    ref, om, cnt = orc.run_perfo(kind, x, param, pk, m, rate, 77, herded, threads=T, out=ref)
+    assert np.array_equal(gm, om)
+    skip = om == 2
+    assert np.all(np.isnan(g[skip]))
+    tol = output_tol(kind, x.astype(np.float64), param, dt)
+    assert np.all(np.abs(g[~skip].astype(np.float64) - ref[~skip].astype(np.float64)) <= tol[~skip])
+    assert st["skipped"] == int(skip.sum()) == cnt[2]
+
+
+# ---------------------------------------------------------------- TAF
+
+def taf_case(H, orc, kind, dt, n, T, B, h, p, thr, level, ikind="walk", seed=2308):
+    x, param = inputs(kind, n, dt, seed=seed, d=1, ikind=ikind)
+    tdt = torch.float32 if dt == np.float32 else torch.float64
+    out = torch.full((n,), float("nan"), dtype=tdt, device="cuda")
+    stat = torch.full((n,), -1.0, dtype=tdt, device="cuda")
+    mask = torch.full((n,), 255, dtype=torch.uint8, device="cuda")
+    with H.Region(kind, dev(x), param=param, logical_threads=T, block_threads=B) as R:
+        st = R.run_taf(dev(x), out, h, p, thr, level, mask=mask, stat=stat, stats=True)
+    g, gm, gs = host(out), host(mask), host(stat)
+    o, om, os_, cnt = orc.run_taf(kind, x, param, h, p, thr, level=level, threads=T, block=B)
+    return x, param, g, gm, gs, o, om, os_, cnt, st
+
+
+@pytest.mark.parametrize("dt", [np.float32, np.float64])
+@pytest.mark.parametrize("level", [0, 1, 2])
+@pytest.mark.parametrize("n,T,B,h,p,thr", [
+    (20000, 500, 128, 3, 5, 2e-3), (20000, 2500, 256, 4, 8, 5e-2), (777, 77, 64, 2, 2, 1e-2),
+    (4096, 4096, 32, 1, 3, 0.1), (3000, 96, 1024, 5, 1, np.inf), (3000, 100, 96, 4, 8, 0.0),
+    (1, 0, 256, 2, 2, 0.5), (0, 0, 256, 2, 2, 0.5)])
+def test_taf_identity_bitexact(H, orc, dt, level, n, T, B, h, p, thr):
+    """Identity region: both sides see bit-identical windows, so masks,
+    outputs and statistics agree exactly."""
+    _, _, g, gm, gs, o, om, os_, cnt, st = taf_case(H, orc, 3, dt, n, T, B, h, p, thr, level)
+    assert np.array_equal(gm, om)
+    assert np.array_equal(g, o)
+    assert np.array_equal(gs, os_, equal_nan=True)
+    assert st["approximated"] == cnt[1] and st["borderline"] == cnt[3]
+    if T > 0 and n >= 4 * T and thr > 0:
+        assert cnt[1] > 0
+
+
+@pytest.mark.parametrize("kind,dt", [(0, np.float32), (0, np.float64), (1, np.float64)])
+@pytest.mark.parametrize("level", [0, 1, 2])
+@pytest.mark.parametrize("thr", [5e-3, 0.05, 0.5, 2.0])
+def test_taf_regions(H, orc, kind, dt, level, thr):
+    n = 65536
+    T, B, h, p = n // 8, 256, 4, 8
+    x, param, g, gm, gs, o, om, os_, cnt, st = taf_case(H, orc, kind, dt, n, T, B, h, p, thr, level)
+    x64 = x.astype(np.float64)
+    tol_x = output_tol(kind, x64, param, dt)
+    src = source_index(n, T, om)
+    ref64 = orc.run_exact(kind, x64, param)
+    rel = tol_x / np.maximum(np.abs(ref64), 1e-300)
+    eps = EPS32 if dt == np.float32 else EPS64
+    div, comp = taf_compare(n, T, B, level, g, gm, gs, o, om, os_, h, thr, 2 * tol_x[src],
+                            2 * rel, eps)
+    assert div <= max(1, n // 1000), div
+    assert comp >= n - div * 8
+
+
+def test_taf_blackscholes_workload_counts(H, orc):
+    """Black-Scholes, 65,536 options, T = N/8, history 4, prediction 8, RSD
+    threshold 0.5%: the approximation count matches the oracle's."""
+    n = 65536
+    *_, gm, gs, o, om, os_, cnt, st = taf_case(H, orc, 0, np.float32, n, n // 8, 256, 4, 8, 5e-3, 0)
+    assert abs(st["approximated"] - cnt[1]) <= 8 * 2
+
+
+# ---------------------------------------------------------------- iACT
+
+@pytest.mark.parametrize("kind,dt,d", [(3, np.float32, 2), (3, np.float64, 3), (0, np.float32, 4),
+                                       (1, np.float64, 4)])
+@pytest.mark.parametrize("level", [0, 1, 2])
+@pytest.mark.parametrize("g,ts", [(32, 8), (16, 4), (4, 2), (1, 1), (2, 64)])
+def test_iact(H, orc, kind, dt, d, level, g, ts):
+    n, T, B = 30011, 3000, 128
+    x, param = inputs(kind, n, dt, d=d, ikind="levels")
+    if kind == 1:
+        x = W.eos_inputs(n, smooth=16)
+    sc = W.iact_scale(x, n)
+    thr = 0.05 if kind != 1 else 0.02
+    tdt = torch.float32 if dt == np.float32 else torch.float64
+    out = torch.full((n,), float("nan"), dtype=tdt, device="cuda")
+    stat = torch.full((n,), -1.0, dtype=tdt, device="cuda")
+    mask = torch.full((n,), 255, dtype=torch.uint8, device="cuda")
+    with H.Region(kind, dev(x), param=param, logical_threads=T, block_threads=B) as R:
+        st = R.run_iact(dev(x), out, ts, g, thr, level, in_scale=sc, mask=mask, stat=stat, stats=True)
+    gout, gm, gs = host(out), host(mask), host(stat)
+    o, om, os_, cnt = orc.run_iact(kind, x, param, ts, g, thr, level=level, in_scale=sc, threads=T, block=B)
+    assert np.array_equal(gm, om)                      # decisions are input-only: exact
+    assert np.array_equal(gs, os_)                     # distances are bit-identical
+    assert st["approximated"] == cnt[1] and st["borderline"] == cnt[3]
+    if kind == 3:
+        assert np.array_equal(gout, o)
+    else:
+        # an approximated output repeats the exact output of the slot's writer,
+        # whose own tolerance bounds it; the bound of the largest-scale output
+        # is used for every element
+        tol = output_tol(kind, x.astype(np.float64), param, dt)
+        assert np.all(np.abs(gout.astype(np.float64) - o.astype(np.float64)) <= tol.max())
+    if level == 0 and kind == 3:
+        assert cnt[1] > 0
+
+
+# ---------------------------------------------------------------- quality
+
+@pytest.mark.parametrize("metric", [0, 1, 2])
+@pytest.mark.parametrize("dt", [np.float32, np.float64])
+@pytest.mark.parametrize("n", [0, 1, 1000, 1 << 20])
+def test_quality(H, orc, metric, dt, n):
+    rng = np.random.default_rng(metric + n)
+    a = rng.uniform(0.1, 2.0, n)
+    a[: n // 10] = 0.0
+    b = (a * (1 + rng.normal(0, 0.01, n))).astype(dt)
+    b[: n // 20] = 1.0
+    if metric == 2:
+        b[n // 2:] = a[n // 2:].astype(dt)
+    r = H.quality(dev(a), dev(b), metric)
+    v, info = orc.quality(a, b.astype(np.float64), metric)
+    assert r["value"] == pytest.approx(v, rel=1e-12, abs=1e-300)
+    if metric == 0:
+        assert r["zeros"] == info["zeros"] and r["zeros_mismatch"] == info["zeros_mismatch"]
+        assert r["zero_max_abs"] == info["zero_max_abs"]
+
+
+# ---------------------------------------------------------------- errors
+
+def test_invalid_arguments_are_rejected(H):
+    x = dev(W.identity_inputs(100))
+    out = torch.empty(100, dtype=torch.float32, device="cuda")
+    with pytest.raises(H.HpacError) as e:
+        H.Region(0, x)                      # Black-Scholes needs 4 inputs
+    assert e.value.status == H.HPAC_EINVAL
+    with pytest.raises(H.HpacError):
+        H.Region(3, x, block_threads=48)
+    with H.Region(3, x) as R:
+        for args in ((0, 0, 0.1, 0), (2, -1, 0.1, 0), (2, 2, -1.0, 0), (2, 2, float("nan"), 0),
+                     (2, 2, 0.1, 7), (65, 1, 0.1, 0)):
+            with pytest.raises(H.HpacError) as e:
+                R.run_taf(x, out, *args)
+            assert e.value.status == H.HPAC_EINVAL
+        for args in ((0, 32, 0.1, 0), (2, 3, 0.1, 0), (2, 64, 0.1, 0), (2, 32, -1.0, 0)):
+            with pytest.raises(H.HpacError):
+                R.run_iact(x, out, *args)
+        with pytest.raises(H.HpacError):
+            R.run_perfo(x, out, 9, 1)
+        with pytest.raises(H.HpacError):
+            R.run_perfo(x, out, 4, 0, rate=1.5)
+    x64 = dev(W.identity_inputs(100, d=4, dtype=np.float64))
+    with pytest.raises(H.HpacError) as e:
+        H.Region(1, x64.float().contiguous())   # EOS is double precision only
+    assert e.value.status == H.HPAC_EUNSUPPORTED
+    # the context is still usable afterwards
+    with H.Region(3, x) as R:
+        R.run_exact(x, out)
+    assert torch.equal(out, x[0])
