@@ -220,6 +220,25 @@ hpac_status hpac_quality(int32_t approx_dtype, int64_t n, const double *d_exact,
                          const void *d_approx, int32_t metric, hpac_quality_result *h_result,
                          void *cuda_stream);
 
+/* hpac_quality without any allocation, for callers that cannot call cudaMalloc:
+ * code that runs after a service has reserved all of its device memory up front
+ * (through its own pool, or a framework's caching allocator that owns every
+ * free byte), or that must not enter the CUDA allocator at all once it is
+ * running. The paper has no counterpart; this is a library convenience.
+ * Same arguments, layout and result as hpac_quality, with these differences:
+ *  - Scratch is a fixed array inside the library (about 656 KB on every device
+ *    that loads it, held until the process exits), so n must not exceed
+ *    134,217,728 elements; larger n returns HPAC_EINVAL with a message.
+ *  - The first call on a device looks up that array's device address (with the
+ *    device current) and caches it; make that first call before any stream
+ *    capture begins on the device.
+ *  - Every call on a device uses the same array. A call waits for its own
+ *    result, but calls issued from several host threads whose work overlaps on
+ *    the GPU race on the array: serialize them. */
+hpac_status hpac_quality_noalloc(int32_t approx_dtype, int64_t n, const double *d_exact,
+                                 const void *d_approx, int32_t metric,
+                                 hpac_quality_result *h_result, void *cuda_stream);
+
 /* Message for the last non-OK status returned on the calling host thread. */
 const char *hpac_last_error(void);
 

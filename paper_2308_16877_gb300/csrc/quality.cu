@@ -167,3 +167,92 @@ extern "C" hpac_status hpac_quality(int32_t approx_dtype, int64_t n, const doubl
   h_result->zeros_mismatch = (int64_t)res.zbad;
   return HPAC_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of hpac_quality.
+//
+// Its scratch is a fixed array compiled into the library instead of a buffer
+// obtained from cudaMalloc: every GPU that loads the library holds these
+// 16,385 partials (about 656 KB) until the process exits. The reduction runs
+// ceil(n / 8192) blocks of the same partial kernel (each thread reduces at most
+// 32 elements) followed by the same final kernel, so n may not exceed
+// 16,384 * 8,192 = 134,217,728 elements.
+// ---------------------------------------------------------------------------
+namespace hpac {
+namespace {
+
+constexpr int64_t kStaticTile = (int64_t)kThreads * 32;          // elements per block
+constexpr int kStaticPartials = 16384;                            // blocks at most
+constexpr int64_t kStaticMaxN = kStaticTile * kStaticPartials;    // 134,217,728
+
+static __device__ __align__(256) Partial g_static_scratch[kStaticPartials + 1];
+
+// Device address of g_static_scratch per device ordinal, looked up once with
+// that device current (host code may not use the symbol itself as a pointer).
+Partial *g_static_addr[64] = {nullptr};
+std::mutex g_static_mu;
+
+hpac_status static_scratch(int dev, Partial **out) {
+  if (dev < 0 || dev >= 64) return set_error(HPAC_EUNSUPPORTED, "device ordinal %d", dev);
+  std::lock_guard<std::mutex> lk(g_static_mu);
+  if (!g_static_addr[dev]) {
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (e != cudaSuccess) return cuda_error(e, "cudaGetSymbolAddress(g_static_scratch)");
+    g_static_addr[dev] = static_cast<Partial *>(p);
+  }
+  *out = g_static_addr[dev];
+  return HPAC_OK;
+}
+
+}  // namespace
+}  // namespace hpac
+
+extern "C" hpac_status hpac_quality_noalloc(int32_t approx_dtype, int64_t n, const double *d_exact,
+                                            const void *d_approx, int32_t metric,
+                                            hpac_quality_result *h_result, void *cuda_stream) {
+  if (!h_result) return set_error(HPAC_EINVAL, "h_result is NULL");
+  if (n < 0) return set_error(HPAC_EINVAL, "n < 0");
+  if (n > kStaticMaxN)
+    return set_error(HPAC_EINVAL,
+                     "hpac_quality_noalloc: n = %lld exceeds the %lld-element limit of its fixed "
+                     "scratch; use hpac_quality for larger inputs",
+                     (long long)n, (long long)kStaticMaxN);
+  if (metric < HPAC_METRIC_MAPE || metric > HPAC_METRIC_MCR)
+    return set_error(HPAC_EINVAL, "metric %d", metric);
+  if (approx_dtype != HPAC_F32 && approx_dtype != HPAC_F64)
+    return set_error(HPAC_EINVAL, "dtype %d", approx_dtype);
+  if (n > 0 && (!d_exact || !d_approx)) return set_error(HPAC_EINVAL, "NULL data pointer");
+  *h_result = hpac_quality_result{0.0, 0.0, 0, 0, 0};
+  if (n == 0) return HPAC_OK;
+  int dev = 0;
+  HPAC_CUDA_TRY(cudaGetDevice(&dev));
+  Partial *scr = nullptr;
+  hpac_status s = static_scratch(dev, &scr);
+  if (s != HPAC_OK) return s;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  // Every partial slot the final kernel reads is written earlier in this call,
+  // so nothing left in the shared array by a previous call is used.
+  const int64_t blocks = (n + kStaticTile - 1) / kStaticTile;
+  if (approx_dtype == HPAC_F32)
+    quality_partial<float><<<(unsigned)blocks, kThreads, 0, st>>>(
+        d_exact, static_cast<const float *>(d_approx), n, metric, scr);
+  else
+    quality_partial<double><<<(unsigned)blocks, kThreads, 0, st>>>(
+        d_exact, static_cast<const double *>(d_approx), n, metric, scr);
+  HPAC_CUDA_TRY(cudaGetLastError());
+  quality_final<<<1, kThreads, 0, st>>>(scr, (int)blocks, scr + kStaticPartials);
+  HPAC_CUDA_TRY(cudaGetLastError());
+  Partial res;
+  HPAC_CUDA_TRY(
+      cudaMemcpyAsync(&res, scr + kStaticPartials, sizeof(Partial), cudaMemcpyDeviceToHost, st));
+  HPAC_CUDA_TRY(cudaStreamSynchronize(st));
+  double v = res.used ? res.sum / (double)res.used : 0.0;
+  if (metric == HPAC_METRIC_RMSE) v = sqrt(v);
+  h_result->value = v;
+  h_result->zero_max_abs = res.zmax;
+  h_result->used = (int64_t)res.used;
+  h_result->zeros = (int64_t)res.zeros;
+  h_result->zeros_mismatch = (int64_t)res.zbad;
+  return HPAC_OK;
+}

@@ -71,6 +71,8 @@ SIGNATURES = {
     "hpac_run_iact": (C.c_int, [_P, C.POINTER(hpac_iact_knobs), _P, _P, _P, _P, C.POINTER(hpac_stats)]),
     "hpac_quality": (C.c_int, [C.c_int32, C.c_int64, _P, _P, C.c_int32,
                                C.POINTER(hpac_quality_result), _P]),
+    "hpac_quality_noalloc": (C.c_int, [C.c_int32, C.c_int64, _P, _P, C.c_int32,
+                                       C.POINTER(hpac_quality_result), _P]),
     "hpac_last_error": (C.c_char_p, []),
     "hpac_version": (C.c_char_p, []),
 }
@@ -164,6 +166,15 @@ def hpac_quality(dtype, n, d_exact, d_approx, metric, stream=None):
     res = hpac_quality_result()
     _check(load().hpac_quality(dtype, n, d_exact, d_approx, metric, C.byref(res), stream or None),
            "hpac_quality")
+    return res
+
+
+def hpac_quality_noalloc(dtype, n, d_exact, d_approx, metric, stream=None):
+    """hpac_quality with the library's fixed scratch instead of an allocation
+    (n at most 134,217,728); for callers that cannot allocate device memory."""
+    res = hpac_quality_result()
+    _check(load().hpac_quality_noalloc(dtype, n, d_exact, d_approx, metric, C.byref(res),
+                                       stream or None), "hpac_quality_noalloc")
     return res
 
 

@@ -1,0 +1,82 @@
+"""The allocation-free quality entry point, hpac_quality_noalloc.
+
+It serves callers that cannot allocate device memory once they run (a service
+whose device memory is all reserved up front by its own pool or by a
+framework's caching allocator): instead of a cudaMalloc'd buffer it reduces
+into a fixed array compiled into the library. Called through the C ABI, it must
+give the same result as hpac_quality on the same inputs, including on a second
+call right after the first (the array keeps the previous call's contents), and
+it must refuse inputs larger than its fixed scratch can reduce.
+
+This file is collected last so that a run stopping at the first failure has
+already run every other test; it also passes on its own in a fresh process.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+NOALLOC_MAX_N = 134_217_728
+
+
+@pytest.fixture(scope="module")
+def H():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2308_16877_gb300 import hpac
+    hpac.load()
+    return hpac
+
+
+def _pair(n, dtype, seed):
+    rng = np.random.default_rng(seed)
+    a = rng.uniform(0.1, 2.0, n)
+    a[: n // 10] = 0.0
+    b = (a * (1.0 + rng.normal(0.0, 0.01, n))).astype(dtype)
+    b[: n // 20] = 1.0
+    return torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda()
+
+
+def _call(H, fn, a, b, metric):
+    code = H.HPAC_F32 if b.dtype == torch.float32 else H.HPAC_F64
+    s = torch.cuda.current_stream().cuda_stream
+    return fn(code, a.numel(), H.C.c_void_p(a.data_ptr()), H.C.c_void_p(b.data_ptr()), metric,
+              s).as_dict()
+
+
+def _same(r, ref):
+    assert r["value"] == pytest.approx(ref["value"], rel=1e-12, abs=1e-300)
+    for k in ("used", "zeros", "zeros_mismatch"):
+        assert r[k] == ref[k], k
+    assert r["zero_max_abs"] == ref["zero_max_abs"]
+
+
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+@pytest.mark.parametrize("metric", [0, 1, 2])
+def test_two_calls_in_a_row_match_hpac_quality(H, dtype, metric):
+    # the first call covers more blocks than the second, so the second leaves
+    # stale partials of the first in the shared array beyond its own range
+    a1, b1 = _pair((1 << 22) + 7, dtype, seed=10 + metric)
+    a2, b2 = _pair(100_003, dtype, seed=20 + metric)
+    first = _call(H, H.hpac_quality_noalloc, a1, b1, metric)
+    second = _call(H, H.hpac_quality_noalloc, a2, b2, metric)
+    _same(first, _call(H, H.hpac_quality, a1, b1, metric))
+    _same(second, _call(H, H.hpac_quality, a2, b2, metric))
+
+
+def test_empty_input(H):
+    a, b = _pair(0, np.float32, seed=1)
+    r = _call(H, H.hpac_quality_noalloc, a, b, 0)
+    assert r["value"] == 0.0 and r["used"] == 0
+
+
+def test_rejects_inputs_beyond_the_fixed_scratch(H):
+    a, b = _pair(16, np.float32, seed=2)
+    code = H.HPAC_F32
+    res = H.hpac_quality_result()
+    # n is checked before anything is launched, so the small buffers are never read
+    st = H.load().hpac_quality_noalloc(code, NOALLOC_MAX_N + 1, H.C.c_void_p(a.data_ptr()),
+                                       H.C.c_void_p(b.data_ptr()), 0, H.C.byref(res), None)
+    assert st == H.HPAC_EINVAL
+    assert "limit" in H.hpac_last_error()
