@@ -56,15 +56,21 @@ def lib() -> C.CDLL:
     return _lib
 
 
+class EosKnobs(C.Structure):
+    _fields_ = [("mode", C.c_int32), ("hsize", C.c_int32), ("psize", C.c_int32),
+                ("tsize", C.c_int32), ("tperwarp", C.c_int32), ("level", C.c_int32),
+                ("thresh", C.c_double), ("threads", C.c_int64), ("block", C.c_int32),
+                ("reserved", C.c_int32), ("in_scale", C.c_double * 4)]
+
+
 def _hydro_bind(L):
-    if not hasattr(L, "orc_hydro_init"):
-        return
     P, I32, D = C.c_void_p, C.c_int32, C.c_double
-    L.orc_hydro_init.argtypes = [I32, P, P, P, P, P, P, P]
-    L.orc_hydro_step.argtypes = [I32, D, D, P, P, P, P, P, P, P, P, P, P, P, P, P, I32, P, P, P]
+    L.orc_hydro_init.argtypes = [I32, P, P, P, P, P, P]
+    L.orc_hydro_step.argtypes = [I32, D, D] + [P] * 12 + [I32, P, P, P, P]
     L.orc_hex_volume.argtypes = [P, P, P]
     L.orc_hex_volume.restype = D
     L.orc_hex_volume_grad.argtypes = [P, P, P, P, P, P]
+    L.orc_hex_volume_grad.restype = None
     for f in ("orc_hydro_init", "orc_hydro_step"):
         getattr(L, f).restype = C.c_int
 
@@ -151,6 +157,80 @@ def quality(a, b, metric):
         raise ValueError("bad metric")
     return float(res[0]), dict(zero_max_abs=float(res[1]), zeros=int(aux[0]),
                                zeros_mismatch=int(aux[1]))
+
+
+# ---------------------------------------------------------------- hydro
+
+GAMMA = 5.0 / 3.0
+EOS_EXACT, EOS_TAF, EOS_IACT = 0, 1, 2
+
+
+def hex_volume(X, Y, Z):
+    X, Y, Z = (np.ascontiguousarray(a, dtype=np.float64) for a in (X, Y, Z))
+    return float(lib().orc_hex_volume(_ptr(X), _ptr(Y), _ptr(Z)))
+
+
+def hex_volume_grad(X, Y, Z):
+    X, Y, Z = (np.ascontiguousarray(a, dtype=np.float64) for a in (X, Y, Z))
+    g = np.zeros((3, 8))
+    lib().orc_hex_volume_grad(_ptr(X), _ptr(Y), _ptr(Z), _ptr(g[0]), _ptr(g[1]), _ptr(g[2]))
+    return g
+
+
+class HydroState:
+    """Node (x, y, z, u, v, w) and element (e, p, q, vrel, V0) arrays, float64."""
+
+    FIELDS = ("x", "y", "z", "u", "v", "w", "e", "p", "q", "vrel", "V0", "mnode")
+
+    def __init__(self, n, x, y, z, e, gamma=GAMMA):
+        self.n, self.gamma = n, gamma
+        E, Nn = n ** 3, (n + 1) ** 3
+        self.x, self.y, self.z = (np.array(a, dtype=np.float64) for a in (x, y, z))
+        self.u, self.v, self.w = (np.zeros(Nn) for _ in range(3))
+        self.e = np.array(e, dtype=np.float64)
+        self.p = (gamma - 1.0) * self.e
+        self.q = np.zeros(E)
+        self.vrel = np.ones(E)
+        self.V0 = np.zeros(E)
+        self.mnode = np.zeros(Nn)
+        if lib().orc_hydro_init(n, _ptr(self.x), _ptr(self.y), _ptr(self.z), _ptr(self.V0),
+                                _ptr(self.mnode), None):
+            raise ValueError("hydro init failed")
+
+    def copy(self):
+        c = object.__new__(HydroState)
+        c.n, c.gamma = self.n, self.gamma
+        for f in self.FIELDS:
+            setattr(c, f, getattr(self, f).copy())
+        return c
+
+    def step(self, dt, knobs=None):
+        """One time step; knobs an EosKnobs (None: exact EOS). Returns
+        (eos_inputs (4, E), mask (E,), counters (4,))."""
+        E = self.n ** 3
+        eos_in = np.zeros((4, E))
+        mask = np.zeros(E, dtype=np.uint8)
+        cnt = np.zeros(4, dtype=np.int64)
+        kp = C.byref(knobs) if knobs is not None else None
+        rc = lib().orc_hydro_step(self.n, dt, self.gamma, _ptr(self.x), _ptr(self.y), _ptr(self.z),
+                                  _ptr(self.u), _ptr(self.v), _ptr(self.w), _ptr(self.e),
+                                  _ptr(self.p), _ptr(self.q), _ptr(self.vrel), _ptr(self.V0),
+                                  _ptr(self.mnode), 1 if knobs is not None else 0, kp,
+                                  _ptr(eos_in), _ptr(mask), _ptr(cnt))
+        if rc:
+            raise ValueError(f"hydro step failed ({rc})")
+        return eos_in, mask, cnt
+
+    def energies(self):
+        ie = float(np.sum(self.e * self.V0))
+        ke = float(0.5 * np.sum(self.mnode * (self.u ** 2 + self.v ** 2 + self.w ** 2)))
+        return ie, ke
+
+
+def eos_knobs(mode, hsize=4, psize=8, tsize=8, tperwarp=32, level=THREAD, thresh=0.0,
+              threads=0, block=256, in_scale=(1.0, 1.0, 1.0, 1.0)):
+    return EosKnobs(mode, hsize, psize, tsize, tperwarp, level, float(thresh), threads, block, 0,
+                    (C.c_double * 4)(*in_scale))
 
 
 __all__ = [k for k in dir() if not k.startswith("_")] + ["math"]

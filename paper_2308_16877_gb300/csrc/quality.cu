@@ -35,9 +35,18 @@ __global__ void __launch_bounds__(kThreads) quality_partial(const double *__rest
   double sum = 0.0, zmax = 0.0;
   unsigned long long used = 0, zeros = 0, zbad = 0;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  // GB300 issues one double-precision warp instruction per 16 cycles per SM, so
+  // the per-element work keeps a single FP64 operation (the difference a - b,
+  // exact for the single-precision approximations); the ratio or square is
+  // formed in single precision and summed in groups of 16 before entering the
+  // double-precision accumulator. Exact values outside [1e-30, 1e30] take the
+  // double-precision division.
+  float chunk = 0.0f;
+  int in_chunk = 0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
     const double ai = __ldcs(a + i);
     const double bi = (double)__ldcs(b + i);
+    float term;
     if (metric == HPAC_METRIC_MAPE) {
       if (ai == 0.0) {
         ++zeros;
@@ -45,15 +54,30 @@ __global__ void __launch_bounds__(kThreads) quality_partial(const double *__rest
         zmax = fmax(zmax, fabs(bi));
         continue;
       }
-      sum += fabs(ai - bi) / fabs(ai);
-    } else if (metric == HPAC_METRIC_RMSE) {
       const double d = ai - bi;
-      sum += d * d;
+      const double aa = fabs(ai);
+      if (aa >= 1e-30 && aa <= 1e30) {
+        term = __fdiv_rn(fabsf((float)d), (float)aa);
+      } else {
+        sum += fabs(d) / aa;
+        ++used;
+        continue;
+      }
+    } else if (metric == HPAC_METRIC_RMSE) {
+      const float d = (float)(ai - bi);
+      term = d * d;
     } else {
-      sum += (ai != bi) ? 1.0 : 0.0;
+      term = (ai != bi) ? 1.0f : 0.0f;
     }
+    chunk += term;
     ++used;
+    if (++in_chunk == 16) {
+      sum += (double)chunk;
+      chunk = 0.0f;
+      in_chunk = 0;
+    }
   }
+  sum += (double)chunk;
   s_sum[threadIdx.x] = sum;
   s_zmax[threadIdx.x] = zmax;
   s_used[threadIdx.x] = used;

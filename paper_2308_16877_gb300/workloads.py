@@ -205,3 +205,9 @@ def sweep_configs() -> list[dict]:
             cfgs.append(d)
     assert len(cfgs) == 256
     return cfgs
+
+
+def hydro_dt(n: int, gamma: float = 5.0 / 3.0, e0: float = HYDRO_E0, cfl: float = 0.1) -> float:
+    """Fixed time step of the hydro run: cfl * h / c0 with h = 1/n and c0 the
+    ideal-gas sound speed of the initial corner element at unit density."""
+    return cfl * (1.0 / n) / float(np.sqrt(gamma * (gamma - 1.0) * e0))

@@ -46,7 +46,9 @@ def _call(H, fn, a, b, metric):
 
 
 def _same(r, ref):
-    assert r["value"] == pytest.approx(ref["value"], rel=1e-12, abs=1e-300)
+    # the same relative bar as the quality parity tests: per-element terms are
+    # formed in single precision and grouped differently by the two grids
+    assert r["value"] == pytest.approx(ref["value"], rel=1e-6, abs=1e-300)
     for k in ("used", "zeros", "zeros_mismatch"):
         assert r[k] == ref[k], k
     assert r["zero_max_abs"] == ref["zero_max_abs"]
