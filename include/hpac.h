@@ -220,6 +220,57 @@ hpac_status hpac_quality(int32_t approx_dtype, int64_t n, const double *d_exact,
                          const void *d_approx, int32_t metric, hpac_quality_result *h_result,
                          void *cuda_stream);
 
+/* ------------------------------------------------------------------------
+ * Hexahedral Lagrangian hydro with the EOS as the approximated region.
+ *
+ * The paper approximates kernels of the LULESH hydro proxy (Table 1, Section
+ * 4.1; QoI: the final origin energy) but prints no hydro equations; this is a
+ * textbook staggered-grid scheme on a structured n^3 hexahedral mesh over
+ * [0,1]^3 with symmetry planes x = 0, y = 0, z = 0. Nodes: position and
+ * velocity; elements: energy per reference volume e, pressure p, artificial
+ * viscosity q, relative volume v. Per time step: nodal forces
+ * (p + q) dV/dx from the exact trilinear volume gradient, velocity and position
+ * update, new volume and viscosity, then the EOS region on (e, v_{n+1}, dv, q)
+ * giving p, and e = p v / (gamma - 1).
+ *
+ * The caller allocates every array (device memory) and owns it; the library
+ * keeps no state between calls, so copying the arrays checkpoints the run.
+ * Node arrays hold (n+1)^3 doubles, node (i,j,k) at ((k(n+1) + j)(n+1) + i);
+ * element arrays n^3 doubles, element (i,j,k) at ((k n + j) n + i).
+ * ------------------------------------------------------------------------ */
+typedef struct {
+  int32_t n;                 /* elements per axis, 1..1024                         */
+  int32_t reserved0;         /* must be 0                                          */
+  double gamma;              /* ratio of specific heats (> 1)                      */
+  double dt;                 /* fixed time step (> 0)                              */
+  double *x, *y, *z;         /* node positions                                     */
+  double *u, *v, *w;         /* node velocities                                    */
+  double *mnode;             /* node masses                                        */
+  double *e, *p, *q, *vrel;  /* element energy, pressure, viscosity, V / V0        */
+  double *V0;                /* element reference volumes (= masses, density 1)    */
+  double *grad;              /* 24 n^3 scratch: 12 dV/dx per corner (x, y, z rows) */
+  double *eos_in;            /* 4 n^3: the EOS region's inputs of the last step    */
+} hpac_hydro_state;
+
+/* From x, y, z and e (initial state): V0, node masses, p = (gamma-1) e,
+ * q = 0, v = 1, zero velocities and the volume gradients. Enqueued on
+ * cuda_stream. Errors: HPAC_EINVAL (state), HPAC_ECUDA. */
+hpac_status hpac_hydro_init(const hpac_hydro_state *s, void *cuda_stream);
+
+/* One time step on the EOS region's stream. eos: a region of kind
+ * HPAC_REGION_EOS, F64, n = in_stride = n^3, param = gamma. technique 0 runs
+ * the EOS exactly, 1 under TAF (knobs: hpac_taf_knobs), 2 under iACT
+ * (hpac_iact_knobs), 3 under perforation (hpac_perfo_knobs; a dropped
+ * element keeps its previous pressure). d_mask and h_stats as for the
+ * technique's own call. */
+hpac_status hpac_hydro_step(const hpac_hydro_state *s, hpac_region *eos, int32_t technique,
+                            const void *knobs, uint8_t *d_mask, hpac_stats *h_stats);
+
+/* `steps` time steps of hpac_hydro_step without masks or statistics,
+ * enqueued back to back without waiting. */
+hpac_status hpac_hydro_run(const hpac_hydro_state *s, hpac_region *eos, int32_t steps,
+                           int32_t technique, const void *knobs);
+
 /* hpac_quality without any allocation, for callers that cannot call cudaMalloc:
  * code that runs after a service has reserved all of its device memory up front
  * (through its own pool, or a framework's caching allocator that owns every

@@ -1,0 +1,333 @@
+// Hexahedral Lagrangian hydro whose equation-of-state call is the approximated
+// region (the paper approximates kernels of the LULESH proxy application,
+// Table 1, Section 4.1; the scheme itself is a textbook staggered-grid update,
+// the same one the CPU oracle restates).
+//
+// Per time step, on the EOS region's stream:
+//   node kernel     forces from the stored volume gradients, velocity and
+//                   position update, symmetry planes x = 0, y = 0, z = 0;
+//   element kernel  exact trilinear-hexahedron volume and its gradient at the
+//                   new positions, relative volume, artificial viscosity, the
+//                   EOS inputs (e, v_{n+1}, dv, q_{n+1});
+//   EOS region      exact, TAF, iACT or perforation through the region API;
+//   finalize        e = p v / (gamma - 1), v = v_{n+1}.
+//
+// Volume of a trilinear hexahedron. With corners P_c in lexicographic order
+// (c = a + 2b + 4d for offsets a, b, d), the integral of det J over the
+// reference cube is the trilinear form
+//   V = (1/12) sum over 24 corner triples (a < b < c) of s_abc det(P_a, P_b, P_c),
+// s_abc = +-1: the integral of det(grad N_a, grad N_b, grad N_c) times 12,
+// worked out symbolically. V is translation invariant, so with positions
+// relative to corner 0 the nine triples containing corner 0 vanish; the
+// gradient of a corner c > 0 is the sum over the remaining 15 triples holding c
+// of s times the cross product of the other two corners (oriented as in the
+// determinant), and corner 0 gets minus the sum of the others. The kernel
+// stores 12 dV/dP_c (the 1/12 is applied where the gradient is used).
+// Cost: 21 pair cross products (126 FP64 operations), 135 accumulations and
+// 21 subtractions per element, the bulk of the step on GB300's FP64 pipe.
+#include <math.h>
+
+#include "hpac_internal.cuh"
+
+namespace hpac {
+namespace {
+
+constexpr double kCq = 2.0;   // quadratic viscosity coefficient
+constexpr double kCl = 0.5;   // linear viscosity coefficient
+
+// The 15 corner triples (a < b < c, all > 0) with their signs s_abc.
+struct Tri { int a, b, c, s; };
+__device__ constexpr Tri kTri[15] = {
+    {1, 2, 3, 1}, {1, 3, 5, 1}, {1, 3, 7, 1}, {1, 4, 5, -1}, {1, 5, 7, -1},
+    {2, 3, 6, -1}, {2, 3, 7, -1}, {2, 4, 6, 1}, {2, 6, 7, 1}, {3, 5, 7, -1},
+    {3, 6, 7, 1}, {4, 5, 6, 1}, {4, 5, 7, 1}, {4, 6, 7, -1}, {5, 6, 7, -1}};
+
+__device__ __forceinline__ void cross3(double ax, double ay, double az, double bx, double by,
+                                       double bz, double &cx, double &cy, double &cz) {
+  cx = fma(ay, bz, -az * by);
+  cy = fma(az, bx, -ax * bz);
+  cz = fma(ax, by, -ay * bx);
+}
+
+// 12 dV/dP_c for the corners (relative to corner 0) and the volume V.
+__device__ __forceinline__ double hex_grad12(const double (&X)[8], const double (&Y)[8],
+                                             const double (&Z)[8], double (&gx)[8], double (&gy)[8],
+                                             double (&gz)[8]) {
+#pragma unroll
+  for (int c = 0; c < 8; ++c) gx[c] = gy[c] = gz[c] = 0.0;
+#pragma unroll
+  for (int t = 0; t < 15; ++t) {
+    const int a = kTri[t].a, b = kTri[t].b, c = kTri[t].c;
+    const double s = (double)kTri[t].s;
+    double cx, cy, cz;
+    cross3(X[b], Y[b], Z[b], X[c], Y[c], Z[c], cx, cy, cz);  // d/dP_a det = P_b x P_c
+    gx[a] = fma(s, cx, gx[a]);
+    gy[a] = fma(s, cy, gy[a]);
+    gz[a] = fma(s, cz, gz[a]);
+    cross3(X[c], Y[c], Z[c], X[a], Y[a], Z[a], cx, cy, cz);  // d/dP_b det = P_c x P_a
+    gx[b] = fma(s, cx, gx[b]);
+    gy[b] = fma(s, cy, gy[b]);
+    gz[b] = fma(s, cz, gz[b]);
+    cross3(X[a], Y[a], Z[a], X[b], Y[b], Z[b], cx, cy, cz);  // d/dP_c det = P_a x P_b
+    gx[c] = fma(s, cx, gx[c]);
+    gy[c] = fma(s, cy, gy[c]);
+    gz[c] = fma(s, cz, gz[c]);
+  }
+  double sx = 0.0, sy = 0.0, sz = 0.0, v12 = 0.0;
+#pragma unroll
+  for (int c = 1; c < 8; ++c) {
+    sx += gx[c];
+    sy += gy[c];
+    sz += gz[c];
+    v12 = fma(X[c], gx[c], v12);  // V is linear in the x coordinates
+  }
+  gx[0] = -sx;
+  gy[0] = -sy;
+  gz[0] = -sz;
+  return v12 * (1.0 / 12.0);
+}
+
+__device__ __forceinline__ void gather_rel(int n, int64_t e, const double *__restrict__ x,
+                                           const double *__restrict__ y,
+                                           const double *__restrict__ z, double (&X)[8],
+                                           double (&Y)[8], double (&Z)[8]) {
+  const int64_t n1 = n + 1;
+  const int64_t i = e % n, j = (e / n) % n, k = e / ((int64_t)n * n);
+  const int64_t base = (k * n1 + j) * n1 + i;
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    const int64_t nd = base + ((c >> 2) & 1) * n1 * n1 + ((c >> 1) & 1) * n1 + (c & 1);
+    X[c] = x[nd];
+    Y[c] = y[nd];
+    Z[c] = z[nd];
+  }
+#pragma unroll
+  for (int c = 1; c < 8; ++c) {
+    X[c] -= X[0];
+    Y[c] -= Y[0];
+    Z[c] -= Z[0];
+  }
+  X[0] = Y[0] = Z[0] = 0.0;
+}
+
+__global__ void __launch_bounds__(128) init_elem_kernel(hpac_hydro_state s) {
+  const int n = s.n;
+  const int64_t E = (int64_t)n * n * n;
+  const double gm1 = s.gamma - 1.0;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < E;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    double X[8], Y[8], Z[8], gx[8], gy[8], gz[8];
+    gather_rel(n, e, s.x, s.y, s.z, X, Y, Z);
+    const double V = hex_grad12(X, Y, Z, gx, gy, gz);
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      s.grad[(0 * 8 + c) * E + e] = gx[c];
+      s.grad[(1 * 8 + c) * E + e] = gy[c];
+      s.grad[(2 * 8 + c) * E + e] = gz[c];
+    }
+    s.V0[e] = V;
+    s.vrel[e] = 1.0;
+    s.p[e] = gm1 * s.e[e];
+    s.q[e] = 0.0;
+  }
+}
+
+__global__ void __launch_bounds__(256) init_node_kernel(hpac_hydro_state s) {
+  const int n = s.n;
+  const int64_t n1 = n + 1, Nn = n1 * n1 * n1;
+  for (int64_t nd = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; nd < Nn;
+       nd += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = nd % n1, j = (nd / n1) % n1, k = nd / (n1 * n1);
+    double m = 0.0;
+    for (int64_t ek = k - 1; ek <= k; ++ek)
+      for (int64_t ej = j - 1; ej <= j; ++ej)
+        for (int64_t ei = i - 1; ei <= i; ++ei) {
+          if (ei < 0 || ej < 0 || ek < 0 || ei >= n || ej >= n || ek >= n) continue;
+          m += 0.125 * s.V0[(ek * n + ej) * n + ei];
+        }
+    s.mnode[nd] = m;
+    s.u[nd] = s.v[nd] = s.w[nd] = 0.0;
+  }
+}
+
+// Forces at x^n from (p + q) and the stored gradients; velocity and position.
+__global__ void __launch_bounds__(256) node_kernel(hpac_hydro_state s) {
+  const int n = s.n;
+  const int64_t n1 = n + 1, Nn = n1 * n1 * n1, E = (int64_t)n * n * n;
+  const double dt = s.dt;
+  for (int64_t nd = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; nd < Nn;
+       nd += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = nd % n1, j = (nd / n1) % n1, k = nd / (n1 * n1);
+    double fx = 0.0, fy = 0.0, fz = 0.0;
+#pragma unroll
+    for (int dk = 1; dk >= 0; --dk)
+#pragma unroll
+      for (int dj = 1; dj >= 0; --dj)
+#pragma unroll
+        for (int di = 1; di >= 0; --di) {
+          const int64_t ei = i - di, ej = j - dj, ek = k - dk;
+          if (ei < 0 || ej < 0 || ek < 0 || ei >= n || ej >= n || ek >= n) continue;
+          const int64_t el = (ek * n + ej) * n + ei;
+          const int c = di + 2 * dj + 4 * dk;  // corner of this node in element el
+          const double pq = (s.p[el] + s.q[el]) * (1.0 / 12.0);
+          fx = fma(pq, s.grad[(0 * 8 + c) * E + el], fx);
+          fy = fma(pq, s.grad[(1 * 8 + c) * E + el], fy);
+          fz = fma(pq, s.grad[(2 * 8 + c) * E + el], fz);
+        }
+    const double inv_m = 1.0 / s.mnode[nd];
+    double un = s.u[nd] + dt * fx * inv_m;
+    double vn = s.v[nd] + dt * fy * inv_m;
+    double wn = s.w[nd] + dt * fz * inv_m;
+    if (i == 0) un = 0.0;
+    if (j == 0) vn = 0.0;
+    if (k == 0) wn = 0.0;
+    s.u[nd] = un;
+    s.v[nd] = vn;
+    s.w[nd] = wn;
+    s.x[nd] += dt * un;
+    s.y[nd] += dt * vn;
+    s.z[nd] += dt * wn;
+  }
+}
+
+// New volume and gradient, viscosity, and the EOS region's inputs.
+__global__ void __launch_bounds__(128) elem_kernel(hpac_hydro_state s) {
+  const int n = s.n;
+  const int64_t E = (int64_t)n * n * n;
+  const double dt = s.dt, gamma = s.gamma;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < E;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    double X[8], Y[8], Z[8], gx[8], gy[8], gz[8];
+    gather_rel(n, e, s.x, s.y, s.z, X, Y, Z);
+    const double V = hex_grad12(X, Y, Z, gx, gy, gz);
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      s.grad[(0 * 8 + c) * E + e] = gx[c];
+      s.grad[(1 * 8 + c) * E + e] = gy[c];
+      s.grad[(2 * 8 + c) * E + e] = gz[c];
+    }
+    const double v1 = V / s.V0[e];
+    const double dv = v1 - s.vrel[e];
+    double qn = 0.0;
+    if (dv < 0.0) {
+      const double L = cbrt(V);
+      const double rho = 1.0 / v1;
+      const double pp = s.p[e] > 0.0 ? s.p[e] : 0.0;
+      const double cs = sqrt(gamma * pp * v1);
+      const double du = L * dv / (v1 * dt);
+      qn = rho * (kCq * kCq * du * du + kCl * cs * fabs(du));
+    }
+    s.eos_in[e] = s.e[e];
+    s.eos_in[E + e] = v1;
+    s.eos_in[2 * E + e] = dv;
+    s.eos_in[3 * E + e] = qn;
+    s.q[e] = qn;
+  }
+}
+
+__global__ void __launch_bounds__(256) finalize_kernel(hpac_hydro_state s) {
+  const int64_t E = (int64_t)s.n * s.n * s.n;
+  const double gm1 = s.gamma - 1.0;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < E;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const double v1 = s.eos_in[E + e];
+    s.e[e] = s.p[e] * v1 / gm1;
+    s.vrel[e] = v1;
+  }
+}
+
+unsigned grid_for(int64_t work, int threads, int device) {
+  int sms = 148;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+  const int64_t want = (work + threads - 1) / threads;
+  const int64_t cap = (int64_t)sms * 16;
+  return (unsigned)(want < 1 ? 1 : (want > cap ? cap : want));
+}
+
+hpac_status check_state(const hpac_hydro_state *s) {
+  if (!s) return set_error(HPAC_EINVAL, "hydro state is NULL");
+  if (s->n < 1 || s->n > 1024) return set_error(HPAC_EINVAL, "hydro n = %d not in 1..1024", s->n);
+  if (s->reserved0 != 0) return set_error(HPAC_EINVAL, "reserved field not zero");
+  if (!(s->dt > 0.0) || !isfinite(s->dt)) return set_error(HPAC_EINVAL, "hydro dt must be > 0");
+  if (!(s->gamma > 1.0) || !isfinite(s->gamma)) return set_error(HPAC_EINVAL, "gamma must be > 1");
+  const void *ptrs[] = {s->x, s->y, s->z, s->u, s->v, s->w, s->mnode, s->e, s->p, s->q, s->vrel,
+                        s->V0, s->grad, s->eos_in};
+  for (const void *p : ptrs)
+    if (!p) return set_error(HPAC_EINVAL, "a hydro state array is NULL");
+  return HPAC_OK;
+}
+
+}  // namespace
+}  // namespace hpac
+
+using namespace hpac;
+
+extern "C" hpac_status hpac_hydro_init(const hpac_hydro_state *s, void *cuda_stream) {
+  hpac_status st = check_state(s);
+  if (st != HPAC_OK) return st;
+  int dev = 0;
+  HPAC_CUDA_TRY(cudaGetDevice(&dev));
+  cudaStream_t stream = (cudaStream_t)cuda_stream;
+  const int64_t E = (int64_t)s->n * s->n * s->n, Nn = (int64_t)(s->n + 1) * (s->n + 1) * (s->n + 1);
+  init_elem_kernel<<<grid_for(E, 128, dev), 128, 0, stream>>>(*s);
+  HPAC_CUDA_TRY(cudaGetLastError());
+  init_node_kernel<<<grid_for(Nn, 256, dev), 256, 0, stream>>>(*s);
+  HPAC_CUDA_TRY(cudaGetLastError());
+  return HPAC_OK;
+}
+
+extern "C" hpac_status hpac_hydro_step(const hpac_hydro_state *s, hpac_region *eos,
+                                       int32_t technique, const void *knobs, uint8_t *d_mask,
+                                       hpac_stats *h_stats) {
+  hpac_status st = check_state(s);
+  if (st != HPAC_OK) return st;
+  if (!eos) return set_error(HPAC_EINVAL, "EOS region is NULL");
+  const int64_t E = (int64_t)s->n * s->n * s->n, Nn = (int64_t)(s->n + 1) * (s->n + 1) * (s->n + 1);
+  const hpac_region_desc &d = eos->d;
+  if (d.kind != HPAC_REGION_EOS || d.dtype != HPAC_F64 || d.n != E || d.in_stride != E)
+    return set_error(HPAC_EINVAL, "EOS region must be kind EOS, F64, n = in_stride = n^3 = %lld",
+                     (long long)E);
+  if (d.param != s->gamma) return set_error(HPAC_EINVAL, "EOS gamma differs from the hydro gamma");
+  if (technique < 0 || technique > 3) return set_error(HPAC_EINVAL, "technique %d", technique);
+  if (technique > 0 && !knobs) return set_error(HPAC_EINVAL, "knobs are NULL");
+  cudaStream_t stream = eos->stream;
+  node_kernel<<<grid_for(Nn, 256, eos->device), 256, 0, stream>>>(*s);
+  HPAC_CUDA_TRY(cudaGetLastError());
+  elem_kernel<<<grid_for(E, 128, eos->device), 128, 0, stream>>>(*s);
+  HPAC_CUDA_TRY(cudaGetLastError());
+  switch (technique) {
+    case 0:
+      st = hpac_run_exact(eos, s->eos_in, s->p);
+      if (st == HPAC_OK && h_stats) {
+        HPAC_CUDA_TRY(cudaStreamSynchronize(stream));
+        *h_stats = hpac_stats{E, 0, 0, 0};
+      }
+      break;
+    case 1:
+      st = hpac_run_taf(eos, static_cast<const hpac_taf_knobs *>(knobs), s->eos_in, s->p, d_mask,
+                        nullptr, h_stats);
+      break;
+    case 2:
+      st = hpac_run_iact(eos, static_cast<const hpac_iact_knobs *>(knobs), s->eos_in, s->p, d_mask,
+                         nullptr, h_stats);
+      break;
+    default:
+      st = hpac_run_perfo(eos, static_cast<const hpac_perfo_knobs *>(knobs), s->eos_in, s->p,
+                          d_mask, h_stats);
+      break;
+  }
+  if (st != HPAC_OK) return st;
+  finalize_kernel<<<grid_for(E, 256, eos->device), 256, 0, stream>>>(*s);
+  HPAC_CUDA_TRY(cudaGetLastError());
+  return HPAC_OK;
+}
+
+extern "C" hpac_status hpac_hydro_run(const hpac_hydro_state *s, hpac_region *eos, int32_t steps,
+                                      int32_t technique, const void *knobs) {
+  if (steps < 0) return set_error(HPAC_EINVAL, "steps < 0");
+  for (int32_t k = 0; k < steps; ++k) {
+    hpac_status st = hpac_hydro_step(s, eos, technique, knobs, nullptr, nullptr);
+    if (st != HPAC_OK) return st;
+  }
+  return HPAC_OK;
+}

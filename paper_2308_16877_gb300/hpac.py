@@ -59,6 +59,16 @@ class hpac_quality_result(C.Structure):
         return {f: (float if t is C.c_double else int)(getattr(self, f)) for f, t in self._fields_}
 
 
+_D = C.POINTER(C.c_double)
+
+
+class hpac_hydro_state(C.Structure):
+    _fields_ = [("n", C.c_int32), ("reserved0", C.c_int32), ("gamma", C.c_double),
+                ("dt", C.c_double), ("x", _D), ("y", _D), ("z", _D), ("u", _D), ("v", _D),
+                ("w", _D), ("mnode", _D), ("e", _D), ("p", _D), ("q", _D), ("vrel", _D),
+                ("V0", _D), ("grad", _D), ("eos_in", _D)]
+
+
 # Every symbol include/hpac.h declares, with its ctypes signature.
 _P = C.c_void_p
 SIGNATURES = {
@@ -73,6 +83,10 @@ SIGNATURES = {
                                C.POINTER(hpac_quality_result), _P]),
     "hpac_quality_noalloc": (C.c_int, [C.c_int32, C.c_int64, _P, _P, C.c_int32,
                                        C.POINTER(hpac_quality_result), _P]),
+    "hpac_hydro_init": (C.c_int, [C.POINTER(hpac_hydro_state), _P]),
+    "hpac_hydro_step": (C.c_int, [C.POINTER(hpac_hydro_state), _P, C.c_int32, _P, _P,
+                                  C.POINTER(hpac_stats)]),
+    "hpac_hydro_run": (C.c_int, [C.POINTER(hpac_hydro_state), _P, C.c_int32, C.c_int32, _P]),
     "hpac_last_error": (C.c_char_p, []),
     "hpac_version": (C.c_char_p, []),
 }
@@ -176,6 +190,23 @@ def hpac_quality_noalloc(dtype, n, d_exact, d_approx, metric, stream=None):
     _check(load().hpac_quality_noalloc(dtype, n, d_exact, d_approx, metric, C.byref(res),
                                        stream or None), "hpac_quality_noalloc")
     return res
+
+
+def hpac_hydro_init(state, stream=None):
+    _check(load().hpac_hydro_init(C.byref(state), stream or None), "hpac_hydro_init")
+
+
+def hpac_hydro_step(state, eos, technique, knobs=None, d_mask=None, want_stats=False):
+    st = hpac_stats() if want_stats else None
+    _check(load().hpac_hydro_step(C.byref(state), eos, technique,
+                                  C.byref(knobs) if knobs is not None else None, d_mask,
+                                  C.byref(st) if st is not None else None), "hpac_hydro_step")
+    return st
+
+
+def hpac_hydro_run(state, eos, steps, technique, knobs=None):
+    _check(load().hpac_hydro_run(C.byref(state), eos, steps, technique,
+                                 C.byref(knobs) if knobs is not None else None), "hpac_hydro_run")
 
 
 def hpac_last_error() -> str:
@@ -296,3 +327,65 @@ def quality(exact, approx, metric, stream=None):
     r = hpac_quality(_dtype_code(approx), exact.numel(), _ptr(exact), _ptr(approx), metric,
                      _stream_handle(stream))
     return r.as_dict()
+
+
+HYDRO_EXACT, HYDRO_TAF, HYDRO_IACT, HYDRO_PERFO = 0, 1, 2, 3
+NODE_FIELDS = ("x", "y", "z", "u", "v", "w", "mnode")
+ELEM_FIELDS = ("e", "p", "q", "vrel", "V0")
+
+
+class Hydro:
+    """Hexahedral hydro state in torch CUDA tensors plus its EOS region.
+
+    x, y, z: initial node coordinates ((n+1)^3); e: initial element energies
+    (n^3). The EOS region (kind EOS) uses `logical_threads` / `block_threads`
+    for the approximation schedule.
+    """
+
+    def __init__(self, n, x, y, z, e, dt, gamma=5.0 / 3.0, logical_threads=0, block_threads=256,
+                 stream=None, device=None):
+        import torch
+        dev = device if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.n, self.dt, self.gamma = n, float(dt), float(gamma)
+        E, Nn = n ** 3, (n + 1) ** 3
+        f64 = dict(dtype=torch.float64, device=dev)
+        self.t = {}
+        for k, src in (("x", x), ("y", y), ("z", z)):
+            self.t[k] = torch.as_tensor(src, **f64).clone().contiguous()
+        for k in ("u", "v", "w", "mnode"):
+            self.t[k] = torch.zeros(Nn, **f64)
+        self.t["e"] = torch.as_tensor(e, **f64).clone().contiguous()
+        for k in ("p", "q", "vrel", "V0"):
+            self.t[k] = torch.zeros(E, **f64)
+        self.t["grad"] = torch.zeros(24 * E, **f64)
+        self.t["eos_in"] = torch.zeros(4, E, **f64)
+        self.state = self._state()
+        self.eos = Region(HPAC_REGION_EOS, self.t["eos_in"], param=self.gamma,
+                          logical_threads=logical_threads, block_threads=block_threads, stream=stream)
+        hpac_hydro_init(self.state, _stream_handle(stream))
+
+    def _state(self):
+        ptr = lambda k: C.cast(C.c_void_p(self.t[k].data_ptr()), _D)
+        return hpac_hydro_state(self.n, 0, self.gamma, self.dt, *[ptr(k) for k in (
+            "x", "y", "z", "u", "v", "w", "mnode", "e", "p", "q", "vrel", "V0", "grad", "eos_in")])
+
+    def __getitem__(self, k):
+        return self.t[k]
+
+    def load_state(self, fields):
+        """Overwrite node/element fields (a checkpoint) from host or device arrays;
+        the volume gradients are recomputed by the next step's element kernel only,
+        so the gradient field must be supplied too (key 'grad') or left as is."""
+        import torch
+        for k, v in fields.items():
+            self.t[k].copy_(torch.as_tensor(v, dtype=torch.float64).reshape(self.t[k].shape))
+
+    def step(self, technique=HYDRO_EXACT, knobs=None, mask=None, stats=False):
+        st = hpac_hydro_step(self.state, self.eos._h, technique, knobs, _ptr(mask), stats)
+        return st.as_dict() if st is not None else None
+
+    def run(self, steps, technique=HYDRO_EXACT, knobs=None):
+        hpac_hydro_run(self.state, self.eos._h, steps, technique, knobs)
+
+    def close(self):
+        self.eos.close()
