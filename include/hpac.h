@@ -257,6 +257,16 @@ typedef struct {
  * cuda_stream. Errors: HPAC_EINVAL (state), HPAC_ECUDA. */
 hpac_status hpac_hydro_init(const hpac_hydro_state *s, void *cuda_stream);
 
+/* The three non-region phases of a time step, each one kernel on cuda_stream,
+ * for callers that run the EOS region themselves between them:
+ * nodes (forces from p + q and the stored gradients, velocity, position,
+ * symmetry planes), elements (volume and gradient at the new positions,
+ * viscosity, the EOS inputs in eos_in), finalize (e = p v_{n+1} / (gamma - 1),
+ * v = v_{n+1}). hpac_hydro_step is nodes, elements, the region, finalize. */
+hpac_status hpac_hydro_nodes(const hpac_hydro_state *s, void *cuda_stream);
+hpac_status hpac_hydro_elements(const hpac_hydro_state *s, void *cuda_stream);
+hpac_status hpac_hydro_finalize(const hpac_hydro_state *s, void *cuda_stream);
+
 /* One time step on the EOS region's stream. eos: a region of kind
  * HPAC_REGION_EOS, F64, n = in_stride = n^3, param = gamma. technique 0 runs
  * the EOS exactly, 1 under TAF (knobs: hpac_taf_knobs), 2 under iACT
@@ -270,6 +280,12 @@ hpac_status hpac_hydro_step(const hpac_hydro_state *s, hpac_region *eos, int32_t
  * enqueued back to back without waiting. */
 hpac_status hpac_hydro_run(const hpac_hydro_state *s, hpac_region *eos, int32_t steps,
                            int32_t technique, const void *knobs);
+
+/* Measured double-precision FMA rate of the current device in TFLOP/s
+ * (2 flops per FMA), from a kernel of independent FMA chains on every SM: the
+ * arithmetic ceiling of the FP64-bound hydro kernels. Not from the paper.
+ * Waits for its own work; allocates 8 bytes of device memory for the call. */
+hpac_status hpac_device_fp64_rate(double *h_tflops, void *cuda_stream);
 
 /* hpac_quality without any allocation, for callers that cannot call cudaMalloc:
  * code that runs after a service has reserved all of its device memory up front

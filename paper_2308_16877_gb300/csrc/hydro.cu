@@ -23,8 +23,10 @@
 // of s times the cross product of the other two corners (oriented as in the
 // determinant), and corner 0 gets minus the sum of the others. The kernel
 // stores 12 dV/dP_c (the 1/12 is applied where the gradient is used).
-// Cost: 21 pair cross products (126 FP64 operations), 135 accumulations and
-// 21 subtractions per element, the bulk of the step on GB300's FP64 pipe.
+// Cost per element: 45 cross products (270 FP64 multiply / FMA), 135 signed
+// accumulations (FMA), 21 subtractions for the relative positions, 21 sums for
+// corner 0 and 7 FMA for the volume: about 460 FP64 instructions (734 flops
+// counting an FMA as two), the bulk of the step on GB300's narrow FP64 pipe.
 #include <math.h>
 
 #include "hpac_internal.cuh"
@@ -276,13 +278,46 @@ extern "C" hpac_status hpac_hydro_init(const hpac_hydro_state *s, void *cuda_str
   return HPAC_OK;
 }
 
+extern "C" hpac_status hpac_hydro_nodes(const hpac_hydro_state *s, void *cuda_stream) {
+  hpac_status st = check_state(s);
+  if (st != HPAC_OK) return st;
+  int dev = 0;
+  HPAC_CUDA_TRY(cudaGetDevice(&dev));
+  const int64_t Nn = (int64_t)(s->n + 1) * (s->n + 1) * (s->n + 1);
+  node_kernel<<<grid_for(Nn, 256, dev), 256, 0, (cudaStream_t)cuda_stream>>>(*s);
+  HPAC_CUDA_TRY(cudaGetLastError());
+  return HPAC_OK;
+}
+
+extern "C" hpac_status hpac_hydro_elements(const hpac_hydro_state *s, void *cuda_stream) {
+  hpac_status st = check_state(s);
+  if (st != HPAC_OK) return st;
+  int dev = 0;
+  HPAC_CUDA_TRY(cudaGetDevice(&dev));
+  const int64_t E = (int64_t)s->n * s->n * s->n;
+  elem_kernel<<<grid_for(E, 128, dev), 128, 0, (cudaStream_t)cuda_stream>>>(*s);
+  HPAC_CUDA_TRY(cudaGetLastError());
+  return HPAC_OK;
+}
+
+extern "C" hpac_status hpac_hydro_finalize(const hpac_hydro_state *s, void *cuda_stream) {
+  hpac_status st = check_state(s);
+  if (st != HPAC_OK) return st;
+  int dev = 0;
+  HPAC_CUDA_TRY(cudaGetDevice(&dev));
+  const int64_t E = (int64_t)s->n * s->n * s->n;
+  finalize_kernel<<<grid_for(E, 256, dev), 256, 0, (cudaStream_t)cuda_stream>>>(*s);
+  HPAC_CUDA_TRY(cudaGetLastError());
+  return HPAC_OK;
+}
+
 extern "C" hpac_status hpac_hydro_step(const hpac_hydro_state *s, hpac_region *eos,
                                        int32_t technique, const void *knobs, uint8_t *d_mask,
                                        hpac_stats *h_stats) {
   hpac_status st = check_state(s);
   if (st != HPAC_OK) return st;
   if (!eos) return set_error(HPAC_EINVAL, "EOS region is NULL");
-  const int64_t E = (int64_t)s->n * s->n * s->n, Nn = (int64_t)(s->n + 1) * (s->n + 1) * (s->n + 1);
+  const int64_t E = (int64_t)s->n * s->n * s->n;
   const hpac_region_desc &d = eos->d;
   if (d.kind != HPAC_REGION_EOS || d.dtype != HPAC_F64 || d.n != E || d.in_stride != E)
     return set_error(HPAC_EINVAL, "EOS region must be kind EOS, F64, n = in_stride = n^3 = %lld",
@@ -291,10 +326,10 @@ extern "C" hpac_status hpac_hydro_step(const hpac_hydro_state *s, hpac_region *e
   if (technique < 0 || technique > 3) return set_error(HPAC_EINVAL, "technique %d", technique);
   if (technique > 0 && !knobs) return set_error(HPAC_EINVAL, "knobs are NULL");
   cudaStream_t stream = eos->stream;
-  node_kernel<<<grid_for(Nn, 256, eos->device), 256, 0, stream>>>(*s);
-  HPAC_CUDA_TRY(cudaGetLastError());
-  elem_kernel<<<grid_for(E, 128, eos->device), 128, 0, stream>>>(*s);
-  HPAC_CUDA_TRY(cudaGetLastError());
+  st = hpac_hydro_nodes(s, stream);
+  if (st != HPAC_OK) return st;
+  st = hpac_hydro_elements(s, stream);
+  if (st != HPAC_OK) return st;
   switch (technique) {
     case 0:
       st = hpac_run_exact(eos, s->eos_in, s->p);
@@ -317,9 +352,7 @@ extern "C" hpac_status hpac_hydro_step(const hpac_hydro_state *s, hpac_region *e
       break;
   }
   if (st != HPAC_OK) return st;
-  finalize_kernel<<<grid_for(E, 256, eos->device), 256, 0, stream>>>(*s);
-  HPAC_CUDA_TRY(cudaGetLastError());
-  return HPAC_OK;
+  return hpac_hydro_finalize(s, stream);
 }
 
 extern "C" hpac_status hpac_hydro_run(const hpac_hydro_state *s, hpac_region *eos, int32_t steps,

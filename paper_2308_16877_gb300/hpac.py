@@ -86,7 +86,11 @@ SIGNATURES = {
     "hpac_hydro_init": (C.c_int, [C.POINTER(hpac_hydro_state), _P]),
     "hpac_hydro_step": (C.c_int, [C.POINTER(hpac_hydro_state), _P, C.c_int32, _P, _P,
                                   C.POINTER(hpac_stats)]),
+    "hpac_hydro_nodes": (C.c_int, [C.POINTER(hpac_hydro_state), _P]),
+    "hpac_hydro_elements": (C.c_int, [C.POINTER(hpac_hydro_state), _P]),
+    "hpac_hydro_finalize": (C.c_int, [C.POINTER(hpac_hydro_state), _P]),
     "hpac_hydro_run": (C.c_int, [C.POINTER(hpac_hydro_state), _P, C.c_int32, C.c_int32, _P]),
+    "hpac_device_fp64_rate": (C.c_int, [C.POINTER(C.c_double), _P]),
     "hpac_last_error": (C.c_char_p, []),
     "hpac_version": (C.c_char_p, []),
 }
@@ -204,9 +208,27 @@ def hpac_hydro_step(state, eos, technique, knobs=None, d_mask=None, want_stats=F
     return st
 
 
+def hpac_hydro_nodes(state, stream=None):
+    _check(load().hpac_hydro_nodes(C.byref(state), stream or None), "hpac_hydro_nodes")
+
+
+def hpac_hydro_elements(state, stream=None):
+    _check(load().hpac_hydro_elements(C.byref(state), stream or None), "hpac_hydro_elements")
+
+
+def hpac_hydro_finalize(state, stream=None):
+    _check(load().hpac_hydro_finalize(C.byref(state), stream or None), "hpac_hydro_finalize")
+
+
 def hpac_hydro_run(state, eos, steps, technique, knobs=None):
     _check(load().hpac_hydro_run(C.byref(state), eos, steps, technique,
                                  C.byref(knobs) if knobs is not None else None), "hpac_hydro_run")
+
+
+def hpac_device_fp64_rate(stream=None) -> float:
+    v = C.c_double()
+    _check(load().hpac_device_fp64_rate(C.byref(v), stream or None), "hpac_device_fp64_rate")
+    return float(v.value)
 
 
 def hpac_last_error() -> str:
