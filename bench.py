@@ -267,6 +267,70 @@ def bench_blackscholes(hpac, torch, dev, stream, reps=20):
                     "resolution; NRMSE = RMSE / RMS(exact price)"}
 
 
+def bench_sweep(hpac, torch, dev, stream, baseline=True):
+    """The batched knob sweep: 256 configurations x 32 Black-Scholes regions of
+    2^12..2^22 options in one graph launch (autotuned schedule), against the
+    same work as 8192 separate region-API runs each followed by its quality."""
+    from paper_2308_16877_gb300 import autotune
+    sizes = W.sweep_region_sizes()
+    configs = W.sweep_configs()
+    x, regions = W.sweep_inputs(sizes)
+    xd = torch.from_numpy(x).to(dev)
+    x64 = xd.double().contiguous()
+    ref = torch.zeros(x.shape[1], dtype=torch.float64, device=dev)
+    with hpac.Region(hpac.HPAC_REGION_BLACKSCHOLES, x64, param=W.BS_RATE, stream=stream) as R:
+        R.run_exact(x64, ref)
+    del x64
+    make = lambda bt, bps, tb: hpac.Sweep(configs, regions, xd, ref, W.BS_RATE, bt, bps, tb, stream=stream)
+    best, tune_ms = autotune.tune_sweep(make, regions, len(configs))
+    sw = make(*best)
+    sw.run()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 5
+    e0.record(stream)
+    for _ in range(reps):
+        sw.run()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    graph_ms = e0.elapsed_time(e1) / reps
+    res = sw.results()
+    sw.close()
+    work = len(configs) * int(sum(sizes))
+    out = {"configs": len(configs), "regions": len(sizes), "options": int(sum(sizes)),
+           "schedule": {"block_threads": best[0], "blocks_per_sm": best[1], "tile_blocks": best[2]},
+           "graph_ms": graph_ms, "config_elements_per_s": work / (graph_ms * 1e-3),
+           "approximated_total": int(res["approximated"].sum()), "skipped_total": int(res["skipped"].sum())}
+    if baseline:
+        # separate launches: one region call per (configuration, region) on a
+        # column view of the concatenated inputs, then its quality
+        regs = []
+        for (n, off, T) in regions:
+            xs = xd[:, off:off + n].contiguous()
+            regs.append((hpac.Region(hpac.HPAC_REGION_BLACKSCHOLES, xs, param=W.BS_RATE,
+                                     logical_threads=T, stream=stream), xs, ref[off:off + n].contiguous(),
+                         torch.zeros(n, dtype=torch.float32, device=dev)))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for cfg in configs:
+            for R, xs, rs, o in regs:
+                if cfg["tech"] == "taf":
+                    R.run_taf(xs, o, cfg["hsize"], cfg["psize"], cfg["thresh"], 0)
+                else:
+                    o.zero_()
+                    R.run_perfo(xs, o, cfg["kind"], cfg["m"], cfg.get("rate", 0.0), cfg.get("seed", 0),
+                                bool(cfg["herded"]))
+                hpac.quality(rs, o, hpac.HPAC_METRIC_MAPE, stream=stream)
+        torch.cuda.synchronize()
+        sep_s = time.perf_counter() - t0
+        for R, *_ in regs:
+            R.close()
+        out.update({"separate_launches": len(configs) * len(regions), "separate_ms": sep_s * 1e3,
+                    "separate_config_elements_per_s": work / sep_s,
+                    "graph_speedup_vs_separate": sep_s * 1e3 / graph_ms})
+    return out
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -277,6 +341,7 @@ def main(argv=None):
     ap.add_argument("--time-steps", type=int, default=HYDRO_STEPS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-blackscholes", action="store_true")
+    ap.add_argument("--no-sweep", action="store_true")
     args = ap.parse_args(argv)
     if args.impl == "reference":
         return run_reference(args)
@@ -468,6 +533,7 @@ def main(argv=None):
            "d2h_bytes_per_step": int(E * 8)}
 
     bs = None if args.no_blackscholes else bench_blackscholes(hpac, torch, dev, stream)
+    sweep = None if args.no_sweep else bench_sweep(hpac, torch, dev, stream)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = hydro_cpu()
@@ -498,6 +564,7 @@ def main(argv=None):
             "eos_region_approximated": region_stats,
             "quality": quality,
             "blackscholes": bs,
+            "sweep": sweep,
         }
         print(json.dumps(line))
     Hy.close()

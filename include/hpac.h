@@ -281,6 +281,70 @@ hpac_status hpac_hydro_step(const hpac_hydro_state *s, hpac_region *eos, int32_t
 hpac_status hpac_hydro_run(const hpac_hydro_state *s, hpac_region *eos, int32_t steps,
                            int32_t technique, const void *knobs);
 
+/* ------------------------------------------------------------------------
+ * Batched knob sweep (the paper's design-space exploration, Section 2.4 and
+ * Section 4 / Table 2, which builds and runs each configuration separately):
+ * every configuration over every Black-Scholes region (single precision) in
+ * one persistent kernel captured in a CUDA graph. Per (configuration, region)
+ * it returns counts and error sums against a double-precision exact price, no
+ * output arrays. TAF runs at thread level; a dropped (perforated) invocation
+ * counts with output 0 (a zero-prefilled output buffer).
+ * ------------------------------------------------------------------------ */
+enum { HPAC_SWEEP_TAF = 1, HPAC_SWEEP_PERFO = 3 };
+
+typedef struct {
+  int32_t technique;      /* HPAC_SWEEP_TAF or HPAC_SWEEP_PERFO                   */
+  int32_t level;          /* TAF: must be HPAC_LEVEL_THREAD                        */
+  int32_t hsize, psize;   /* TAF knobs (as hpac_taf_knobs)                         */
+  double thresh;
+  int32_t perfo_kind;     /* perforation knobs (as hpac_perfo_knobs)               */
+  int32_t m_or_percent;
+  double rate;
+  uint64_t seed;
+  int32_t herded;
+  int32_t reserved0;
+} hpac_sweep_config;
+
+typedef struct {
+  int64_t n;               /* options in the region                                */
+  int64_t offset;          /* its first column in d_in / d_ref                     */
+  int64_t logical_threads; /* T of the region's logical schedule (0 = n)           */
+} hpac_sweep_region;
+
+typedef struct {
+  int64_t invocations;
+  int64_t approximated;    /* TAF predictions                                      */
+  int64_t skipped;         /* perforated invocations                               */
+  int64_t mape_terms;      /* invocations whose exact price is not 0               */
+  double sum_abs_rel;      /* sum |a - y| / |a| over those: MAPE = sum / terms     */
+  double sum_sq;           /* sum (a - y)^2 over all: RMSE = sqrt(sum / invocations) */
+} hpac_sweep_stats;
+
+typedef struct hpac_sweep hpac_sweep;
+
+/* Build a sweep: copies the configurations and regions, precomputes the
+ * reference split, and captures the launch in a CUDA graph. d_in: 4 rows
+ * (S, K, T, sigma) of in_stride floats holding every region's options at its
+ * offset; d_ref: the double-precision exact prices at the same positions;
+ * rate: r. Schedule (not semantics): block_threads (64/128/256), persistent
+ * blocks per SM, logical blocks per work item (tile_blocks). Allocates device
+ * memory; waits for cuda_stream's pending work once. d_in and d_ref must stay
+ * valid and unchanged while the sweep exists (every run reads them). */
+hpac_status hpac_sweep_create(int32_t n_configs, const hpac_sweep_config *h_configs,
+                              int32_t n_regions, const hpac_sweep_region *h_regions,
+                              const float *d_in, int64_t in_stride, const double *d_ref,
+                              double rate, int32_t block_threads, int32_t blocks_per_sm,
+                              int32_t tile_blocks, void *cuda_stream, hpac_sweep **out);
+
+/* Launch the captured graph on the creation stream (asynchronous). */
+hpac_status hpac_sweep_run(hpac_sweep *sweep);
+
+/* Wait for the last run and copy n_configs x n_regions stats, configuration
+ * major (h_stats[c * n_regions + r]). */
+hpac_status hpac_sweep_results(hpac_sweep *sweep, hpac_sweep_stats *h_stats);
+
+hpac_status hpac_sweep_destroy(hpac_sweep *sweep);
+
 /* Measured double-precision FMA rate of the current device in TFLOP/s
  * (2 flops per FMA), from a kernel of independent FMA chains on every SM: the
  * arithmetic ceiling of the FP64-bound hydro kernels. Not from the paper.

@@ -69,6 +69,22 @@ class hpac_hydro_state(C.Structure):
                 ("V0", _D), ("grad", _D), ("eos_in", _D)]
 
 
+class hpac_sweep_config(C.Structure):
+    _fields_ = [("technique", C.c_int32), ("level", C.c_int32), ("hsize", C.c_int32),
+                ("psize", C.c_int32), ("thresh", C.c_double), ("perfo_kind", C.c_int32),
+                ("m_or_percent", C.c_int32), ("rate", C.c_double), ("seed", C.c_uint64),
+                ("herded", C.c_int32), ("reserved0", C.c_int32)]
+
+
+class hpac_sweep_region(C.Structure):
+    _fields_ = [("n", C.c_int64), ("offset", C.c_int64), ("logical_threads", C.c_int64)]
+
+
+class hpac_sweep_stats(C.Structure):
+    _fields_ = [("invocations", C.c_int64), ("approximated", C.c_int64), ("skipped", C.c_int64),
+                ("mape_terms", C.c_int64), ("sum_abs_rel", C.c_double), ("sum_sq", C.c_double)]
+
+
 # Every symbol include/hpac.h declares, with its ctypes signature.
 _P = C.c_void_p
 SIGNATURES = {
@@ -91,6 +107,12 @@ SIGNATURES = {
     "hpac_hydro_finalize": (C.c_int, [C.POINTER(hpac_hydro_state), _P]),
     "hpac_hydro_run": (C.c_int, [C.POINTER(hpac_hydro_state), _P, C.c_int32, C.c_int32, _P]),
     "hpac_device_fp64_rate": (C.c_int, [C.POINTER(C.c_double), _P]),
+    "hpac_sweep_create": (C.c_int, [C.c_int32, C.POINTER(hpac_sweep_config), C.c_int32,
+                                    C.POINTER(hpac_sweep_region), _P, C.c_int64, _P, C.c_double,
+                                    C.c_int32, C.c_int32, C.c_int32, _P, C.POINTER(_P)]),
+    "hpac_sweep_run": (C.c_int, [_P]),
+    "hpac_sweep_results": (C.c_int, [_P, C.POINTER(hpac_sweep_stats)]),
+    "hpac_sweep_destroy": (C.c_int, [_P]),
     "hpac_last_error": (C.c_char_p, []),
     "hpac_version": (C.c_char_p, []),
 }
@@ -411,3 +433,65 @@ class Hydro:
 
     def close(self):
         self.eos.close()
+
+
+HPAC_SWEEP_TAF, HPAC_SWEEP_PERFO = 1, 3
+
+
+def sweep_config(d):
+    """hpac_sweep_config from a dict: {"tech": "taf", hsize, psize, thresh[, level]} or
+    {"tech": "perfo", kind, m[, rate, seed, herded]}."""
+    if d["tech"] == "taf":
+        return hpac_sweep_config(HPAC_SWEEP_TAF, d.get("level", 0), d["hsize"], d["psize"],
+                                 float(d["thresh"]), 0, 0, 0.0, 0, 0, 0)
+    return hpac_sweep_config(HPAC_SWEEP_PERFO, 0, 0, 0, 0.0, d["kind"], d.get("m", 0),
+                             float(d.get("rate", 0.0)), int(d.get("seed", 0)),
+                             1 if d.get("herded", 1) else 0, 0)
+
+
+class Sweep:
+    """A batched knob sweep over Black-Scholes regions (hpac_sweep_*).
+
+    x: (4, stride) float32 CUDA tensor holding every region at its offset;
+    ref: float64 CUDA tensor of exact prices; regions: list of (n, offset,
+    logical_threads); configs: list of dicts (see sweep_config).
+    """
+
+    def __init__(self, configs, regions, x, ref, rate, block_threads=256, blocks_per_sm=4,
+                 tile_blocks=1, stream=None):
+        self.configs = list(configs)
+        self.regions = list(regions)
+        cfg = (hpac_sweep_config * len(self.configs))(*[sweep_config(c) for c in self.configs])
+        reg = (hpac_sweep_region * len(self.regions))(*[hpac_sweep_region(*r) for r in self.regions])
+        self._keep = (x, ref)
+        h = _P()
+        _check(load().hpac_sweep_create(len(cfg), cfg, len(reg), reg, C.c_void_p(x.data_ptr()),
+                                        x.shape[1], C.c_void_p(ref.data_ptr()), float(rate),
+                                        block_threads, blocks_per_sm, tile_blocks,
+                                        _stream_handle(stream), C.byref(h)), "hpac_sweep_create")
+        self._h = h
+
+    def run(self):
+        _check(load().hpac_sweep_run(self._h), "hpac_sweep_run")
+
+    def results(self):
+        """numpy array (n_configs, n_regions) of records with the stats fields."""
+        import numpy as np
+        n = len(self.configs) * len(self.regions)
+        buf = (hpac_sweep_stats * n)()
+        _check(load().hpac_sweep_results(self._h, buf), "hpac_sweep_results")
+        dt = np.dtype([(f, np.int64 if t is C.c_int64 else np.float64)
+                       for f, t in hpac_sweep_stats._fields_])
+        arr = np.frombuffer(bytes(buf), dtype=dt).copy()
+        return arr.reshape(len(self.configs), len(self.regions))
+
+    def close(self):
+        if self._h:
+            load().hpac_sweep_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -193,8 +193,8 @@ def sweep_configs() -> list[dict]:
     for pct in (10, 15, 20, 25, 30, 35, 40, 45, 50):
         perf.append(dict(tech="perfo", kind=2, m=pct, rate=0.0))        # ini
         perf.append(dict(tech="perfo", kind=3, m=pct, rate=0.0))        # fini
-    for j in range(35):
-        rate = 0.1 + 0.4 * j / 34.0
+    for j in range(36):
+        rate = 0.1 + 0.4 * j / 35.0
         perf.append(dict(tech="perfo", kind=4, m=0, rate=float(rate), seed=1000 + j))
     assert len(perf) == 64, len(perf)
     for herded in (1, 0):
@@ -211,3 +211,21 @@ def hydro_dt(n: int, gamma: float = 5.0 / 3.0, e0: float = HYDRO_E0, cfl: float 
     """Fixed time step of the hydro run: cfl * h / c0 with h = 1/n and c0 the
     ideal-gas sound speed of the initial corner element at unit density."""
     return cfl * (1.0 / n) / float(np.sqrt(gamma * (gamma - 1.0) * e0))
+
+
+def sweep_inputs(sizes, seed: int = DEFAULT_SEED, ipt: int = 8):
+    """Black-Scholes inputs of the sweep's regions laid end to end.
+
+    Returns (x, regions): x float32 (4, total) with region r's options (drawn
+    with seed + 100 + r, strike-sorted runs of 32) at its offset, and regions
+    the list of (n, offset, logical_threads = n / ipt).
+    """
+    total = int(sum(sizes))
+    x = np.zeros((4, total), dtype=np.float32)
+    regions = []
+    off = 0
+    for r, n in enumerate(sizes):
+        x[:, off:off + n] = blackscholes_inputs(n, seed=seed + 100 + r)
+        regions.append((int(n), off, max(1, int(n) // ipt)))
+        off += n
+    return x, regions
