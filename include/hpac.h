@@ -345,6 +345,81 @@ hpac_status hpac_sweep_results(hpac_sweep *sweep, hpac_sweep_stats *h_stats);
 
 hpac_status hpac_sweep_destroy(hpac_sweep *sweep);
 
+/* ------------------------------------------------------------------------
+ * Adjoint of the exact region: d out / d in for every invocation, the
+ * derivative targets of the learned surrogate. Not from the paper.
+ * Black-Scholes (inputs S, K, T, sigma): dC/dS = N(d1), dC/dK = -e^{-rT} N(d2),
+ * dC/dT = S phi(d1) sigma / (2 sqrt T) + r K e^{-rT} N(d2), dC/dsigma =
+ * S phi(d1) sqrt T. EOS: the closed-form partials of p_{n+1} with respect to
+ * (e_n, v_{n+1}, dv, q) (zero where the energy clamp is active).
+ * IDENTITY: 1 for the first input, 0 for the others.
+ * d_grad: D x n values of the region dtype, row d at d_grad[d * n + i].
+ * ------------------------------------------------------------------------ */
+hpac_status hpac_region_adjoint(hpac_region *region, const void *d_in, void *d_grad);
+
+/* ------------------------------------------------------------------------
+ * Learned surrogate of a region (not from the paper): an MLP
+ * n_feat -> hidden -> hidden -> 1 with GELU (tanh form), BF16 weights and
+ * activations and FP32 accumulation; layer 1 on FP32 features, layer 2 on the
+ * tensor cores. Black-Scholes features: ln(S/K), sigma sqrt(T), r T, T, sigma;
+ * output C = S (out_shift + out_scale net). EOS features: e, v_{n+1}, dv, q
+ * (as FP32); output p = out_shift + out_scale net. Features are normalized as
+ * (f - feat_shift) * feat_scale. Trained with Adam (beta 0.9 / 0.999,
+ * eps 1e-8, cosine-decayed step) on the mean squared error of net against the
+ * normalized region outputs.
+ * ------------------------------------------------------------------------ */
+typedef struct {
+  int32_t kind;            /* HPAC_REGION_BLACKSCHOLES (n_feat 5) or HPAC_REGION_EOS (4) */
+  int32_t n_feat;
+  int32_t hidden;          /* 64 or 128                                            */
+  int32_t reserved0;
+  float feat_shift[8];
+  float feat_scale[8];
+  float out_shift, out_scale;
+} hpac_mlp_desc;
+
+typedef struct hpac_mlp hpac_mlp;
+
+/* Create a surrogate on the current device, enqueued on cuda_stream.
+ * h_params: hpac_mlp_num_params FP32 values (W1 [hidden][n_feat], b1, W2
+ * [hidden][hidden], b2, W3 [hidden], b3) or NULL for a seeded uniform
+ * +-1/sqrt(fan_in) initialization with zero biases. */
+hpac_status hpac_mlp_create(const hpac_mlp_desc *desc, const float *h_params, uint64_t seed,
+                            void *cuda_stream, hpac_mlp **out);
+hpac_status hpac_mlp_destroy(hpac_mlp *mlp);
+int32_t hpac_mlp_num_params(const hpac_mlp *mlp);
+hpac_status hpac_mlp_get_params(hpac_mlp *mlp, float *h_params);
+hpac_status hpac_mlp_set_params(hpac_mlp *mlp, const float *h_params); /* resets Adam */
+
+/* Inference over n invocations of the region inputs (the region's layout:
+ * float for Black-Scholes, double for EOS; param = r or gamma). d_out: n
+ * floats. fallback_below: where a Black-Scholes prediction is below this price
+ * the exact region is evaluated instead (NaN: never); d_mask (nullable) gets
+ * HPAC_MASK_APPROX for surrogate outputs and HPAC_MASK_EXACT for fallbacks;
+ * h_stats (nullable, synchronous) counts approximated = surrogate outputs. */
+hpac_status hpac_mlp_infer(hpac_mlp *mlp, int64_t n, const void *d_in, int64_t in_stride,
+                           double param, float *d_out, float fallback_below, uint8_t *d_mask,
+                           hpac_stats *h_stats);
+
+/* Gradient of the mean squared error over n invocations with targets d_target
+ * (region outputs, n floats) into d_grad (num_params floats, overwritten; NULL:
+ * the surrogate's internal buffer). h_loss (nullable, synchronous): the loss. */
+hpac_status hpac_mlp_grad(hpac_mlp *mlp, int64_t n, const void *d_in, int64_t in_stride,
+                          double param, const float *d_target, float *d_grad, float *h_loss);
+
+/* Adam training: `epochs` passes over the n invocations in consecutive
+ * batches of `batch`, each one gradient launch and one update launch; lr is
+ * the peak step size. h_loss (nullable, synchronous): final loss over all n. */
+hpac_status hpac_mlp_train(hpac_mlp *mlp, int64_t n, const void *d_in, int64_t in_stride,
+                           double param, const float *d_target, int32_t batch, int32_t epochs,
+                           float lr, float *h_loss);
+
+/* Derivatives of the surrogate's region output with respect to the region
+ * inputs (the surrogate's counterpart of hpac_region_adjoint): d_grad receives
+ * 4 x n floats, row d at d_grad[d * n + i]. */
+hpac_status hpac_mlp_input_grad(hpac_mlp *mlp, int64_t n, const void *d_in, int64_t in_stride,
+                                double param, float *d_grad);
+
 /* Measured double-precision FMA rate of the current device in TFLOP/s
  * (2 flops per FMA), from a kernel of independent FMA chains on every SM: the
  * arithmetic ceiling of the FP64-bound hydro kernels. Not from the paper.

@@ -1,0 +1,785 @@
+// Learned surrogate of a region: a D -> H -> H -> 1 MLP with GELU (tanh form,
+// Hendrycks & Gimpel 2016), BF16 weights and activations, FP32 accumulation,
+// trained with Adam (Kingma & Ba 2014) by the library's own forward and
+// backward kernels, with the exact region as fallback. Not from the paper: it
+// stands beside TAF and iACT as a third way to skip the region's arithmetic.
+//
+// Layer 1 (D <= 8 FP32 features) runs on the CUDA cores in FP32 with BF16
+// weights; layer 2 (H x H, the bulk of the work) on the tensor cores with
+// warp-level mma.sync m16n8k16 BF16 -> FP32; layer 3 (H -> 1) is a dot product.
+// A warp owns 16 samples at a time: its layer-1 outputs land directly in the
+// accumulator layout of the m16n8 tiles, so GELU + BF16 packing turns them into
+// the A fragments of layer 2 in registers (no shared-memory round trip).
+//
+// Backward (training): dy -> dh2 = dy W3 -> dz2 = dh2 gelu'(z2) -> dh1 = dz2 W2
+// (tensor cores, W2 transposed in shared memory) -> dz1 = dh1 gelu'(z1). The
+// weight gradients dW2 = dz2^T h1 and dW1 = dz1^T f reduce over samples: the
+// block's warps stage dz2, h1, dz1, f in shared memory and each warp then owns
+// 16 output rows of dW2 / dW1, accumulated in registers across the whole
+// persistent loop with transposed ldmatrix loads feeding mma.sync. Bias and
+// layer-3 gradients go through shared-memory atomics; everything reaches the
+// global gradient with one atomic add per value per block.
+#include <cuda_bf16.h>
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include "hpac_internal.cuh"
+#include "regions.cuh"
+
+struct hpac_mlp {
+  hpac_mlp_desc d;
+  int device;
+  cudaStream_t stream;
+  int n_params;
+  float *params;   // FP32 master copy
+  float *grad;
+  float *m, *v;    // Adam moments
+  float *loss;     // device scalar: sum of squared errors of the last gradient pass
+  unsigned long long *counters;
+  int64_t step;
+};
+
+namespace hpac {
+namespace {
+
+constexpr float kGeluA = 0.7978845608028654f;  // sqrt(2/pi)
+constexpr float kGeluB = 0.044715f;
+
+__device__ __forceinline__ float tanh_fast(float x) {
+  float y;
+  asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float gelu(float z) {
+  const float th = tanh_fast(kGeluA * fmaf(kGeluB * z, z * z, z));
+  return 0.5f * z * (1.0f + th);
+}
+__device__ __forceinline__ float gelu_grad(float z) {
+  const float th = tanh_fast(kGeluA * fmaf(kGeluB * z, z * z, z));
+  return 0.5f * (1.0f + th) + 0.5f * z * (1.0f - th * th) * kGeluA * fmaf(3.0f * kGeluB, z * z, 1.0f);
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+  const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<const uint32_t *>(&v);
+}
+__device__ __forceinline__ float bf16r(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
+
+__device__ __forceinline__ void mma16816(float (&d)[4], const uint32_t (&a)[4], uint32_t b0,
+                                         uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+      "{%8,%9}, {%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ void ldsm_x4_trans(uint32_t &r0, uint32_t &r1, uint32_t &r2, uint32_t &r3,
+                                              const void *p) {
+  const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+               : "r"(a));
+}
+
+enum { MODE_INFER = 0, MODE_GRAD = 1, MODE_INPUT_GRAD = 2 };
+
+struct MlpArgs {
+  const void *in;       // region inputs (SoA, in_stride)
+  int64_t stride, n;
+  double param;         // r (Black-Scholes) or gamma (EOS)
+  const float *target;  // MODE_GRAD: region outputs
+  float *out;           // MODE_INFER: region outputs; MODE_INPUT_GRAD: D x n derivatives
+  uint8_t *mask;        // MODE_INFER (nullable)
+  float fallback_below; // MODE_INFER: exact region where the prediction is below (NaN: never)
+  const float *params;
+  float *grad;
+  float *loss;
+  unsigned long long *counters;  // [0] fallbacks
+  float inv_n;          // MODE_GRAD: 1 / total samples of the batch
+};
+
+// Features of one invocation (FP32) and the output multiplier of the region.
+template <int KIND>
+__device__ __forceinline__ void features(const void *in, int64_t stride, int64_t i, double param,
+                                         const hpac_mlp_desc &d, float (&f)[8], float &mult,
+                                         float (&raw)[4]) {
+  if (KIND == HPAC_REGION_BLACKSCHOLES) {
+    const float *x = static_cast<const float *>(in);
+    const float S = x[i], K = x[stride + i], T = x[2 * stride + i], sig = x[3 * stride + i];
+    raw[0] = S, raw[1] = K, raw[2] = T, raw[3] = sig;
+    const float r = (float)param;
+    f[0] = __logf(__fdividef(S, K));
+    f[1] = sig * sqrtf(T);
+    f[2] = r * T;
+    f[3] = T;
+    f[4] = sig;
+    mult = S;
+  } else {
+    const double *x = static_cast<const double *>(in);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      raw[k] = (float)x[k * stride + i];
+      f[k] = raw[k];
+    }
+    mult = 1.0f;
+  }
+#pragma unroll
+  for (int k = 0; k < 8; ++k) f[k] = k < d.n_feat ? (f[k] - d.feat_shift[k]) * d.feat_scale[k] : 0.f;
+}
+
+template <int H>
+struct Smem {
+  static constexpr int LD = H + 8;  // padded row (bf16): conflict-free 32-bit and ldmatrix loads
+  __nv_bfloat16 w2[H * LD];         // W2[out][in]
+  __nv_bfloat16 w2t[H * LD];        // W2[out][in] transposed: [in][out]
+  float w1[H * 8];                  // W1[unit][feature], BF16-rounded values
+  float b1[H], b2[H], w3[H];
+  float b3;
+};
+
+template <int H>
+struct Stage {  // per warp, MODE_GRAD
+  static constexpr int LD = H + 8;
+  __nv_bfloat16 dz2[16 * LD];
+  __nv_bfloat16 h1[16 * LD];
+  __nv_bfloat16 dz1[16 * LD];
+  __nv_bfloat16 f[16 * 24];         // features padded to 16 (+8)
+};
+
+template <int H>
+__device__ void load_params(Smem<H> &s, const float *p, int D) {
+  constexpr int LD = Smem<H>::LD;
+  const int oW1 = 0, ob1 = H * D, oW2 = ob1 + H, ob2 = oW2 + H * H, oW3 = ob2 + H, ob3 = oW3 + H;
+  for (int j = threadIdx.x; j < H * H; j += blockDim.x) {
+    const int o = j / H, k = j % H;
+    const __nv_bfloat16 w = __float2bfloat16_rn(p[oW2 + j]);
+    s.w2[o * LD + k] = w;
+    s.w2t[k * LD + o] = w;
+  }
+  for (int j = threadIdx.x; j < H * 8; j += blockDim.x) {
+    const int u = j / 8, k = j % 8;
+    s.w1[j] = k < D ? bf16r(p[oW1 + u * D + k]) : 0.f;
+  }
+  for (int j = threadIdx.x; j < H; j += blockDim.x) {
+    s.b1[j] = p[ob1 + j];
+    s.b2[j] = p[ob2 + j];
+    s.w3[j] = bf16r(p[oW3 + j]);
+  }
+  if (threadIdx.x == 0) s.b3 = p[ob3];
+}
+
+// Layer-1 pre-activations of n-tile j in the m16n8 accumulator layout of lane
+// (g, t): rows g and g + 8 (features f0, f1), units 8j + 2t and 8j + 2t + 1.
+template <int H>
+__device__ __forceinline__ void layer1_tile(const Smem<H> &s, int j, int t, int D, const float (&f0)[8],
+                                            const float (&f1)[8], float (&z)[4]) {
+  const int u0 = 8 * j + 2 * t, u1 = u0 + 1;
+  float s00 = s.b1[u0], s01 = s.b1[u1], s10 = s.b1[u0], s11 = s.b1[u1];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    if (k < D) {
+      s00 = fmaf(s.w1[u0 * 8 + k], f0[k], s00);
+      s01 = fmaf(s.w1[u1 * 8 + k], f0[k], s01);
+      s10 = fmaf(s.w1[u0 * 8 + k], f1[k], s10);
+      s11 = fmaf(s.w1[u1 * 8 + k], f1[k], s11);
+    }
+  }
+  z[0] = s00, z[1] = s01, z[2] = s10, z[3] = s11;
+}
+
+// One persistent kernel for inference, training gradients and input gradients.
+template <int H, int KIND, int MODE>
+__global__ void __launch_bounds__(H * 2) mlp_kernel(MlpArgs a, hpac_mlp_desc d) {
+  constexpr int NT = H / 8;    // n-tiles of 8 hidden units
+  constexpr int KS = H / 16;   // k-steps of 16 hidden units
+  constexpr int W = H / 16;    // warps per block
+  constexpr int LD = Smem<H>::LD;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Smem<H> &s = *reinterpret_cast<Smem<H> *>(smem_raw);
+  Stage<H> *stage = reinterpret_cast<Stage<H> *>(smem_raw + ((sizeof(Smem<H>) + 15) & ~size_t(15)));
+  __shared__ float g_b1[H], g_b2[H], g_w3[H];
+  __shared__ float g_b3, g_loss;
+  __shared__ unsigned long long g_fallback;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int g = lane >> 2, t = lane & 3;
+  load_params<H>(s, a.params, d.n_feat);
+  if (MODE == MODE_GRAD) {
+    for (int j = threadIdx.x; j < H; j += blockDim.x) g_b1[j] = g_b2[j] = g_w3[j] = 0.f;
+    if (threadIdx.x == 0) g_b3 = g_loss = 0.f;
+  }
+  if (threadIdx.x == 0) g_fallback = 0;
+  __syncthreads();
+
+  // MODE_GRAD register accumulators: this warp's 16 rows of dW2 (all H
+  // columns) and of dW1 (16 feature columns).
+  float acc2[NT][4];
+  float acc1[2][4];
+  if (MODE == MODE_GRAD) {
+#pragma unroll
+    for (int j = 0; j < NT; ++j) acc2[j][0] = acc2[j][1] = acc2[j][2] = acc2[j][3] = 0.f;
+#pragma unroll
+    for (int j = 0; j < 2; ++j) acc1[j][0] = acc1[j][1] = acc1[j][2] = acc1[j][3] = 0.f;
+  }
+
+  const int64_t chunk = 16 * W;
+  const int64_t n_chunks = (a.n + chunk - 1) / chunk;
+  for (int64_t c = blockIdx.x; c < n_chunks; c += gridDim.x) {
+    const int64_t base = c * chunk + warp * 16;
+    const int64_t r0 = base + g, r1 = base + g + 8;
+    const bool v0 = r0 < a.n, v1 = r1 < a.n;
+    // ---- features of rows g and g + 8
+    float f0[8], f1[8], m0 = 0.f, m1 = 0.f, raw0[4], raw1[4];
+    features<KIND>(a.in, a.stride, v0 ? r0 : 0, a.param, d, f0, m0, raw0);
+    features<KIND>(a.in, a.stride, v1 ? r1 : 0, a.param, d, f1, m1, raw1);
+    Stage<H> &st = stage[warp];
+    // ---- layer 1 (FP32, CUDA cores) straight into the accumulator layout of
+    // n-tile j, then GELU and BF16 packing into the A fragments of layer 2
+    uint32_t a2[KS][4];
+#pragma unroll
+    for (int kk = 0; kk < KS; ++kk) {
+      float z[2][4];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) layer1_tile(s, 2 * kk + h, t, d.n_feat, f0, f1, z[h]);
+      a2[kk][0] = pack_bf16(gelu(z[0][0]), gelu(z[0][1]));
+      a2[kk][1] = pack_bf16(gelu(z[0][2]), gelu(z[0][3]));
+      a2[kk][2] = pack_bf16(gelu(z[1][0]), gelu(z[1][1]));
+      a2[kk][3] = pack_bf16(gelu(z[1][2]), gelu(z[1][3]));
+      if (MODE == MODE_GRAD) {  // stage h1 (BF16) for dW2
+        const int col = 16 * kk + 2 * t;
+        *reinterpret_cast<uint32_t *>(&st.h1[g * LD + col]) = a2[kk][0];
+        *reinterpret_cast<uint32_t *>(&st.h1[(g + 8) * LD + col]) = a2[kk][1];
+        *reinterpret_cast<uint32_t *>(&st.h1[g * LD + col + 8]) = a2[kk][2];
+        *reinterpret_cast<uint32_t *>(&st.h1[(g + 8) * LD + col + 8]) = a2[kk][3];
+      }
+    }
+    // ---- layer 2 (tensor cores)
+    float z2[NT][4];
+#pragma unroll
+    for (int j = 0; j < NT; ++j) {
+      const float bb0 = s.b2[8 * j + 2 * t], bb1 = s.b2[8 * j + 2 * t + 1];
+      z2[j][0] = bb0, z2[j][1] = bb1, z2[j][2] = bb0, z2[j][3] = bb1;
+      const __nv_bfloat16 *wrow = s.w2 + (8 * j + g) * LD + 2 * t;
+#pragma unroll
+      for (int kk = 0; kk < KS; ++kk) {
+        const uint32_t b0 = *reinterpret_cast<const uint32_t *>(wrow + 16 * kk);
+        const uint32_t b1 = *reinterpret_cast<const uint32_t *>(wrow + 16 * kk + 8);
+        mma16816(z2[j], a2[kk], b0, b1);
+      }
+    }
+    // ---- GELU, BF16 h2, layer 3 (h2 is recomputed where the backward needs it)
+    float y0 = 0.f, y1 = 0.f;
+#pragma unroll
+    for (int j = 0; j < NT; ++j) {
+      const float w0 = s.w3[8 * j + 2 * t], w1 = s.w3[8 * j + 2 * t + 1];
+      y0 = fmaf(bf16r(gelu(z2[j][0])), w0, fmaf(bf16r(gelu(z2[j][1])), w1, y0));
+      y1 = fmaf(bf16r(gelu(z2[j][2])), w0, fmaf(bf16r(gelu(z2[j][3])), w1, y1));
+    }
+    y0 += __shfl_xor_sync(0xffffffffu, y0, 1);
+    y0 += __shfl_xor_sync(0xffffffffu, y0, 2);
+    y1 += __shfl_xor_sync(0xffffffffu, y1, 1);
+    y1 += __shfl_xor_sync(0xffffffffu, y1, 2);
+    y0 += s.b3;
+    y1 += s.b3;
+
+    if (MODE == MODE_INFER) {
+      if (t == 0) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const bool v = h ? v1 : v0;
+          if (!v) continue;
+          const int64_t i = h ? r1 : r0;
+          const float pred = (h ? m1 : m0) * fmaf(d.out_scale, h ? y1 : y0, d.out_shift);
+          float o = pred;
+          uint8_t mk = HPAC_MASK_APPROX;
+          if (pred < a.fallback_below) {  // calibrated exact fallback (NaN never falls back)
+            float xr[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) xr[k] = h ? raw1[k] : raw0[k];
+            if (KIND == HPAC_REGION_BLACKSCHOLES) o = BlackScholes32{(float)a.param}(xr);
+            mk = HPAC_MASK_EXACT;
+            atomicAdd(&g_fallback, 1ull);
+          }
+          a.out[i] = o;
+          if (a.mask) a.mask[i] = mk;
+        }
+      }
+      continue;
+    }
+
+    // ---- backward: dy per row
+    float dy0, dy1;
+    if (MODE == MODE_GRAD) {
+      const float t0 = v0 ? (a.target[r0] / (KIND == HPAC_REGION_BLACKSCHOLES ? m0 : 1.f) - d.out_shift) /
+                                d.out_scale
+                          : 0.f;
+      const float t1 = v1 ? (a.target[r1] / (KIND == HPAC_REGION_BLACKSCHOLES ? m1 : 1.f) - d.out_shift) /
+                                d.out_scale
+                          : 0.f;
+      const float e0 = v0 ? y0 - t0 : 0.f, e1 = v1 ? y1 - t1 : 0.f;
+      dy0 = 2.f * e0 * a.inv_n;
+      dy1 = 2.f * e1 * a.inv_n;
+      if (t == 0) atomicAdd(&g_loss, e0 * e0 + e1 * e1);
+      if (t == 0) atomicAdd(&g_b3, dy0 + dy1);
+    } else {
+      dy0 = v0 ? 1.f : 0.f;  // d(net)/d(inputs)
+      dy1 = v1 ? 1.f : 0.f;
+    }
+    // dz2 = dy W3 gelu'(z2) (packed as BF16 A fragments for dh1 = dz2 W2 and
+    // staged for dW2); dW3 += dy h2; db2 += dz2
+    uint32_t ad[KS][4];
+#pragma unroll
+    for (int kk = 0; kk < KS; ++kk) {
+      float dz[2][4];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int j = 2 * kk + h;
+        const float w0 = s.w3[8 * j + 2 * t], w1 = s.w3[8 * j + 2 * t + 1];
+        dz[h][0] = dy0 * w0 * gelu_grad(z2[j][0]);
+        dz[h][1] = dy0 * w1 * gelu_grad(z2[j][1]);
+        dz[h][2] = dy1 * w0 * gelu_grad(z2[j][2]);
+        dz[h][3] = dy1 * w1 * gelu_grad(z2[j][3]);
+        if (MODE == MODE_GRAD) {
+          const int col = 8 * j + 2 * t;
+          atomicAdd(&g_w3[col], dy0 * bf16r(gelu(z2[j][0])) + dy1 * bf16r(gelu(z2[j][2])));
+          atomicAdd(&g_w3[col + 1], dy0 * bf16r(gelu(z2[j][1])) + dy1 * bf16r(gelu(z2[j][3])));
+          atomicAdd(&g_b2[col], dz[h][0] + dz[h][2]);
+          atomicAdd(&g_b2[col + 1], dz[h][1] + dz[h][3]);
+        }
+      }
+      ad[kk][0] = pack_bf16(dz[0][0], dz[0][1]);
+      ad[kk][1] = pack_bf16(dz[0][2], dz[0][3]);
+      ad[kk][2] = pack_bf16(dz[1][0], dz[1][1]);
+      ad[kk][3] = pack_bf16(dz[1][2], dz[1][3]);
+      if (MODE == MODE_GRAD) {
+        const int col = 16 * kk + 2 * t;
+        *reinterpret_cast<uint32_t *>(&st.dz2[g * LD + col]) = ad[kk][0];
+        *reinterpret_cast<uint32_t *>(&st.dz2[(g + 8) * LD + col]) = ad[kk][1];
+        *reinterpret_cast<uint32_t *>(&st.dz2[g * LD + col + 8]) = ad[kk][2];
+        *reinterpret_cast<uint32_t *>(&st.dz2[(g + 8) * LD + col + 8]) = ad[kk][3];
+      }
+    }
+    // dh1 = dz2 W2 (tensor cores, B from the transposed copy); dz1 = dh1 gelu'(z1)
+    // with z1 recomputed from the features
+    float df0[8], df1[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) df0[k] = df1[k] = 0.f;
+#pragma unroll
+    for (int j = 0; j < NT; ++j) {
+      float acc[4] = {0.f, 0.f, 0.f, 0.f};
+      const __nv_bfloat16 *wrow = s.w2t + (8 * j + g) * LD + 2 * t;
+#pragma unroll
+      for (int kk = 0; kk < KS; ++kk) {
+        const uint32_t b0 = *reinterpret_cast<const uint32_t *>(wrow + 16 * kk);
+        const uint32_t b1 = *reinterpret_cast<const uint32_t *>(wrow + 16 * kk + 8);
+        mma16816(acc, ad[kk], b0, b1);
+      }
+      float z1[4];
+      layer1_tile(s, j, t, d.n_feat, f0, f1, z1);
+      float dz1[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) dz1[q] = acc[q] * gelu_grad(z1[q]);
+      const int u0 = 8 * j + 2 * t, u1 = u0 + 1;
+      if (MODE == MODE_GRAD) {
+        *reinterpret_cast<uint32_t *>(&st.dz1[g * LD + u0]) = pack_bf16(dz1[0], dz1[1]);
+        *reinterpret_cast<uint32_t *>(&st.dz1[(g + 8) * LD + u0]) = pack_bf16(dz1[2], dz1[3]);
+        atomicAdd(&g_b1[u0], dz1[0] + dz1[2]);
+        atomicAdd(&g_b1[u1], dz1[1] + dz1[3]);
+      } else {
+        // d(net)/d(features) = dz1 W1
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          df0[k] = fmaf(dz1[0], s.w1[u0 * 8 + k], fmaf(dz1[1], s.w1[u1 * 8 + k], df0[k]));
+          df1[k] = fmaf(dz1[2], s.w1[u0 * 8 + k], fmaf(dz1[3], s.w1[u1 * 8 + k], df1[k]));
+        }
+      }
+    }
+
+    if (MODE == MODE_INPUT_GRAD) {
+      // the chain rule from the features to the region inputs
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        df0[k] += __shfl_xor_sync(0xffffffffu, df0[k], 1);
+        df0[k] += __shfl_xor_sync(0xffffffffu, df0[k], 2);
+        df1[k] += __shfl_xor_sync(0xffffffffu, df1[k], 1);
+        df1[k] += __shfl_xor_sync(0xffffffffu, df1[k], 2);
+      }
+      if (t == 0) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          if (!(h ? v1 : v0)) continue;
+          const int64_t i = h ? r1 : r0;
+          float df[8], raw[4];
+#pragma unroll
+          for (int k = 0; k < 8; ++k) df[k] = (h ? df1[k] : df0[k]) * d.feat_scale[k];
+#pragma unroll
+          for (int k = 0; k < 4; ++k) raw[k] = h ? raw1[k] : raw0[k];
+          const float net = h ? y1 : y0;
+          float gin[4];
+          if (KIND == HPAC_REGION_BLACKSCHOLES) {
+            // region output C = S (shift + scale net); features ln(S/K),
+            // sigma sqrt(T), r T, T, sigma
+            const float S = raw[0], K = raw[1], Tm = raw[2], sig = raw[3];
+            const float sc = d.out_scale, sq = sqrtf(Tm), r = (float)a.param;
+            const float dnet_dS = df[0] / S;
+            const float dnet_dK = -df[0] / K;
+            const float dnet_dT = df[1] * sig * 0.5f / sq + df[2] * r + df[3];
+            const float dnet_dsig = df[1] * sq + df[4];
+            gin[0] = fmaf(sc, net, d.out_shift) + S * sc * dnet_dS;
+            gin[1] = S * sc * dnet_dK;
+            gin[2] = S * sc * dnet_dT;
+            gin[3] = S * sc * dnet_dsig;
+          } else {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) gin[k] = d.out_scale * df[k];
+          }
+#pragma unroll
+          for (int k = 0; k < 4; ++k) a.out[k * a.n + i] = gin[k];
+        }
+      }
+      continue;
+    }
+
+    // ---- MODE_GRAD: stage the features; weight-gradient GEMMs
+    if (t == 0) {  // features (zero beyond n_feat, zero rows beyond n)
+#pragma unroll
+      for (int k = 0; k < 16; ++k) {
+        st.f[g * 24 + k] = __float2bfloat16_rn(k < 8 && v0 ? f0[k & 7] : 0.f);
+        st.f[(g + 8) * 24 + k] = __float2bfloat16_rn(k < 8 && v1 ? f1[k & 7] : 0.f);
+      }
+    }
+    __syncthreads();
+    // dW2[16w .. 16w+16][:] += sum over the block's 16 W samples of dz2^T h1;
+    // dW1[16w .. 16w+16][0..16) likewise with the features
+    for (int ks = 0; ks < W; ++ks) {   // 16 samples per k-step: warp ks's tile
+      const Stage<H> &sk = stage[ks];
+      uint32_t aa[4];
+      // A = dz2^T rows 16w.., samples of tile ks: transposed 8x8 blocks
+      {
+        const int mtx = lane >> 3, r = lane & 7;
+        const int srow = (mtx >> 1) * 8 + r, ucol = 16 * warp + (mtx & 1) * 8;
+        ldsm_x4_trans(aa[0], aa[1], aa[2], aa[3], &sk.dz2[srow * LD + ucol]);
+      }
+#pragma unroll
+      for (int j = 0; j < NT; j += 2) {
+        uint32_t b0, b1, b2, b3;
+        const int mtx = lane >> 3, r = lane & 7;
+        const int srow = (mtx & 1) * 8 + r, ucol = 8 * j + (mtx >> 1) * 8;
+        ldsm_x4_trans(b0, b1, b2, b3, &sk.h1[srow * LD + ucol]);
+        mma16816(acc2[j], aa, b0, b1);
+        mma16816(acc2[j + 1], aa, b2, b3);
+      }
+      {
+        const int mtx = lane >> 3, r = lane & 7;
+        const int srow = (mtx >> 1) * 8 + r, ucol = 16 * warp + (mtx & 1) * 8;
+        ldsm_x4_trans(aa[0], aa[1], aa[2], aa[3], &sk.dz1[srow * LD + ucol]);
+        uint32_t b0, b1, b2, b3;
+        const int srow2 = (mtx & 1) * 8 + r, fcol = (mtx >> 1) * 8;
+        ldsm_x4_trans(b0, b1, b2, b3, &sk.f[srow2 * 24 + fcol]);
+        mma16816(acc1[0], aa, b0, b1);
+        mma16816(acc1[1], aa, b2, b3);
+      }
+    }
+    __syncthreads();
+  }
+
+  if (MODE == MODE_GRAD) {
+    const int D = d.n_feat;
+    const int oW1 = 0, ob1 = H * D, oW2 = ob1 + H, ob2 = oW2 + H * H, oW3 = ob2 + H, ob3 = oW3 + H;
+    // accumulator rows 16w + g (+8), columns 8j + 2t (+1)
+#pragma unroll
+    for (int j = 0; j < NT; ++j) {
+      const int row = 16 * warp + g, col = 8 * j + 2 * t;
+      atomicAdd(&a.grad[oW2 + row * H + col], acc2[j][0]);
+      atomicAdd(&a.grad[oW2 + row * H + col + 1], acc2[j][1]);
+      atomicAdd(&a.grad[oW2 + (row + 8) * H + col], acc2[j][2]);
+      atomicAdd(&a.grad[oW2 + (row + 8) * H + col + 1], acc2[j][3]);
+    }
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const int row = 16 * warp + g, col = 8 * j + 2 * t;
+      if (col < D) {
+        atomicAdd(&a.grad[oW1 + row * D + col], acc1[j][0]);
+        atomicAdd(&a.grad[oW1 + (row + 8) * D + col], acc1[j][2]);
+      }
+      if (col + 1 < D) {
+        atomicAdd(&a.grad[oW1 + row * D + col + 1], acc1[j][1]);
+        atomicAdd(&a.grad[oW1 + (row + 8) * D + col + 1], acc1[j][3]);
+      }
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < H; j += blockDim.x) {
+      atomicAdd(&a.grad[ob1 + j], g_b1[j]);
+      atomicAdd(&a.grad[ob2 + j], g_b2[j]);
+      atomicAdd(&a.grad[oW3 + j], g_w3[j]);
+    }
+    if (threadIdx.x == 0) {
+      atomicAdd(&a.grad[ob3], g_b3);
+      atomicAdd(a.loss, g_loss);
+    }
+  }
+  if (MODE == MODE_INFER) {
+    __syncthreads();
+    if (threadIdx.x == 0 && g_fallback && a.counters) atomicAdd(&a.counters[0], g_fallback);
+  }
+}
+
+__global__ void adam_kernel(float *p, const float *g, float *m, float *v, int n, float lr, float b1,
+                            float b2, float eps, float c1, float c2) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float gi = g[i];
+  const float mi = b1 * m[i] + (1.f - b1) * gi;
+  const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+  m[i] = mi;
+  v[i] = vi;
+  p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+}
+
+int n_params_of(const hpac_mlp_desc &d) {
+  const int H = d.hidden, D = d.n_feat;
+  return H * D + H + H * H + H + H + 1;
+}
+
+template <int H, int KIND, int MODE>
+hpac_status launch_t(hpac_mlp *m, const MlpArgs &a) {
+  const size_t smem = ((sizeof(Smem<H>) + 15) & ~size_t(15)) +
+                      (MODE == MODE_GRAD ? sizeof(Stage<H>) * (H / 16) : 0);
+  auto fn = mlp_kernel<H, KIND, MODE>;
+  HPAC_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int per_sm = 1;
+  HPAC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, H * 2, smem));
+  int sms = 148;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, m->device);
+  const int64_t chunks = (a.n + 16 * (H / 16) - 1) / (16 * (H / 16));
+  int64_t blocks = (int64_t)sms * (per_sm < 1 ? 1 : per_sm);
+  if (blocks > chunks) blocks = chunks < 1 ? 1 : chunks;
+  fn<<<(unsigned)blocks, H * 2, smem, m->stream>>>(a, m->d);
+  HPAC_CUDA_TRY(cudaGetLastError());
+  return HPAC_OK;
+}
+
+template <int MODE>
+hpac_status launch(hpac_mlp *m, const MlpArgs &a) {
+  const bool bs = m->d.kind == HPAC_REGION_BLACKSCHOLES;
+  if (m->d.hidden == 64)
+    return bs ? launch_t<64, HPAC_REGION_BLACKSCHOLES, MODE>(m, a) : launch_t<64, HPAC_REGION_EOS, MODE>(m, a);
+  return bs ? launch_t<128, HPAC_REGION_BLACKSCHOLES, MODE>(m, a) : launch_t<128, HPAC_REGION_EOS, MODE>(m, a);
+}
+
+uint64_t sm64(uint64_t &s) {
+  uint64_t z = (s += 0x9E3779B97F4A7C15ull);
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+hpac_status check_io(hpac_mlp *m, int64_t n, const void *in, int64_t stride) {
+  if (!m) return set_error(HPAC_EINVAL, "surrogate is NULL");
+  if (n < 0 || stride < n) return set_error(HPAC_EINVAL, "n < 0 or stride < n");
+  if (n > 0 && !in) return set_error(HPAC_EINVAL, "inputs are NULL");
+  return HPAC_OK;
+}
+
+}  // namespace
+}  // namespace hpac
+
+using namespace hpac;
+
+extern "C" hpac_status hpac_mlp_create(const hpac_mlp_desc *desc, const float *h_params,
+                                       uint64_t seed, void *cuda_stream, hpac_mlp **out) {
+  if (!out || !desc) return set_error(HPAC_EINVAL, "NULL argument");
+  *out = nullptr;
+  const hpac_mlp_desc &d = *desc;
+  if (d.kind != HPAC_REGION_BLACKSCHOLES && d.kind != HPAC_REGION_EOS)
+    return set_error(HPAC_EINVAL, "surrogate region kind %d", d.kind);
+  if ((d.kind == HPAC_REGION_BLACKSCHOLES && d.n_feat != 5) || (d.kind == HPAC_REGION_EOS && d.n_feat != 4))
+    return set_error(HPAC_EINVAL, "n_feat must be 5 (Black-Scholes) or 4 (EOS)");
+  if (d.hidden != 64 && d.hidden != 128) return set_error(HPAC_EINVAL, "hidden must be 64 or 128");
+  if (!(d.out_scale != 0.f) || !isfinite(d.out_scale)) return set_error(HPAC_EINVAL, "out_scale");
+  hpac_mlp *m = (hpac_mlp *)calloc(1, sizeof(hpac_mlp));
+  if (!m) return set_error(HPAC_ENOMEM, "host allocation failed");
+  m->d = d;
+  m->stream = (cudaStream_t)cuda_stream;
+  m->n_params = n_params_of(d);
+  cudaError_t e = cudaGetDevice(&m->device);
+  const size_t pb = sizeof(float) * m->n_params;
+  if (e == cudaSuccess) e = cudaMalloc(&m->params, pb);
+  if (e == cudaSuccess) e = cudaMalloc(&m->grad, pb);
+  if (e == cudaSuccess) e = cudaMalloc(&m->m, pb);
+  if (e == cudaSuccess) e = cudaMalloc(&m->v, pb);
+  if (e == cudaSuccess) e = cudaMalloc(&m->loss, sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&m->counters, 4 * sizeof(unsigned long long));
+  if (e != cudaSuccess) {
+    hpac_mlp_destroy(m);
+    return cuda_error(e, "hpac_mlp_create");
+  }
+  float *h = (float *)malloc(pb);
+  if (!h) {
+    hpac_mlp_destroy(m);
+    return set_error(HPAC_ENOMEM, "host allocation failed");
+  }
+  if (h_params) {
+    memcpy(h, h_params, pb);
+  } else {
+    // uniform(-1/sqrt(fan_in), 1/sqrt(fan_in)) weights, zero biases
+    const int H = d.hidden, D = d.n_feat;
+    uint64_t st = seed;
+    auto uni = [&](float bound) {
+      return (float)((double)(sm64(st) >> 11) * (1.0 / 9007199254740992.0) * 2.0 - 1.0) * bound;
+    };
+    int o = 0;
+    for (int i = 0; i < H * D; ++i) h[o++] = uni(1.f / sqrtf((float)D));
+    for (int i = 0; i < H; ++i) h[o++] = 0.f;
+    for (int i = 0; i < H * H; ++i) h[o++] = uni(1.f / sqrtf((float)H));
+    for (int i = 0; i < H; ++i) h[o++] = 0.f;
+    for (int i = 0; i < H; ++i) h[o++] = uni(1.f / sqrtf((float)H));
+    h[o++] = 0.f;
+  }
+  e = cudaMemcpy(m->params, h, pb, cudaMemcpyHostToDevice);
+  free(h);
+  if (e == cudaSuccess) e = cudaMemset(m->m, 0, pb);
+  if (e == cudaSuccess) e = cudaMemset(m->v, 0, pb);
+  if (e != cudaSuccess) {
+    hpac_mlp_destroy(m);
+    return cuda_error(e, "hpac_mlp_create upload");
+  }
+  *out = m;
+  return HPAC_OK;
+}
+
+extern "C" hpac_status hpac_mlp_destroy(hpac_mlp *m) {
+  if (!m) return HPAC_OK;
+  cudaStreamSynchronize(m->stream);
+  cudaFree(m->params);
+  cudaFree(m->grad);
+  cudaFree(m->m);
+  cudaFree(m->v);
+  cudaFree(m->loss);
+  cudaFree(m->counters);
+  free(m);
+  return HPAC_OK;
+}
+
+extern "C" int32_t hpac_mlp_num_params(const hpac_mlp *m) { return m ? m->n_params : 0; }
+
+extern "C" hpac_status hpac_mlp_get_params(hpac_mlp *m, float *h_params) {
+  if (!m || !h_params) return set_error(HPAC_EINVAL, "NULL argument");
+  HPAC_CUDA_TRY(cudaMemcpyAsync(h_params, m->params, sizeof(float) * m->n_params,
+                                cudaMemcpyDeviceToHost, m->stream));
+  HPAC_CUDA_TRY(cudaStreamSynchronize(m->stream));
+  return HPAC_OK;
+}
+
+extern "C" hpac_status hpac_mlp_set_params(hpac_mlp *m, const float *h_params) {
+  if (!m || !h_params) return set_error(HPAC_EINVAL, "NULL argument");
+  HPAC_CUDA_TRY(cudaMemcpyAsync(m->params, h_params, sizeof(float) * m->n_params,
+                                cudaMemcpyHostToDevice, m->stream));
+  HPAC_CUDA_TRY(cudaStreamSynchronize(m->stream));
+  m->step = 0;
+  HPAC_CUDA_TRY(cudaMemsetAsync(m->m, 0, sizeof(float) * m->n_params, m->stream));
+  HPAC_CUDA_TRY(cudaMemsetAsync(m->v, 0, sizeof(float) * m->n_params, m->stream));
+  return HPAC_OK;
+}
+
+extern "C" hpac_status hpac_mlp_infer(hpac_mlp *m, int64_t n, const void *d_in, int64_t in_stride,
+                                      double param, float *d_out, float fallback_below,
+                                      uint8_t *d_mask, hpac_stats *h_stats) {
+  hpac_status s = check_io(m, n, d_in, in_stride);
+  if (s != HPAC_OK) return s;
+  if (n > 0 && !d_out) return set_error(HPAC_EINVAL, "output is NULL");
+  if (m->d.kind != HPAC_REGION_BLACKSCHOLES && !isnan(fallback_below))
+    return set_error(HPAC_EUNSUPPORTED, "exact fallback is implemented for Black-Scholes only");
+  if (h_stats) HPAC_CUDA_TRY(cudaMemsetAsync(m->counters, 0, sizeof(unsigned long long), m->stream));
+  if (n > 0) {
+    MlpArgs a{};
+    a.in = d_in, a.stride = in_stride, a.n = n, a.param = param, a.out = d_out, a.mask = d_mask;
+    a.fallback_below = fallback_below;
+    a.params = m->params;
+    a.counters = m->counters;
+    s = launch<MODE_INFER>(m, a);
+    if (s != HPAC_OK) return s;
+  }
+  if (h_stats) {
+    unsigned long long fb = 0;
+    HPAC_CUDA_TRY(cudaMemcpyAsync(&fb, m->counters, sizeof(fb), cudaMemcpyDeviceToHost, m->stream));
+    HPAC_CUDA_TRY(cudaStreamSynchronize(m->stream));
+    *h_stats = hpac_stats{n, n - (int64_t)fb, 0, 0};
+  }
+  return HPAC_OK;
+}
+
+extern "C" hpac_status hpac_mlp_grad(hpac_mlp *m, int64_t n, const void *d_in, int64_t in_stride,
+                                     double param, const float *d_target, float *d_grad,
+                                     float *h_loss) {
+  hpac_status s = check_io(m, n, d_in, in_stride);
+  if (s != HPAC_OK) return s;
+  if (n < 1 || !d_target) return set_error(HPAC_EINVAL, "empty batch or NULL targets");
+  float *grad = d_grad ? d_grad : m->grad;
+  HPAC_CUDA_TRY(cudaMemsetAsync(grad, 0, sizeof(float) * m->n_params, m->stream));
+  HPAC_CUDA_TRY(cudaMemsetAsync(m->loss, 0, sizeof(float), m->stream));
+  MlpArgs a{};
+  a.in = d_in, a.stride = in_stride, a.n = n, a.param = param, a.target = d_target;
+  a.params = m->params;
+  a.grad = grad;
+  a.loss = m->loss;
+  a.inv_n = 1.0f / (float)n;
+  s = launch<MODE_GRAD>(m, a);
+  if (s != HPAC_OK) return s;
+  if (h_loss) {
+    float l = 0.f;
+    HPAC_CUDA_TRY(cudaMemcpyAsync(&l, m->loss, sizeof(float), cudaMemcpyDeviceToHost, m->stream));
+    HPAC_CUDA_TRY(cudaStreamSynchronize(m->stream));
+    *h_loss = l / (float)n;
+  }
+  return HPAC_OK;
+}
+
+extern "C" hpac_status hpac_mlp_train(hpac_mlp *m, int64_t n, const void *d_in, int64_t in_stride,
+                                      double param, const float *d_target, int32_t batch,
+                                      int32_t epochs, float lr, float *h_loss) {
+  hpac_status s = check_io(m, n, d_in, in_stride);
+  if (s != HPAC_OK) return s;
+  if (n < 1 || !d_target || batch < 16 || epochs < 0 || !(lr > 0.f))
+    return set_error(HPAC_EINVAL, "bad training arguments");
+  const int64_t nb = (n + batch - 1) / batch;
+  const int64_t total = nb * epochs;
+  int64_t it = 0;
+  for (int ep = 0; ep < epochs; ++ep) {
+    for (int64_t b = 0; b < nb; ++b, ++it) {
+      const int64_t lo = b * batch, cnt = (n - lo) < batch ? (n - lo) : batch;
+      // the batch is a column window of the structure-of-arrays inputs
+      const void *in_b = m->d.kind == HPAC_REGION_BLACKSCHOLES
+                             ? (const void *)((const float *)d_in + lo)
+                             : (const void *)((const double *)d_in + lo);
+      s = hpac_mlp_grad(m, cnt, in_b, in_stride, param, d_target + lo, nullptr, nullptr);
+      if (s != HPAC_OK) return s;
+      // cosine-decayed learning rate
+      const float lr_t = 0.5f * lr * (1.0f + cosf(3.14159265f * (float)it / (float)total));
+      ++m->step;
+      const float c1 = 1.f - powf(0.9f, (float)m->step), c2 = 1.f - powf(0.999f, (float)m->step);
+      adam_kernel<<<(m->n_params + 255) / 256, 256, 0, m->stream>>>(
+          m->params, m->grad, m->m, m->v, m->n_params, lr_t, 0.9f, 0.999f, 1e-8f, c1, c2);
+      HPAC_CUDA_TRY(cudaGetLastError());
+    }
+  }
+  if (h_loss) {
+    // loss of the whole set with the final parameters
+    s = hpac_mlp_grad(m, n, d_in, in_stride, param, d_target, nullptr, h_loss);
+    if (s != HPAC_OK) return s;
+  }
+  return HPAC_OK;
+}
+
+extern "C" hpac_status hpac_mlp_input_grad(hpac_mlp *m, int64_t n, const void *d_in,
+                                           int64_t in_stride, double param, float *d_grad) {
+  hpac_status s = check_io(m, n, d_in, in_stride);
+  if (s != HPAC_OK) return s;
+  if (n > 0 && !d_grad) return set_error(HPAC_EINVAL, "output is NULL");
+  if (n == 0) return HPAC_OK;
+  MlpArgs a{};
+  a.in = d_in, a.stride = in_stride, a.n = n, a.param = param, a.out = d_grad;
+  a.params = m->params;
+  return launch<MODE_INPUT_GRAD>(m, a);
+}

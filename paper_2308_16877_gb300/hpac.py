@@ -85,6 +85,12 @@ class hpac_sweep_stats(C.Structure):
                 ("mape_terms", C.c_int64), ("sum_abs_rel", C.c_double), ("sum_sq", C.c_double)]
 
 
+class hpac_mlp_desc(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("n_feat", C.c_int32), ("hidden", C.c_int32),
+                ("reserved0", C.c_int32), ("feat_shift", C.c_float * 8),
+                ("feat_scale", C.c_float * 8), ("out_shift", C.c_float), ("out_scale", C.c_float)]
+
+
 # Every symbol include/hpac.h declares, with its ctypes signature.
 _P = C.c_void_p
 SIGNATURES = {
@@ -113,6 +119,19 @@ SIGNATURES = {
     "hpac_sweep_run": (C.c_int, [_P]),
     "hpac_sweep_results": (C.c_int, [_P, C.POINTER(hpac_sweep_stats)]),
     "hpac_sweep_destroy": (C.c_int, [_P]),
+    "hpac_region_adjoint": (C.c_int, [_P, _P, _P]),
+    "hpac_mlp_create": (C.c_int, [C.POINTER(hpac_mlp_desc), _P, C.c_uint64, _P, C.POINTER(_P)]),
+    "hpac_mlp_destroy": (C.c_int, [_P]),
+    "hpac_mlp_num_params": (C.c_int32, [_P]),
+    "hpac_mlp_get_params": (C.c_int, [_P, _P]),
+    "hpac_mlp_set_params": (C.c_int, [_P, _P]),
+    "hpac_mlp_infer": (C.c_int, [_P, C.c_int64, _P, C.c_int64, C.c_double, _P, C.c_float, _P,
+                                 C.POINTER(hpac_stats)]),
+    "hpac_mlp_grad": (C.c_int, [_P, C.c_int64, _P, C.c_int64, C.c_double, _P, _P,
+                                C.POINTER(C.c_float)]),
+    "hpac_mlp_train": (C.c_int, [_P, C.c_int64, _P, C.c_int64, C.c_double, _P, C.c_int32, C.c_int32,
+                                 C.c_float, C.POINTER(C.c_float)]),
+    "hpac_mlp_input_grad": (C.c_int, [_P, C.c_int64, _P, C.c_int64, C.c_double, _P]),
     "hpac_last_error": (C.c_char_p, []),
     "hpac_version": (C.c_char_p, []),
 }
@@ -495,3 +514,90 @@ class Sweep:
             self.close()
         except Exception:
             pass
+
+
+def region_adjoint(region, x, grad):
+    """d out / d in of the exact region (hpac_region_adjoint) into grad (D, n)."""
+    _check(load().hpac_region_adjoint(region._h, _ptr(x), _ptr(grad)), "hpac_region_adjoint")
+    return grad
+
+
+class Surrogate:
+    """The learned surrogate of a region (hpac_mlp_*). desc: hpac_mlp_desc."""
+
+    def __init__(self, desc, params=None, seed=0, stream=None):
+        import numpy as np
+        self.desc = desc
+        h = _P()
+        buf = None
+        if params is not None:
+            params = np.ascontiguousarray(params, dtype=np.float32)
+            buf = params.ctypes.data_as(_P)
+        _check(load().hpac_mlp_create(C.byref(desc), buf, int(seed), _stream_handle(stream),
+                                      C.byref(h)), "hpac_mlp_create")
+        self._h = h
+        self.n_params = int(load().hpac_mlp_num_params(h))
+
+    def params(self):
+        import numpy as np
+        out = np.zeros(self.n_params, dtype=np.float32)
+        _check(load().hpac_mlp_get_params(self._h, out.ctypes.data_as(_P)), "hpac_mlp_get_params")
+        return out
+
+    def set_params(self, p):
+        import numpy as np
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        _check(load().hpac_mlp_set_params(self._h, p.ctypes.data_as(_P)), "hpac_mlp_set_params")
+
+    def infer(self, x, out, param, n=None, fallback_below=float("nan"), mask=None, stats=False):
+        n = x.shape[1] if n is None else n
+        st = hpac_stats() if stats else None
+        _check(load().hpac_mlp_infer(self._h, n, _ptr(x), x.shape[1], float(param), _ptr(out),
+                                     float(fallback_below), _ptr(mask),
+                                     C.byref(st) if st is not None else None), "hpac_mlp_infer")
+        return st.as_dict() if st is not None else None
+
+    def grad(self, x, target, param, grad=None, n=None, loss=False):
+        n = x.shape[1] if n is None else n
+        l = C.c_float()
+        _check(load().hpac_mlp_grad(self._h, n, _ptr(x), x.shape[1], float(param), _ptr(target),
+                                    _ptr(grad), C.byref(l) if loss else None), "hpac_mlp_grad")
+        return float(l.value) if loss else None
+
+    def train(self, x, target, param, batch=4096, epochs=1, lr=1e-3, n=None):
+        n = x.shape[1] if n is None else n
+        l = C.c_float()
+        _check(load().hpac_mlp_train(self._h, n, _ptr(x), x.shape[1], float(param), _ptr(target),
+                                     int(batch), int(epochs), float(lr), C.byref(l)), "hpac_mlp_train")
+        return float(l.value)
+
+    def input_grad(self, x, out, param, n=None):
+        n = x.shape[1] if n is None else n
+        _check(load().hpac_mlp_input_grad(self._h, n, _ptr(x), x.shape[1], float(param), _ptr(out)),
+               "hpac_mlp_input_grad")
+        return out
+
+    def close(self):
+        if self._h:
+            load().hpac_mlp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def blackscholes_desc(hidden=64):
+    """Surrogate descriptor for the Black-Scholes region with feature
+    normalisation set for the option ranges of the workloads (features
+    ln(S/K), sigma sqrt T, r T, T, sigma; output C / S)."""
+    d = hpac_mlp_desc()
+    d.kind, d.n_feat, d.hidden = HPAC_REGION_BLACKSCHOLES, 5, hidden
+    shift = [-1.5, 0.8, 0.1, 5.1, 0.35]
+    scale = [1 / 1.2, 1 / 0.6, 1 / 0.06, 1 / 2.8, 1 / 0.17]
+    for k in range(5):
+        d.feat_shift[k], d.feat_scale[k] = shift[k], scale[k]
+    d.out_shift, d.out_scale = 0.0, 0.25
+    return d

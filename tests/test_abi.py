@@ -49,7 +49,7 @@ def test_struct_layouts_match_header(tmp_path):
     probe = tmp_path / "probe.c"
     structs = ["hpac_region_desc", "hpac_perfo_knobs", "hpac_taf_knobs", "hpac_iact_knobs",
                "hpac_stats", "hpac_quality_result", "hpac_hydro_state", "hpac_sweep_config",
-               "hpac_sweep_region", "hpac_sweep_stats"]
+               "hpac_sweep_region", "hpac_sweep_stats", "hpac_mlp_desc"]
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "hpac.h"', "int main(void){"]
     for s in structs:
         lines.append(f'printf("{s} %zu\\n", sizeof({s}));')

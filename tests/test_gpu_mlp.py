@@ -1,0 +1,183 @@
+"""The learned surrogate and the exact region's adjoint through the C ABI,
+against the CPU oracle: forward within a bound propagated from bfloat16
+rounding, parameter and input gradients, the training loop, the calibrated
+exact fallback, and the adjoint against finite differences and a textbook
+value."""
+import os
+
+import numpy as np
+import pytest
+
+from oracle import mlp as M
+from paper_2308_16877_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+@pytest.fixture(scope="module")
+def H():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2308_16877_gb300 import hpac
+    hpac.load()
+    return hpac
+
+
+def dd(d):
+    return M.desc_dict(d)
+
+
+def forward_bound(p, desc, x, r):
+    """Worst-case |net_gpu - net_oracle| from the arithmetic: every rounded
+    activation may land one bfloat16 ulp (2^-7 relative) apart, the hardware
+    tanh adds 2^-11 |z| to a GELU, FP32 accumulation 2^-20 of the absolute sum;
+    propagated through |W2| and |W3| with |gelu'| <= 1.13."""
+    params = M.unpack(p, desc["n_feat"], desc["hidden"])
+    f, _ = M.features(0, x, r)
+    _, (fn, z1, h1, z2, h2) = M.net(params, desc, f)
+    W2 = M.bf16(params[2]).abs()
+    W3 = M.bf16(params[4]).abs()
+    dh1 = 2 ** -7 * h1.abs() + 2 ** -11 * z1.abs() + 1e-6 * (fn.abs() @ M.bf16(params[0]).abs().T)
+    dz2 = dh1 @ W2.T + 2 ** -20 * (h1.abs() @ W2.T)
+    dh2 = 1.13 * dz2 + 2 ** -7 * h2.abs() + 2 ** -11 * z2.abs()
+    return (dh2 @ W3 + 2 ** -20 * (h2.abs() @ W3)).numpy()
+
+
+@pytest.mark.parametrize("hidden", [64, 128])
+def test_forward_matches_oracle(H, hidden):
+    desc = H.blackscholes_desc(hidden)
+    n = 3000
+    x = W.blackscholes_inputs(n, seed=21)
+    S = H.Surrogate(desc, seed=5)
+    xd = torch.from_numpy(x).cuda()
+    out = torch.zeros(n, dtype=torch.float32, device="cuda")
+    S.infer(xd, out, W.BS_RATE)
+    p = S.params()
+    ref, net_ref, _ = M.forward(p, dd(desc), 0, x, W.BS_RATE)
+    g = out.cpu().numpy().astype(np.float64)
+    bound = forward_bound(p, dd(desc), x, W.BS_RATE) * desc.out_scale * x[0].astype(np.float64)
+    assert np.all(np.abs(g - ref) <= bound + 1e-6 * np.abs(ref))
+    rel = np.abs(g - ref) / np.maximum(np.abs(ref), 1e-3)
+    assert np.median(rel) < 2 ** -9
+    S.close()
+
+
+def test_gradient_matches_oracle(H):
+    desc = H.blackscholes_desc(64)
+    n = 4096
+    x = W.blackscholes_inputs(n, seed=22)
+    xd = torch.from_numpy(x).cuda()
+    target = M.forward(np.random.default_rng(1).uniform(-0.3, 0.3, M.n_params(5, 64)), dd(desc), 0, x,
+                       W.BS_RATE)[0].astype(np.float32)
+    td = torch.from_numpy(target).cuda()
+    S = H.Surrogate(desc, seed=6)
+    grad = torch.zeros(S.n_params, dtype=torch.float32, device="cuda")
+    loss = S.grad(xd, td, W.BS_RATE, grad=grad, loss=True)
+    p = S.params()
+    l_ref, g_ref, *_ = M.loss_and_grad(p, dd(desc), 0, x.astype(np.float64), W.BS_RATE, target)
+    g = grad.cpu().numpy().astype(np.float64)
+    cos = float(g @ g_ref / (np.linalg.norm(g) * np.linalg.norm(g_ref)))
+    assert cos > 0.999, cos
+    assert np.linalg.norm(g - g_ref) / np.linalg.norm(g_ref) < 0.03
+    assert loss == pytest.approx(l_ref, rel=0.02)
+    S.close()
+
+
+def test_input_gradient_matches_oracle(H):
+    desc = H.blackscholes_desc(64)
+    n = 2048
+    x = W.blackscholes_inputs(n, seed=23)
+    S = H.Surrogate(desc, seed=7)
+    xd = torch.from_numpy(x).cuda()
+    out = torch.zeros(4, n, dtype=torch.float32, device="cuda")
+    S.input_grad(xd, out, W.BS_RATE)
+    ref = M.input_grad(S.params(), dd(desc), 0, x.astype(np.float64), W.BS_RATE)
+    g = out.cpu().numpy().astype(np.float64)
+    for d in range(4):
+        err = np.linalg.norm(g[d] - ref[d]) / np.linalg.norm(ref[d])
+        assert err < 0.03, (d, err)
+    S.close()
+
+
+def test_training_reduces_loss_and_fallback_is_exact(H):
+    desc = H.blackscholes_desc(64)
+    n = 1 << 18
+    x = W.blackscholes_inputs(n, seed=24)
+    xd = torch.from_numpy(x).cuda()
+    tgt = torch.zeros(n, dtype=torch.float32, device="cuda")
+    with H.Region(H.HPAC_REGION_BLACKSCHOLES, xd, param=W.BS_RATE) as R:
+        R.run_exact(xd, tgt)
+    S = H.Surrogate(desc, seed=8)
+    l0 = S.grad(xd, tgt, W.BS_RATE, loss=True)
+    l1 = S.train(xd, tgt, W.BS_RATE, batch=4096, epochs=4, lr=3e-3)
+    assert l1 < 0.05 * l0, (l0, l1)
+    # calibrated fallback: predictions below tau are recomputed exactly
+    out = torch.zeros(n, dtype=torch.float32, device="cuda")
+    mask = torch.zeros(n, dtype=torch.uint8, device="cuda")
+    S.infer(xd, out, W.BS_RATE)
+    pred = out.cpu().numpy()
+    tau = float(np.quantile(pred, 0.3))
+    st = S.infer(xd, out, W.BS_RATE, fallback_below=tau, mask=mask, stats=True)
+    m = mask.cpu().numpy()
+    o = out.cpu().numpy()
+    ex = tgt.cpu().numpy()
+    assert np.array_equal(m == 0, pred < tau)
+    assert st["approximated"] == int((m == 1).sum())
+    assert np.allclose(o[m == 0], ex[m == 0], rtol=1e-6, atol=1e-7)
+    assert np.array_equal(o[m == 1], pred[m == 1])
+    S.close()
+
+
+def test_adjoint_blackscholes_textbook_and_finite_differences(H, orc):
+    rows = [l.split() for l in open(os.path.join(GOLD, "blackscholes_hull.txt"))
+            if l.strip() and not l.startswith("#")]
+    S0, K0, T0, sig0, r0 = map(float, rows[0][:5])
+    x = np.array([[S0], [K0], [T0], [sig0]])
+    with H.Region(H.HPAC_REGION_BLACKSCHOLES, torch.from_numpy(x).cuda(), param=r0) as R:
+        g = torch.zeros(4, 1, dtype=torch.float64, device="cuda")
+        H.region_adjoint(R, torch.from_numpy(x).cuda(), g)
+    # Hull's worked example: delta N(d1) = 0.7791 (d1 = 0.7693)
+    assert float(g[0, 0]) == pytest.approx(0.7791, abs=5e-5)
+    n = 500
+    for dt in (np.float32, np.float64):
+        x = W.blackscholes_inputs(n, seed=25).astype(dt)
+        xd = torch.from_numpy(x).cuda()
+        gd = torch.zeros(4, n, dtype=torch.float32 if dt == np.float32 else torch.float64, device="cuda")
+        with H.Region(H.HPAC_REGION_BLACKSCHOLES, xd, param=W.BS_RATE) as R:
+            H.region_adjoint(R, xd, gd)
+        got = gd.cpu().numpy().astype(np.float64)
+        x64 = x.astype(np.float64)
+        for d in range(4):
+            h = 1e-6 * np.abs(x64[d])
+            xp, xm = x64.copy(), x64.copy()
+            xp[d] += h
+            xm[d] -= h
+            fd = (orc.run_exact(orc.BLACKSCHOLES, xp, W.BS_RATE) - orc.run_exact(orc.BLACKSCHOLES, xm, W.BS_RATE)) / (2 * h)
+            scale = np.abs(fd).max()
+            tol = 1e-4 if dt == np.float32 else 1e-6
+            assert np.all(np.abs(got[d] - fd) <= tol * scale), (dt, d)
+
+
+def test_adjoint_eos_finite_differences(H, orc):
+    n = 1000
+    x = W.eos_inputs(n, seed=26)
+    xd = torch.from_numpy(x).cuda()
+    g = torch.zeros(4, n, dtype=torch.float64, device="cuda")
+    with H.Region(H.HPAC_REGION_EOS, xd, param=5 / 3) as R:
+        H.region_adjoint(R, xd, g)
+    got = g.cpu().numpy()
+    for d in range(4):
+        # the step scales with the column's magnitude so that the change of p
+        # (about 1e5) stays far above its double-precision resolution
+        h = 1e-7 * np.abs(x[d]).max()
+        xp, xm = x.copy(), x.copy()
+        xp[d] += h
+        xm[d] -= h
+        fd = (orc.run_exact(orc.EOS, xp, 5 / 3) - orc.run_exact(orc.EOS, xm, 5 / 3)) / (2 * h)
+        # the central difference itself carries the rounding of p (a few ulps)
+        # divided by the step, plus its O(h^2) truncation (relative 1e-5 here)
+        p = orc.run_exact(orc.EOS, x, 5 / 3)
+        noise = 8 * np.finfo(np.float64).eps * np.abs(p) / h
+        assert np.all(np.abs(got[d] - fd) <= 1e-5 * np.abs(fd) + noise + 1e-300), d

@@ -1,0 +1,93 @@
+"""Pins of the surrogate oracle (no GPU): bfloat16 rounding against the bit
+pattern, GELU identities, the parameter gradient and the input gradient
+against central finite differences, and a closed-form first Adam step."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import mlp as M
+from paper_2308_16877_gb300 import workloads as W
+
+DESC = {"n_feat": 5, "hidden": 8, "feat_shift": [-1.5, 0.8, 0.1, 5.1, 0.35, 0, 0, 0],
+        "feat_scale": [1 / 1.2, 1 / 0.6, 1 / 0.06, 1 / 2.8, 1 / 0.17, 0, 0, 0],
+        "out_shift": 0.0, "out_scale": 0.25}
+
+
+def test_bf16_round_to_nearest_even():
+    vals = torch.tensor([1.0, 1.0 + 2 ** -8, 1.0 + 3 * 2 ** -9, 1.0 + 2 ** -7 + 2 ** -8, -2.5e-3],
+                        dtype=torch.float64)
+    got = M.bf16(vals).numpy()
+    # 8 significant bits: 1 + 2^-8 is a tie -> even (1.0); 1 + 3*2^-9 -> 1 + 2^-7;
+    # 1 + 2^-7 + 2^-8 is a tie between 1 + 2^-7 (odd) and 1 + 2^-6 (even) -> 1 + 2^-6
+    assert got[0] == 1.0 and got[1] == 1.0 and got[2] == 1.0 + 2 ** -7 and got[3] == 1.0 + 2 ** -6
+    b = np.float32(-2.5e-3).view(np.uint32)
+    lsb = (b >> 16) & 1
+    rounded = ((b + 0x7FFF + lsb) & 0xFFFF0000).astype(np.uint32).view(np.float32)
+    assert got[4] == np.float64(rounded)
+
+
+def test_gelu_identities():
+    x = torch.linspace(-6, 6, 101, dtype=torch.float64)
+    assert torch.allclose(M.gelu(x) - M.gelu(-x), x, atol=1e-14)
+    assert M.gelu(torch.tensor(0.0, dtype=torch.float64)) == 0.0
+    assert float(M.gelu(torch.tensor(10.0, dtype=torch.float64))) == pytest.approx(10.0, rel=1e-12)
+
+
+def _problem(n=12, seed=0):
+    rng = np.random.default_rng(seed)
+    p = rng.uniform(-0.5, 0.5, M.n_params(5, 8))
+    x = W.blackscholes_inputs(n, seed=seed + 1).astype(np.float64)
+    target = rng.uniform(0, 10, n)
+    return p, x, target
+
+
+def test_parameter_gradient_matches_finite_differences():
+    p, x, target = _problem()
+    loss, g, fwd, leaves, tn = M.loss_and_grad(p, DESC, 0, x, W.BS_RATE, target)
+    # finite differences on the loss as a function of the bf16-valued weights:
+    # perturb the rounded weights (the gradient is taken with respect to them)
+    D, H = 5, 8
+    base = [M.bf16(t) if i in (0, 2, 4) else t.clone() for i, t in enumerate(M.unpack(p, D, H))]
+    flat_idx = [0, 17, 39, 45, 101, 112, 120, 128]
+    sizes = [H * D, H, H * H, H, H, 1]
+    h = 1e-6
+    for fi in flat_idx:
+        seg = 0
+        off = fi
+        while off >= sizes[seg]:
+            off -= sizes[seg]
+            seg += 1
+
+        def L(delta):
+            ls = [t.clone() for t in base]
+            ls[seg].view(-1)[off] += delta
+            W1, b1, W2, b2, W3, b3 = ls
+            f, _ = M.features(0, x, W.BS_RATE)
+            fn = (f - torch.tensor(DESC["feat_shift"][:D], dtype=torch.float64)) * \
+                torch.tensor(DESC["feat_scale"][:D], dtype=torch.float64)
+            y = M.gelu(M.gelu(fn @ W1.T + b1) @ W2.T + b2) @ W3 + b3
+            return float(torch.mean((y - tn) ** 2))
+
+        fd = (L(h) - L(-h)) / (2 * h)
+        assert g[fi] == pytest.approx(fd, rel=1e-6, abs=1e-9), fi
+
+
+def test_input_gradient_matches_finite_differences():
+    p, x, _ = _problem(n=5, seed=3)
+    gi = M.input_grad(p, DESC, 0, x, W.BS_RATE)
+    h = 1e-6
+    for d in range(4):
+        xp, xm = x.copy(), x.copy()
+        xp[d] += h
+        xm[d] -= h
+        fp, _, _ = M.forward(p, DESC, 0, xp, W.BS_RATE, round_act=False)
+        fm, _, _ = M.forward(p, DESC, 0, xm, W.BS_RATE, round_act=False)
+        assert np.allclose(gi[d], (fp - fm) / (2 * h), rtol=1e-6, atol=1e-8), d
+
+
+def test_first_adam_step_closed_form():
+    g = np.array([0.3, -2.0, 1e-3, 0.0])
+    p = np.zeros(4)
+    p1, m, v = M.adam(p, g, np.zeros(4), np.zeros(4), 1, lr=0.01)
+    # bias-corrected moments equal g and g^2 after one step: update = lr g / (|g| + eps)
+    assert np.allclose(p1, -0.01 * g / (np.abs(g) + 1e-8), rtol=1e-12)
