@@ -331,6 +331,98 @@ def bench_sweep(hpac, torch, dev, stream, baseline=True):
     return out
 
 
+def calibrate_floor(pred, exact, target=0.01, q=0.99):
+    """Smallest price floor tau such that, among predictions >= tau, the q-th
+    quantile of the relative error |pred - exact| / |exact| is at most target."""
+    order = np.argsort(pred)[::-1]                  # largest predictions first
+    rel = np.abs(pred[order] - exact[order]) / np.maximum(np.abs(exact[order]), 1e-30)
+    # running q-quantile over growing prefixes, on a grid of prefix sizes
+    best = None
+    for frac in np.linspace(0.02, 1.0, 50):
+        k = max(1, int(frac * len(order)))
+        if np.quantile(rel[:k], q) <= target:
+            best = float(pred[order][k - 1])
+    return best if best is not None else float("inf")
+
+
+def bench_surrogate(hpac, torch, dev, stream, n_train=1 << 22, n_cal=1 << 20, n_inf=1 << 24,
+                    epochs=24, batch=8192, lr=3e-3):
+    """The learned surrogate of the Black-Scholes region: trained by the
+    library's kernels on 4M exact pairs, calibrated on 1M held-out options,
+    inference on 16M options with the exact fallback below the calibrated
+    price, against the exact kernel and TAF on the same options."""
+    def exact(x, dtype):
+        out = torch.zeros(x.shape[1], dtype=dtype, device=dev)
+        xx = x if dtype == torch.float32 else x.double().contiguous()
+        with hpac.Region(hpac.HPAC_REGION_BLACKSCHOLES, xx, param=W.BS_RATE, stream=stream) as R:
+            R.run_exact(xx, out)
+        return out
+    xt = torch.from_numpy(W.blackscholes_inputs(n_train, seed=31)).to(dev)
+    xc = torch.from_numpy(W.blackscholes_inputs(n_cal, seed=32)).to(dev)
+    xi = torch.from_numpy(W.blackscholes_inputs(n_inf, seed=33)).to(dev)
+    yt = exact(xt, torch.float32)
+    desc = hpac.blackscholes_desc(64)
+    S = hpac.Surrogate(desc, seed=2308, stream=stream)
+    S.fit_normalization(xt, yt, W.BS_RATE)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    loss = S.train(xt, yt, W.BS_RATE, batch=batch, epochs=epochs, lr=lr)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    train_ms = e0.elapsed_time(e1)
+    # calibration
+    pc = torch.zeros(n_cal, dtype=torch.float32, device=dev)
+    S.infer(xc, pc, W.BS_RATE)
+    yc = exact(xc, torch.float64)
+    tau = calibrate_floor(pc.cpu().numpy().astype(np.float64), yc.cpu().numpy())
+    # inference with fallback vs the exact kernel
+    out = torch.zeros(n_inf, dtype=torch.float32, device=dev)
+    mask = torch.zeros(n_inf, dtype=torch.uint8, device=dev)
+    st = S.infer(xi, out, W.BS_RATE, fallback_below=tau, mask=mask, stats=True)
+    def timed(f, reps=10):
+        f()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            f()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+    ex32 = torch.zeros(n_inf, dtype=torch.float32, device=dev)
+    with hpac.Region(hpac.HPAC_REGION_BLACKSCHOLES, xi, param=W.BS_RATE, logical_threads=n_inf // 8,
+                     stream=stream) as R:
+        exact_ms = timed(lambda: R.run_exact(xi, ex32))
+        taf_out = torch.zeros(n_inf, dtype=torch.float32, device=dev)
+        taf_stats = R.run_taf(xi, taf_out, 4, 8, 0.005, 0, stats=True)
+    sur_ms = timed(lambda: S.infer(xi, out, W.BS_RATE, fallback_below=tau, mask=mask))
+    nofb_ms = timed(lambda: S.infer(xi, out, W.BS_RATE))
+    S.infer(xi, out, W.BS_RATE, fallback_below=tau, mask=mask)
+    ref = exact(xi, torch.float64)
+    o, r, m = out.cpu().numpy().astype(np.float64), ref.cpu().numpy(), mask.cpu().numpy()
+    rel = np.abs(o - r) / np.maximum(np.abs(r), 1e-30)
+    rms = float(np.sqrt(np.mean(r * r)))
+    tafo = taf_out.cpu().numpy().astype(np.float64)
+    approx = m == 1
+    # tensor work: layer 2 (H x H) per sample on the tensor cores
+    flops = 2.0 * desc.hidden * desc.hidden * n_inf
+    S.close()
+    return {
+        "train": {"pairs": n_train, "epochs": epochs, "batch": batch, "ms": train_ms,
+                  "samples_per_s": n_train * epochs / (train_ms * 1e-3), "final_mse_normalized": loss},
+        "calibrated_floor": tau,
+        "inference": {"options": n_inf, "ms": sur_ms, "ms_without_fallback": nofb_ms,
+                      "exact_kernel_ms": exact_ms, "speedup_vs_exact": exact_ms / sur_ms,
+                      "surrogate_fraction": st["approximated"] / n_inf,
+                      "layer2_tensor_tflops": flops / (nofb_ms * 1e-3) / 1e12},
+        "quality": {"nrmse": float(np.sqrt(np.mean((o - r) ** 2)) / rms),
+                    "p99_rel_err_on_surrogate_outputs": float(np.quantile(rel[approx], 0.99)) if approx.any() else None,
+                    "max_rel_err_on_surrogate_outputs": float(rel[approx].max()) if approx.any() else None},
+        "vs_taf_same_options": {"taf_fraction_approximated": taf_stats["approximated"] / n_inf,
+                                "taf_nrmse": float(np.sqrt(np.mean((tafo - r) ** 2)) / rms)},
+    }
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -342,6 +434,7 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-blackscholes", action="store_true")
     ap.add_argument("--no-sweep", action="store_true")
+    ap.add_argument("--no-surrogate", action="store_true")
     args = ap.parse_args(argv)
     if args.impl == "reference":
         return run_reference(args)
@@ -534,6 +627,7 @@ def main(argv=None):
 
     bs = None if args.no_blackscholes else bench_blackscholes(hpac, torch, dev, stream)
     sweep = None if args.no_sweep else bench_sweep(hpac, torch, dev, stream)
+    surrogate = None if args.no_surrogate else bench_surrogate(hpac, torch, dev, stream)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = hydro_cpu()
@@ -565,6 +659,7 @@ def main(argv=None):
             "quality": quality,
             "blackscholes": bs,
             "sweep": sweep,
+            "surrogate": surrogate,
         }
         print(json.dumps(line))
     Hy.close()

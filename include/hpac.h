@@ -361,7 +361,8 @@ hpac_status hpac_region_adjoint(hpac_region *region, const void *d_in, void *d_g
  * Learned surrogate of a region (not from the paper): an MLP
  * n_feat -> hidden -> hidden -> 1 with GELU (tanh form), BF16 weights and
  * activations and FP32 accumulation; layer 1 on FP32 features, layer 2 on the
- * tensor cores. Black-Scholes features: ln(S/K), sigma sqrt(T), r T, T, sigma;
+ * tensor cores. Black-Scholes features: ln(S/K), sigma sqrt(T), r T, d1 (the
+ * Black-Scholes d1 clamped to [-10, 10]), sigma;
  * output C = S (out_shift + out_scale net). EOS features: e, v_{n+1}, dv, q
  * (as FP32); output p = out_shift + out_scale net. Features are normalized as
  * (f - feat_shift) * feat_scale. Trained with Adam (beta 0.9 / 0.999,
@@ -390,6 +391,16 @@ hpac_status hpac_mlp_destroy(hpac_mlp *mlp);
 int32_t hpac_mlp_num_params(const hpac_mlp *mlp);
 hpac_status hpac_mlp_get_params(hpac_mlp *mlp, float *h_params);
 hpac_status hpac_mlp_set_params(hpac_mlp *mlp, const float *h_params); /* resets Adam */
+
+/* Set the feature and output normalisation (feat_shift/feat_scale to the
+ * mean and 1/std of each feature, out_shift/out_scale to the mean and std of
+ * the targets divided by the output multiplier) from n training invocations;
+ * waits for the result. Allocates 144 bytes of device memory for the call. */
+hpac_status hpac_mlp_fit_normalization(hpac_mlp *mlp, int64_t n, const void *d_in,
+                                       int64_t in_stride, double param, const float *d_target);
+
+/* Copy the surrogate's current descriptor (normalisation included). */
+hpac_status hpac_mlp_get_desc(const hpac_mlp *mlp, hpac_mlp_desc *out);
 
 /* Inference over n invocations of the region inputs (the region's layout:
  * float for Black-Scholes, double for EOS; param = r or gamma). d_out: n

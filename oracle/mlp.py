@@ -46,11 +46,14 @@ def n_params(D, H):
 
 
 def features(kind, x, param):
-    """(n, D) float64 features and the output multiplier of each invocation."""
+    """(n, D) float64 features and the output multiplier of each invocation.
+    Black-Scholes: ln(S/K), sigma sqrt T, r T, d1 clamped to [-10, 10], sigma."""
     x = torch.as_tensor(np.asarray(x, dtype=np.float64))
     if kind == 0:      # Black-Scholes: S, K, T, sigma
         S, K, T, sig = x[0], x[1], x[2], x[3]
-        f = torch.stack([torch.log(S / K), sig * torch.sqrt(T), param * T, T, sig], dim=1)
+        d1 = (torch.log(S / K) + (param + 0.5 * sig * sig) * T) / (sig * torch.sqrt(T))
+        f = torch.stack([torch.log(S / K), sig * torch.sqrt(T), param * T,
+                         torch.clamp(d1, -10.0, 10.0), sig], dim=1)
         return f, S
     return x[:4].T.clone(), torch.ones(x.shape[1], dtype=torch.float64)
 
@@ -115,7 +118,9 @@ def input_grad(p, desc, kind, x, param):
     xt = torch.as_tensor(np.asarray(x, dtype=np.float64)).clone().requires_grad_(True)
     if kind == 0:
         S, K, T, sig = xt[0], xt[1], xt[2], xt[3]
-        f = torch.stack([torch.log(S / K), sig * torch.sqrt(T), param * T, T, sig], dim=1)
+        d1 = (torch.log(S / K) + (param + 0.5 * sig * sig) * T) / (sig * torch.sqrt(T))
+        f = torch.stack([torch.log(S / K), sig * torch.sqrt(T), param * T,
+                         torch.clamp(d1, -10.0, 10.0), sig], dim=1)
         mult = S
     else:
         f = xt[:4].T

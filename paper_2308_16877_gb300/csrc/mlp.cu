@@ -113,7 +113,7 @@ __device__ __forceinline__ void features(const void *in, int64_t stride, int64_t
     f[0] = __logf(__fdividef(S, K));
     f[1] = sig * sqrtf(T);
     f[2] = r * T;
-    f[3] = T;
+    f[3] = fminf(fmaxf(__fdividef(f[0] + (r + 0.5f * sig * sig) * T, f[1]), -10.f), 10.f);  // d1
     f[4] = sig;
     mult = S;
   } else {
@@ -419,13 +419,17 @@ __global__ void __launch_bounds__(H * 2) mlp_kernel(MlpArgs a, hpac_mlp_desc d) 
           float gin[4];
           if (KIND == HPAC_REGION_BLACKSCHOLES) {
             // region output C = S (shift + scale net); features ln(S/K),
-            // sigma sqrt(T), r T, T, sigma
+            // sigma sqrt(T), r T, d1 (clamped to [-10, 10]), sigma
             const float S = raw[0], K = raw[1], Tm = raw[2], sig = raw[3];
             const float sc = d.out_scale, sq = sqrtf(Tm), r = (float)a.param;
-            const float dnet_dS = df[0] / S;
-            const float dnet_dK = -df[0] / K;
-            const float dnet_dT = df[1] * sig * 0.5f / sq + df[2] * r + df[3];
-            const float dnet_dsig = df[1] * sq + df[4];
+            const float sst = sig * sq;
+            const float d1 = (logf(S / K) + (r + 0.5f * sig * sig) * Tm) / sst;
+            const float g3 = (d1 > -10.f && d1 < 10.f) ? df[3] : 0.f;  // clamp
+            const float dnet_dS = df[0] / S + g3 / (S * sst);
+            const float dnet_dK = -df[0] / K - g3 / (K * sst);
+            const float dnet_dT = df[1] * sig * 0.5f / sq + df[2] * r +
+                                  g3 * ((r + 0.5f * sig * sig) / sst - 0.5f * d1 / Tm);
+            const float dnet_dsig = df[1] * sq + df[4] + g3 * (sq - d1 / sig);
             gin[0] = fmaf(sc, net, d.out_shift) + S * sc * dnet_dS;
             gin[1] = S * sc * dnet_dK;
             gin[2] = S * sc * dnet_dT;
@@ -523,6 +527,43 @@ __global__ void __launch_bounds__(H * 2) mlp_kernel(MlpArgs a, hpac_mlp_desc d) 
     __syncthreads();
     if (threadIdx.x == 0 && g_fallback && a.counters) atomicAdd(&a.counters[0], g_fallback);
   }
+}
+
+// Sums of the features, their squares and the per-invocation targets
+// (region output / multiplier) for the normalisation statistics.
+template <int KIND>
+__global__ void moments_kernel(const void *in, int64_t stride, int64_t n, double param,
+                               const float *target, hpac_mlp_desc d, double *acc) {
+  __shared__ double s[18];
+  if (threadIdx.x < 18) s[threadIdx.x] = 0.0;
+  __syncthreads();
+  double loc[18];
+#pragma unroll
+  for (int k = 0; k < 18; ++k) loc[k] = 0.0;
+  hpac_mlp_desc id = d;  // raw (unnormalised) features
+#pragma unroll
+  for (int k = 0; k < 8; ++k) id.feat_shift[k] = 0.f, id.feat_scale[k] = 1.f;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    float f[8], mult, raw[4];
+    features<KIND>(in, stride, i, param, id, f, mult, raw);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      loc[k] += f[k];
+      loc[8 + k] += (double)f[k] * f[k];
+    }
+    const double t = (double)target[i] / mult;
+    loc[16] += t;
+    loc[17] += t * t;
+  }
+#pragma unroll
+  for (int k = 0; k < 18; ++k) {
+    double v = loc[k];
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+    if ((threadIdx.x & 31) == 0) atomicAdd(&s[k], v);
+  }
+  __syncthreads();
+  if (threadIdx.x < 18) atomicAdd(&acc[threadIdx.x], s[threadIdx.x]);
 }
 
 __global__ void adam_kernel(float *p, const float *g, float *m, float *v, int n, float lr, float b1,
@@ -782,4 +823,48 @@ extern "C" hpac_status hpac_mlp_input_grad(hpac_mlp *m, int64_t n, const void *d
   a.in = d_in, a.stride = in_stride, a.n = n, a.param = param, a.out = d_grad;
   a.params = m->params;
   return launch<MODE_INPUT_GRAD>(m, a);
+}
+
+extern "C" hpac_status hpac_mlp_fit_normalization(hpac_mlp *m, int64_t n, const void *d_in,
+                                                  int64_t in_stride, double param,
+                                                  const float *d_target) {
+  hpac_status s = check_io(m, n, d_in, in_stride);
+  if (s != HPAC_OK) return s;
+  if (n < 2 || !d_target) return set_error(HPAC_EINVAL, "need at least 2 samples and targets");
+  double *acc = nullptr;
+  HPAC_CUDA_TRY(cudaMalloc(&acc, 18 * sizeof(double)));
+  cudaError_t e = cudaMemsetAsync(acc, 0, 18 * sizeof(double), m->stream);
+  int sms = 148;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, m->device);
+  int64_t blocks = (n + 255) / 256;
+  if (blocks > (int64_t)sms * 4) blocks = (int64_t)sms * 4;
+  if (e == cudaSuccess) {
+    if (m->d.kind == HPAC_REGION_BLACKSCHOLES)
+      moments_kernel<HPAC_REGION_BLACKSCHOLES><<<(unsigned)blocks, 256, 0, m->stream>>>(
+          d_in, in_stride, n, param, d_target, m->d, acc);
+    else
+      moments_kernel<HPAC_REGION_EOS><<<(unsigned)blocks, 256, 0, m->stream>>>(
+          d_in, in_stride, n, param, d_target, m->d, acc);
+    e = cudaGetLastError();
+  }
+  double h[18];
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h, acc, sizeof(h), cudaMemcpyDeviceToHost, m->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
+  cudaFree(acc);
+  if (e != cudaSuccess) return cuda_error(e, "hpac_mlp_fit_normalization");
+  for (int k = 0; k < m->d.n_feat; ++k) {
+    const double mu = h[k] / n, var = h[8 + k] / n - mu * mu;
+    m->d.feat_shift[k] = (float)mu;
+    m->d.feat_scale[k] = var > 0 ? (float)(1.0 / sqrt(var)) : 1.f;
+  }
+  const double mu = h[16] / n, var = h[17] / n - mu * mu;
+  m->d.out_shift = (float)mu;
+  m->d.out_scale = var > 0 ? (float)sqrt(var) : 1.f;
+  return HPAC_OK;
+}
+
+extern "C" hpac_status hpac_mlp_get_desc(const hpac_mlp *m, hpac_mlp_desc *out) {
+  if (!m || !out) return set_error(HPAC_EINVAL, "NULL argument");
+  *out = m->d;
+  return HPAC_OK;
 }

@@ -132,6 +132,8 @@ SIGNATURES = {
     "hpac_mlp_train": (C.c_int, [_P, C.c_int64, _P, C.c_int64, C.c_double, _P, C.c_int32, C.c_int32,
                                  C.c_float, C.POINTER(C.c_float)]),
     "hpac_mlp_input_grad": (C.c_int, [_P, C.c_int64, _P, C.c_int64, C.c_double, _P]),
+    "hpac_mlp_fit_normalization": (C.c_int, [_P, C.c_int64, _P, C.c_int64, C.c_double, _P]),
+    "hpac_mlp_get_desc": (C.c_int, [_P, C.POINTER(hpac_mlp_desc)]),
     "hpac_last_error": (C.c_char_p, []),
     "hpac_version": (C.c_char_p, []),
 }
@@ -538,6 +540,18 @@ class Surrogate:
         self._h = h
         self.n_params = int(load().hpac_mlp_num_params(h))
 
+    def fit_normalization(self, x, target, param, n=None):
+        n = x.shape[1] if n is None else n
+        _check(load().hpac_mlp_fit_normalization(self._h, n, _ptr(x), x.shape[1], float(param),
+                                                 _ptr(target)), "hpac_mlp_fit_normalization")
+        self.desc = self.get_desc()
+        return self.desc
+
+    def get_desc(self):
+        d = hpac_mlp_desc()
+        _check(load().hpac_mlp_get_desc(self._h, C.byref(d)), "hpac_mlp_get_desc")
+        return d
+
     def params(self):
         import numpy as np
         out = np.zeros(self.n_params, dtype=np.float32)
@@ -590,13 +604,14 @@ class Surrogate:
 
 
 def blackscholes_desc(hidden=64):
-    """Surrogate descriptor for the Black-Scholes region with feature
-    normalisation set for the option ranges of the workloads (features
-    ln(S/K), sigma sqrt T, r T, T, sigma; output C / S)."""
+    """Surrogate descriptor for the Black-Scholes region (features ln(S/K),
+    sigma sqrt T, r T, d1, sigma; output C / S) with a fixed normalisation for
+    the option ranges of the workloads; Surrogate.fit_normalization replaces
+    it with the statistics of a training set."""
     d = hpac_mlp_desc()
     d.kind, d.n_feat, d.hidden = HPAC_REGION_BLACKSCHOLES, 5, hidden
-    shift = [-1.5, 0.8, 0.1, 5.1, 0.35]
-    scale = [1 / 1.2, 1 / 0.6, 1 / 0.06, 1 / 2.8, 1 / 0.17]
+    shift = [-1.5, 0.8, 0.1, -1.5, 0.35]
+    scale = [1 / 1.2, 1 / 0.6, 1 / 0.06, 1 / 3.0, 1 / 0.17]
     for k in range(5):
         d.feat_shift[k], d.feat_scale[k] = shift[k], scale[k]
     d.out_shift, d.out_scale = 0.0, 0.25

@@ -8,8 +8,8 @@ import torch
 from oracle import mlp as M
 from paper_2308_16877_gb300 import workloads as W
 
-DESC = {"n_feat": 5, "hidden": 8, "feat_shift": [-1.5, 0.8, 0.1, 5.1, 0.35, 0, 0, 0],
-        "feat_scale": [1 / 1.2, 1 / 0.6, 1 / 0.06, 1 / 2.8, 1 / 0.17, 0, 0, 0],
+DESC = {"n_feat": 5, "hidden": 8, "feat_shift": [-1.5, 0.8, 0.1, -1.5, 0.35, 0, 0, 0],
+        "feat_scale": [1 / 1.2, 1 / 0.6, 1 / 0.06, 1 / 3.0, 1 / 0.17, 0, 0, 0],
         "out_shift": 0.0, "out_scale": 0.25}
 
 
