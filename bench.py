@@ -72,6 +72,19 @@ KERNEL_SOURCES = {"map_kernel": ["exact_perfo.cu", "regions.cuh"], "taf_kernel":
                   "node_kernel": ["hydro.cu"]}
 
 
+def aggregate(total_ms, units_per_rank, world, device=None):
+    """Whole-job throughput of `world` replicas: the slowest rank's time (max
+    over ranks with an all-reduce when world > 1) and the units all ranks
+    processed. Returns (max_ms, units per second)."""
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    return total_ms, world * units_per_rank / (total_ms * 1e-3)
+
+
 def env_rank():
     return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
             int(os.environ.get("LOCAL_RANK", 0)))
@@ -423,6 +436,141 @@ def bench_surrogate(hpac, torch, dev, stream, n_train=1 << 22, n_cal=1 << 20, n_
     }
 
 
+def bench_hydro_large(hpac, torch, dev, stream, n=256, nsteps=200, train_pairs=1 << 22, epochs=16,
+                      sweep_configs=64):
+    """The large hydro configuration: a 256^3 mesh for 200 time steps with the
+    EOS exact, under TAF, under iACT and replaced by a learned surrogate
+    (4 -> 128 -> 128 -> 1, trained on EOS pairs recorded from the exact run),
+    plus a 64-configuration knob sweep of the EOS region at mid-run."""
+    x, y, z, e = W.hydro_initial(n)
+    dt = W.hydro_dt(n)
+    E = n ** 3
+    T = E // HYDRO_IPT
+    Hy = hpac.Hydro(n, x, y, z, e, dt, logical_threads=T, block_threads=256, stream=stream)
+    sh = stream.cuda_stream
+    torch.cuda.synchronize()
+    init = {k: v.clone() for k, v in Hy.t.items()}
+    scale_arr = (hpac.C.c_double * 4)(*IACT_SCALE)
+    taf_k = hpac.hpac_taf_knobs(TAF["hsize"], TAF["psize"], TAF["thresh"], TAF["level"], 0)
+    iact_k = hpac.hpac_iact_knobs(IACT["tsize"], IACT["tperwarp"], IACT["thresh"], IACT["level"], 0,
+                                  hpac.C.cast(scale_arr, hpac.C.POINTER(hpac.C.c_double)))
+    eos_h = Hy.eos._h
+    eos_ptr, p_ptr = hpac.C.c_void_p(Hy["eos_in"].data_ptr()), hpac.C.c_void_p(Hy["p"].data_ptr())
+
+    def reset():
+        for k, v in init.items():
+            Hy.t[k].copy_(v)
+
+    pairs, mid = [], []
+    S = None
+
+    def run(tech, record=False):
+        reset()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for s in range(nsteps):
+            hpac.hpac_hydro_nodes(Hy.state, sh)
+            hpac.hpac_hydro_elements(Hy.state, sh)
+            if tech == "exact":
+                hpac.hpac_run_exact(eos_h, eos_ptr, p_ptr)
+            elif tech == "taf":
+                hpac.hpac_run_taf(eos_h, taf_k, eos_ptr, p_ptr)
+            elif tech == "iact":
+                hpac.hpac_run_iact(eos_h, iact_k, eos_ptr, p_ptr)
+            else:
+                S.infer(Hy["eos_in"], Hy["p"], GAMMA)
+            if record:
+                # EOS pairs of this step: the active elements (energy, viscosity
+                # or volume change), the mid-run state kept whole for the sweep
+                ein = Hy["eos_in"]
+                act = torch.nonzero((ein[0] > 0) | (ein[3] > 0) | (ein[2] != 0)).flatten()
+                pairs.append((ein[:, act].clone(), Hy["p"][act].clone()))
+                if s + 1 == nsteps // 2:
+                    mid.append((ein.clone(), Hy["p"].clone()))
+            hpac.hpac_hydro_finalize(Hy.state, sh)
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b), Hy["e"][:1].item(), Hy["p"].clone()
+
+    res = {}
+    t_ex, qoi_ex, p_ex = run("exact", record=True)
+    res["exact"] = {"ms": t_ex}
+    for tech in ("taf", "iact"):
+        t, qoi, p_fin = run(tech)
+        res[tech] = {"ms": t, "speedup_vs_exact": t_ex / t, "qoi_rel_err": abs(qoi - qoi_ex) / abs(qoi_ex),
+                     "p_nrmse": float(torch.sqrt(torch.mean((p_fin - p_ex) ** 2)).item()
+                                      / torch.sqrt(torch.mean(p_ex ** 2)).item())}
+    # surrogate trained on the EOS pairs of the exact run: the active elements
+    # of every step plus as many untouched ones (inputs (0, 1, 0, 0) -> p = 0)
+    xa = torch.cat([a for a, _ in pairs], dim=1)
+    ya = torch.cat([b for _, b in pairs])
+    nq = xa.shape[1]
+    xq = torch.zeros(4, nq, dtype=torch.float64, device=dev)
+    xq[1] = 1.0
+    perm = torch.randperm(2 * nq, device=dev, generator=torch.Generator(device=dev).manual_seed(7))
+    xtr = torch.cat([xa, xq], dim=1)[:, perm][:, :train_pairs].contiguous()
+    ytr = torch.cat([ya, torch.zeros(nq, dtype=torch.float64, device=dev)])[perm][:train_pairs].float().contiguous()
+    S = hpac.Surrogate(hpac.eos_desc(128), seed=4, stream=stream)
+    S.fit_normalization(xtr, ytr, GAMMA)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    loss = S.train(xtr, ytr, GAMMA, batch=8192, epochs=epochs, lr=2e-3)
+    b.record(stream)
+    torch.cuda.synchronize()
+    t, qoi, p_fin = run("surrogate")
+    res["surrogate"] = {"ms": t, "speedup_vs_exact": t_ex / t, "qoi_rel_err": abs(qoi - qoi_ex) / abs(qoi_ex),
+                        "p_nrmse": float(torch.sqrt(torch.mean((p_fin - p_ex) ** 2)).item()
+                                         / torch.sqrt(torch.mean(p_ex ** 2)).item()),
+                        "train_pairs": int(xtr.shape[1]), "train_ms": a.elapsed_time(b),
+                        "train_mse_normalized": loss}
+    # 64-configuration EOS knob sweep on the mid-run inputs (region only)
+    ein_mid, p_mid = mid[0]
+    Hy["eos_in"].copy_(ein_mid)
+    ref = torch.zeros(E, dtype=torch.float64, device=dev)
+    hpac.hpac_run_exact(eos_h, eos_ptr, hpac.C.c_void_p(ref.data_ptr()))
+    outp = torch.zeros(E, dtype=torch.float64, device=dev)
+    o_ptr = hpac.C.c_void_p(outp.data_ptr())
+
+    def timed(f, reps=5):
+        f()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            f()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+    t_exact = timed(lambda: hpac.hpac_run_exact(eos_h, eos_ptr, o_ptr))
+    rms = torch.sqrt(torch.mean(ref * ref)).item()
+    table = []
+    cfgs = []
+    for thr in (1e-4, 1e-3, 1e-2, 1e-1):
+        for h in (2, 4):
+            for pz in (4, 16):
+                for lv in (0, 1):
+                    cfgs.append(("taf", hpac.hpac_taf_knobs(h, pz, thr, lv, 0), dict(h=h, p=pz, thr=thr, level=lv)))
+    for thr in (1e-4, 1e-3, 1e-2, 1e-1):
+        for g in (32, 4):
+            for ts in (2, 8):
+                for lv in (0, 1):
+                    cfgs.append(("iact", hpac.hpac_iact_knobs(ts, g, thr, lv, 0, hpac.C.cast(
+                        scale_arr, hpac.C.POINTER(hpac.C.c_double))), dict(tsize=ts, tperwarp=g, thr=thr, level=lv)))
+    for kind, k, info in cfgs[:sweep_configs]:
+        fn = (lambda k=k: hpac.hpac_run_taf(eos_h, k, eos_ptr, o_ptr)) if kind == "taf" else \
+             (lambda k=k: hpac.hpac_run_iact(eos_h, k, eos_ptr, o_ptr))
+        tm = timed(fn)
+        err = torch.sqrt(torch.mean((outp - ref) ** 2)).item() / rms
+        table.append(dict(technique=kind, **info, speedup=t_exact / tm, p_nrmse=err))
+    ok = [r for r in table if r["p_nrmse"] <= 0.01]
+    best = max(ok, key=lambda r: r["speedup"]) if ok else None
+    S.close()
+    Hy.close()
+    return {"mesh": f"{n}^3", "time_steps": nsteps, "runs": res, "eos_sweep": {
+        "configs": len(table), "exact_region_ms": t_exact, "best_within_1pct": best,
+        "table": table}}
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -435,6 +583,7 @@ def main(argv=None):
     ap.add_argument("--no-blackscholes", action="store_true")
     ap.add_argument("--no-sweep", action="store_true")
     ap.add_argument("--no-surrogate", action="store_true")
+    ap.add_argument("--no-hydro-large", action="store_true")
     args = ap.parse_args(argv)
     if args.impl == "reference":
         return run_reference(args)
@@ -543,11 +692,7 @@ def main(argv=None):
         step()
     torch.cuda.synchronize()
     clk.stop()
-    total_ms = start.elapsed_time(stop)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms, _ = aggregate(start.elapsed_time(stop), 1, world, dev)
     ms_per_step = total_ms / args.steps
     value = world * len(runs) * E * nsteps / (ms_per_step * 1e-3)
     run_ms = {tech: float(np.mean([run_ev[s][j][0].elapsed_time(run_ev[s][j][1])
@@ -628,6 +773,7 @@ def main(argv=None):
     bs = None if args.no_blackscholes else bench_blackscholes(hpac, torch, dev, stream)
     sweep = None if args.no_sweep else bench_sweep(hpac, torch, dev, stream)
     surrogate = None if args.no_surrogate else bench_surrogate(hpac, torch, dev, stream)
+    large = None if args.no_hydro_large else bench_hydro_large(hpac, torch, dev, stream)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = hydro_cpu()
@@ -660,6 +806,7 @@ def main(argv=None):
             "blackscholes": bs,
             "sweep": sweep,
             "surrogate": surrogate,
+            "hydro_large": large,
         }
         print(json.dumps(line))
     Hy.close()

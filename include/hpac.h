@@ -404,12 +404,12 @@ hpac_status hpac_mlp_get_desc(const hpac_mlp *mlp, hpac_mlp_desc *out);
 
 /* Inference over n invocations of the region inputs (the region's layout:
  * float for Black-Scholes, double for EOS; param = r or gamma). d_out: n
- * floats. fallback_below: where a Black-Scholes prediction is below this price
+ * outputs in the region's dtype (float / double). fallback_below: where a Black-Scholes prediction is below this price
  * the exact region is evaluated instead (NaN: never); d_mask (nullable) gets
  * HPAC_MASK_APPROX for surrogate outputs and HPAC_MASK_EXACT for fallbacks;
  * h_stats (nullable, synchronous) counts approximated = surrogate outputs. */
 hpac_status hpac_mlp_infer(hpac_mlp *mlp, int64_t n, const void *d_in, int64_t in_stride,
-                           double param, float *d_out, float fallback_below, uint8_t *d_mask,
+                           double param, void *d_out, float fallback_below, uint8_t *d_mask,
                            hpac_stats *h_stats);
 
 /* Gradient of the mean squared error over n invocations with targets d_target

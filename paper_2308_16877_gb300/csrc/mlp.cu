@@ -301,7 +301,10 @@ __global__ void __launch_bounds__(H * 2) mlp_kernel(MlpArgs a, hpac_mlp_desc d) 
             mk = HPAC_MASK_EXACT;
             atomicAdd(&g_fallback, 1ull);
           }
-          a.out[i] = o;
+          if (KIND == HPAC_REGION_EOS)
+            reinterpret_cast<double *>(a.out)[i] = (double)o;  // the region's own dtype
+          else
+            a.out[i] = o;
           if (a.mask) a.mask[i] = mk;
         }
       }
@@ -725,10 +728,11 @@ extern "C" hpac_status hpac_mlp_set_params(hpac_mlp *m, const float *h_params) {
 }
 
 extern "C" hpac_status hpac_mlp_infer(hpac_mlp *m, int64_t n, const void *d_in, int64_t in_stride,
-                                      double param, float *d_out, float fallback_below,
+                                      double param, void *d_out_, float fallback_below,
                                       uint8_t *d_mask, hpac_stats *h_stats) {
   hpac_status s = check_io(m, n, d_in, in_stride);
   if (s != HPAC_OK) return s;
+  float *d_out = static_cast<float *>(d_out_);
   if (n > 0 && !d_out) return set_error(HPAC_EINVAL, "output is NULL");
   if (m->d.kind != HPAC_REGION_BLACKSCHOLES && !isnan(fallback_below))
     return set_error(HPAC_EUNSUPPORTED, "exact fallback is implemented for Black-Scholes only");

@@ -616,3 +616,14 @@ def blackscholes_desc(hidden=64):
         d.feat_shift[k], d.feat_scale[k] = shift[k], scale[k]
     d.out_shift, d.out_scale = 0.0, 0.25
     return d
+
+
+def eos_desc(hidden=128):
+    """Surrogate descriptor for the EOS region (FP32 features e, v, dv, q;
+    output p); Surrogate.fit_normalization sets the normalisation."""
+    d = hpac_mlp_desc()
+    d.kind, d.n_feat, d.hidden = HPAC_REGION_EOS, 4, hidden
+    for k in range(4):
+        d.feat_shift[k], d.feat_scale[k] = 0.0, 1.0
+    d.out_shift, d.out_scale = 0.0, 1.0
+    return d
