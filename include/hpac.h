@@ -364,8 +364,10 @@ hpac_status hpac_region_adjoint(hpac_region *region, const void *d_in, void *d_g
  * tensor cores. Black-Scholes features: ln(S/K), sigma sqrt(T), r T, d1 (the
  * Black-Scholes d1 clamped to [-10, 10]), sigma;
  * output C = S (out_shift + out_scale net). EOS features: e, v_{n+1}, dv, q
- * (as FP32); output p = out_shift + out_scale net. Features are normalized as
- * (f - feat_shift) * feat_scale. Trained with Adam (beta 0.9 / 0.999,
+ * (as FP32); output p = m max(out_shift + out_scale net, 0) with the
+ * multiplier m = (gamma - 1) max(e - dv q, 0) / v_{n+1} (the ideal-gas
+ * pressure after the viscous work; 0 for an untouched element). Features are
+ * normalized as (f - feat_shift) * feat_scale. Trained with Adam (beta 0.9 / 0.999,
  * eps 1e-8, cosine-decayed step) on the mean squared error of net against the
  * normalized region outputs.
  * ------------------------------------------------------------------------ */

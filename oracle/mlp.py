@@ -55,7 +55,11 @@ def features(kind, x, param):
         f = torch.stack([torch.log(S / K), sig * torch.sqrt(T), param * T,
                          torch.clamp(d1, -10.0, 10.0), sig], dim=1)
         return f, S
-    return x[:4].T.clone(), torch.ones(x.shape[1], dtype=torch.float64)
+    # EOS (e, v1, dv, q): the multiplier is the ideal-gas pressure of the energy
+    # after the viscous work, (gamma - 1) max(e - dv q, 0) / v1
+    e, v1, dv, q = x[0], x[1], x[2], x[3]
+    mult = (param - 1.0) * torch.clamp(e - dv * q, min=0.0) / v1
+    return x[:4].T.clone(), mult
 
 
 def net(params, desc, f, round_act=True):
@@ -80,7 +84,10 @@ def forward(p, desc, kind, x, param, round_act=True):
     params = unpack(p, desc["n_feat"], desc["hidden"])
     f, mult = features(kind, x, param)
     y, inter = net(params, desc, f, round_act)
-    return (mult * (desc["out_shift"] + desc["out_scale"] * y)).numpy(), y.numpy(), inter
+    out = mult * (desc["out_shift"] + desc["out_scale"] * y)
+    if kind == 1:
+        out = torch.clamp(out, min=0.0)   # pressure is non-negative
+    return out.numpy(), y.numpy(), inter
 
 
 def loss_and_grad(p, desc, kind, x, param, target):
@@ -90,7 +97,8 @@ def loss_and_grad(p, desc, kind, x, param, target):
     leaves = [t.clone().requires_grad_(True) for t in unpack(p, D, H)]
     f, mult = features(kind, x, param)
     t = torch.as_tensor(np.asarray(target, dtype=np.float64))
-    tn = (t / mult - desc["out_shift"]) / desc["out_scale"]
+    used = mult != 0          # rows with a zero multiplier carry no target
+    tn = torch.where(used, (t / torch.where(used, mult, 1.0) - desc["out_shift"]) / desc["out_scale"], 0.0)
 
     def fwd(ls):
         W1, b1, W2, b2, W3, b3 = ls
@@ -105,7 +113,7 @@ def loss_and_grad(p, desc, kind, x, param, target):
         return h2 @ w3 + b3
 
     y = fwd(leaves)
-    loss = torch.mean((y - tn) ** 2)
+    loss = torch.mean(torch.where(used, y - tn, 0.0) ** 2)
     loss.backward()
     g = torch.cat([l.grad.reshape(-1) for l in leaves]).numpy()
     return float(loss.item()), g, fwd, leaves, tn
@@ -124,7 +132,8 @@ def input_grad(p, desc, kind, x, param):
         mult = S
     else:
         f = xt[:4].T
-        mult = torch.ones(xt.shape[1], dtype=torch.float64)
+        e, v1, dv, q = xt[0], xt[1], xt[2], xt[3]
+        mult = (param - 1.0) * torch.clamp(e - dv * q, min=0.0) / v1
     y, _ = net(params, desc, f, round_act=False)
     out = mult * (desc["out_shift"] + desc["out_scale"] * y)
     out.sum().backward()

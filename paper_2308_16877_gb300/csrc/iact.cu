@@ -154,7 +154,7 @@ __global__ void __launch_bounds__(1024) iact_kernel(R reg, const typename R::T *
         }
         out[i] = y;
         if (stat) stat[i] = (V)dmin;
-        if (has && borderline((double)dmin, P.thr_d)) ++n_border;
+        if (counters && has && borderline((double)dmin, P.thr_d)) ++n_border;
       }
       __syncwarp();
       // ---- write phase: per table, the farthest exactly computing lane

@@ -117,13 +117,16 @@ __device__ __forceinline__ void features(const void *in, int64_t stride, int64_t
     f[4] = sig;
     mult = S;
   } else {
+    // EOS: the output multiplier is the ideal-gas pressure of the energy after
+    // the viscous work, (gamma - 1) max(e - dv q, 0) / v1, so the network learns
+    // a ratio near 1 and an untouched element (e = q = 0) gives exactly 0
     const double *x = static_cast<const double *>(in);
+    const double e = x[i], v1 = x[stride + i], dv = x[2 * stride + i], q = x[3 * stride + i];
+    raw[0] = (float)e, raw[1] = (float)v1, raw[2] = (float)dv, raw[3] = (float)q;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      raw[k] = (float)x[k * stride + i];
-      f[k] = raw[k];
-    }
-    mult = 1.0f;
+    for (int k = 0; k < 4; ++k) f[k] = raw[k];
+    const double u = e - dv * q;
+    mult = u > 0.0 ? (float)((param - 1.0) * u / v1) : 0.f;
   }
 #pragma unroll
   for (int k = 0; k < 8; ++k) f[k] = k < d.n_feat ? (f[k] - d.feat_shift[k]) * d.feat_scale[k] : 0.f;
@@ -301,8 +304,8 @@ __global__ void __launch_bounds__(H * 2) mlp_kernel(MlpArgs a, hpac_mlp_desc d) 
             mk = HPAC_MASK_EXACT;
             atomicAdd(&g_fallback, 1ull);
           }
-          if (KIND == HPAC_REGION_EOS)
-            reinterpret_cast<double *>(a.out)[i] = (double)o;  // the region's own dtype
+          if (KIND == HPAC_REGION_EOS)  // the region's own dtype; pressure is non-negative
+            reinterpret_cast<double *>(a.out)[i] = (double)fmaxf(o, 0.f);
           else
             a.out[i] = o;
           if (a.mask) a.mask[i] = mk;
@@ -314,13 +317,11 @@ __global__ void __launch_bounds__(H * 2) mlp_kernel(MlpArgs a, hpac_mlp_desc d) 
     // ---- backward: dy per row
     float dy0, dy1;
     if (MODE == MODE_GRAD) {
-      const float t0 = v0 ? (a.target[r0] / (KIND == HPAC_REGION_BLACKSCHOLES ? m0 : 1.f) - d.out_shift) /
-                                d.out_scale
-                          : 0.f;
-      const float t1 = v1 ? (a.target[r1] / (KIND == HPAC_REGION_BLACKSCHOLES ? m1 : 1.f) - d.out_shift) /
-                                d.out_scale
-                          : 0.f;
-      const float e0 = v0 ? y0 - t0 : 0.f, e1 = v1 ? y1 - t1 : 0.f;
+      // rows whose multiplier is 0 (an untouched EOS element) carry no target
+      const bool u0 = v0 && m0 != 0.f, u1 = v1 && m1 != 0.f;
+      const float t0 = u0 ? (a.target[r0] / m0 - d.out_shift) / d.out_scale : 0.f;
+      const float t1 = u1 ? (a.target[r1] / m1 - d.out_shift) / d.out_scale : 0.f;
+      const float e0 = u0 ? y0 - t0 : 0.f, e1 = u1 ? y1 - t1 : 0.f;
       dy0 = 2.f * e0 * a.inv_n;
       dy1 = 2.f * e1 * a.inv_n;
       if (t == 0) atomicAdd(&g_loss, e0 * e0 + e1 * e1);
@@ -438,8 +439,16 @@ __global__ void __launch_bounds__(H * 2) mlp_kernel(MlpArgs a, hpac_mlp_desc d) 
             gin[2] = S * sc * dnet_dT;
             gin[3] = S * sc * dnet_dsig;
           } else {
+            // p = mult (shift + scale net), mult = (g - 1) (e - dv q) / v1 where positive
+            const float e = raw[0], v1 = raw[1], dv = raw[2], q = raw[3];
+            const float g1 = (float)a.param - 1.f;
+            const float m = h ? m1 : m0;
+            const float ratio = fmaf(d.out_scale, net, d.out_shift);
+            const bool on = m > 0.f;
+            const float dm[4] = {on ? g1 / v1 : 0.f, on ? -m / v1 : 0.f, on ? -g1 * q / v1 : 0.f,
+                                 on ? -g1 * dv / v1 : 0.f};
 #pragma unroll
-            for (int k = 0; k < 4; ++k) gin[k] = d.out_scale * df[k];
+            for (int k = 0; k < 4; ++k) gin[k] = ratio * dm[k] + m * d.out_scale * df[k];
           }
 #pragma unroll
           for (int k = 0; k < 4; ++k) a.out[k * a.n + i] = gin[k];
@@ -555,9 +564,12 @@ __global__ void moments_kernel(const void *in, int64_t stride, int64_t n, double
       loc[k] += f[k];
       loc[8 + k] += (double)f[k] * f[k];
     }
-    const double t = (double)target[i] / mult;
-    loc[16] += t;
-    loc[17] += t * t;
+    if (mult != 0.f) {
+      const double t = (double)target[i] / mult;
+      loc[16] += t;
+      loc[17] += t * t;
+      loc[7] += 1.0;  // count of targets (feature slot 7 is unused: n_feat <= 5)
+    }
   }
 #pragma unroll
   for (int k = 0; k < 18; ++k) {
@@ -861,7 +873,8 @@ extern "C" hpac_status hpac_mlp_fit_normalization(hpac_mlp *m, int64_t n, const 
     m->d.feat_shift[k] = (float)mu;
     m->d.feat_scale[k] = var > 0 ? (float)(1.0 / sqrt(var)) : 1.f;
   }
-  const double mu = h[16] / n, var = h[17] / n - mu * mu;
+  const double nt = h[7] > 0 ? h[7] : 1.0;
+  const double mu = h[16] / nt, var = h[17] / nt - mu * mu;
   m->d.out_shift = (float)mu;
   m->d.out_scale = var > 0 ? (float)sqrt(var) : 1.f;
   return HPAC_OK;

@@ -270,3 +270,37 @@ def test_invalid_arguments_are_rejected(H):
     with H.Region(3, x) as R:
         R.run_exact(x, out)
     assert torch.equal(out, x[0])
+
+
+@pytest.mark.parametrize("kind,dt", [(0, np.float32), (1, np.float64), (3, np.float32), (3, np.float64)])
+@pytest.mark.parametrize("level", [0, 1, 2])
+def test_taf_fast_decision_equals_ieee_statistic(H, orc, kind, dt, level):
+    """Without a statistic output or counters the kernel decides RSD < thr by a
+    division-free test with an exact fallback inside a guard band; its masks
+    and outputs equal the IEEE-statistic path bit for bit, also with the
+    threshold at the median statistic (many decisions next to it)."""
+    n, T, B, h, p = 40000, 5000, 128, 4, 3
+    x, param = inputs(kind, n, dt, d=1, ikind="walk")
+    tdt = torch.float32 if dt == np.float32 else torch.float64
+    xd = dev(x)
+    with H.Region(kind, xd, param=param, logical_threads=T, block_threads=B) as R:
+        stat = torch.full((n,), float("nan"), dtype=tdt, device="cuda")
+        out0 = torch.zeros(n, dtype=tdt, device="cuda")
+        m0 = torch.zeros(n, dtype=torch.uint8, device="cuda")
+        R.run_taf(xd, out0, h, p, 0.01, level, mask=m0, stat=stat, stats=True)
+        s = host(stat)
+        thr_med = float(np.nanmedian(s))
+        for thr in (0.0, 1e-3, 0.01, thr_med, float(np.nextafter(np.float32(thr_med), np.float32(1)))):
+            outs, masks = [], []
+            for fast in (False, True):
+                o = torch.zeros(n, dtype=tdt, device="cuda")
+                m = torch.zeros(n, dtype=torch.uint8, device="cuda")
+                if fast:
+                    R.run_taf(xd, o, h, p, thr, level, mask=m)
+                else:
+                    st = torch.zeros(n, dtype=tdt, device="cuda")
+                    R.run_taf(xd, o, h, p, thr, level, mask=m, stat=st, stats=True)
+                outs.append(host(o))
+                masks.append(host(m))
+            assert np.array_equal(masks[0], masks[1]), thr
+            assert np.array_equal(outs[0], outs[1]), thr
