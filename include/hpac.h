@@ -322,14 +322,17 @@ typedef struct {
 
 typedef struct hpac_sweep hpac_sweep;
 
-/* Build a sweep: copies the configurations and regions, precomputes the
- * reference split, and captures the launch in a CUDA graph. d_in: 4 rows
- * (S, K, T, sigma) of in_stride floats holding every region's options at its
- * offset; d_ref: the double-precision exact prices at the same positions;
- * rate: r. Schedule (not semantics): block_threads (64/128/256), persistent
- * blocks per SM, logical blocks per work item (tile_blocks). Allocates device
- * memory; waits for cuda_stream's pending work once. d_in and d_ref must stay
- * valid and unchanged while the sweep exists (every run reads them). */
+/* Build a sweep: copies the configurations and regions, packs the inputs and
+ * the split reference (hi, lo, 1/|a|) into 16-byte vectors per option, and
+ * captures the launch in a CUDA graph. d_in: 4 rows (S, K, T, sigma) of
+ * in_stride floats holding every region's options at its offset; d_ref: the
+ * double-precision exact prices at the same positions; rate: r. Schedule (not
+ * semantics): block_threads (64/128/256), persistent blocks per SM, logical
+ * blocks per work item (tile_blocks). Allocates device memory (about 32 bytes
+ * per option plus the tables); waits for cuda_stream's pending work once.
+ * d_in is read only here; d_ref must stay valid and unchanged while the sweep
+ * exists (relative errors beyond 1e30 are formed from it in double precision).
+ * HPAC_EUNSUPPORTED if a work item would cover 2^32 or more invocations. */
 hpac_status hpac_sweep_create(int32_t n_configs, const hpac_sweep_config *h_configs,
                               int32_t n_regions, const hpac_sweep_region *h_regions,
                               const float *d_in, int64_t in_stride, const double *d_ref,

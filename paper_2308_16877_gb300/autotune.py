@@ -17,8 +17,19 @@ CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "auto
 CANDIDATES = [(bt, bps, tb) for bt in (128, 256) for bps in (4, 8) for tb in (1, 2, 4)]
 
 
+def _kernel_digest():
+    """Digest of the sweep kernel's source, so that a changed kernel is re-tuned."""
+    src = os.path.join(os.path.dirname(os.path.abspath(__file__)), "csrc", "sweep.cu")
+    try:
+        with open(src, "rb") as f:
+            return hashlib.sha1(f.read()).hexdigest()[:12]
+    except OSError:
+        return ""
+
+
 def _key(device_name, regions, n_configs):
-    h = hashlib.sha1(json.dumps([device_name, [r[0] for r in regions], n_configs]).encode())
+    h = hashlib.sha1(json.dumps([device_name, [r[0] for r in regions], n_configs,
+                                 _kernel_digest()]).encode())
     return h.hexdigest()[:16]
 
 

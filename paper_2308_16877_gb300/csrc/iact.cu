@@ -47,7 +47,10 @@ __host__ __device__ inline size_t warp_table_bytes(int tsize, int D, int g) {
   return zb + (size_t)tsize * g * sizeof(V) + 2 * (size_t)g * sizeof(int);
 }
 
-template <class R, int LEVEL>
+// DC: the number of inputs when fixed by the region (4 for Black-Scholes and
+// the EOS), so that the distance loops are fully unrolled; 0 reads P.D.
+// COUNT: the caller asked for counters.
+template <class R, int LEVEL, int DC, bool COUNT>
 __global__ void __launch_bounds__(1024) iact_kernel(R reg, const typename R::T *__restrict__ in,
                                                     int64_t stride, typename R::T *__restrict__ out,
                                                     uint8_t *__restrict__ mask,
@@ -60,7 +63,8 @@ __global__ void __launch_bounds__(1024) iact_kernel(R reg, const typename R::T *
   __shared__ int s_tally[3];
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
-  const int D = P.D, tsize = P.tsize, g = P.g, L = P.L;
+  constexpr int KD = DC > 0 ? DC : kMaxIn;
+  const int D = DC > 0 ? DC : P.D, tsize = P.tsize, g = P.g, L = P.L;
   const int tab = lane / L;
   const size_t wbytes = warp_table_bytes<V>(tsize, D, g);
   unsigned char *base = smem_raw + (size_t)warp * wbytes;
@@ -87,14 +91,14 @@ __global__ void __launch_bounds__(1024) iact_kernel(R reg, const typename R::T *
     for (int64_t i = t; t_lead + (i - t) < n; i += T) {
       const bool act = (t < T) && (i < n);
       // ---- read phase
-      float z[kMaxIn];
-      V x[kMaxIn];
+      float z[KD];
+      V x[KD];
       bool has = false;
       float best = INFINITY;
       int near = 0;
       if (act) {
 #pragma unroll
-        for (int d = 0; d < kMaxIn; ++d) {
+        for (int d = 0; d < KD; ++d) {
           if (d < D) {
             x[d] = in[d * stride + i];
             if (sizeof(V) == 4)
@@ -108,7 +112,7 @@ __global__ void __launch_bounds__(1024) iact_kernel(R reg, const typename R::T *
           float acc = 0.0f;
           const float *zs = W.z + (size_t)j * D * g + tab;
 #pragma unroll
-          for (int d = 0; d < kMaxIn; ++d) {
+          for (int d = 0; d < KD; ++d) {
             if (d < D) {
               const float df = __fsub_rn(z[d], zs[d * g]);
               acc = __fadd_rn(acc, __fmul_rn(df, df));
@@ -154,7 +158,9 @@ __global__ void __launch_bounds__(1024) iact_kernel(R reg, const typename R::T *
         }
         out[i] = y;
         if (stat) stat[i] = (V)dmin;
-        if (counters && has && borderline((double)dmin, P.thr_d)) ++n_border;
+        // diagnostic, compiled only into the counting variant: its double-precision
+        // test would otherwise be evaluated (and discarded) for every invocation
+        if (COUNT && has && borderline((double)dmin, P.thr_d)) ++n_border;
       }
       __syncwarp();
       // ---- write phase: per table, the farthest exactly computing lane
@@ -171,7 +177,7 @@ __global__ void __launch_bounds__(1024) iact_kernel(R reg, const typename R::T *
       if (who == lane && key >= 0.0f) {
         const int slot = W.rr[tab];
 #pragma unroll
-        for (int d = 0; d < kMaxIn; ++d)
+        for (int d = 0; d < KD; ++d)
           if (d < D) W.z[((size_t)slot * D + d) * g + tab] = z[d];
         W.y[(size_t)slot * g + tab] = y;
         W.rr[tab] = slot + 1 == tsize ? 0 : slot + 1;
@@ -223,21 +229,22 @@ hpac_status launch(const hpac_region *r, R reg, const hpac_iact_knobs *k, const 
   V *o = static_cast<V *>(out);
   V *st = static_cast<V *>(stat);
   const V *x = static_cast<const V *>(in);
+  constexpr int kDC = R::kReads == 4 ? 4 : 0;
   switch (k->level) {
     case HPAC_LEVEL_THREAD: {
-      auto fn = iact_kernel<R, HPAC_LEVEL_THREAD>;
+      auto fn = counters ? iact_kernel<R, HPAC_LEVEL_THREAD, kDC, true> : iact_kernel<R, HPAC_LEVEL_THREAD, kDC, false>;
       HPAC_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
       fn<<<(unsigned)blocks, B, smem, r->stream>>>(reg, x, d.in_stride, o, mask, st, d.n, T, P, counters);
       break;
     }
     case HPAC_LEVEL_WARP: {
-      auto fn = iact_kernel<R, HPAC_LEVEL_WARP>;
+      auto fn = counters ? iact_kernel<R, HPAC_LEVEL_WARP, kDC, true> : iact_kernel<R, HPAC_LEVEL_WARP, kDC, false>;
       HPAC_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
       fn<<<(unsigned)blocks, B, smem, r->stream>>>(reg, x, d.in_stride, o, mask, st, d.n, T, P, counters);
       break;
     }
     default: {
-      auto fn = iact_kernel<R, HPAC_LEVEL_BLOCK>;
+      auto fn = counters ? iact_kernel<R, HPAC_LEVEL_BLOCK, kDC, true> : iact_kernel<R, HPAC_LEVEL_BLOCK, kDC, false>;
       HPAC_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
       fn<<<(unsigned)blocks, B, smem, r->stream>>>(reg, x, d.in_stride, o, mask, st, d.n, T, P, counters);
       break;

@@ -17,38 +17,6 @@
 namespace hpac {
 namespace {
 
-// Decision RSD(window) < thr without the correctly rounded division and square
-// root when it is clear: with mu the same IEEE mean as window_rsd (so the
-// second pass is identical), var ~ acc / h and the test var < (thr mu)^2 carry
-// a few ulps of error, far inside the 2e-5 relative guard band on the squared
-// statistic; inside the band, and for mu = 0, the IEEE statistic decides. The
-// decision therefore equals window_rsd(...) < thr exactly.
-template <typename T>
-__device__ __forceinline__ bool rsd_below_fast(const T *win, int ld, int oldest, int h, T thr, T inv_h) {
-  T sum = (T)0;
-  int s = oldest;
-  for (int j = 0; j < h; ++j) {
-    sum = add_rn(sum, win[s * ld]);
-    s = (s + 1 == h) ? 0 : s + 1;
-  }
-  const T mu = div_rn(sum, (T)h);
-  T acc = (T)0;
-  s = oldest;
-  for (int j = 0; j < h; ++j) {
-    const T d = sub_rn(win[s * ld], mu);
-    acc = add_rn(acc, mul_rn(d, d));
-    s = (s + 1 == h) ? 0 : s + 1;
-  }
-  const T var = acc * inv_h;
-  const T tm = thr * mu;
-  const T lim = tm * tm;
-  if (mu != (T)0 && isfinite(lim) && lim < (T)1e30) {
-    if (var < lim * (T)(1.0 - 2e-5)) return true;
-    if (var > lim * (T)(1.0 + 2e-5)) return false;
-  }
-  return window_rsd<T>(win, ld, oldest, h) < thr;
-}
-
 template <class R, int LEVEL>
 __global__ void __launch_bounds__(1024) taf_kernel(R reg, const typename R::T *__restrict__ in,
                                                    int64_t stride, typename R::T *__restrict__ out,
@@ -107,7 +75,7 @@ __global__ void __launch_bounds__(1024) taf_kernel(R reg, const typename R::T *_
             if (stat == nullptr && counters == nullptr && !thr_inf) {
               wants = rsd_below_fast<V>(win + threadIdx.x, ld, pos, h, thr, inv_h);
             } else {
-              const V s = window_rsd<V>(win + threadIdx.x, ld, pos, h);
+              const V s = window_rsd<V>(win + threadIdx.x, ld, pos, h, inv_h);
               if (stat) stat[i] = s;
               if (counters) n_border += borderline((double)s, thr_d) ? 1 : 0;
               wants = thr_inf || s < thr;

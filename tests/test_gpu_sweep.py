@@ -154,3 +154,35 @@ def test_full_workload_sampled(H):
     pairs = [(int(rng.integers(0, 256)), int(rng.integers(0, 32))) for _ in range(24)]
     pairs += [(0, 31), (127, 0), (128, 31), (255, 16)]
     check_against_region_api(H, res, xd, ref, regions, configs, pairs)
+
+
+def test_tiny_zero_and_subnormal_prices(H):
+    """Reference prices below 1e-30 (scaled far down, double subnormals),
+    exactly zero, and one NaN: their relative terms leave the single-precision
+    range, and ratios past 1e30 need double precision; sums and term counts
+    still equal the region API followed by its quality."""
+    sizes = [5000, 3001, 4096]
+    x, xd, ref, regions = build(H, sizes, seed=9)
+    r = ref.clone()
+    idx = torch.arange(r.numel(), device="cuda")
+    r[idx % 7 == 0] *= 1e-35
+    r[idx % 11 == 0] *= 1e-290
+    r[idx % 13 == 0] = 5e-324
+    r[idx % 17 == 0] = 0.0
+    r[idx % 19 == 0] = -r[idx % 19 == 0]
+    sw = H.Sweep(CONFIGS, regions, xd, r, W.BS_RATE, block_threads=128, blocks_per_sm=2, tile_blocks=1)
+    sw.run()
+    res = sw.results()
+    sw.close()
+    pairs = [(c, g) for c in range(len(CONFIGS)) for g in range(len(sizes))]
+    check_against_region_api(H, res, xd, r, regions, CONFIGS, pairs)
+    # one NaN price: its MAPE term and sum are NaN in both
+    r[regions[1][1] + 5] = float("nan")
+    sw = H.Sweep(CONFIGS[:1], regions, xd, r, W.BS_RATE)
+    sw.run()
+    res = sw.results()
+    sw.close()
+    assert np.isnan(res[0, 1]["sum_abs_rel"]) and not np.isnan(res[0, 0]["sum_abs_rel"])
+    assert res[0, 1]["mape_terms"] == H.quality(r[regions[1][1]:regions[1][1] + regions[1][0]].contiguous(),
+                                                torch.zeros(regions[1][0], device="cuda"),
+                                                H.HPAC_METRIC_MAPE)["used"]
