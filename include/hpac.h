@@ -120,13 +120,16 @@ typedef struct {
 
 /* memo(out:hsize:psize:thresh) clause (Sections 2.3, 3.2). hsize in 1..64,
  * psize >= 0, thresh >= 0 (a plain ratio; +inf always predicts once the window
- * is full), level is an hpac_level. */
+ * is full), level is an hpac_level. reset_on_exit: 0 (the default reading)
+ * keeps the window across a prediction run, so the next accurate output slides
+ * it and re-tests; 1 (the alternative reading) empties it when the run ends,
+ * so hsize accurate outputs refill it before the next test. */
 typedef struct {
   int32_t hsize;
   int32_t psize;
   double thresh;
   int32_t level;
-  int32_t reserved0;
+  int32_t reset_on_exit;
 } hpac_taf_knobs;
 
 /* memo(in:tsize:thresh:tperwarp) clause (Sections 2.3, 3.1.4, 3.2). tsize in
@@ -194,7 +197,7 @@ hpac_status hpac_run_perfo(hpac_region *region, const hpac_perfo_knobs *knobs, c
  * relative standard deviation RSD = sigma/|mu| (population moments, 0/0 := 0)
  * is compared with thresh and, if lower, the next psize invocations output the
  * newest window value without reading their inputs. The window is kept across
- * a prediction run. d_mask (nullable) gets EXACT/APPROX; d_stat (nullable, N
+ * a prediction run unless knobs->reset_on_exit. d_mask (nullable) gets EXACT/APPROX; d_stat (nullable, N
  * values of the region dtype) gets the RSD of every accurate invocation with a
  * full window, NaN elsewhere. */
 hpac_status hpac_run_taf(hpac_region *region, const hpac_taf_knobs *knobs, const void *d_in,

@@ -45,11 +45,13 @@ def lib() -> C.CDLL:
         RP = C.POINTER(Region)
         L.orc_run_exact.argtypes = [RP, P, P]
         L.orc_run_perfo.argtypes = [RP, P, I32, I32, D, C.c_uint64, I32, P, P, P]
-        L.orc_run_taf.argtypes = [RP, P, I32, I32, D, I32, P, P, P, P]
+        L.orc_run_taf.argtypes = [RP, P, I32, I32, D, I32, I32, P, P, P, P]
         L.orc_run_iact.argtypes = [RP, P, I32, I32, D, I32, P, P, P, P, P]
+        L.orc_replay_taf.argtypes = [RP, P, I32, I32, D, I32, I32, P, P, P, P, P]
         L.orc_quality.argtypes = [I64, P, P, I32, P, P]
         L.orc_num_threads.restype = C.c_int
-        for f in ("orc_run_exact", "orc_run_perfo", "orc_run_taf", "orc_run_iact", "orc_quality"):
+        for f in ("orc_run_exact", "orc_run_perfo", "orc_run_taf", "orc_replay_taf", "orc_run_iact",
+                  "orc_quality"):
             getattr(L, f).restype = C.c_int
         _hydro_bind(L)
         _lib = L
@@ -120,16 +122,39 @@ def run_perfo(kind, x, param, pkind, m=0, rate=0.0, seed=0, herded=1, threads=0,
     return out, mask, cnt
 
 
-def run_taf(kind, x, param, hsize, psize, thresh, level=THREAD, threads=0, block=256, n=None):
+def run_taf(kind, x, param, hsize, psize, thresh, level=THREAD, threads=0, block=256, n=None,
+            reset=False):
     r, x, n = _region(kind, x, n, param, threads, block)
     out = np.zeros(n, dtype=x.dtype)
     stat = np.zeros(n, dtype=x.dtype)
     mask = np.full(n, 255, dtype=np.uint8)
     cnt = np.zeros(4, dtype=np.int64)
-    if lib().orc_run_taf(C.byref(r), _ptr(x), hsize, psize, thresh, level, _ptr(out), _ptr(mask),
+    if lib().orc_run_taf(C.byref(r), _ptr(x), hsize, psize, thresh, level, int(bool(reset)),
+                         _ptr(out), _ptr(mask),
                          _ptr(stat), _ptr(cnt)):
         raise ValueError("oracle rejected TAF arguments")
     return out, mask, stat, cnt
+
+
+def replay_taf(kind, x, param, hsize, psize, thresh, force, level=THREAD, threads=0, block=256, n=None,
+               reset=False):
+    """TAF along a given mask: outputs and statistics of the oracle's own
+    arithmetic on the mask's path, the decision points where the oracle's own
+    decision differs from the mask's (disagree[i] = 1 at the deciding
+    invocation), and counts (compared, disagreements, structural errors)."""
+    r, x, n = _region(kind, x, n, param, threads, block)
+    force = np.ascontiguousarray(force, dtype=np.uint8)
+    if force.shape != (n,):
+        raise ValueError("mask length differs from n")
+    out = np.zeros(n, dtype=x.dtype)
+    stat = np.zeros(n, dtype=x.dtype)
+    dis = np.zeros(n, dtype=np.uint8)
+    counts = np.zeros(3, dtype=np.int64)
+    if lib().orc_replay_taf(C.byref(r), _ptr(x), hsize, psize, thresh, level, int(bool(reset)),
+                            _ptr(force), _ptr(out),
+                            _ptr(stat), _ptr(dis), _ptr(counts)):
+        raise ValueError("oracle rejected TAF arguments")
+    return out, stat, dis, counts
 
 
 def run_iact(kind, x, param, tsize, tperwarp, thresh, level=THREAD, in_scale=None, threads=0,

@@ -277,21 +277,34 @@ static int is_borderline(double s, double thr) {
  * (Section 3.3, majority rules): among the group's lanes that computed exactly
  * at this step, if more than half want to, every one of them with a full
  * window sets pred = p; otherwise none does. After the p predictions the
- * window is kept, so the next accurate output slides it and re-tests. */
-int orc_run_taf(const orc_region *R, const void *in, int32_t hsize, int32_t psize, double thr,
-                int32_t level, void *out, uint8_t *mask, void *stat, int64_t *counters) {
+ * window is kept, so the next accurate output slides it and re-tests (the
+ * default reading; with reset = 1, the alternative reading, it is emptied and
+ * h accurate outputs refill it before the next test). */
+/* Replay (force != NULL): the decisions are read from a mask produced
+ * elsewhere instead of being taken; the state advances along that mask (an
+ * invocation marked approximate outputs the newest window value), and at
+ * every decision point (a group step whose lanes computed exactly) the
+ * oracle's own decision is compared with the mask's, read from each deciding
+ * lane's next invocation. disagree[i] = 1 at the decision invocation of a lane
+ * whose mask decision differs from the oracle's; counts[0] = deciding lanes
+ * compared, counts[1] = disagreements, counts[2] = structural errors (the mask
+ * approximates where no prediction can be owed, or breaks a prediction run). */
+static int taf_core(const orc_region *R, const void *in, int32_t hsize, int32_t psize, double thr,
+                    int32_t level, int32_t reset, const uint8_t *force, void *out, uint8_t *mask, void *stat,
+                    uint8_t *disagree, int64_t *counters, int64_t *counts) {
   if (check_region(R)) return 1;
   if (hsize < 1 || hsize > 64 || psize < 0 || !(thr >= 0.0)) return 1;
-  if (level < ORC_THREAD || level > ORC_BLOCK) return 1;
+  if (level < ORC_THREAD || level > ORC_BLOCK || (reset != 0 && reset != 1)) return 1;
   const int64_t N = R->n, T = logical_threads(R);
   const int B = R->block, h = hsize;
   const int64_t nblocks = (T + B - 1) / B;
   const int f32 = R->dtype == ORC_F32;
   const float thr_f = (float)thr;
   const int thr_inf = isinf(thr);
-  int64_t approx_total = 0, border_total = 0;
+  int64_t approx_total = 0, border_total = 0, n_cmp = 0, n_dis = 0, n_bad = 0;
   int64_t b;
-#pragma omp parallel for schedule(dynamic, 1) reduction(+ : approx_total, border_total)
+#pragma omp parallel for schedule(dynamic, 1) \
+    reduction(+ : approx_total, border_total, n_cmp, n_dis, n_bad)
   for (b = 0; b < nblocks; ++b) {
     double *win = (double *)calloc((size_t)B * h, sizeof(double));
     int *head = (int *)calloc(B, sizeof(int));   /* slot of the oldest value   */
@@ -300,6 +313,7 @@ int orc_run_taf(const orc_region *R, const void *in, int32_t hsize, int32_t psiz
     int *act = (int *)calloc(B, sizeof(int));
     int *decided = (int *)calloc(B, sizeof(int)); /* computed exactly this step */
     int *wants = (int *)calloc(B, sizeof(int));
+    int *own = (int *)calloc(B, sizeof(int));     /* the oracle's own decision */
     float wf[64];
     double wd[64];
     for (int64_t k = 0; b * B + k * T < N; ++k) {
@@ -311,6 +325,15 @@ int orc_run_taf(const orc_region *R, const void *in, int32_t hsize, int32_t psiz
         wants[l] = 0;
         if (!act[l]) continue;
         double *w = win + (size_t)l * h;
+        if (force) {
+          /* the mask's decision; an owed prediction must be honoured */
+          int apx = force[i] == ORC_APPROX;
+          if (apx != (pred[l] > 0)) {
+            n_bad++;
+            if (apx && cnt[l] == 0) apx = 0;  /* nothing to repeat: compute */
+          }
+          pred[l] = apx ? (pred[l] > 0 ? pred[l] : 1) : 0;
+        }
         if (pred[l] > 0) {
           int newest = (head[l] + cnt[l] - 1) % h;
           out_put(R, out, i, w[newest]);
@@ -318,6 +341,8 @@ int orc_run_taf(const orc_region *R, const void *in, int32_t hsize, int32_t psiz
           stat_put(R, stat, i, NAN);
           pred[l] -= 1;
           approx_total++;
+          /* alternative reading: the window is emptied when a run ends */
+          if (reset && pred[l] == 0) cnt[l] = 0;
           continue;
         }
         double y = region_eval(R, in, i);
@@ -352,9 +377,9 @@ int orc_run_taf(const orc_region *R, const void *in, int32_t hsize, int32_t psiz
         }
       }
       /* phase 2: decision at the requested level */
+      for (int l = 0; l < B; ++l) own[l] = 0;
       if (level == ORC_THREAD) {
-        for (int l = 0; l < B; ++l)
-          if (decided[l] && wants[l]) pred[l] = psize;
+        for (int l = 0; l < B; ++l) own[l] = decided[l] && wants[l];
       } else {
         int gsize = level == ORC_WARP ? ORC_WARP_SIZE : B;
         for (int g0 = 0; g0 < B; g0 += gsize) {
@@ -364,12 +389,30 @@ int orc_run_taf(const orc_region *R, const void *in, int32_t hsize, int32_t psiz
             n_want += decided[l] && wants[l];
           }
           if (2 * n_want > n_dec)
-            for (int l = g0; l < g0 + gsize; ++l)
-              if (decided[l] && cnt[l] == h) pred[l] = psize;
+            for (int l = g0; l < g0 + gsize; ++l) own[l] = decided[l] && cnt[l] == h;
         }
       }
+      for (int l = 0; l < B; ++l) {
+        if (!decided[l]) continue;
+        if (!force) {
+          if (own[l]) pred[l] = psize;
+          continue;
+        }
+        /* replay: the mask's decision shows at the lane's next invocation */
+        int64_t t = b * B + l, inext = t + (k + 1) * T;
+        if (inext >= N) continue;
+        int mask_yes = force[inext] == ORC_APPROX;
+        int own_yes = own[l] && psize > 0;
+        n_cmp++;
+        if (mask_yes != own_yes) {
+          n_dis++;
+          if (disagree) disagree[t + k * T] = 1;
+        }
+        pred[l] = mask_yes ? psize : 0;
+        if (mask_yes && psize == 0) n_bad++;
+      }
     }
-    free(win); free(head); free(cnt); free(pred); free(act); free(decided); free(wants);
+    free(win); free(head); free(cnt); free(pred); free(act); free(decided); free(wants); free(own);
   }
   if (counters) {
     counters[0] = N;
@@ -377,7 +420,28 @@ int orc_run_taf(const orc_region *R, const void *in, int32_t hsize, int32_t psiz
     counters[2] = 0;
     counters[3] = border_total;
   }
+  if (counts) {
+    counts[0] = n_cmp;
+    counts[1] = n_dis;
+    counts[2] = n_bad;
+  }
   return 0;
+}
+
+int orc_run_taf(const orc_region *R, const void *in, int32_t hsize, int32_t psize, double thr,
+                int32_t level, int32_t reset, void *out, uint8_t *mask, void *stat,
+                int64_t *counters) {
+  return taf_core(R, in, hsize, psize, thr, level, reset, NULL, out, mask, stat, NULL, counters,
+                  NULL);
+}
+
+/* Replay of a TAF run along a given mask (see taf_core). */
+int orc_replay_taf(const orc_region *R, const void *in, int32_t hsize, int32_t psize, double thr,
+                   int32_t level, int32_t reset, const uint8_t *force, void *out, void *stat,
+                   uint8_t *disagree, int64_t *counts) {
+  if (!force) return 1;
+  return taf_core(R, in, hsize, psize, thr, level, reset, force, out, NULL, stat, disagree, NULL,
+                  counts);
 }
 
 /* ------------------------------------------------------------------------ */

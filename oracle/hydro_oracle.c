@@ -46,7 +46,8 @@ typedef struct {
 } orc_region;
 int orc_run_exact(const orc_region *R, const void *in, void *out);
 int orc_run_taf(const orc_region *R, const void *in, int32_t hsize, int32_t psize, double thr,
-                int32_t level, void *out, uint8_t *mask, void *stat, int64_t *counters);
+                int32_t level, int32_t reset, void *out, uint8_t *mask, void *stat,
+                int64_t *counters);
 int orc_run_iact(const orc_region *R, const void *in, int32_t tsize, int32_t tperwarp,
                  double thr, int32_t level, const double *in_scale, void *out, uint8_t *mask,
                  void *stat, int64_t *counters);
@@ -269,7 +270,8 @@ int orc_hydro_step(int32_t n, double dt, double gamma, double *x, double *y, dou
     if (mask) memset(mask, 0, (size_t)E);
     if (counters) counters[0] = E, counters[1] = counters[2] = counters[3] = 0;
   } else if (mode == 1) {
-    rc = orc_run_taf(&R, eos_in, K->hsize, K->psize, K->thresh, K->level, pn, mask, NULL, counters);
+    rc = orc_run_taf(&R, eos_in, K->hsize, K->psize, K->thresh, K->level, 0, pn, mask, NULL,
+                     counters);
   } else {
     rc = orc_run_iact(&R, eos_in, K->tsize, K->tperwarp, K->thresh, K->level, K->in_scale, pn, mask,
                       NULL, counters);

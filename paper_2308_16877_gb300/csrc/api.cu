@@ -194,7 +194,8 @@ hpac_status hpac_run_taf(hpac_region *r, const hpac_taf_knobs *k, const void *d_
   if (!(k->thresh >= 0.0)) return set_error(HPAC_EINVAL, "threshold must be >= 0 (got %g)", k->thresh);
   if (k->level < HPAC_LEVEL_THREAD || k->level > HPAC_LEVEL_BLOCK)
     return set_error(HPAC_EINVAL, "level %d", k->level);
-  if (k->reserved0 != 0) return set_error(HPAC_EINVAL, "reserved field not zero");
+  if (k->reset_on_exit != 0 && k->reset_on_exit != 1)
+    return set_error(HPAC_EINVAL, "reset_on_exit %d not 0 or 1", k->reset_on_exit);
   s = begin_counters(r, h_stats);
   if (s != HPAC_OK) return s;
   s = launch_taf(r, k, d_in, d_out, d_mask, d_stat, h_stats ? r->d_counters : nullptr);

@@ -440,7 +440,7 @@ __global__ void __launch_bounds__(H * 2) mlp_kernel(MlpArgs a, hpac_mlp_desc d) 
             gin[3] = S * sc * dnet_dsig;
           } else {
             // p = mult (shift + scale net), mult = (g - 1) (e - dv q) / v1 where positive
-            const float e = raw[0], v1 = raw[1], dv = raw[2], q = raw[3];
+            const float v1 = raw[1], dv = raw[2], q = raw[3];
             const float g1 = (float)a.param - 1.f;
             const float m = h ? m1 : m0;
             const float ratio = fmaf(d.out_scale, net, d.out_shift);

@@ -161,12 +161,33 @@ __device__ __forceinline__ T window_rsd(const T *win, int ld, int oldest, int h,
   return rsd_from_moments(mu, acc, h, inv_h);
 }
 
+// RSD < thr from the IEEE moments, the correctly rounded statistic taken only
+// inside the guard band (see rsd_below_fast).
+// The fast test needs (thr mu)^2 far inside the normal range: a subnormal
+// square keeps too few bits for the guard band (and the absolute error of
+// acc / h, at most one subnormal spacing, must stay far below 2e-5 of it).
+template <typename T>
+__device__ __forceinline__ T fast_test_floor() { return sizeof(T) == 4 ? (T)1e-30 : (T)1e-290; }
+
+template <typename T>
+__device__ __forceinline__ bool rsd_below_moments(T mu, T acc, int h, T thr, T inv_h) {
+  const T var = acc * inv_h;
+  const T tm = thr * mu;
+  const T lim = tm * tm;
+  if (mu != (T)0 && isfinite(lim) && lim < (T)1e30 && lim > fast_test_floor<T>()) {
+    if (var < lim * (T)(1.0 - 2e-5)) return true;
+    if (var > lim * (T)(1.0 + 2e-5)) return false;
+  }
+  return rsd_from_moments(mu, acc, h, inv_h) < thr;
+}
+
 // Decision RSD(window) < thr without the correctly rounded division and square
 // root when it is clear: with mu the same IEEE mean as window_rsd (so the
 // second pass is identical), var ~ acc / h and the test var < (thr mu)^2 carry
 // a few ulps of error, far inside the 2e-5 relative guard band on the squared
-// statistic; inside the band, and for mu = 0, the IEEE statistic decides. The
-// decision therefore equals window_rsd(...) < thr exactly.
+// statistic; inside the band, for mu = 0, and where (thr mu)^2 is not a
+// comfortably normal number, the IEEE statistic decides. The decision
+// therefore equals window_rsd(...) < thr exactly.
 template <typename T>
 __device__ __forceinline__ bool rsd_below_fast(const T *win, int ld, int oldest, int h, T thr, T inv_h) {
   T sum = (T)0;
@@ -183,14 +204,23 @@ __device__ __forceinline__ bool rsd_below_fast(const T *win, int ld, int oldest,
     acc = add_rn(acc, mul_rn(d, d));
     s = (s + 1 == h) ? 0 : s + 1;
   }
-  const T var = acc * inv_h;
-  const T tm = thr * mu;
-  const T lim = tm * tm;
-  if (mu != (T)0 && isfinite(lim) && lim < (T)1e30) {
-    if (var < lim * (T)(1.0 - 2e-5)) return true;
-    if (var > lim * (T)(1.0 + 2e-5)) return false;
+  return rsd_below_moments(mu, acc, h, thr, inv_h);
+}
+
+// The window held in registers, oldest first (compile-time size): the same
+// two IEEE passes in the same order as window_rsd.
+template <typename T, int KH>
+__device__ __forceinline__ void reg_window_moments(const T (&w)[KH], T inv_h, T &mu, T &acc) {
+  T sum = (T)0;
+#pragma unroll
+  for (int j = 0; j < KH; ++j) sum = add_rn(sum, w[j]);
+  mu = div_count(sum, KH, inv_h);
+  acc = (T)0;
+#pragma unroll
+  for (int j = 0; j < KH; ++j) {
+    const T d = sub_rn(w[j], mu);
+    acc = add_rn(acc, mul_rn(d, d));
   }
-  return rsd_from_moments(mu, acc, h, inv_h) < thr;
 }
 
 __device__ __forceinline__ bool borderline(double s, double thr) {

@@ -171,12 +171,7 @@ __device__ __forceinline__ bool rsd_below_contig(const float *p, int h, float th
     const float d = __fsub_rn(p[j * BT], mu);
     acc = __fadd_rn(acc, __fmul_rn(d, d));
   }
-  const float tm = thr * mu, lim = tm * tm, var_a = acc * inv_h;
-  if (mu != 0.f && isfinite(lim) && lim < 1e30f) {
-    if (var_a < lim * (float)(1.0 - 2e-5)) return true;
-    if (var_a > lim * (float)(1.0 + 2e-5)) return false;
-  }
-  return rsd_from_moments(mu, acc, h, inv_h) < thr;
+  return rsd_below_moments(mu, acc, h, thr, inv_h);
 }
 
 // One work item: `tile_blocks` x BT logical threads of region R under

@@ -17,19 +17,28 @@
 namespace hpac {
 namespace {
 
-template <class R, int LEVEL>
+// KH > 0: the history size is KH, known at compile time, and the window lives
+// in registers (shifted on insertion, oldest first), so the statistic is two
+// unrolled passes over registers. KH = 0: the window is in shared memory and h
+// is a run-time argument.
+template <class R, int LEVEL, int KH>
 __global__ void __launch_bounds__(1024) taf_kernel(R reg, const typename R::T *__restrict__ in,
                                                    int64_t stride, typename R::T *__restrict__ out,
                                                    uint8_t *__restrict__ mask,
                                                    typename R::T *__restrict__ stat, int64_t n,
                                                    int64_t T, int h, int p,
                                                    typename R::T thr, int thr_inf, double thr_d,
+                                                   int reset_on_exit,
                                                    unsigned long long *__restrict__ counters) {
   using V = typename R::T;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ unsigned long long s_cnt[2];
   __shared__ int s_tally[3];
   V *win = reinterpret_cast<V *>(smem_raw);
+  V w[KH > 0 ? KH : 1];  // register window (KH > 0), defined from the start
+#pragma unroll
+  for (int j = 0; j < (KH > 0 ? KH : 1); ++j) w[j] = (V)0;
+  if (KH > 0) h = KH;
   const V inv_h = (V)1 / (V)h;
   const int ld = blockDim.x;
   const int lane = threadIdx.x & 31;
@@ -55,11 +64,12 @@ __global__ void __launch_bounds__(1024) taf_kernel(R reg, const typename R::T *_
       if (act) {
         if (pred > 0) {
           const int newest = pos == 0 ? h - 1 : pos - 1;
-          out[i] = win[newest * ld + threadIdx.x];
+          out[i] = KH > 0 ? w[KH > 0 ? KH - 1 : 0] : win[newest * ld + threadIdx.x];
           if (mask) mask[i] = HPAC_MASK_APPROX;
           if (stat) stat[i] = nan_v<V>();
           --pred;
           ++n_apx;
+          if (reset_on_exit && pred == 0) cnt = 0;  // the run ends: refill the window
         } else {
           V x[R::kReads];
 #pragma unroll
@@ -67,15 +77,25 @@ __global__ void __launch_bounds__(1024) taf_kernel(R reg, const typename R::T *_
           const V y = reg(x);
           out[i] = y;
           if (mask) mask[i] = HPAC_MASK_EXACT;
-          win[pos * ld + threadIdx.x] = y;
-          pos = (pos + 1 == h) ? 0 : pos + 1;
+          if (KH > 0) {
+#pragma unroll
+            for (int j = 0; j + 1 < KH; ++j) w[j] = w[j + 1];
+            w[KH > 0 ? KH - 1 : 0] = y;
+          } else {
+            win[pos * ld + threadIdx.x] = y;
+            pos = (pos + 1 == h) ? 0 : pos + 1;
+          }
           cnt = cnt < h ? cnt + 1 : h;
           decided = true;
           if (cnt == h) {
+            V mu = (V)0, acc = (V)0;
+            if (KH > 0) reg_window_moments(w, inv_h, mu, acc);
             if (stat == nullptr && counters == nullptr && !thr_inf) {
-              wants = rsd_below_fast<V>(win + threadIdx.x, ld, pos, h, thr, inv_h);
+              wants = KH > 0 ? rsd_below_moments(mu, acc, h, thr, inv_h)
+                             : rsd_below_fast<V>(win + threadIdx.x, ld, pos, h, thr, inv_h);
             } else {
-              const V s = window_rsd<V>(win + threadIdx.x, ld, pos, h, inv_h);
+              const V s = KH > 0 ? rsd_from_moments(mu, acc, h, inv_h)
+                                 : window_rsd<V>(win + threadIdx.x, ld, pos, h, inv_h);
               if (stat) stat[i] = s;
               if (counters) n_border += borderline((double)s, thr_d) ? 1 : 0;
               wants = thr_inf || s < thr;
@@ -124,7 +144,9 @@ hpac_status launch(const hpac_region *r, R reg, const hpac_taf_knobs *k, const v
   if (d.n == 0) return HPAC_OK;
   const int64_t T = logical_threads(d);
   const int B = d.block_threads;
-  const size_t smem = (size_t)k->hsize * B * sizeof(V);
+  const int h = k->hsize;
+  const int kh = (h == 2 || h == 4 || h == 8) ? h : 0;  // register-window sizes
+  const size_t smem = kh ? 0 : (size_t)h * B * sizeof(V);
   const int limit = max_dyn_smem(r->device);
   if ((int64_t)smem > limit)
     return set_error(HPAC_EUNSUPPORTED, "TAF window of %zu bytes per block exceeds %d", smem, limit);
@@ -135,29 +157,20 @@ hpac_status launch(const hpac_region *r, R reg, const hpac_taf_knobs *k, const v
   V *o = static_cast<V *>(out);
   V *st = static_cast<V *>(stat);
   const V *x = static_cast<const V *>(in);
-  switch (k->level) {
-    case HPAC_LEVEL_THREAD: {
-      auto fn = taf_kernel<R, HPAC_LEVEL_THREAD>;
-      HPAC_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      fn<<<(unsigned)blocks, B, smem, r->stream>>>(reg, x, d.in_stride, o, mask, st, d.n, T, k->hsize,
-                                                   k->psize, thr, thr_inf, k->thresh, counters);
-      break;
-    }
-    case HPAC_LEVEL_WARP: {
-      auto fn = taf_kernel<R, HPAC_LEVEL_WARP>;
-      HPAC_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      fn<<<(unsigned)blocks, B, smem, r->stream>>>(reg, x, d.in_stride, o, mask, st, d.n, T, k->hsize,
-                                                   k->psize, thr, thr_inf, k->thresh, counters);
-      break;
-    }
-    default: {
-      auto fn = taf_kernel<R, HPAC_LEVEL_BLOCK>;
-      HPAC_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      fn<<<(unsigned)blocks, B, smem, r->stream>>>(reg, x, d.in_stride, o, mask, st, d.n, T, k->hsize,
-                                                   k->psize, thr, thr_inf, k->thresh, counters);
-      break;
-    }
-  }
+  const int lvl = k->level == HPAC_LEVEL_THREAD ? 0 : k->level == HPAC_LEVEL_WARP ? 1 : 2;
+  using Fn = decltype(&taf_kernel<R, HPAC_LEVEL_THREAD, 0>);
+  static const Fn table[3][4] = {
+      {taf_kernel<R, HPAC_LEVEL_THREAD, 0>, taf_kernel<R, HPAC_LEVEL_THREAD, 2>,
+       taf_kernel<R, HPAC_LEVEL_THREAD, 4>, taf_kernel<R, HPAC_LEVEL_THREAD, 8>},
+      {taf_kernel<R, HPAC_LEVEL_WARP, 0>, taf_kernel<R, HPAC_LEVEL_WARP, 2>,
+       taf_kernel<R, HPAC_LEVEL_WARP, 4>, taf_kernel<R, HPAC_LEVEL_WARP, 8>},
+      {taf_kernel<R, HPAC_LEVEL_BLOCK, 0>, taf_kernel<R, HPAC_LEVEL_BLOCK, 2>,
+       taf_kernel<R, HPAC_LEVEL_BLOCK, 4>, taf_kernel<R, HPAC_LEVEL_BLOCK, 8>}};
+  const Fn fn = table[lvl][kh == 0 ? 0 : kh == 2 ? 1 : kh == 4 ? 2 : 3];
+  if (smem > 0)
+    HPAC_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  fn<<<(unsigned)blocks, B, smem, r->stream>>>(reg, x, d.in_stride, o, mask, st, d.n, T, h, k->psize,
+                                               thr, thr_inf, k->thresh, k->reset_on_exit, counters);
   HPAC_CUDA_TRY(cudaGetLastError());
   return HPAC_OK;
 }

@@ -35,7 +35,7 @@ class hpac_perfo_knobs(C.Structure):
 
 class hpac_taf_knobs(C.Structure):
     _fields_ = [("hsize", C.c_int32), ("psize", C.c_int32), ("thresh", C.c_double),
-                ("level", C.c_int32), ("reserved0", C.c_int32)]
+                ("level", C.c_int32), ("reset_on_exit", C.c_int32)]
 
 
 class hpac_iact_knobs(C.Structure):
@@ -363,9 +363,9 @@ class Region:
         return st.as_dict() if st is not None else None
 
     def run_taf(self, x, out, hsize, psize, thresh, level=HPAC_LEVEL_THREAD, mask=None, stat=None,
-                stats=False):
+                stats=False, reset_on_exit=False):
         self._check_io(x, out, mask, stat)
-        k = hpac_taf_knobs(int(hsize), int(psize), float(thresh), int(level), 0)
+        k = hpac_taf_knobs(int(hsize), int(psize), float(thresh), int(level), int(bool(reset_on_exit)))
         st = hpac_run_taf(self._h, k, _ptr(x), _ptr(out), _ptr(mask), _ptr(stat), stats)
         return st.as_dict() if st is not None else None
 

@@ -12,18 +12,25 @@ sides' statistics. The count of such threads is reported and kept small.
 import numpy as np
 
 
-def rsd_band(window, rel_err):
-    """Bound on |RSD(w') - RSD(w)| when each w_j moves by at most rel_err_j |w_j|:
-    first-order sensitivity sum_j |dRSD/dw_j| |w_j| rel_err_j plus the rounding
-    of the statistic itself (a few ulps of its precision)."""
+def rsd_band(window, rel_err, abs_err=None, tiny=0.0):
+    """Bound on |RSD(w') - RSD(w)| when each w_j moves by at most
+    max(rel_err_j |w_j|, abs_err_j): first-order sensitivity
+    sum_j |dRSD/dw_j| err_j. tiny is the subnormal spacing of the statistic's
+    precision: squared deviations below the normal range are rounded to
+    multiples of it, an absolute error of up to h tiny in the variance sum,
+    which moves RSD by about h tiny / (2 sd |mu|) (large for windows of tiny
+    values). The caller adds the rounding of the statistic itself."""
     w = np.asarray(window, dtype=np.float64)
     h = w.size
     mu = w.mean()
     sd = w.std()
     if mu == 0 or sd == 0:
         return np.inf if sd > 0 else 0.0
+    err = np.abs(w) * rel_err
+    if abs_err is not None:
+        err = np.maximum(err, abs_err)
     grad = np.abs((w - mu) / (h * sd * abs(mu)) - sd * np.sign(mu) / (h * mu * mu))
-    return float(np.sum(grad * np.abs(w) * rel_err))
+    return float(np.sum(grad * err) + 2 * h * tiny / (sd * abs(mu)))
 
 
 def taf_compare(n, T, B, level, out_g, mask_g, stat_g, out_o, mask_o, stat_o, hsize, thr, tol,
@@ -94,3 +101,58 @@ def source_index(n, T, mask):
         ok = c >= 0
         src[idx[ok]] = idx[ex][c[ok]]
     return src
+
+
+def taf_replay_check(n, T, B, level, out_g, mask_g, stat_g, out_r, stat_r, dis, counts, hsize, thr,
+                     tol, rel_err, eps, sample=2000, seed=0):
+    """GPU TAF trace against the oracle replayed along the GPU's mask.
+
+    The replay follows the GPU's decisions, so every invocation is compared:
+    outputs within tol (per invocation: the bound of the exact output it
+    carries). At each decision point where the oracle's own decision differs
+    from the GPU's (dis[i] = 1), some lane of the deciding group (the thread,
+    its warp or its block) must hold an oracle statistic within the rounding
+    band of the threshold. Statistics of both sides agree within that band at
+    the disagreements and at a sample of accurate invocations. The mask must
+    be a valid TAF trace (no structural error). Returns the disagreement count.
+    """
+    T = T if T > 0 else n
+    tiny = 2.0 ** -149 if eps > 1e-10 else 2.0 ** -1074  # subnormal spacing of the statistic
+    assert counts[2] == 0, ("structural errors in the GPU mask", int(counts[2]))
+    err = np.abs(out_g.astype(np.float64) - out_r.astype(np.float64))
+    bad = np.nonzero(~(err <= tol))[0]
+    assert bad.size == 0, ("output mismatch", bad[:5], err[bad[:5]], tol[bad[:5]])
+
+    def band_at(j):
+        t = j % T
+        hist = np.arange(t, j + 1, T)
+        ex = hist[mask_g[hist] == 0][-hsize:]
+        if ex.size < hsize:
+            return None
+        return (rsd_band(out_r[ex], rel_err[ex], tol[ex], tiny)
+                + 8 * eps * abs(float(stat_r[j])))
+
+    G = 1 if level == 0 else 32 if level == 1 else B
+    for i in np.nonzero(dis)[0]:
+        t, k = i % T, i // T
+        g0 = (t // G) * G
+        near = False
+        for l in range(g0, min(g0 + G, T)):
+            j = l + k * T
+            if j >= n or mask_g[j] != 0 or np.isnan(stat_r[j]):
+                continue
+            b = band_at(j)
+            if b is not None and abs(float(stat_r[j]) - thr) <= b:
+                near = True
+                assert abs(float(stat_g[j]) - float(stat_r[j])) <= 2 * b + 1e-300, ("stats apart", j)
+        assert near, ("non-borderline disagreement", int(i))
+    acc = np.nonzero((mask_g == 0) & ~np.isnan(stat_r))[0]
+    rng = np.random.default_rng(seed)
+    for j in rng.choice(acc, size=min(sample, acc.size), replace=False) if acc.size else []:
+        b = band_at(j)
+        # first order holds where the band is small against the statistic
+        # (not for windows whose mean nearly cancels)
+        if b is not None and np.isfinite(b) and b <= 1e-3 * abs(float(stat_r[j])):
+            assert abs(float(stat_g[j]) - float(stat_r[j])) <= 2 * b + 1e-300, \
+                ("stats apart", int(j), float(stat_g[j]), float(stat_r[j]), b)
+    return int(counts[1])

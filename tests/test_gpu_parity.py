@@ -6,7 +6,7 @@ import numpy as np
 import pytest
 
 from paper_2308_16877_gb300 import workloads as W
-from parity import source_index, taf_compare
+from parity import source_index, taf_compare, taf_replay_check
 from tolerances import EPS32, EPS64, output_tol
 
 torch = pytest.importorskip("torch")
@@ -140,7 +140,8 @@ def taf_case(H, orc, kind, dt, n, T, B, h, p, thr, level, ikind="walk", seed=230
 @pytest.mark.parametrize("n,T,B,h,p,thr", [
     (20000, 500, 128, 3, 5, 2e-3), (20000, 2500, 256, 4, 8, 5e-2), (777, 77, 64, 2, 2, 1e-2),
     (4096, 4096, 32, 1, 3, 0.1), (3000, 96, 1024, 5, 1, np.inf), (3000, 100, 96, 4, 8, 0.0),
-    (1, 0, 256, 2, 2, 0.5), (0, 0, 256, 2, 2, 0.5)])
+    (1, 0, 256, 2, 2, 0.5), (0, 0, 256, 2, 2, 0.5), (30000, 1000, 128, 8, 4, 2e-2),
+    (9000, 300, 64, 16, 3, 5e-2)])
 def test_taf_identity_bitexact(H, orc, dt, level, n, T, B, h, p, thr):
     """Identity region: both sides see bit-identical windows, so masks,
     outputs and statistics agree exactly."""
@@ -151,6 +152,31 @@ def test_taf_identity_bitexact(H, orc, dt, level, n, T, B, h, p, thr):
     assert st["approximated"] == cnt[1] and st["borderline"] == cnt[3]
     if T > 0 and n >= 4 * T and thr > 0:
         assert cnt[1] > 0
+
+
+@pytest.mark.parametrize("dt", [np.float32, np.float64])
+@pytest.mark.parametrize("level", [0, 1, 2])
+@pytest.mark.parametrize("h,p,thr", [(4, 8, 5e-2), (3, 2, 0.2), (8, 16, np.inf), (2, 5, 1e-2)])
+def test_taf_reset_on_exit_bitexact(H, orc, dt, level, h, p, thr):
+    """The alternative reading (window emptied when a prediction run ends),
+    identity region: masks, outputs and statistics equal the oracle's."""
+    n, T, B = 30000, 1500, 128
+    x, param = inputs(3, n, dt, d=1, ikind="walk")
+    tdt = torch.float32 if dt == np.float32 else torch.float64
+    out = torch.full((n,), float("nan"), dtype=tdt, device="cuda")
+    stat = torch.full((n,), -1.0, dtype=tdt, device="cuda")
+    mask = torch.full((n,), 255, dtype=torch.uint8, device="cuda")
+    with H.Region(3, dev(x), param=param, logical_threads=T, block_threads=B) as R:
+        st = R.run_taf(dev(x), out, h, p, thr, level, mask=mask, stat=stat, stats=True,
+                       reset_on_exit=True)
+        fast_out = torch.zeros(n, dtype=tdt, device="cuda")
+        fast_mask = torch.zeros(n, dtype=torch.uint8, device="cuda")
+        R.run_taf(dev(x), fast_out, h, p, thr, level, mask=fast_mask, reset_on_exit=True)
+    o, om, os_, cnt = orc.run_taf(3, x, param, h, p, thr, level=level, threads=T, block=B, reset=True)
+    assert np.array_equal(host(mask), om) and np.array_equal(host(out), o)
+    assert np.array_equal(host(stat), os_, equal_nan=True)
+    assert np.array_equal(host(fast_mask), om) and np.array_equal(host(fast_out), o)
+    assert st["approximated"] == cnt[1] > 0
 
 
 @pytest.mark.parametrize("kind,dt", [(0, np.float32), (0, np.float64), (1, np.float64)])
@@ -170,6 +196,30 @@ def test_taf_regions(H, orc, kind, dt, level, thr):
                             2 * rel, eps)
     assert div <= max(1, n // 1000), div
     assert comp >= n - div * 8
+
+
+@pytest.mark.parametrize("kind,dt", [(0, np.float32), (0, np.float64), (1, np.float64)])
+@pytest.mark.parametrize("level", [0, 1, 2])
+@pytest.mark.parametrize("h,thr", [(4, 5e-3), (4, 0.5), (3, 0.05), (8, 2.0), (2, 0.2)])
+def test_taf_regions_replay(H, orc, kind, dt, level, h, thr):
+    """Parity by replay: the oracle follows the GPU's mask, so every output is
+    compared within its bound, and every decision where the oracle's own
+    criterion differs from the GPU's is borderline (the threshold lies within
+    the rounding band of a deciding lane's statistic)."""
+    n = 65536
+    T, B, p = n // 8, 256, 8
+    x, param, g, gm, gs, *_ = taf_case(H, orc, kind, dt, n, T, B, h, p, thr, level)
+    x64 = x.astype(np.float64)
+    tol_x = output_tol(kind, x64, param, dt)
+    ref64 = orc.run_exact(kind, x64, param)
+    rel = tol_x / np.maximum(np.abs(ref64), 1e-300)
+    eps = EPS32 if dt == np.float32 else EPS64
+    o_r, s_r, dis, counts = orc.replay_taf(kind, x, param, h, p, thr, gm, level=level, threads=T, block=B)
+    src = source_index(n, T, gm)
+    ndis = taf_replay_check(n, T, B, level, g, gm, gs, o_r, s_r, dis, counts, h, thr, 2 * tol_x[src],
+                            2 * rel, eps)
+    assert counts[0] > 0
+    assert ndis <= max(1, counts[0] // 1000), ndis
 
 
 def test_taf_blackscholes_workload_counts(H, orc):
@@ -274,12 +324,14 @@ def test_invalid_arguments_are_rejected(H):
 
 @pytest.mark.parametrize("kind,dt", [(0, np.float32), (1, np.float64), (3, np.float32), (3, np.float64)])
 @pytest.mark.parametrize("level", [0, 1, 2])
-def test_taf_fast_decision_equals_ieee_statistic(H, orc, kind, dt, level):
+@pytest.mark.parametrize("h", [3, 4, 8])
+def test_taf_fast_decision_equals_ieee_statistic(H, orc, kind, dt, level, h):
     """Without a statistic output or counters the kernel decides RSD < thr by a
     division-free test with an exact fallback inside a guard band; its masks
     and outputs equal the IEEE-statistic path bit for bit, also with the
-    threshold at the median statistic (many decisions next to it)."""
-    n, T, B, h, p = 40000, 5000, 128, 4, 3
+    threshold at the median statistic (many decisions next to it). h = 4 and 8
+    run the register-window kernels, h = 3 the shared-memory one."""
+    n, T, B, p = 40000, 5000, 128, 3
     x, param = inputs(kind, n, dt, d=1, ikind="walk")
     tdt = torch.float32 if dt == np.float32 else torch.float64
     xd = dev(x)

@@ -199,3 +199,61 @@ def test_rejects_bad_knobs(orc):
                           (2, 1, np.nan, 0), (2, 1, 0.1, 3)):
         with pytest.raises(ValueError):
             orc.run_taf(orc.IDENTITY, x, 0.0, h, p, thr, level=lv)
+
+
+@pytest.mark.parametrize("level", [0, 1, 2])
+def test_replay_of_own_mask_agrees_everywhere(orc, level):
+    """Replaying the oracle's own mask reproduces its outputs and statistics
+    bit for bit, with no disagreement and no structural error."""
+    n, T = 20000, 2500
+    x = W.blackscholes_inputs(n)
+    out, mask, stat, cnt = orc.run_taf(0, x, W.BS_RATE, 4, 8, 0.05, level=level, threads=T, block=128)
+    o2, s2, dis, counts = orc.replay_taf(0, x, W.BS_RATE, 4, 8, 0.05, mask, level=level, threads=T,
+                                         block=128)
+    assert np.array_equal(out, o2) and np.array_equal(stat, s2, equal_nan=True)
+    assert counts[1] == 0 and counts[2] == 0 and not dis.any()
+    # every accurate step with a successor is a compared decision point
+    assert counts[0] == np.count_nonzero(mask[:n - T] == 0)
+
+
+def test_replay_flags_a_flipped_decision_and_a_broken_run(orc):
+    """A prediction run removed from the mask is one disagreement at its
+    decision invocation (later ones may follow on the changed path); an
+    approximation before the window is full lengthens the next run past p,
+    a structural error."""
+    n, T, h, p = 4096, 64, 2, 3
+    x = W.identity_inputs(n, d=1, dtype=np.float64, kind="levels")
+    out, mask, stat, cnt = orc.run_taf(3, x, 0.0, h, p, 0.5, threads=T, block=64)
+    t = next(t for t in range(T) if np.any(mask[t::T] == 1))
+    seq = np.arange(t, n, T)
+    k = int(np.argmax(mask[seq] == 1))          # first approximated step of lane t
+    flipped = mask.copy()
+    flipped[seq[k:k + p]] = 0
+    _, _, dis, counts = orc.replay_taf(3, x, 0.0, h, p, 0.5, flipped, threads=T, block=64)
+    assert dis[seq[k - 1]] == 1 and counts[1] >= 1 and counts[2] == 0
+    assert mask[seq[1]] == 0                    # the window is still filling
+    broken = mask.copy()
+    broken[seq[1]] = 1                          # a prediction nothing could have owed
+    _, _, _, counts = orc.replay_taf(3, x, 0.0, h, p, 0.5, broken, threads=T, block=64)
+    assert counts[2] >= 1
+
+
+@pytest.mark.parametrize("n,T,h,p", [(1000, 10, 4, 8), (999, 100, 1, 1), (4096, 256, 5, 3),
+                                     (333, 7, 3, 0), (50, 64, 2, 2)])
+@pytest.mark.parametrize("level", [0, 1, 2])
+def test_reset_on_exit_closed_form(orc, n, T, h, p, level):
+    """Alternative reading (window emptied when a prediction run ends) at
+    thr = +inf: each thread repeats h accurate steps then p predictions, so its
+    accurate count is h floor(n_t/(h+p)) + min(h, n_t mod (h+p)); all lanes of a
+    group share the pattern, so the levels agree."""
+    x = W.identity_inputs(n, dtype=np.float64)
+    out, mask, _, _ = orc.run_taf(orc.IDENTITY, x, 0.0, h, p, np.inf, level=level, threads=T,
+                                  block=64, reset=True)
+    want = 0
+    for t in range(min(T, n)):
+        nt = len(thread_trace(T, n, t))
+        want += h * (nt // (h + p)) + min(h, nt % (h + p))
+    assert int((mask == 0).sum()) == want
+    if p > 0 and h > 1 and n // T > h + p:  # with h = 1 the two readings coincide
+        keep = orc.run_taf(orc.IDENTITY, x, 0.0, h, p, np.inf, level=level, threads=T, block=64)[1]
+        assert int((keep == 0).sum()) < want    # the kept window re-tests after one step
