@@ -572,6 +572,73 @@ def bench_hydro_large(hpac, torch, dev, stream, n=256, nsteps=200, train_pairs=1
         "table": table}}
 
 
+def bench_persistent(hpac, torch, dev, stream, n=HYDRO_N, nsteps=HYDRO_STEPS, reps=3):
+    """Approximation state kept across time steps (TAF windows, iACT tables in
+    device memory owned by the EOS region): hydro at n^3 for nsteps with one
+    logical thread per element, so a thread's window holds its own element's
+    last accurate pressures and a warp's tables its 32 elements' recent
+    states. Kernel-scoped state cannot approximate here (one invocation per
+    thread per launch); the persistent runs are compared with the exact run."""
+    E = n ** 3
+    sh = stream.cuda_stream
+    x, y, z, e = W.hydro_initial(n)
+    Hy = hpac.Hydro(n, x, y, z, e, W.hydro_dt(n), logical_threads=E, block_threads=256, stream=stream)
+    torch.cuda.synchronize()
+    init = {k: v.clone() for k, v in Hy.t.items()}
+    scale_arr = (hpac.C.c_double * 4)(*IACT_SCALE)
+    variants = {
+        "exact": (hpac.HYDRO_EXACT, None, False),
+        "taf_kernel_scoped": (hpac.HYDRO_TAF, hpac.hpac_taf_knobs(4, 8, 0.005, 0, 0), False),
+        "taf_persistent": (hpac.HYDRO_TAF, hpac.hpac_taf_knobs(4, 8, 0.005, 0, 0), True),
+        "taf_persistent_h2p4": (hpac.HYDRO_TAF, hpac.hpac_taf_knobs(2, 4, 0.005, 0, 0), True),
+        "iact_kernel_scoped": (hpac.HYDRO_IACT, hpac.hpac_iact_knobs(
+            8, 32, 1e-3, 0, 0, hpac.C.cast(scale_arr, hpac.C.POINTER(hpac.C.c_double))), False),
+        "iact_persistent": (hpac.HYDRO_IACT, hpac.hpac_iact_knobs(
+            8, 32, 1e-3, 0, 0, hpac.C.cast(scale_arr, hpac.C.POINTER(hpac.C.c_double))), True),
+    }
+
+    def reset(persist):
+        for k, v in init.items():
+            Hy.t[k].copy_(v, non_blocking=True)
+        Hy.eos.set_persistent(persist)
+        Hy.eos.reset_state()
+
+    res = {}
+    ref_p = ref_q = None
+    for name, (tech, kn, persist) in variants.items():
+        times = []
+        for r in range(reps + 1):
+            reset(persist)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            hpac.hpac_hydro_run(Hy.state, Hy.eos._h, nsteps, tech, kn)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if r > 0:
+                times.append(e0.elapsed_time(e1))
+        p_fin, q_fin = Hy["p"].clone(), float(Hy["e"][0].item())
+        # approximation count: the same run with per-step counters (untimed)
+        reset(persist)
+        apx = 0
+        for s in range(nsteps):
+            st = hpac.hpac_hydro_step(Hy.state, Hy.eos._h, tech, kn, None, tech != hpac.HYDRO_EXACT)
+            apx += st.approximated if st is not None else 0
+        ms = float(np.median(times))
+        row = {"ms": ms, "approximated_fraction": apx / (E * nsteps)}
+        if name == "exact":
+            ref_p, ref_q = p_fin, q_fin
+        else:
+            rms = float(torch.sqrt(torch.mean(ref_p * ref_p)).item())
+            row["speedup_vs_exact"] = res["exact"]["ms"] / ms
+            row["qoi_rel_err"] = abs(q_fin - ref_q) / abs(ref_q)
+            row["p_nrmse"] = hpac.quality(ref_p, p_fin, hpac.HPAC_METRIC_RMSE, stream=stream)["value"] / rms
+        res[name] = row
+    Hy.eos.set_persistent(False)
+    Hy.close()
+    return {"mesh": f"{n}^3", "time_steps": nsteps, "logical_threads": E,
+            "knobs": {"taf": "h4 p8 0.5% (and h2 p4)", "iact": "t8 g32 1e-3 scaled"}, "runs": res}
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -585,6 +652,7 @@ def main(argv=None):
     ap.add_argument("--no-sweep", action="store_true")
     ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--no-hydro-large", action="store_true")
+    ap.add_argument("--no-persistent", action="store_true")
     args = ap.parse_args(argv)
     if args.impl == "reference":
         return run_reference(args)
@@ -775,6 +843,7 @@ def main(argv=None):
     sweep = None if args.no_sweep else bench_sweep(hpac, torch, dev, stream)
     surrogate = None if args.no_surrogate else bench_surrogate(hpac, torch, dev, stream)
     large = None if args.no_hydro_large else bench_hydro_large(hpac, torch, dev, stream)
+    persistent = None if args.no_persistent else bench_persistent(hpac, torch, dev, stream)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = hydro_cpu()
@@ -808,6 +877,7 @@ def main(argv=None):
             "sweep": sweep,
             "surrogate": surrogate,
             "hydro_large": large,
+            "persistent_state": persistent,
         }
         print(json.dumps(line))
     Hy.close()

@@ -181,6 +181,23 @@ hpac_status hpac_region_destroy(hpac_region *region);
 /* Change the stream later calls on the handle are enqueued on. */
 hpac_status hpac_region_set_stream(hpac_region *region, void *cuda_stream);
 
+/* Approximation state kept across calls. Not in the paper, whose TAF windows
+ * and iACT tables live in one kernel's shared memory (Section 3.1.1) and so
+ * restart at every launch. With enable = 1, every later TAF call on the region
+ * resumes each logical thread's window and owed predictions where its previous
+ * TAF call left them, and every iACT call resumes each logical warp's tables:
+ * a sequence of calls then behaves as one call over the concatenated
+ * iteration spaces (when each call's N is a multiple of T). The state lives in
+ * device memory owned by the region (TAF: hsize x T values + 8 bytes per
+ * logical thread; iACT: one table image per logical warp), allocated on first
+ * use, and starts empty whenever the technique or its shape (TAF hsize; iACT
+ * tsize, tperwarp) or T changes. enable = 0 frees it (after waiting for the
+ * region's stream). Calls on one region must not run concurrently. */
+hpac_status hpac_region_set_persistent(hpac_region *region, int32_t enable);
+
+/* Empty the kept state (asynchronous on the region's stream). */
+hpac_status hpac_region_reset_state(hpac_region *region);
+
 /* Accurate execution path: d_out[i] = region(d_in[:, i]) for all i < N
  * (the non-approximated region the paper's speedups are measured against). */
 hpac_status hpac_run_exact(hpac_region *region, const void *d_in, void *d_out);

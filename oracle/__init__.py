@@ -48,10 +48,12 @@ def lib() -> C.CDLL:
         L.orc_run_taf.argtypes = [RP, P, I32, I32, D, I32, I32, P, P, P, P]
         L.orc_run_iact.argtypes = [RP, P, I32, I32, D, I32, P, P, P, P, P]
         L.orc_replay_taf.argtypes = [RP, P, I32, I32, D, I32, I32, P, P, P, P, P]
+        L.orc_run_taf_persist.argtypes = [RP, P, I32, I32, D, I32, I32, P, P, P, P, P, P, P]
+        L.orc_run_iact_persist.argtypes = [RP, P, I32, I32, D, I32, P, P, P, P, P, P, P, P, P]
         L.orc_quality.argtypes = [I64, P, P, I32, P, P]
         L.orc_num_threads.restype = C.c_int
         for f in ("orc_run_exact", "orc_run_perfo", "orc_run_taf", "orc_replay_taf", "orc_run_iact",
-                  "orc_quality"):
+                  "orc_quality", "orc_run_taf_persist", "orc_run_iact_persist"):
             getattr(L, f).restype = C.c_int
         _hydro_bind(L)
         _lib = L
@@ -122,13 +124,34 @@ def run_perfo(kind, x, param, pkind, m=0, rate=0.0, seed=0, herded=1, threads=0,
     return out, mask, cnt
 
 
+def taf_state(T, hsize):
+    """Empty persistent TAF state of T logical threads (see run_taf)."""
+    return {"vals": np.zeros((hsize, T), dtype=np.float64), "cnt": np.zeros(T, dtype=np.int32),
+            "pred": np.zeros(T, dtype=np.int32)}
+
+
+def iact_state(T, tsize, tperwarp, D):
+    """Empty persistent iACT state: the tables of ceil(T/32) logical warps."""
+    g = ((T + 31) // 32) * tperwarp
+    return {"z": np.zeros((g, tsize, D), dtype=np.float32), "y": np.zeros((g, tsize), dtype=np.float64),
+            "valid": np.zeros((g, tsize), dtype=np.int32), "rr": np.zeros(g, dtype=np.int32)}
+
+
 def run_taf(kind, x, param, hsize, psize, thresh, level=THREAD, threads=0, block=256, n=None,
-            reset=False):
+            reset=False, state=None):
+    """TAF over the logical schedule; with state (taf_state), the windows and
+    owed predictions continue from the previous call and are updated in place."""
     r, x, n = _region(kind, x, n, param, threads, block)
     out = np.zeros(n, dtype=x.dtype)
     stat = np.zeros(n, dtype=x.dtype)
     mask = np.full(n, 255, dtype=np.uint8)
     cnt = np.zeros(4, dtype=np.int64)
+    if state is not None:
+        if lib().orc_run_taf_persist(C.byref(r), _ptr(x), hsize, psize, thresh, level, int(bool(reset)),
+                                     _ptr(state["vals"]), _ptr(state["cnt"]), _ptr(state["pred"]),
+                                     _ptr(out), _ptr(mask), _ptr(stat), _ptr(cnt)):
+            raise ValueError("oracle rejected TAF arguments")
+        return out, mask, stat, cnt
     if lib().orc_run_taf(C.byref(r), _ptr(x), hsize, psize, thresh, level, int(bool(reset)),
                          _ptr(out), _ptr(mask),
                          _ptr(stat), _ptr(cnt)):
@@ -158,13 +181,21 @@ def replay_taf(kind, x, param, hsize, psize, thresh, force, level=THREAD, thread
 
 
 def run_iact(kind, x, param, tsize, tperwarp, thresh, level=THREAD, in_scale=None, threads=0,
-             block=256, n=None):
+             block=256, n=None, state=None):
+    """iACT over the logical schedule; with state (iact_state), the tables
+    continue from the previous call and are updated in place."""
     r, x, n = _region(kind, x, n, param, threads, block)
     out = np.zeros(n, dtype=x.dtype)
     stat = np.zeros(n, dtype=x.dtype)
     mask = np.full(n, 255, dtype=np.uint8)
     cnt = np.zeros(4, dtype=np.int64)
     sc = None if in_scale is None else np.ascontiguousarray(in_scale, dtype=np.float64)
+    if state is not None:
+        if lib().orc_run_iact_persist(C.byref(r), _ptr(x), tsize, tperwarp, thresh, level, _ptr(sc),
+                                      _ptr(state["z"]), _ptr(state["y"]), _ptr(state["valid"]),
+                                      _ptr(state["rr"]), _ptr(out), _ptr(mask), _ptr(stat), _ptr(cnt)):
+            raise ValueError("oracle rejected iACT arguments")
+        return out, mask, stat, cnt
     if lib().orc_run_iact(C.byref(r), _ptr(x), tsize, tperwarp, thresh, level, _ptr(sc),
                           _ptr(out), _ptr(mask), _ptr(stat), _ptr(cnt)):
         raise ValueError("oracle rejected iACT arguments")

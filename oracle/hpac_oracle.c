@@ -291,7 +291,8 @@ static int is_borderline(double s, double thr) {
  * approximates where no prediction can be owed, or breaks a prediction run). */
 static int taf_core(const orc_region *R, const void *in, int32_t hsize, int32_t psize, double thr,
                     int32_t level, int32_t reset, const uint8_t *force, void *out, uint8_t *mask, void *stat,
-                    uint8_t *disagree, int64_t *counters, int64_t *counts) {
+                    uint8_t *disagree, int64_t *counters, int64_t *counts, double *st_vals,
+                    int32_t *st_cnt, int32_t *st_pred) {
   if (check_region(R)) return 1;
   if (hsize < 1 || hsize > 64 || psize < 0 || !(thr >= 0.0)) return 1;
   if (level < ORC_THREAD || level > ORC_BLOCK || (reset != 0 && reset != 1)) return 1;
@@ -316,6 +317,14 @@ static int taf_core(const orc_region *R, const void *in, int32_t hsize, int32_t 
     int *own = (int *)calloc(B, sizeof(int));     /* the oracle's own decision */
     float wf[64];
     double wd[64];
+    if (st_cnt) /* persistent state: each logical thread resumes where it stopped */
+      for (int l = 0; l < B && b * B + l < T; ++l) {
+        int64_t t = b * B + l;
+        cnt[l] = st_cnt[t];
+        pred[l] = st_pred[t];
+        head[l] = 0;
+        for (int j = 0; j < cnt[l]; ++j) win[(size_t)l * h + j] = st_vals[(int64_t)j * T + t];
+      }
     for (int64_t k = 0; b * B + k * T < N; ++k) {
       /* phase 1: per-thread path */
       for (int l = 0; l < B; ++l) {
@@ -412,6 +421,14 @@ static int taf_core(const orc_region *R, const void *in, int32_t hsize, int32_t 
         if (mask_yes && psize == 0) n_bad++;
       }
     }
+    if (st_cnt)
+      for (int l = 0; l < B && b * B + l < T; ++l) {
+        int64_t t = b * B + l;
+        st_cnt[t] = cnt[l];
+        st_pred[t] = (int32_t)pred[l];
+        for (int j = 0; j < cnt[l]; ++j)
+          st_vals[(int64_t)j * T + t] = win[(size_t)l * h + (head[l] + j) % h];
+      }
     free(win); free(head); free(cnt); free(pred); free(act); free(decided); free(wants); free(own);
   }
   if (counters) {
@@ -432,7 +449,21 @@ int orc_run_taf(const orc_region *R, const void *in, int32_t hsize, int32_t psiz
                 int32_t level, int32_t reset, void *out, uint8_t *mask, void *stat,
                 int64_t *counters) {
   return taf_core(R, in, hsize, psize, thr, level, reset, NULL, out, mask, stat, NULL, counters,
-                  NULL);
+                  NULL, NULL, NULL, NULL);
+}
+
+/* TAF with state kept across calls (not in the paper, whose state is scoped to
+ * one kernel, Section 3.1.1): per logical thread t the window (st_vals[j*T + t],
+ * oldest first, j < st_cnt[t]) and the predictions still owed (st_pred[t]) are
+ * read at the start and written back at the end. Zeroed arrays are the empty
+ * state of a first call. */
+int orc_run_taf_persist(const orc_region *R, const void *in, int32_t hsize, int32_t psize,
+                        double thr, int32_t level, int32_t reset, double *st_vals,
+                        int32_t *st_cnt, int32_t *st_pred, void *out, uint8_t *mask, void *stat,
+                        int64_t *counters) {
+  if (!st_vals || !st_cnt || !st_pred) return 1;
+  return taf_core(R, in, hsize, psize, thr, level, reset, NULL, out, mask, stat, NULL, counters,
+                  NULL, st_vals, st_cnt, st_pred);
 }
 
 /* Replay of a TAF run along a given mask (see taf_core). */
@@ -441,7 +472,7 @@ int orc_replay_taf(const orc_region *R, const void *in, int32_t hsize, int32_t p
                    uint8_t *disagree, int64_t *counts) {
   if (!force) return 1;
   return taf_core(R, in, hsize, psize, thr, level, reset, force, out, NULL, stat, disagree, NULL,
-                  counts);
+                  counts, NULL, NULL, NULL);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -475,9 +506,10 @@ static float scaled_input(const orc_region *R, const void *in, const double *sca
  *           exactly, the one farthest from the table (largest d, +inf for an
  *           empty table; ties to the lowest lane) stores (z, y) in the
  *           round-robin slot, which then advances. One write per table per step. */
-int orc_run_iact(const orc_region *R, const void *in, int32_t tsize, int32_t tperwarp,
-                 double thr, int32_t level, const double *in_scale, void *out, uint8_t *mask,
-                 void *stat, int64_t *counters) {
+static int iact_core(const orc_region *R, const void *in, int32_t tsize, int32_t tperwarp,
+                     double thr, int32_t level, const double *in_scale, void *out, uint8_t *mask,
+                     void *stat, int64_t *counters, float *st_z, double *st_y, int32_t *st_valid,
+                     int32_t *st_rr) {
   if (check_region(R)) return 1;
   if (tsize < 1 || tsize > 64 || !(thr >= 0.0)) return 1;
   if (tperwarp < 1 || tperwarp > 32 || 32 % tperwarp != 0) return 1;
@@ -503,6 +535,22 @@ int orc_run_iact(const orc_region *R, const void *in, int32_t tsize, int32_t tpe
     float *dmin = (float *)calloc(B, sizeof(float));
     float *z = (float *)calloc((size_t)B * D, sizeof(float));
     double *yv = (double *)calloc(B, sizeof(double));
+    /* persistent state: the tables of logical warp w are st_*[w][table][slot] */
+    const int64_t nwarps = (T + 31) / 32;
+    if (st_rr)
+      for (int tab = 0; tab < ntab; ++tab) {
+        int64_t w = (b * B) / 32 + tab / tperwarp;
+        if (w >= nwarps) break;
+        int64_t g = w * tperwarp + tab % tperwarp;
+        rr[tab] = st_rr[g];
+        for (int j = 0; j < tsize; ++j) {
+          size_t s = (size_t)tab * tsize + j;
+          int64_t gs = g * tsize + j;
+          tvalid[s] = st_valid[gs];
+          ty[s] = st_y[gs];
+          for (int d = 0; d < D; ++d) tz[s * D + d] = st_z[gs * D + d];
+        }
+      }
     for (int64_t k = 0; b * B + k * T < N; ++k) {
       /* read phase */
       for (int l = 0; l < B; ++l) {
@@ -583,6 +631,20 @@ int orc_run_iact(const orc_region *R, const void *in, int32_t tsize, int32_t tpe
         rr[tab] = (rr[tab] + 1) % tsize;
       }
     }
+    if (st_rr)
+      for (int tab = 0; tab < ntab; ++tab) {
+        int64_t w = (b * B) / 32 + tab / tperwarp;
+        if (w >= nwarps) break;
+        int64_t g = w * tperwarp + tab % tperwarp;
+        st_rr[g] = rr[tab];
+        for (int j = 0; j < tsize; ++j) {
+          size_t s = (size_t)tab * tsize + j;
+          int64_t gs = g * tsize + j;
+          st_valid[gs] = tvalid[s];
+          st_y[gs] = ty[s];
+          for (int d = 0; d < D; ++d) st_z[gs * D + d] = tz[s * D + d];
+        }
+      }
     free(tz); free(ty); free(tvalid); free(rr); free(act); free(has); free(wants);
     free(apx); free(near); free(dmin); free(z); free(yv);
   }
@@ -593,6 +655,27 @@ int orc_run_iact(const orc_region *R, const void *in, int32_t tsize, int32_t tpe
     counters[3] = border_total;
   }
   return 0;
+}
+
+int orc_run_iact(const orc_region *R, const void *in, int32_t tsize, int32_t tperwarp,
+                 double thr, int32_t level, const double *in_scale, void *out, uint8_t *mask,
+                 void *stat, int64_t *counters) {
+  return iact_core(R, in, tsize, tperwarp, thr, level, in_scale, out, mask, stat, counters, NULL,
+                   NULL, NULL, NULL);
+}
+
+/* iACT with the tables kept across calls (not in the paper, Section 3.1.1
+ * scopes them to one kernel): for logical warp w and its table j (g = w *
+ * tperwarp + j), slot s holds st_z[(g*tsize + s)*D + d], st_y[g*tsize + s] and
+ * st_valid[g*tsize + s]; st_rr[g] is the round-robin slot. Read at the start,
+ * written back at the end; zeroed arrays are the empty state. */
+int orc_run_iact_persist(const orc_region *R, const void *in, int32_t tsize, int32_t tperwarp,
+                         double thr, int32_t level, const double *in_scale, float *st_z,
+                         double *st_y, int32_t *st_valid, int32_t *st_rr, void *out,
+                         uint8_t *mask, void *stat, int64_t *counters) {
+  if (!st_z || !st_y || !st_valid || !st_rr) return 1;
+  return iact_core(R, in, tsize, tperwarp, thr, level, in_scale, out, mask, stat, counters, st_z,
+                   st_y, st_valid, st_rr);
 }
 
 /* ------------------------------------------------------------------------ */

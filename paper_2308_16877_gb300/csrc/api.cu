@@ -97,6 +97,32 @@ static hpac_status end_counters(hpac_region *r, hpac_stats *h, int64_t skipped_k
 
 }  // namespace hpac
 
+namespace hpac {
+
+hpac_status region_state(hpac_region *r, const int64_t (&key)[6], size_t bytes, void **out) {
+  *out = nullptr;
+  if (!r->persist) return HPAC_OK;
+  if (r->d_state && r->state_bytes == bytes && memcmp(r->state_key, key, sizeof(key)) == 0) {
+    *out = r->d_state;
+    return HPAC_OK;
+  }
+  // a new shape: the previous state cannot continue, start empty
+  if (r->d_state) {
+    HPAC_CUDA_TRY(cudaStreamSynchronize(r->stream));
+    HPAC_CUDA_TRY(cudaFree(r->d_state));
+    r->d_state = nullptr;
+    r->state_bytes = 0;
+  }
+  HPAC_CUDA_TRY(cudaMalloc(&r->d_state, bytes));
+  r->state_bytes = bytes;
+  memcpy(r->state_key, key, sizeof(key));
+  HPAC_CUDA_TRY(cudaMemsetAsync(r->d_state, 0, bytes, r->stream));
+  *out = r->d_state;
+  return HPAC_OK;
+}
+
+}  // namespace hpac
+
 using namespace hpac;
 
 extern "C" {
@@ -128,9 +154,33 @@ hpac_status hpac_region_destroy(hpac_region *r) {
   if (!r) return HPAC_OK;
   cudaError_t e = cudaStreamSynchronize(r->stream);
   cudaError_t f = cudaFree(r->d_counters);
+  if (r->d_state) {
+    const cudaError_t g = cudaFree(r->d_state);
+    if (f == cudaSuccess) f = g;
+  }
   free(r);
   if (e != cudaSuccess) return cuda_error(e, "hpac_region_destroy: stream");
   if (f != cudaSuccess) return cuda_error(f, "hpac_region_destroy: free");
+  return HPAC_OK;
+}
+
+hpac_status hpac_region_set_persistent(hpac_region *r, int32_t enable) {
+  if (!r) return set_error(HPAC_EINVAL, "region is NULL");
+  if (enable != 0 && enable != 1) return set_error(HPAC_EINVAL, "enable %d not 0 or 1", enable);
+  if (!enable && r->d_state) {
+    HPAC_CUDA_TRY(cudaStreamSynchronize(r->stream));
+    HPAC_CUDA_TRY(cudaFree(r->d_state));
+    r->d_state = nullptr;
+    r->state_bytes = 0;
+    memset(r->state_key, 0, sizeof(r->state_key));
+  }
+  r->persist = enable;
+  return HPAC_OK;
+}
+
+hpac_status hpac_region_reset_state(hpac_region *r) {
+  if (!r) return set_error(HPAC_EINVAL, "region is NULL");
+  if (r->d_state) HPAC_CUDA_TRY(cudaMemsetAsync(r->d_state, 0, r->state_bytes, r->stream));
   return HPAC_OK;
 }
 

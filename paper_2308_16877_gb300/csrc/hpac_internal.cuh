@@ -11,6 +11,10 @@ struct hpac_region {
   cudaStream_t stream;
   int device;
   unsigned long long *d_counters;  // [0] approximated, [1] borderline
+  int persist;                     // TAF windows / iACT tables kept across calls
+  void *d_state;                   // their device copy (region-owned)
+  size_t state_bytes;
+  int64_t state_key[6];            // technique and shape the copy holds
 };
 
 namespace hpac {
@@ -34,10 +38,17 @@ inline int64_t logical_threads(const hpac_region_desc &d) {
 hpac_status launch_exact(const hpac_region *r, const void *in, void *out);
 hpac_status launch_perfo(const hpac_region *r, const hpac_perfo_knobs *k, const void *in, void *out,
                          uint8_t *mask, unsigned long long *counters);
-hpac_status launch_taf(const hpac_region *r, const hpac_taf_knobs *k, const void *in, void *out,
+hpac_status launch_taf(hpac_region *r, const hpac_taf_knobs *k, const void *in, void *out,
                        uint8_t *mask, void *stat, unsigned long long *counters);
-hpac_status launch_iact(const hpac_region *r, const hpac_iact_knobs *k, const void *in, void *out,
+hpac_status launch_iact(hpac_region *r, const hpac_iact_knobs *k, const void *in, void *out,
                         uint8_t *mask, void *stat, unsigned long long *counters);
+
+// The persistent state buffer of a TAF or iACT run: nullptr when the region
+// keeps no state; otherwise a zeroed buffer of `bytes` the first time a shape
+// (key) is seen, the previous run's buffer when the key repeats.
+hpac_status region_state(hpac_region *r, const int64_t (&key)[6], size_t bytes, void **out);
+
+inline size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 // Largest dynamic shared memory a block of this device may use.
 int max_dyn_smem(int device);

@@ -171,15 +171,16 @@ __global__ void __launch_bounds__(256) node_kernel(hpac_hydro_state s) {
           if (ei < 0 || ej < 0 || ek < 0 || ei >= n || ej >= n || ek >= n) continue;
           const int64_t el = (ek * n + ej) * n + ei;
           const int c = di + 2 * dj + 4 * dk;  // corner of this node in element el
-          const double pq = (s.p[el] + s.q[el]) * (1.0 / 12.0);
+          const double pq = s.p[el] + s.q[el];
           fx = fma(pq, s.grad[(0 * 8 + c) * E + el], fx);
           fy = fma(pq, s.grad[(1 * 8 + c) * E + el], fy);
           fz = fma(pq, s.grad[(2 * 8 + c) * E + el], fz);
         }
-    const double inv_m = 1.0 / s.mnode[nd];
-    double un = s.u[nd] + dt * fx * inv_m;
-    double vn = s.v[nd] + dt * fy * inv_m;
-    double wn = s.w[nd] + dt * fz * inv_m;
+    // the stored gradients are 12 dV/dx: the 1/12 joins dt / m in one factor
+    const double sc = dt * (1.0 / 12.0) / s.mnode[nd];
+    double un = fma(fx, sc, s.u[nd]);
+    double vn = fma(fy, sc, s.v[nd]);
+    double wn = fma(fz, sc, s.w[nd]);
     if (i == 0) un = 0.0;
     if (j == 0) vn = 0.0;
     if (k == 0) wn = 0.0;
@@ -229,11 +230,11 @@ __global__ void __launch_bounds__(128) elem_kernel(hpac_hydro_state s) {
 
 __global__ void __launch_bounds__(256) finalize_kernel(hpac_hydro_state s) {
   const int64_t E = (int64_t)s.n * s.n * s.n;
-  const double gm1 = s.gamma - 1.0;
+  const double inv_gm1 = 1.0 / (s.gamma - 1.0);  // one division per launch, not per element
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < E;
        e += (int64_t)gridDim.x * blockDim.x) {
     const double v1 = s.eos_in[E + e];
-    s.e[e] = s.p[e] * v1 / gm1;
+    s.e[e] = s.p[e] * v1 * inv_gm1;
     s.vrel[e] = v1;
   }
 }

@@ -56,7 +56,8 @@ __global__ void __launch_bounds__(1024) iact_kernel(R reg, const typename R::T *
                                                     uint8_t *__restrict__ mask,
                                                     typename R::T *__restrict__ stat, int64_t n,
                                                     int64_t T, IactParams P,
-                                                    unsigned long long *__restrict__ counters) {
+                                                    unsigned long long *__restrict__ counters,
+                                                    uint32_t *__restrict__ st) {
   using V = typename R::T;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ unsigned long long s_cnt[2];
@@ -74,7 +75,15 @@ __global__ void __launch_bounds__(1024) iact_kernel(R reg, const typename R::T *
   W.y = reinterpret_cast<V *>(base + zb);
   W.filled = reinterpret_cast<int *>(base + zb + (size_t)tsize * g * sizeof(V));
   W.rr = W.filled + g;
-  if (lane < g) {
+  // logical warp of this physical warp; with persistent state (st, one table
+  // image of wbytes per logical warp) its tables resume from the last call
+  const int64_t gwarp = ((int64_t)blockIdx.x * blockDim.x) / 32 + warp;
+  const bool has_state = st != nullptr && gwarp * 32 < T;
+  uint32_t *wst = has_state ? st + (size_t)gwarp * (wbytes / 4) : nullptr;
+  if (has_state) {
+    uint32_t *dst = reinterpret_cast<uint32_t *>(base);
+    for (size_t q = lane; q < wbytes / 4; q += 32) dst[q] = wst[q];
+  } else if (lane < g) {
     W.filled[lane] = 0;
     W.rr[lane] = 0;
   }
@@ -186,6 +195,11 @@ __global__ void __launch_bounds__(1024) iact_kernel(R reg, const typename R::T *
       __syncwarp();
     }
   }
+  if (has_state) {  // save this warp's tables for the next call
+    __syncwarp();
+    const uint32_t *src = reinterpret_cast<const uint32_t *>(base);
+    for (size_t q = lane; q < wbytes / 4; q += 32) wst[q] = src[q];
+  }
   warp_count(s_cnt, n_apx, n_border);
   __syncthreads();
   if (counters && threadIdx.x == 0) {
@@ -195,7 +209,7 @@ __global__ void __launch_bounds__(1024) iact_kernel(R reg, const typename R::T *
 }
 
 template <class R>
-hpac_status launch(const hpac_region *r, R reg, const hpac_iact_knobs *k, const void *in, void *out,
+hpac_status launch(hpac_region *r, R reg, const hpac_iact_knobs *k, const void *in, void *out,
                    uint8_t *mask, void *stat, unsigned long long *counters) {
   using V = typename R::T;
   const hpac_region_desc &d = r->d;
@@ -224,6 +238,12 @@ hpac_status launch(const hpac_region *r, R reg, const hpac_iact_knobs *k, const 
   const size_t smem = (size_t)(B / 32) * wbytes;
   if (smem > (size_t)limit)
     return set_error(HPAC_EUNSUPPORTED, "iACT tables of %zu bytes per block exceed %d", smem, limit);
+  // persistent state: one image of a warp's tables per logical warp
+  const int64_t key[6] = {2, P.tsize, P.g, P.D, T, (int64_t)sizeof(V)};
+  void *stv = nullptr;
+  hpac_status ss = region_state(r, key, (size_t)((T + 31) / 32) * wbytes, &stv);
+  if (ss != HPAC_OK) return ss;
+  uint32_t *st_words = static_cast<uint32_t *>(stv);
   const int64_t blocks = (T + B - 1) / B;
   if (blocks > 0x7fffffffLL) return set_error(HPAC_EINVAL, "too many logical threads");
   V *o = static_cast<V *>(out);
@@ -234,19 +254,22 @@ hpac_status launch(const hpac_region *r, R reg, const hpac_iact_knobs *k, const 
     case HPAC_LEVEL_THREAD: {
       auto fn = counters ? iact_kernel<R, HPAC_LEVEL_THREAD, kDC, true> : iact_kernel<R, HPAC_LEVEL_THREAD, kDC, false>;
       HPAC_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      fn<<<(unsigned)blocks, B, smem, r->stream>>>(reg, x, d.in_stride, o, mask, st, d.n, T, P, counters);
+      fn<<<(unsigned)blocks, B, smem, r->stream>>>(reg, x, d.in_stride, o, mask, st, d.n, T, P, counters,
+                                                   st_words);
       break;
     }
     case HPAC_LEVEL_WARP: {
       auto fn = counters ? iact_kernel<R, HPAC_LEVEL_WARP, kDC, true> : iact_kernel<R, HPAC_LEVEL_WARP, kDC, false>;
       HPAC_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      fn<<<(unsigned)blocks, B, smem, r->stream>>>(reg, x, d.in_stride, o, mask, st, d.n, T, P, counters);
+      fn<<<(unsigned)blocks, B, smem, r->stream>>>(reg, x, d.in_stride, o, mask, st, d.n, T, P, counters,
+                                                   st_words);
       break;
     }
     default: {
       auto fn = counters ? iact_kernel<R, HPAC_LEVEL_BLOCK, kDC, true> : iact_kernel<R, HPAC_LEVEL_BLOCK, kDC, false>;
       HPAC_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      fn<<<(unsigned)blocks, B, smem, r->stream>>>(reg, x, d.in_stride, o, mask, st, d.n, T, P, counters);
+      fn<<<(unsigned)blocks, B, smem, r->stream>>>(reg, x, d.in_stride, o, mask, st, d.n, T, P, counters,
+                                                   st_words);
       break;
     }
   }
@@ -258,7 +281,7 @@ hpac_status launch(const hpac_region *r, R reg, const hpac_iact_knobs *k, const 
 // D inputs for the distance; the kernel loads them regardless of kReads.
 }  // namespace
 
-hpac_status launch_iact(const hpac_region *r, const hpac_iact_knobs *k, const void *in, void *out,
+hpac_status launch_iact(hpac_region *r, const hpac_iact_knobs *k, const void *in, void *out,
                         uint8_t *mask, void *stat, unsigned long long *counters) {
   const hpac_region_desc &d = r->d;
   switch (d.kind) {

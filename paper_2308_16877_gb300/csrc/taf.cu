@@ -29,7 +29,10 @@ __global__ void __launch_bounds__(1024) taf_kernel(R reg, const typename R::T *_
                                                    int64_t T, int h, int p,
                                                    typename R::T thr, int thr_inf, double thr_d,
                                                    int reset_on_exit,
-                                                   unsigned long long *__restrict__ counters) {
+                                                   unsigned long long *__restrict__ counters,
+                                                   typename R::T *__restrict__ st_vals,
+                                                   int *__restrict__ st_cnt,
+                                                   int *__restrict__ st_pred) {
   using V = typename R::T;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ unsigned long long s_cnt[2];
@@ -55,6 +58,19 @@ __global__ void __launch_bounds__(1024) taf_kernel(R reg, const typename R::T *_
   int cnt = 0;   // filled slots
   int pred = 0;  // predictions still owed
   unsigned long long n_apx = 0, n_border = 0;
+  // persistent state (st_vals[j * T + t], oldest first, j < cnt): resume
+  if (st_cnt && t < T) {
+    cnt = st_cnt[t];
+    pred = st_pred[t];
+    if (KH > 0) {
+#pragma unroll
+      for (int j = 0; j < (KH > 0 ? KH : 1); ++j)
+        if (j >= KH - cnt) w[j] = st_vals[(int64_t)(j - (KH - cnt)) * T + t];
+    } else {
+      for (int j = 0; j < cnt; ++j) win[j * ld + threadIdx.x] = st_vals[(int64_t)j * T + t];
+      pos = cnt == h ? 0 : cnt;
+    }
+  }
 
   if (t_lead < T) {
     int k3 = 0;  // step index mod 3 (block-level tally buffer)
@@ -128,6 +144,21 @@ __global__ void __launch_bounds__(1024) taf_kernel(R reg, const typename R::T *_
       }
     }
   }
+  if (st_cnt && t < T) {  // persistent state: save where this thread stopped
+    st_cnt[t] = cnt;
+    st_pred[t] = pred;
+    if (KH > 0) {
+#pragma unroll
+      for (int j = 0; j < (KH > 0 ? KH : 1); ++j)
+        if (j >= KH - cnt) st_vals[(int64_t)(j - (KH - cnt)) * T + t] = w[j];
+    } else {
+      const int oldest = pos - cnt < 0 ? pos - cnt + h : pos - cnt;
+      for (int j = 0; j < cnt; ++j) {
+        const int slot = oldest + j >= h ? oldest + j - h : oldest + j;
+        st_vals[(int64_t)j * T + t] = win[slot * ld + threadIdx.x];
+      }
+    }
+  }
   warp_count(s_cnt, n_apx, n_border);
   __syncthreads();
   if (counters && threadIdx.x == 0) {
@@ -137,12 +168,22 @@ __global__ void __launch_bounds__(1024) taf_kernel(R reg, const typename R::T *_
 }
 
 template <class R>
-hpac_status launch(const hpac_region *r, R reg, const hpac_taf_knobs *k, const void *in, void *out,
+hpac_status launch(hpac_region *r, R reg, const hpac_taf_knobs *k, const void *in, void *out,
                    uint8_t *mask, void *stat, unsigned long long *counters) {
   using V = typename R::T;
   const hpac_region_desc &d = r->d;
   if (d.n == 0) return HPAC_OK;
   const int64_t T = logical_threads(d);
+  // persistent state: window values [h][T], then counts [T] and owed predictions [T]
+  const size_t b_vals = align256((size_t)k->hsize * T * sizeof(V)), b_int = align256((size_t)T * 4);
+  const int64_t key[6] = {1, k->hsize, T, (int64_t)sizeof(V), 0, 0};
+  void *sbuf = nullptr;
+  hpac_status ss = region_state(r, key, b_vals + 2 * b_int, &sbuf);
+  if (ss != HPAC_OK) return ss;
+  char *sb = static_cast<char *>(sbuf);
+  V *st_vals = reinterpret_cast<V *>(sb);
+  int *st_cnt = sb ? reinterpret_cast<int *>(sb + b_vals) : nullptr;
+  int *st_pred = sb ? reinterpret_cast<int *>(sb + b_vals + b_int) : nullptr;
   const int B = d.block_threads;
   const int h = k->hsize;
   const int kh = (h == 2 || h == 4 || h == 8) ? h : 0;  // register-window sizes
@@ -170,14 +211,15 @@ hpac_status launch(const hpac_region *r, R reg, const hpac_taf_knobs *k, const v
   if (smem > 0)
     HPAC_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   fn<<<(unsigned)blocks, B, smem, r->stream>>>(reg, x, d.in_stride, o, mask, st, d.n, T, h, k->psize,
-                                               thr, thr_inf, k->thresh, k->reset_on_exit, counters);
+                                               thr, thr_inf, k->thresh, k->reset_on_exit, counters,
+                                               st_vals, st_cnt, st_pred);
   HPAC_CUDA_TRY(cudaGetLastError());
   return HPAC_OK;
 }
 
 }  // namespace
 
-hpac_status launch_taf(const hpac_region *r, const hpac_taf_knobs *k, const void *in, void *out,
+hpac_status launch_taf(hpac_region *r, const hpac_taf_knobs *k, const void *in, void *out,
                        uint8_t *mask, void *stat, unsigned long long *counters) {
   const hpac_region_desc &d = r->d;
   switch (d.kind) {

@@ -97,6 +97,8 @@ SIGNATURES = {
     "hpac_region_create": (C.c_int, [C.POINTER(hpac_region_desc), _P, C.POINTER(_P)]),
     "hpac_region_destroy": (C.c_int, [_P]),
     "hpac_region_set_stream": (C.c_int, [_P, _P]),
+    "hpac_region_set_persistent": (C.c_int, [_P, C.c_int32]),
+    "hpac_region_reset_state": (C.c_int, [_P]),
     "hpac_run_exact": (C.c_int, [_P, _P, _P]),
     "hpac_run_perfo": (C.c_int, [_P, C.POINTER(hpac_perfo_knobs), _P, _P, _P, C.POINTER(hpac_stats)]),
     "hpac_run_taf": (C.c_int, [_P, C.POINTER(hpac_taf_knobs), _P, _P, _P, _P, C.POINTER(hpac_stats)]),
@@ -192,6 +194,14 @@ def hpac_region_create(desc: hpac_region_desc, stream: int | None):
 
 def hpac_region_destroy(h):
     _check(load().hpac_region_destroy(h), "hpac_region_destroy")
+
+
+def hpac_region_set_persistent(h, enable):
+    _check(load().hpac_region_set_persistent(h, int(bool(enable))), "hpac_region_set_persistent")
+
+
+def hpac_region_reset_state(h):
+    _check(load().hpac_region_reset_state(h), "hpac_region_reset_state")
 
 
 def hpac_region_set_stream(h, stream):
@@ -339,6 +349,13 @@ class Region:
 
     def set_stream(self, stream):
         hpac_region_set_stream(self._h, _stream_handle(stream))
+
+    def set_persistent(self, enable=True):
+        """Keep TAF windows / iACT tables across calls (see hpac.h)."""
+        hpac_region_set_persistent(self._h, enable)
+
+    def reset_state(self):
+        hpac_region_reset_state(self._h)
 
     def _check_io(self, x, out, mask=None, stat=None):
         if x.dtype != self.dtype or out.dtype != self.dtype:
