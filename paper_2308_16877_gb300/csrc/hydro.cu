@@ -228,9 +228,10 @@ __global__ void __launch_bounds__(128) elem_kernel(hpac_hydro_state s) {
   }
 }
 
-__global__ void __launch_bounds__(256) finalize_kernel(hpac_hydro_state s) {
+// inv_gm1 = 1 / (gamma - 1), formed once on the host: a double division per
+// thread would cost more than the element update itself.
+__global__ void __launch_bounds__(256) finalize_kernel(hpac_hydro_state s, double inv_gm1) {
   const int64_t E = (int64_t)s.n * s.n * s.n;
-  const double inv_gm1 = 1.0 / (s.gamma - 1.0);  // one division per launch, not per element
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < E;
        e += (int64_t)gridDim.x * blockDim.x) {
     const double v1 = s.eos_in[E + e];
@@ -307,7 +308,7 @@ extern "C" hpac_status hpac_hydro_finalize(const hpac_hydro_state *s, void *cuda
   int dev = 0;
   HPAC_CUDA_TRY(cudaGetDevice(&dev));
   const int64_t E = (int64_t)s->n * s->n * s->n;
-  finalize_kernel<<<grid_for(E, 256, dev), 256, 0, (cudaStream_t)cuda_stream>>>(*s);
+  finalize_kernel<<<grid_for(E, 256, dev), 256, 0, (cudaStream_t)cuda_stream>>>(*s, 1.0 / (s->gamma - 1.0));
   HPAC_CUDA_TRY(cudaGetLastError());
   return HPAC_OK;
 }
