@@ -344,6 +344,73 @@ def bench_sweep(hpac, torch, dev, stream, baseline=True):
     return out
 
 
+def bench_search(hpac, torch, dev, stream, bound=0.01, reps=5):
+    """Genetic knob search (population 32, 12 generations: 384 evaluations, one
+    sweep launch per generation) against the exhaustive 256-configuration grid
+    on the same 32 Black-Scholes regions: the best feasible saved share (TAF
+    predictions + perforated invocations over all invocations at normalised
+    RMSE <= bound) of each, and the measured speedup of each best configuration
+    over the exact kernel through the region API, summed over the regions."""
+    from paper_2308_16877_gb300 import search as S
+    sizes = W.sweep_region_sizes()
+    x, regions = W.sweep_inputs(sizes)
+    xd = torch.from_numpy(x).to(dev)
+    x64 = xd.double().contiguous()
+    ref = torch.zeros(x.shape[1], dtype=torch.float64, device=dev)
+    with hpac.Region(hpac.HPAC_REGION_BLACKSCHOLES, x64, param=W.BS_RATE, stream=stream) as R:
+        R.run_exact(x64, ref)
+    del x64
+    t0 = time.perf_counter()
+    ev = S.sweep_evaluator(hpac, regions, xd, ref, W.BS_RATE, stream=stream)
+    best, best_r, hist = S.genetic_search(ev, bound=bound)
+    torch.cuda.synchronize()
+    search_s = time.perf_counter() - t0
+    grid = W.sweep_configs()
+    t0 = time.perf_counter()
+    gev = S.sweep_evaluator(hpac, regions, xd, ref, W.BS_RATE, stream=stream)
+    gres = gev(grid)
+    grid_s = time.perf_counter() - t0
+    gi = max(range(len(grid)), key=lambda i: S.score(*gres[i], bound))
+
+    regs = []
+    for (n, off, T) in regions:
+        xs = xd[:, off:off + n].contiguous()
+        regs.append((hpac.Region(hpac.HPAC_REGION_BLACKSCHOLES, xs, param=W.BS_RATE, logical_threads=T,
+                                 stream=stream), xs, torch.zeros(n, dtype=torch.float32, device=dev)))
+
+    def call(cfg):
+        for R, xs, o in regs:
+            if cfg is None:
+                R.run_exact(xs, o)
+            elif cfg["tech"] == "taf":
+                R.run_taf(xs, o, cfg["hsize"], cfg["psize"], cfg["thresh"], 0)
+            else:
+                R.run_perfo(xs, o, cfg["kind"], cfg["m"], cfg.get("rate", 0.0), cfg.get("seed", 0),
+                            bool(cfg["herded"]))
+
+    def timed(cfg):
+        call(cfg)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            call(cfg)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    exact_ms = timed(None)
+    s_ms, g_ms = timed(best), timed(grid[gi])
+    for R, *_ in regs:
+        R.close()
+    return {"bound_nrmse": bound, "evaluations": ev.calls["configs"], "launches": ev.calls["launches"],
+            "search_s": search_s, "grid_s": grid_s,
+            "search_best": {"config": best, "saved": best_r[0], "nrmse": best_r[1],
+                            "speedup_vs_exact": exact_ms / s_ms},
+            "grid_best": {"config": grid[gi], "saved": gres[gi][0], "nrmse": gres[gi][1],
+                          "speedup_vs_exact": exact_ms / g_ms},
+            "history_best_saved": hist, "exact_ms_all_regions": exact_ms}
+
+
 def calibrate_floor(pred, exact, target=0.01, q=0.99):
     """Smallest price floor tau such that, among predictions >= tau, the q-th
     quantile of the relative error |pred - exact| / |exact| is at most target."""
@@ -653,6 +720,7 @@ def main(argv=None):
     ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--no-hydro-large", action="store_true")
     ap.add_argument("--no-persistent", action="store_true")
+    ap.add_argument("--no-search", action="store_true")
     args = ap.parse_args(argv)
     if args.impl == "reference":
         return run_reference(args)
@@ -841,6 +909,7 @@ def main(argv=None):
 
     bs = None if args.no_blackscholes else bench_blackscholes(hpac, torch, dev, stream)
     sweep = None if args.no_sweep else bench_sweep(hpac, torch, dev, stream)
+    knob_search = None if args.no_search else bench_search(hpac, torch, dev, stream)
     surrogate = None if args.no_surrogate else bench_surrogate(hpac, torch, dev, stream)
     large = None if args.no_hydro_large else bench_hydro_large(hpac, torch, dev, stream)
     persistent = None if args.no_persistent else bench_persistent(hpac, torch, dev, stream)
@@ -875,6 +944,7 @@ def main(argv=None):
             "quality": quality,
             "blackscholes": bs,
             "sweep": sweep,
+            "search": knob_search,
             "surrogate": surrogate,
             "hydro_large": large,
             "persistent_state": persistent,
