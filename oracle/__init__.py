@@ -18,7 +18,8 @@ import numpy as np
 
 from . import build as _build
 
-BLACKSCHOLES, EOS, IDENTITY = 0, 1, 3
+BLACKSCHOLES, EOS, IDENTITY, BINOMIAL = 0, 1, 3, 4
+BINOMIAL_STEPS = 512         # default tree depth of the Binomial region
 F32, F64 = 0, 1
 THREAD, WARP, BLOCK = 0, 1, 2
 SMALL, LARGE, INI, FINI, RANDOM = 0, 1, 2, 3, 4
@@ -30,7 +31,7 @@ class Region(C.Structure):
     _fields_ = [("kind", C.c_int32), ("dtype", C.c_int32), ("n", C.c_int64),
                 ("n_in", C.c_int32), ("n_out", C.c_int32), ("in_stride", C.c_int64),
                 ("out_stride", C.c_int64), ("threads", C.c_int64), ("block", C.c_int32),
-                ("param", C.c_double)]
+                ("param", C.c_double), ("arg", C.c_int32), ("pad", C.c_int32)]
 
 
 _lib = None
@@ -87,14 +88,16 @@ def num_threads() -> int:
     return int(lib().orc_num_threads())
 
 
-def _region(kind, x, n, param, threads, block):
+def _region(kind, x, n, param, threads, block, arg=0):
     x = np.ascontiguousarray(x)
     dtype = F32 if x.dtype == np.float32 else F64
     if x.dtype not in (np.float32, np.float64):
         raise TypeError(x.dtype)
     d, stride = x.shape
     n = stride if n is None else n
-    r = Region(kind, dtype, n, d, 1, stride, n, threads, block, float(param))
+    if kind == BINOMIAL and not arg:
+        arg = BINOMIAL_STEPS
+    r = Region(kind, dtype, n, d, 1, stride, n, threads, block, float(param), int(arg), 0)
     return r, x, n
 
 
@@ -104,8 +107,8 @@ def _out(x, n, out):
     return out
 
 
-def run_exact(kind, x, param=0.0, n=None):
-    r, x, n = _region(kind, x, n, param, 0, 32)
+def run_exact(kind, x, param=0.0, n=None, steps=0):
+    r, x, n = _region(kind, x, n, param, 0, 32, steps)
     out = np.zeros(n, dtype=x.dtype)
     if lib().orc_run_exact(C.byref(r), _ptr(x), _ptr(out)):
         raise ValueError("oracle rejected the region")
@@ -113,8 +116,8 @@ def run_exact(kind, x, param=0.0, n=None):
 
 
 def run_perfo(kind, x, param, pkind, m=0, rate=0.0, seed=0, herded=1, threads=0, block=256,
-              n=None, out=None):
-    r, x, n = _region(kind, x, n, param, threads, block)
+              n=None, out=None, steps=0):
+    r, x, n = _region(kind, x, n, param, threads, block, steps)
     out = _out(x, n, out)
     mask = np.full(n, 255, dtype=np.uint8)
     cnt = np.zeros(4, dtype=np.int64)
@@ -138,10 +141,10 @@ def iact_state(T, tsize, tperwarp, D):
 
 
 def run_taf(kind, x, param, hsize, psize, thresh, level=THREAD, threads=0, block=256, n=None,
-            reset=False, state=None):
+            reset=False, state=None, steps=0):
     """TAF over the logical schedule; with state (taf_state), the windows and
     owed predictions continue from the previous call and are updated in place."""
-    r, x, n = _region(kind, x, n, param, threads, block)
+    r, x, n = _region(kind, x, n, param, threads, block, steps)
     out = np.zeros(n, dtype=x.dtype)
     stat = np.zeros(n, dtype=x.dtype)
     mask = np.full(n, 255, dtype=np.uint8)
@@ -160,12 +163,12 @@ def run_taf(kind, x, param, hsize, psize, thresh, level=THREAD, threads=0, block
 
 
 def replay_taf(kind, x, param, hsize, psize, thresh, force, level=THREAD, threads=0, block=256, n=None,
-               reset=False):
+               reset=False, steps=0):
     """TAF along a given mask: outputs and statistics of the oracle's own
     arithmetic on the mask's path, the decision points where the oracle's own
     decision differs from the mask's (disagree[i] = 1 at the deciding
     invocation), and counts (compared, disagreements, structural errors)."""
-    r, x, n = _region(kind, x, n, param, threads, block)
+    r, x, n = _region(kind, x, n, param, threads, block, steps)
     force = np.ascontiguousarray(force, dtype=np.uint8)
     if force.shape != (n,):
         raise ValueError("mask length differs from n")
@@ -181,10 +184,10 @@ def replay_taf(kind, x, param, hsize, psize, thresh, force, level=THREAD, thread
 
 
 def run_iact(kind, x, param, tsize, tperwarp, thresh, level=THREAD, in_scale=None, threads=0,
-             block=256, n=None, state=None):
+             block=256, n=None, state=None, steps=0):
     """iACT over the logical schedule; with state (iact_state), the tables
     continue from the previous call and are updated in place."""
-    r, x, n = _region(kind, x, n, param, threads, block)
+    r, x, n = _region(kind, x, n, param, threads, block, steps)
     out = np.zeros(n, dtype=x.dtype)
     stat = np.zeros(n, dtype=x.dtype)
     mask = np.full(n, 255, dtype=np.uint8)

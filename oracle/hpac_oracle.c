@@ -31,7 +31,7 @@
 #endif
 
 enum { ORC_F32 = 0, ORC_F64 = 1 };
-enum { ORC_BLACKSCHOLES = 0, ORC_EOS = 1, ORC_IDENTITY = 3 };
+enum { ORC_BLACKSCHOLES = 0, ORC_EOS = 1, ORC_IDENTITY = 3, ORC_BINOMIAL = 4 };
 enum { ORC_THREAD = 0, ORC_WARP = 1, ORC_BLOCK = 2 };
 enum { ORC_SMALL = 0, ORC_LARGE = 1, ORC_INI = 2, ORC_FINI = 3, ORC_RANDOM = 4 };
 enum { ORC_EXACT = 0, ORC_APPROX = 1, ORC_SKIPPED = 2 };
@@ -49,7 +49,9 @@ typedef struct {
   int64_t out_stride;
   int64_t threads;     /* T; 0 means N                                          */
   int32_t block;       /* B, a multiple of 32                                   */
-  double param;        /* r for Black-Scholes, gamma for the EOS               */
+  double param;        /* r for Black-Scholes and Binomial, gamma for the EOS  */
+  int32_t arg;         /* Binomial: tree steps; 0 otherwise                     */
+  int32_t pad;
 } orc_region;
 
 static int64_t logical_threads(const orc_region *R) {
@@ -97,6 +99,40 @@ static double eos_pressure(double e, double v1, double dv, double q, double g) {
   return (g - 1.0) * e1 / v1;
 }
 
+/* American call on a Cox-Ross-Rubinstein tree (Table 1, Binomial Options:
+ * a portfolio of American options; tree after Podlozhnyuk 2008), single
+ * precision, N steps. Per option, in double and then rounded: dt = T/N,
+ * v = sigma sqrt(dt), u = e^v, d = 1/u, a = e^{r dt}, pu = (a - d)/(u - d),
+ * pd = 1 - pu, the discounted weights pu/a and pd/a, and the leaf prices
+ * S_j = S0 e^{v (2j - N)}, j = 0..N. Leaves V_j = max(S_j - X, 0). Each
+ * backward step n = N-1 .. 0 moves every node price one level up (S_j <- S_j u,
+ * since S0 u^{2j-n} = S0 u^{2j-(n+1)} u) and sets
+ * V_j <- max(fma(pu/a, V_{j+1}, (pd/a) V_j), S_j - X) for j = 0..n (early
+ * exercise). Returns V_0. Every single-precision operation is one IEEE
+ * operation in this order (fmaf is the fused multiply-add). */
+static float binomial_call_f32(float S0, float X, float T, float sig, double r, int N) {
+  float V[4097], S[4097];
+  if (N < 1 || N > 4096) return NAN;
+  double dt = (double)T / N;
+  double v = (double)sig * sqrt(dt);
+  double u = exp(v), d = 1.0 / u, a = exp(r * dt);
+  double pu = (a - d) / (u - d), pd = 1.0 - pu;
+  float puA = (float)(pu / a), pdA = (float)(pd / a), uf = (float)u;
+  for (int j = 0; j <= N; ++j) {
+    S[j] = (float)((double)S0 * exp(v * (double)(2 * j - N)));
+    float ex = S[j] - X;
+    V[j] = ex > 0.0f ? ex : 0.0f;
+  }
+  for (int n = N - 1; n >= 0; --n)
+    for (int j = 0; j <= n; ++j) {
+      float cont = fmaf(puA, V[j + 1], pdA * V[j]);
+      S[j] = S[j] * uf;
+      float ex = S[j] - X;
+      V[j] = cont > ex ? cont : ex;
+    }
+  return V[0];
+}
+
 static double in_at(const orc_region *R, const void *in, int d, int64_t i) {
   if (R->dtype == ORC_F32) return (double)((const float *)in)[d * R->in_stride + i];
   return ((const double *)in)[d * R->in_stride + i];
@@ -115,6 +151,10 @@ static double region_eval(const orc_region *R, const void *in, int64_t i) {
     case ORC_EOS:
       return eos_pressure(in_at(R, in, 0, i), in_at(R, in, 1, i), in_at(R, in, 2, i),
                           in_at(R, in, 3, i), R->param);
+    case ORC_BINOMIAL:
+      return (double)binomial_call_f32((float)in_at(R, in, 0, i), (float)in_at(R, in, 1, i),
+                                       (float)in_at(R, in, 2, i), (float)in_at(R, in, 3, i),
+                                       R->param, R->arg);
     case ORC_IDENTITY:
     default:
       return in_at(R, in, 0, i);
@@ -139,6 +179,8 @@ static int check_region(const orc_region *R) {
   if (R->dtype != ORC_F32 && R->dtype != ORC_F64) return 1;
   if (R->kind == ORC_BLACKSCHOLES && R->n_in != 4) return 1;
   if (R->kind == ORC_EOS && (R->n_in != 4 || R->dtype != ORC_F64)) return 1;
+  if (R->kind == ORC_BINOMIAL && (R->n_in != 4 || R->dtype != ORC_F32 || R->arg < 1 || R->arg > 4096))
+    return 1;
   return 0;
 }
 

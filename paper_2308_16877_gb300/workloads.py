@@ -207,6 +207,40 @@ def sweep_configs() -> list[dict]:
     return cfgs
 
 
+BINOMIAL_STEPS = 512
+
+
+def binomial_portfolio(members: int, time_points: int, seed: int = DEFAULT_SEED) -> np.ndarray:
+    """A portfolio of American call options priced at successive time points
+    before expiry (Table 1, Binomial Options), float32, shape (4, members *
+    time_points): rows spot S, strike X, time to expiry T, volatility sigma.
+
+    Member m has S0 ~ U[5, 30], X = S0 * U[0.8, 1.2] (near the money), T0 ~
+    U[0.5, 2] years and sigma ~ U[0.1, 0.5]; at time point k its spot follows
+    a seeded geometric Brownian path with drift r - sigma^2/2 sampled every
+    dt_m = T0 / (2 time_points), and its time to expiry is T0 - k dt_m. Column
+    i = m + k * members, so with one logical team per member (T = members) a
+    team prices its own option at successive time points.
+    """
+    g = _rng(seed, 7)
+    M, K = members, time_points
+    S0 = g.uniform(BS_SPOT[0], BS_SPOT[1], size=M)
+    X = S0 * g.uniform(0.8, 1.2, size=M)
+    T0 = g.uniform(0.5, 2.0, size=M)
+    sig = g.uniform(0.1, 0.5, size=M)
+    dt = T0 / (2 * K)
+    z = g.standard_normal((K, M))
+    z[0] = 0.0
+    logS = np.log(S0)[None, :] + np.cumsum((BS_RATE - 0.5 * sig ** 2) * dt + sig * np.sqrt(dt) * z, axis=0)
+    x = np.empty((4, K * M), dtype=np.float32)
+    k = np.arange(K)[:, None]
+    x[0] = np.exp(logS).reshape(-1).astype(np.float32)
+    x[1] = np.broadcast_to(X, (K, M)).reshape(-1).astype(np.float32)
+    x[2] = (T0[None, :] - k * dt[None, :]).reshape(-1).astype(np.float32)
+    x[3] = np.broadcast_to(sig, (K, M)).reshape(-1).astype(np.float32)
+    return x
+
+
 def hydro_dt(n: int, gamma: float = 5.0 / 3.0, e0: float = HYDRO_E0, cfl: float = 0.1) -> float:
     """Fixed time step of the hydro run: cfl * h / c0 with h = 1/n and c0 the
     ideal-gas sound speed of the initial corner element at unit density."""
