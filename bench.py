@@ -411,6 +411,75 @@ def bench_search(hpac, torch, dev, stream, bound=0.01, reps=5):
             "history_best_saved": hist, "exact_ms_all_regions": exact_ms}
 
 
+def bench_binomial(hpac, torch, dev, stream, members=4096, time_points=64, steps=1024, reps=3):
+    """Binomial Options (Table 1): a portfolio of American calls priced at
+    successive time points on 1024-step trees, one option per team of 32
+    lanes, one team per member (T = members). TAF and iACT decide per team
+    (the paper's block level), perforation drops whole options; each
+    configuration is timed against the exact kernel and scored by the MAPE of
+    its prices against the exact ones (the paper's highest speedup at a
+    quality bound)."""
+    x = W.binomial_portfolio(members, time_points)
+    n = x.shape[1]
+    xd = torch.from_numpy(x).to(dev)
+    sc = W.iact_scale(x, n)
+    exact = torch.zeros(n, dtype=torch.float32, device=dev)
+    out = torch.zeros(n, dtype=torch.float32, device=dev)
+    R = hpac.Region(hpac.HPAC_REGION_BINOMIAL, xd, param=W.BS_RATE, arg=steps, logical_threads=members,
+                    stream=stream)
+
+    def timed(f):
+        f()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            f()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    exact_ms = timed(lambda: R.run_exact(xd, exact))
+    ref = exact.double()
+    rows = []
+
+    def add(tech, knobs, f):
+        ms = timed(f)
+        mape = hpac.quality(ref, out, hpac.HPAC_METRIC_MAPE, stream=stream)["value"]
+        rows.append(dict(technique=tech, **knobs, ms=ms, speedup=exact_ms / ms, mape=mape))
+
+    for h in (1, 2, 4):
+        for p in (2, 4, 8, 16):
+            for thr in (0.005, 0.01, 0.02, 0.05):
+                add("taf", dict(h=h, p=p, thr=thr),
+                    lambda: R.run_taf(xd, out, h, p, thr, hpac.HPAC_LEVEL_BLOCK))
+    for ts in (4, 8):
+        for thr in (0.005, 0.01, 0.02, 0.05):
+            add("iact", dict(tsize=ts, thr=thr),
+                lambda: R.run_iact(xd, out, ts, 32, thr, hpac.HPAC_LEVEL_BLOCK, in_scale=sc))
+    for m in (2, 3, 4, 8):
+        def perf(m=m):
+            out.zero_()                # a dropped option keeps the caller's (zero) prefill
+            R.run_perfo(xd, out, hpac.HPAC_PERFO_SMALL, m, herded=True)
+        add("perfo_small", dict(m=m), perf)
+    R.close()
+
+    def best(tech_prefix, bound):
+        ok = [r for r in rows if r["technique"].startswith(tech_prefix) and r["mape"] <= bound]
+        return max(ok, key=lambda r: r["speedup"]) if ok else None
+
+    # the exact kernel against the FP32 issue rate: 5 single-precision
+    # instructions per node update (multiply, fused multiply-add, multiply,
+    # subtract, max), N (N + 1) / 2 updates per option
+    instr = 5.0 * steps * (steps + 1) / 2 * n
+    peak = 152 * 128 * 2.07e9
+    return {"options": n, "members": members, "time_points": time_points, "steps": steps,
+            "exact_ms": exact_ms, "options_per_s": n / (exact_ms * 1e-3),
+            "exact_fp32_issue_frac": instr / (exact_ms * 1e-3) / peak,
+            "best_at_1pct_mape": {t: best(t, 0.01) for t in ("taf", "iact", "perfo")},
+            "best_at_10pct_mape": {t: best(t, 0.10) for t in ("taf", "iact", "perfo")},
+            "table": rows}
+
+
 def calibrate_floor(pred, exact, target=0.01, q=0.99):
     """Smallest price floor tau such that, among predictions >= tau, the q-th
     quantile of the relative error |pred - exact| / |exact| is at most target."""
@@ -721,6 +790,7 @@ def main(argv=None):
     ap.add_argument("--no-hydro-large", action="store_true")
     ap.add_argument("--no-persistent", action="store_true")
     ap.add_argument("--no-search", action="store_true")
+    ap.add_argument("--no-binomial", action="store_true")
     args = ap.parse_args(argv)
     if args.impl == "reference":
         return run_reference(args)
@@ -910,6 +980,7 @@ def main(argv=None):
     bs = None if args.no_blackscholes else bench_blackscholes(hpac, torch, dev, stream)
     sweep = None if args.no_sweep else bench_sweep(hpac, torch, dev, stream)
     knob_search = None if args.no_search else bench_search(hpac, torch, dev, stream)
+    binomial = None if args.no_binomial else bench_binomial(hpac, torch, dev, stream)
     surrogate = None if args.no_surrogate else bench_surrogate(hpac, torch, dev, stream)
     large = None if args.no_hydro_large else bench_hydro_large(hpac, torch, dev, stream)
     persistent = None if args.no_persistent else bench_persistent(hpac, torch, dev, stream)
@@ -945,6 +1016,7 @@ def main(argv=None):
             "blackscholes": bs,
             "sweep": sweep,
             "search": knob_search,
+            "binomial": binomial,
             "surrogate": surrogate,
             "hydro_large": large,
             "persistent_state": persistent,

@@ -61,11 +61,25 @@ typedef enum { HPAC_LEVEL_THREAD = 0, HPAC_LEVEL_WARP = 1, HPAC_LEVEL_BLOCK = 2 
  *    p = (gamma-1) e_{n+1} / v_{n+1}, e_{n+1} = (e_n - dv (p_n + 2q)/2) /
  *    (1 + (gamma-1) dv / (2 v_{n+1})) clamped at 0, p_n = (gamma-1) e_n / (v_{n+1} - dv).
  *  IDENTITY: output = first input; 1 <= D <= 8; F32 or F64. A region without
- *    arithmetic, for measuring a technique's own cost and for bit-exact tests. */
+ *    arithmetic, for measuring a technique's own cost and for bit-exact tests.
+ *  BINOMIAL: American call on a Cox-Ross-Rubinstein tree (Table 1, Binomial
+ *    Options: a portfolio of American options priced at several time points).
+ *    D = 4 inputs (spot S, strike X, time to expiry T, volatility sigma),
+ *    param = rate r, arg = tree steps N in 1..1024; F32 only. Per option (in
+ *    double, then rounded): dt = T/N, v = sigma sqrt(dt), u = e^v, d = 1/u,
+ *    a = e^{r dt}, pu = (a - d)/(u - d), weights pu/a and (1 - pu)/a, leaves
+ *    S_j = S0 e^{v (2j - N)}, V_j = max(S_j - X, 0); then N single-precision
+ *    backward steps S_j <- S_j u, V_j <- max(fma(pu/a, V_{j+1}, (pd/a) V_j),
+ *    S_j - X). One invocation is a whole tree, computed by a team of 32 lanes:
+ *    the logical schedule's T counts teams, each team prices options
+ *    i = t + k T in turn, and TAF / iACT decide per team (the paper's
+ *    block-level decision, one option per block): level must be
+ *    HPAC_LEVEL_BLOCK and iACT keeps one table per team (tperwarp = 32). */
 typedef enum {
   HPAC_REGION_BLACKSCHOLES = 0,
   HPAC_REGION_EOS = 1,
-  HPAC_REGION_IDENTITY = 3
+  HPAC_REGION_IDENTITY = 3,
+  HPAC_REGION_BINOMIAL = 4
 } hpac_region_kind;
 
 /* Perforation patterns (Section 2.3; the runtime encounter counter of Section
@@ -102,8 +116,8 @@ typedef struct {
   int64_t out_stride;       /* >= n; reserved for multi-output regions           */
   int64_t logical_threads;  /* T >= 0; 0 means N (one invocation per thread)     */
   int32_t block_threads;    /* B: multiple of 32, 32..1024                       */
-  int32_t reserved0;        /* must be 0                                         */
-  double param;             /* r (BLACKSCHOLES), gamma (EOS), unused (IDENTITY)  */
+  int32_t arg;              /* BINOMIAL: tree steps 1..1024; 0 for other kinds   */
+  double param;             /* r (BLACKSCHOLES, BINOMIAL), gamma (EOS), unused   */
 } hpac_region_desc;
 
 /* perfo(kind:arg) clause (Section 3.2, Table 2). m_or_percent is M for

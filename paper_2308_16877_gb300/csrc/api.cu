@@ -48,7 +48,8 @@ static hpac_status check_desc(const hpac_region_desc *d) {
     return set_error(HPAC_EINVAL, "block_threads = %d, must be a multiple of 32 in 32..1024",
                      d->block_threads);
   if (d->dtype != HPAC_F32 && d->dtype != HPAC_F64) return set_error(HPAC_EINVAL, "dtype %d", d->dtype);
-  if (d->reserved0 != 0) return set_error(HPAC_EINVAL, "reserved field not zero");
+  if (d->kind != HPAC_REGION_BINOMIAL && d->arg != 0)
+    return set_error(HPAC_EINVAL, "arg must be 0 for region kind %d", d->kind);
   if (!isfinite(d->param)) return set_error(HPAC_EINVAL, "param is not finite");
   switch (d->kind) {
     case HPAC_REGION_BLACKSCHOLES:
@@ -59,6 +60,12 @@ static hpac_status check_desc(const hpac_region_desc *d) {
       if (d->dtype != HPAC_F64) return set_error(HPAC_EUNSUPPORTED, "EOS is double precision only");
       break;
     case HPAC_REGION_IDENTITY:
+      break;
+    case HPAC_REGION_BINOMIAL:
+      if (d->n_in != 4) return set_error(HPAC_EINVAL, "Binomial takes 4 inputs");
+      if (d->dtype != HPAC_F32) return set_error(HPAC_EUNSUPPORTED, "Binomial is single precision only");
+      if (d->arg < 1 || d->arg > kMaxBinomialSteps)
+        return set_error(HPAC_EINVAL, "Binomial steps %d not in 1..%d", d->arg, kMaxBinomialSteps);
       break;
     default:
       return set_error(HPAC_EINVAL, "unknown region kind %d", d->kind);
@@ -193,6 +200,8 @@ hpac_status hpac_region_set_stream(hpac_region *r, void *cuda_stream) {
 hpac_status hpac_run_exact(hpac_region *r, const void *d_in, void *d_out) {
   hpac_status s = check_call(r, d_in, d_out);
   if (s != HPAC_OK) return s;
+  if (r->d.kind == HPAC_REGION_BINOMIAL)
+    return launch_binomial(r, 0, nullptr, d_in, d_out, nullptr, nullptr, nullptr);
   return launch_exact(r, d_in, d_out);
 }
 
@@ -221,7 +230,9 @@ hpac_status hpac_run_perfo(hpac_region *r, const hpac_perfo_knobs *k, const void
   if (k->reserved0 != 0) return set_error(HPAC_EINVAL, "reserved field not zero");
   s = begin_counters(r, h_stats);
   if (s != HPAC_OK) return s;
-  s = launch_perfo(r, k, d_in, d_out, d_mask, h_stats ? r->d_counters : nullptr);
+  s = r->d.kind == HPAC_REGION_BINOMIAL
+          ? launch_binomial(r, 3, k, d_in, d_out, d_mask, nullptr, h_stats ? r->d_counters : nullptr)
+          : launch_perfo(r, k, d_in, d_out, d_mask, h_stats ? r->d_counters : nullptr);
   if (s != HPAC_OK) return s;
   s = end_counters(r, h_stats, 0);
   if (s == HPAC_OK && h_stats) {
@@ -246,9 +257,16 @@ hpac_status hpac_run_taf(hpac_region *r, const hpac_taf_knobs *k, const void *d_
     return set_error(HPAC_EINVAL, "level %d", k->level);
   if (k->reset_on_exit != 0 && k->reset_on_exit != 1)
     return set_error(HPAC_EINVAL, "reset_on_exit %d not 0 or 1", k->reset_on_exit);
+  if (r->d.kind == HPAC_REGION_BINOMIAL) {
+    if (k->level != HPAC_LEVEL_BLOCK)
+      return set_error(HPAC_EUNSUPPORTED, "Binomial decides per team: level must be HPAC_LEVEL_BLOCK");
+    if (r->persist) return set_error(HPAC_EUNSUPPORTED, "Binomial keeps no state across calls");
+  }
   s = begin_counters(r, h_stats);
   if (s != HPAC_OK) return s;
-  s = launch_taf(r, k, d_in, d_out, d_mask, d_stat, h_stats ? r->d_counters : nullptr);
+  s = r->d.kind == HPAC_REGION_BINOMIAL
+          ? launch_binomial(r, 1, k, d_in, d_out, d_mask, d_stat, h_stats ? r->d_counters : nullptr)
+          : launch_taf(r, k, d_in, d_out, d_mask, d_stat, h_stats ? r->d_counters : nullptr);
   if (s != HPAC_OK) return s;
   return end_counters(r, h_stats, 0);
 }
@@ -269,9 +287,17 @@ hpac_status hpac_run_iact(hpac_region *r, const hpac_iact_knobs *k, const void *
   if (k->in_scale)
     for (int j = 0; j < r->d.n_in; ++j)
       if (!isfinite(k->in_scale[j])) return set_error(HPAC_EINVAL, "in_scale[%d] is not finite", j);
+  if (r->d.kind == HPAC_REGION_BINOMIAL) {
+    if (k->level != HPAC_LEVEL_BLOCK || k->tperwarp != 32)
+      return set_error(HPAC_EUNSUPPORTED,
+                       "Binomial keeps one table per team: level HPAC_LEVEL_BLOCK, tperwarp 32");
+    if (r->persist) return set_error(HPAC_EUNSUPPORTED, "Binomial keeps no state across calls");
+  }
   s = begin_counters(r, h_stats);
   if (s != HPAC_OK) return s;
-  s = launch_iact(r, k, d_in, d_out, d_mask, d_stat, h_stats ? r->d_counters : nullptr);
+  s = r->d.kind == HPAC_REGION_BINOMIAL
+          ? launch_binomial(r, 2, k, d_in, d_out, d_mask, d_stat, h_stats ? r->d_counters : nullptr)
+          : launch_iact(r, k, d_in, d_out, d_mask, d_stat, h_stats ? r->d_counters : nullptr);
   if (s != HPAC_OK) return s;
   return end_counters(r, h_stats, 0);
 }

@@ -23,6 +23,7 @@ constexpr int kWarp = 32;
 constexpr int kMaxIn = 8;
 constexpr int kMaxHsize = 64;
 constexpr int kMaxTsize = 64;
+constexpr int kMaxBinomialSteps = 1024;
 constexpr double kBorderRel = 1e-6;
 
 // Thread-local error reporting (hpac_last_error).
@@ -42,6 +43,11 @@ hpac_status launch_taf(hpac_region *r, const hpac_taf_knobs *k, const void *in, 
                        uint8_t *mask, void *stat, unsigned long long *counters);
 hpac_status launch_iact(hpac_region *r, const hpac_iact_knobs *k, const void *in, void *out,
                         uint8_t *mask, void *stat, unsigned long long *counters);
+
+// The Binomial region: every technique runs in binomial.cu's team kernels
+// (technique 0 exact, 1 TAF, 2 iACT, 3 perforation; knobs of that technique).
+hpac_status launch_binomial(hpac_region *r, int technique, const void *knobs, const void *in,
+                            void *out, uint8_t *mask, void *stat, unsigned long long *counters);
 
 // The persistent state buffer of a TAF or iACT run: nullptr when the region
 // keeps no state; otherwise a zeroed buffer of `bytes` the first time a shape

@@ -15,7 +15,7 @@ import threading
 HPAC_OK, HPAC_EINVAL, HPAC_ENOMEM, HPAC_ECUDA, HPAC_ETIMEOUT, HPAC_EUNSUPPORTED = range(6)
 HPAC_F32, HPAC_F64 = 0, 1
 HPAC_LEVEL_THREAD, HPAC_LEVEL_WARP, HPAC_LEVEL_BLOCK = 0, 1, 2
-HPAC_REGION_BLACKSCHOLES, HPAC_REGION_EOS, HPAC_REGION_IDENTITY = 0, 1, 3
+HPAC_REGION_BLACKSCHOLES, HPAC_REGION_EOS, HPAC_REGION_IDENTITY, HPAC_REGION_BINOMIAL = 0, 1, 3, 4
 HPAC_PERFO_SMALL, HPAC_PERFO_LARGE, HPAC_PERFO_INI, HPAC_PERFO_FINI, HPAC_PERFO_RANDOM = range(5)
 HPAC_MASK_EXACT, HPAC_MASK_APPROX, HPAC_MASK_SKIPPED = 0, 1, 2
 HPAC_METRIC_MAPE, HPAC_METRIC_RMSE, HPAC_METRIC_MCR = 0, 1, 2
@@ -25,7 +25,7 @@ class hpac_region_desc(C.Structure):
     _fields_ = [("kind", C.c_int32), ("dtype", C.c_int32), ("n", C.c_int64), ("n_in", C.c_int32),
                 ("n_out", C.c_int32), ("in_stride", C.c_int64), ("out_stride", C.c_int64),
                 ("logical_threads", C.c_int64), ("block_threads", C.c_int32),
-                ("reserved0", C.c_int32), ("param", C.c_double)]
+                ("arg", C.c_int32), ("param", C.c_double)]
 
 
 class hpac_perfo_knobs(C.Structure):
@@ -319,7 +319,8 @@ class Region:
     """An annotated loop region over a (D, stride) CUDA tensor of inputs."""
 
     def __init__(self, kind: int, x, n: int | None = None, param: float = 0.0,
-                 logical_threads: int = 0, block_threads: int = 256, stream=None):
+                 logical_threads: int = 0, block_threads: int = 256, stream=None, arg: int = 0):
+        """arg: the Binomial region's tree steps (0 for the other kinds)."""
         if not x.is_cuda or x.dim() != 2 or not x.is_contiguous():
             raise ValueError("inputs must be a contiguous 2-D CUDA tensor (D, stride)")
         self.kind = kind
@@ -327,7 +328,7 @@ class Region:
         self.d_in, stride = x.shape
         self.n = stride if n is None else n
         self.desc = hpac_region_desc(kind, _dtype_code(x), self.n, self.d_in, 1, stride, self.n,
-                                     logical_threads, block_threads, 0, float(param))
+                                     logical_threads, block_threads, int(arg), float(param))
         self._h = hpac_region_create(self.desc, _stream_handle(stream))
 
     def close(self):

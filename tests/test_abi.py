@@ -71,6 +71,6 @@ def test_enum_values_match_header():
     from paper_2308_16877_gb300 import hpac
     src = open(HEADER).read()
     for name in ("HPAC_OK", "HPAC_EINVAL", "HPAC_EUNSUPPORTED", "HPAC_F64", "HPAC_LEVEL_BLOCK",
-                 "HPAC_REGION_IDENTITY", "HPAC_PERFO_RANDOM", "HPAC_MASK_SKIPPED", "HPAC_METRIC_MCR"):
+                 "HPAC_REGION_IDENTITY", "HPAC_REGION_BINOMIAL", "HPAC_PERFO_RANDOM", "HPAC_MASK_SKIPPED", "HPAC_METRIC_MCR"):
         m = re.search(rf"\b{name}\s*=\s*(\d+)", src)
         assert m and int(m.group(1)) == getattr(hpac, name), name
