@@ -18,7 +18,7 @@ import numpy as np
 
 from . import build as _build
 
-BLACKSCHOLES, EOS, IDENTITY, BINOMIAL = 0, 1, 3, 4
+BLACKSCHOLES, EOS, IDENTITY, BINOMIAL, KMEANS = 0, 1, 3, 4, 5
 BINOMIAL_STEPS = 512         # default tree depth of the Binomial region
 F32, F64 = 0, 1
 THREAD, WARP, BLOCK = 0, 1, 2
@@ -31,7 +31,8 @@ class Region(C.Structure):
     _fields_ = [("kind", C.c_int32), ("dtype", C.c_int32), ("n", C.c_int64),
                 ("n_in", C.c_int32), ("n_out", C.c_int32), ("in_stride", C.c_int64),
                 ("out_stride", C.c_int64), ("threads", C.c_int64), ("block", C.c_int32),
-                ("param", C.c_double), ("arg", C.c_int32), ("pad", C.c_int32)]
+                ("param", C.c_double), ("arg", C.c_int32), ("pad", C.c_int32),
+                ("aux", C.c_void_p)]
 
 
 _lib = None
@@ -52,6 +53,8 @@ def lib() -> C.CDLL:
         L.orc_run_taf_persist.argtypes = [RP, P, I32, I32, D, I32, I32, P, P, P, P, P, P, P]
         L.orc_run_iact_persist.argtypes = [RP, P, I32, I32, D, I32, P, P, P, P, P, P, P, P, P]
         L.orc_quality.argtypes = [I64, P, P, I32, P, P]
+        L.orc_kmeans_update.argtypes = [I64, I32, P, I64, P, P, P, P]
+        L.orc_kmeans_update.restype = C.c_int
         L.orc_num_threads.restype = C.c_int
         for f in ("orc_run_exact", "orc_run_perfo", "orc_run_taf", "orc_replay_taf", "orc_run_iact",
                   "orc_quality", "orc_run_taf_persist", "orc_run_iact_persist"):
@@ -95,9 +98,17 @@ def _region(kind, x, n, param, threads, block, arg=0):
         raise TypeError(x.dtype)
     d, stride = x.shape
     n = stride if n is None else n
+    aux = None
     if kind == BINOMIAL and not arg:
         arg = BINOMIAL_STEPS
-    r = Region(kind, dtype, n, d, 1, stride, n, threads, block, float(param), int(arg), 0)
+    if kind == KMEANS:
+        # param carries the centroids for this region: a (K, 8) float32 array
+        cent = np.ascontiguousarray(param, dtype=np.float32)
+        arg, aux = cent.shape[0], cent
+        param = 0.0
+    r = Region(kind, dtype, n, d, 1, stride, n, threads, block, float(param), int(arg), 0,
+               aux.ctypes.data if aux is not None else None)
+    r._keep = aux
     return r, x, n
 
 
@@ -203,6 +214,35 @@ def run_iact(kind, x, param, tsize, tperwarp, thresh, level=THREAD, in_scale=Non
                           _ptr(out), _ptr(mask), _ptr(stat), _ptr(cnt)):
         raise ValueError("oracle rejected iACT arguments")
     return out, mask, stat, cnt
+
+
+def kmeans_update(x, assign, cent, prev=None):
+    """One exact centroid update (see orc_kmeans_update): returns (new
+    centroids, changed count); x (8, n) float32, assign / prev float32 ids."""
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    a = np.ascontiguousarray(assign, dtype=np.float32)
+    c = np.array(cent, dtype=np.float32, copy=True)
+    p = None if prev is None else np.ascontiguousarray(prev, dtype=np.float32)
+    ch = np.zeros(1, dtype=np.int64)
+    if lib().orc_kmeans_update(a.size, c.shape[0], _ptr(x), x.shape[1], _ptr(a), _ptr(p), _ptr(c), _ptr(ch)):
+        raise ValueError("oracle rejected K-Means update arguments")
+    return c, int(ch[0])
+
+
+def kmeans(x, cent0, max_iter=100, run=None):
+    """K-Means to convergence (no observation changes cluster) or max_iter:
+    run(cent) -> assignment ids (default: the oracle's exact region). Returns
+    (assignment, centroids, iterations)."""
+    cent = np.array(cent0, dtype=np.float32, copy=True)
+    run = run or (lambda c: run_exact(KMEANS, x, c))
+    prev = None
+    for it in range(1, max_iter + 1):
+        a = run(cent)
+        cent, ch = kmeans_update(x, a, cent, prev)
+        if prev is not None and ch == 0:
+            return a, cent, it
+        prev = a
+    return prev, cent, max_iter
 
 
 def quality(a, b, metric):

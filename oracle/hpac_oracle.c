@@ -31,7 +31,7 @@
 #endif
 
 enum { ORC_F32 = 0, ORC_F64 = 1 };
-enum { ORC_BLACKSCHOLES = 0, ORC_EOS = 1, ORC_IDENTITY = 3, ORC_BINOMIAL = 4 };
+enum { ORC_BLACKSCHOLES = 0, ORC_EOS = 1, ORC_IDENTITY = 3, ORC_BINOMIAL = 4, ORC_KMEANS = 5 };
 enum { ORC_THREAD = 0, ORC_WARP = 1, ORC_BLOCK = 2 };
 enum { ORC_SMALL = 0, ORC_LARGE = 1, ORC_INI = 2, ORC_FINI = 3, ORC_RANDOM = 4 };
 enum { ORC_EXACT = 0, ORC_APPROX = 1, ORC_SKIPPED = 2 };
@@ -50,8 +50,9 @@ typedef struct {
   int64_t threads;     /* T; 0 means N                                          */
   int32_t block;       /* B, a multiple of 32                                   */
   double param;        /* r for Black-Scholes and Binomial, gamma for the EOS  */
-  int32_t arg;         /* Binomial: tree steps; 0 otherwise                     */
+  int32_t arg;         /* Binomial: tree steps; K-Means: clusters K; else 0    */
   int32_t pad;
+  const float *aux;    /* K-Means: centroids [K][8]; NULL otherwise            */
 } orc_region;
 
 static int64_t logical_threads(const orc_region *R) {
@@ -133,6 +134,29 @@ static float binomial_call_f32(float S0, float X, float T, float sig, double r, 
   return V[0];
 }
 
+/* K-Means assignment (Table 1, K-Means: the cluster id of each observation;
+ * Section 4.2 approximates the distance kernel): the index of the nearest of
+ * the K centroids in squared Euclidean distance over the 8 features, each
+ * distance summed in single precision over d = 0..7 in order, ties to the
+ * lowest index. Returned as a float holding the integer id. */
+static float kmeans_assign_f32(const float *x, const float *cent, int K) {
+  int best = 0;
+  float bd = 0.0f;
+  for (int k = 0; k < K; ++k) {
+    float acc = 0.0f;
+    for (int d = 0; d < 8; ++d) {
+      float df = x[d] - cent[k * 8 + d];
+      float sq = df * df;
+      acc = acc + sq;
+    }
+    if (k == 0 || acc < bd) {
+      bd = acc;
+      best = k;
+    }
+  }
+  return (float)best;
+}
+
 static double in_at(const orc_region *R, const void *in, int d, int64_t i) {
   if (R->dtype == ORC_F32) return (double)((const float *)in)[d * R->in_stride + i];
   return ((const double *)in)[d * R->in_stride + i];
@@ -155,6 +179,11 @@ static double region_eval(const orc_region *R, const void *in, int64_t i) {
       return (double)binomial_call_f32((float)in_at(R, in, 0, i), (float)in_at(R, in, 1, i),
                                        (float)in_at(R, in, 2, i), (float)in_at(R, in, 3, i),
                                        R->param, R->arg);
+    case ORC_KMEANS: {
+      float x[8];
+      for (int d = 0; d < 8; ++d) x[d] = (float)in_at(R, in, d, i);
+      return (double)kmeans_assign_f32(x, R->aux, R->arg);
+    }
     case ORC_IDENTITY:
     default:
       return in_at(R, in, 0, i);
@@ -180,6 +209,8 @@ static int check_region(const orc_region *R) {
   if (R->kind == ORC_BLACKSCHOLES && R->n_in != 4) return 1;
   if (R->kind == ORC_EOS && (R->n_in != 4 || R->dtype != ORC_F64)) return 1;
   if (R->kind == ORC_BINOMIAL && (R->n_in != 4 || R->dtype != ORC_F32 || R->arg < 1 || R->arg > 4096))
+    return 1;
+  if (R->kind == ORC_KMEANS && (R->n_in != 8 || R->dtype != ORC_F32 || R->arg < 1 || R->arg > 64 || !R->aux))
     return 1;
   return 0;
 }
@@ -718,6 +749,33 @@ int orc_run_iact_persist(const orc_region *R, const void *in, int32_t tsize, int
   if (!st_z || !st_y || !st_valid || !st_rr) return 1;
   return iact_core(R, in, tsize, tperwarp, thr, level, in_scale, out, mask, stat, counters, st_z,
                    st_y, st_valid, st_rr);
+}
+
+/* K-Means centroid update (the exact step between two assignments): each
+ * centroid becomes the mean of the observations assigned to it, summed in
+ * double over i in order and rounded once; a cluster without observations
+ * keeps its centroid. changed (if prev is given) = observations whose id
+ * differs from prev. x: 8 rows of `stride` floats; assign: ids as floats. */
+int orc_kmeans_update(int64_t n, int32_t K, const float *x, int64_t stride, const float *assign,
+                      const float *prev, float *cent, int64_t *changed) {
+  if (n < 0 || K < 1 || K > 64 || stride < n) return 1;
+  double sum[64 * 8];
+  int64_t cnt[64];
+  memset(sum, 0, sizeof(sum));
+  memset(cnt, 0, sizeof(cnt));
+  int64_t ch = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    int k = (int)assign[i];
+    if (k < 0 || k >= K) return 1;
+    cnt[k] += 1;
+    for (int d = 0; d < 8; ++d) sum[k * 8 + d] += (double)x[d * stride + i];
+    if (prev && prev[i] != assign[i]) ch++;
+  }
+  for (int k = 0; k < K; ++k)
+    if (cnt[k] > 0)
+      for (int d = 0; d < 8; ++d) cent[k * 8 + d] = (float)(sum[k * 8 + d] / (double)cnt[k]);
+  if (changed) *changed = ch;
+  return 0;
 }
 
 /* ------------------------------------------------------------------------ */

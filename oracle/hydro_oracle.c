@@ -44,6 +44,7 @@ typedef struct {
   int32_t block;
   double param;
   int32_t arg, pad;
+  const float *aux;
 } orc_region;
 int orc_run_exact(const orc_region *R, const void *in, void *out);
 int orc_run_taf(const orc_region *R, const void *in, int32_t hsize, int32_t psize, double thr,

@@ -241,6 +241,22 @@ def binomial_portfolio(members: int, time_points: int, seed: int = DEFAULT_SEED)
     return x
 
 
+def kmeans_blobs(n: int, clusters: int, seed: int = DEFAULT_SEED, spread: float = 1.0):
+    """Observations for the K-Means region: float32 (8, n), drawn from
+    `clusters` isotropic Gaussian blobs (standard deviation `spread`) whose
+    centres are uniform on [-10, 10]^8, in random order. Returns (x, labels,
+    init): the generating blob of each observation and the initial centroids
+    (the first observation of each blob, so a run starts with one seed per blob)."""
+    g = _rng(seed, 11)
+    centres = g.uniform(-10.0, 10.0, size=(clusters, 8))
+    labels = g.integers(0, clusters, size=n)
+    labels[:clusters] = np.arange(clusters)          # every blob is present
+    g.shuffle(labels)
+    x = (centres[labels] + spread * g.standard_normal((n, 8))).T.astype(np.float32)
+    first = np.array([np.flatnonzero(labels == k)[0] for k in range(clusters)])
+    return np.ascontiguousarray(x), labels, np.ascontiguousarray(x[:, first].T)
+
+
 def hydro_dt(n: int, gamma: float = 5.0 / 3.0, e0: float = HYDRO_E0, cfl: float = 0.1) -> float:
     """Fixed time step of the hydro run: cfl * h / c0 with h = 1/n and c0 the
     ideal-gas sound speed of the initial corner element at unit density."""
