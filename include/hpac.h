@@ -74,12 +74,19 @@ typedef enum { HPAC_LEVEL_THREAD = 0, HPAC_LEVEL_WARP = 1, HPAC_LEVEL_BLOCK = 2 
  *    the logical schedule's T counts teams, each team prices options
  *    i = t + k T in turn, and TAF / iACT decide per team (the paper's
  *    block-level decision, one option per block): level must be
- *    HPAC_LEVEL_BLOCK and iACT keeps one table per team (tperwarp = 32). */
+ *    HPAC_LEVEL_BLOCK and iACT keeps one table per team (tperwarp = 32).
+ *  KMEANS: nearest-centroid assignment (Table 1, K-Means; Section 4.2
+ *    approximates this distance kernel). D = 8 features, arg = clusters K in
+ *    1..64, the centroids (K x 8 floats, row k at k*8) in device memory set by
+ *    hpac_region_set_aux; F32 only. Output: the id (as a float) of the centroid
+ *    with the smallest sum over d = 0..7 of (x_d - c_kd)^2, accumulated in
+ *    order in single precision, ties to the lowest id. */
 typedef enum {
   HPAC_REGION_BLACKSCHOLES = 0,
   HPAC_REGION_EOS = 1,
   HPAC_REGION_IDENTITY = 3,
-  HPAC_REGION_BINOMIAL = 4
+  HPAC_REGION_BINOMIAL = 4,
+  HPAC_REGION_KMEANS = 5
 } hpac_region_kind;
 
 /* Perforation patterns (Section 2.3; the runtime encounter counter of Section
@@ -116,7 +123,8 @@ typedef struct {
   int64_t out_stride;       /* >= n; reserved for multi-output regions           */
   int64_t logical_threads;  /* T >= 0; 0 means N (one invocation per thread)     */
   int32_t block_threads;    /* B: multiple of 32, 32..1024                       */
-  int32_t arg;              /* BINOMIAL: tree steps 1..1024; 0 for other kinds   */
+  int32_t arg;              /* BINOMIAL: tree steps 1..1024; KMEANS: clusters    */
+                            /* 1..64; 0 for the other kinds                      */
   double param;             /* r (BLACKSCHOLES, BINOMIAL), gamma (EOS), unused   */
 } hpac_region_desc;
 
@@ -211,6 +219,25 @@ hpac_status hpac_region_set_persistent(hpac_region *region, int32_t enable);
 
 /* Empty the kept state (asynchronous on the region's stream). */
 hpac_status hpac_region_reset_state(hpac_region *region);
+
+/* KMEANS regions: the centroids every later run reads (device pointer, K x 8
+ * floats, caller-owned, may change between runs; must stay valid while a run
+ * using it is in flight). HPAC_EINVAL for other kinds or NULL. */
+hpac_status hpac_region_set_aux(hpac_region *region, const void *d_aux);
+
+/* K-Means centroid update, the exact step between two assignments: centroid k
+ * becomes the mean of the observations whose id (d_assign, floats) is k,
+ * summed in double (atomics, so the last bits of the sum may vary) and
+ * rounded once; a cluster without observations keeps its centroid. d_x: 8
+ * rows of `stride` floats; d_cent: K x 8 floats, updated in place; d_work: a
+ * device workspace of hpac_kmeans_workspace_bytes(K) bytes, 8-byte aligned.
+ * d_prev (nullable): the previous assignment; with h_changed non-NULL the call
+ * waits and returns how many observations changed cluster (the convergence
+ * test: none). Asynchronous on cuda_stream otherwise. */
+size_t hpac_kmeans_workspace_bytes(int32_t clusters);
+hpac_status hpac_kmeans_update(int64_t n, int32_t clusters, const float *d_x, int64_t stride,
+                               const float *d_assign, const float *d_prev, float *d_cent,
+                               void *d_work, int64_t *h_changed, void *cuda_stream);
 
 /* Accurate execution path: d_out[i] = region(d_in[:, i]) for all i < N
  * (the non-approximated region the paper's speedups are measured against). */

@@ -101,8 +101,8 @@ extern "C" hpac_status hpac_region_adjoint(hpac_region *r, const void *d_in, voi
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, r->device);
   int64_t blocks = (d.n + 255) / 256;
   if (blocks > (int64_t)sms * 8) blocks = (int64_t)sms * 8;
-  if (d.kind == HPAC_REGION_BINOMIAL)
-    return set_error(HPAC_EUNSUPPORTED, "no adjoint of the Binomial region");
+  if (d.kind == HPAC_REGION_BINOMIAL || d.kind == HPAC_REGION_KMEANS)
+    return set_error(HPAC_EUNSUPPORTED, "no adjoint of region kind %d", d.kind);
   switch (d.kind) {
     case HPAC_REGION_BLACKSCHOLES:
       if (d.dtype == HPAC_F32)

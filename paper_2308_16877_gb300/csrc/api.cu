@@ -48,7 +48,7 @@ static hpac_status check_desc(const hpac_region_desc *d) {
     return set_error(HPAC_EINVAL, "block_threads = %d, must be a multiple of 32 in 32..1024",
                      d->block_threads);
   if (d->dtype != HPAC_F32 && d->dtype != HPAC_F64) return set_error(HPAC_EINVAL, "dtype %d", d->dtype);
-  if (d->kind != HPAC_REGION_BINOMIAL && d->arg != 0)
+  if (d->kind != HPAC_REGION_BINOMIAL && d->kind != HPAC_REGION_KMEANS && d->arg != 0)
     return set_error(HPAC_EINVAL, "arg must be 0 for region kind %d", d->kind);
   if (!isfinite(d->param)) return set_error(HPAC_EINVAL, "param is not finite");
   switch (d->kind) {
@@ -60,6 +60,12 @@ static hpac_status check_desc(const hpac_region_desc *d) {
       if (d->dtype != HPAC_F64) return set_error(HPAC_EUNSUPPORTED, "EOS is double precision only");
       break;
     case HPAC_REGION_IDENTITY:
+      break;
+    case HPAC_REGION_KMEANS:
+      if (d->n_in != 8) return set_error(HPAC_EINVAL, "K-Means takes 8 features");
+      if (d->dtype != HPAC_F32) return set_error(HPAC_EUNSUPPORTED, "K-Means is single precision only");
+      if (d->arg < 1 || d->arg > kMaxClusters)
+        return set_error(HPAC_EINVAL, "K-Means clusters %d not in 1..%d", d->arg, kMaxClusters);
       break;
     case HPAC_REGION_BINOMIAL:
       if (d->n_in != 4) return set_error(HPAC_EINVAL, "Binomial takes 4 inputs");
@@ -76,6 +82,8 @@ static hpac_status check_desc(const hpac_region_desc *d) {
 static hpac_status check_call(hpac_region *r, const void *in, const void *out) {
   if (!r) return set_error(HPAC_EINVAL, "region is NULL");
   if (r->d.n > 0 && (!in || !out)) return set_error(HPAC_EINVAL, "input or output pointer is NULL");
+  if (r->d.kind == HPAC_REGION_KMEANS && !r->aux)
+    return set_error(HPAC_EINVAL, "K-Means region without centroids (hpac_region_set_aux)");
   int dev = -1;
   HPAC_CUDA_TRY(cudaGetDevice(&dev));
   if (dev != r->device)
@@ -182,6 +190,14 @@ hpac_status hpac_region_set_persistent(hpac_region *r, int32_t enable) {
     memset(r->state_key, 0, sizeof(r->state_key));
   }
   r->persist = enable;
+  return HPAC_OK;
+}
+
+hpac_status hpac_region_set_aux(hpac_region *r, const void *d_aux) {
+  if (!r) return set_error(HPAC_EINVAL, "region is NULL");
+  if (r->d.kind != HPAC_REGION_KMEANS) return set_error(HPAC_EINVAL, "region kind %d takes no aux", r->d.kind);
+  if (!d_aux) return set_error(HPAC_EINVAL, "aux is NULL");
+  r->aux = d_aux;
   return HPAC_OK;
 }
 

@@ -186,6 +186,9 @@ hpac_status dispatch_map(const hpac_region *r, const void *in, void *out, uint8_
     case HPAC_REGION_IDENTITY:
       if (d.dtype == HPAC_F32) return launch_map(r, Identity<float>{}, in, out, mask, rule, counters);
       return launch_map(r, Identity<double>{}, in, out, mask, rule, counters);
+    case HPAC_REGION_KMEANS:
+      return launch_map(r, KMeans32{static_cast<const float *>(r->aux), d.arg}, in, out, mask, rule,
+                        counters);
   }
   return set_error(HPAC_EUNSUPPORTED, "region kind %d", d.kind);
 }

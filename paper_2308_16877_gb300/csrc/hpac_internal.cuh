@@ -15,6 +15,7 @@ struct hpac_region {
   void *d_state;                   // their device copy (region-owned)
   size_t state_bytes;
   int64_t state_key[6];            // technique and shape the copy holds
+  const void *aux;                 // K-Means: the caller's centroids (device)
 };
 
 namespace hpac {
@@ -24,6 +25,7 @@ constexpr int kMaxIn = 8;
 constexpr int kMaxHsize = 64;
 constexpr int kMaxTsize = 64;
 constexpr int kMaxBinomialSteps = 1024;
+constexpr int kMaxClusters = 64;
 constexpr double kBorderRel = 1e-6;
 
 // Thread-local error reporting (hpac_last_error).

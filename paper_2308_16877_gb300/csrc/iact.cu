@@ -294,6 +294,9 @@ hpac_status launch_iact(hpac_region *r, const hpac_iact_knobs *k, const void *in
     case HPAC_REGION_IDENTITY:
       if (d.dtype == HPAC_F32) return launch(r, Identity<float>{}, k, in, out, mask, stat, counters);
       return launch(r, Identity<double>{}, k, in, out, mask, stat, counters);
+    case HPAC_REGION_KMEANS:
+      return launch(r, KMeans32{static_cast<const float *>(r->aux), d.arg}, k, in, out, mask, stat,
+                    counters);
   }
   return set_error(HPAC_EUNSUPPORTED, "region kind %d", d.kind);
 }

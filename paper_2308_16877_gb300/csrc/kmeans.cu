@@ -1,0 +1,97 @@
+// K-Means centroid update, the exact step between two (approximated)
+// assignments (Table 1, K-Means: iterate until no observation changes
+// cluster). One pass over the observations: each block accumulates the
+// per-cluster feature sums (double) and counts in shared memory, then adds
+// them to the workspace with one atomic per value; a second tiny kernel
+// divides. Changed assignments are counted in the same pass.
+#include "hpac_internal.cuh"
+
+namespace hpac {
+namespace {
+
+constexpr int kThreads = 256;
+
+__global__ void __launch_bounds__(kThreads) kmeans_sums(const float *__restrict__ x, int64_t stride,
+                                                        int64_t n, int K,
+                                                        const float *__restrict__ assign,
+                                                        const float *__restrict__ prev,
+                                                        double *__restrict__ sum,
+                                                        unsigned long long *__restrict__ cnt,
+                                                        unsigned long long *__restrict__ changed) {
+  __shared__ double s_sum[kMaxClusters * 8];
+  __shared__ unsigned long long s_cnt[kMaxClusters];
+  for (int j = threadIdx.x; j < K * 8; j += blockDim.x) s_sum[j] = 0.0;
+  for (int j = threadIdx.x; j < K; j += blockDim.x) s_cnt[j] = 0;
+  __syncthreads();
+  unsigned ch = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const float a = assign[i];
+    const int k = (int)a;
+    if (k >= 0 && k < K) {  // ids are produced in range; anything else is left out
+      atomicAdd(&s_cnt[k], 1ull);
+#pragma unroll
+      for (int d = 0; d < 8; ++d) atomicAdd(&s_sum[k * 8 + d], (double)x[d * stride + i]);
+    }
+    if (prev && prev[i] != a) ++ch;
+  }
+  ch = __reduce_add_sync(0xffffffffu, ch);
+  if ((threadIdx.x & 31) == 0 && ch) atomicAdd(changed, (unsigned long long)ch);
+  __syncthreads();
+  for (int j = threadIdx.x; j < K * 8; j += blockDim.x)
+    if (s_sum[j] != 0.0) atomicAdd(&sum[j], s_sum[j]);
+  for (int j = threadIdx.x; j < K; j += blockDim.x)
+    if (s_cnt[j]) atomicAdd(&cnt[j], s_cnt[j]);
+}
+
+__global__ void kmeans_divide(int K, const double *__restrict__ sum,
+                              const unsigned long long *__restrict__ cnt, float *__restrict__ cent) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= K * 8) return;
+  const unsigned long long c = cnt[j / 8];
+  if (c) cent[j] = (float)(sum[j] / (double)c);  // an empty cluster keeps its centroid
+}
+
+}  // namespace
+}  // namespace hpac
+
+using namespace hpac;
+
+extern "C" size_t hpac_kmeans_workspace_bytes(int32_t clusters) {
+  if (clusters < 1 || clusters > kMaxClusters) return 0;
+  return (size_t)(clusters * 8 + clusters + 1) * 8;
+}
+
+extern "C" hpac_status hpac_kmeans_update(int64_t n, int32_t clusters, const float *d_x,
+                                          int64_t stride, const float *d_assign,
+                                          const float *d_prev, float *d_cent, void *d_work,
+                                          int64_t *h_changed, void *cuda_stream) {
+  if (n < 0 || clusters < 1 || clusters > kMaxClusters || stride < n)
+    return set_error(HPAC_EINVAL, "K-Means update: bad n, clusters or stride");
+  if (!d_cent || !d_work || (n > 0 && (!d_x || !d_assign)))
+    return set_error(HPAC_EINVAL, "K-Means update: NULL pointer");
+  if ((uintptr_t)d_work % 8) return set_error(HPAC_EINVAL, "workspace not 8-byte aligned");
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  double *sum = static_cast<double *>(d_work);
+  unsigned long long *cnt = reinterpret_cast<unsigned long long *>(sum + clusters * 8);
+  unsigned long long *changed = cnt + clusters;
+  HPAC_CUDA_TRY(cudaMemsetAsync(d_work, 0, hpac_kmeans_workspace_bytes(clusters), s));
+  int dev = 0, sms = 148;
+  HPAC_CUDA_TRY(cudaGetDevice(&dev));
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  int64_t blocks = (n + kThreads - 1) / kThreads;
+  const int64_t cap = (int64_t)sms * 4;
+  blocks = blocks < 1 ? 1 : blocks > cap ? cap : blocks;
+  kmeans_sums<<<(unsigned)blocks, kThreads, 0, s>>>(d_x, stride, n, clusters, d_assign, d_prev, sum,
+                                                      cnt, changed);
+  HPAC_CUDA_TRY(cudaGetLastError());
+  kmeans_divide<<<(clusters * 8 + 255) / 256, 256, 0, s>>>(clusters, sum, cnt, d_cent);
+  HPAC_CUDA_TRY(cudaGetLastError());
+  if (h_changed) {
+    unsigned long long c = 0;
+    HPAC_CUDA_TRY(cudaMemcpyAsync(&c, changed, sizeof(c), cudaMemcpyDeviceToHost, s));
+    HPAC_CUDA_TRY(cudaStreamSynchronize(s));
+    *h_changed = (int64_t)c;
+  }
+  return HPAC_OK;
+}

@@ -93,6 +93,34 @@ struct Eos64 {
   }
 };
 
+// K-Means assignment (Table 1, K-Means; Section 4.2 approximates this
+// distance kernel): the nearest of K centroids (cent[k * 8 + d], read-only
+// cache) in squared Euclidean distance over 8 features, summed over d in order
+// in IEEE single precision, ties to the lowest index; the id as a float.
+struct KMeans32 {
+  using T = float;
+  static constexpr int kReads = 8;
+  const float *cent;
+  int K;
+  __device__ __forceinline__ float operator()(const float *x) const {
+    int best = 0;
+    float bd = 0.0f;
+    for (int k = 0; k < K; ++k) {
+      float acc = 0.0f;
+#pragma unroll
+      for (int d = 0; d < 8; ++d) {
+        const float df = __fsub_rn(x[d], __ldg(cent + k * 8 + d));
+        acc = __fadd_rn(acc, __fmul_rn(df, df));
+      }
+      if (k == 0 || acc < bd) {
+        bd = acc;
+        best = k;
+      }
+    }
+    return (float)best;
+  }
+};
+
 template <typename T_>
 struct Identity {
   using T = T_;

@@ -16,6 +16,7 @@ HPAC_OK, HPAC_EINVAL, HPAC_ENOMEM, HPAC_ECUDA, HPAC_ETIMEOUT, HPAC_EUNSUPPORTED 
 HPAC_F32, HPAC_F64 = 0, 1
 HPAC_LEVEL_THREAD, HPAC_LEVEL_WARP, HPAC_LEVEL_BLOCK = 0, 1, 2
 HPAC_REGION_BLACKSCHOLES, HPAC_REGION_EOS, HPAC_REGION_IDENTITY, HPAC_REGION_BINOMIAL = 0, 1, 3, 4
+HPAC_REGION_KMEANS = 5
 HPAC_PERFO_SMALL, HPAC_PERFO_LARGE, HPAC_PERFO_INI, HPAC_PERFO_FINI, HPAC_PERFO_RANDOM = range(5)
 HPAC_MASK_EXACT, HPAC_MASK_APPROX, HPAC_MASK_SKIPPED = 0, 1, 2
 HPAC_METRIC_MAPE, HPAC_METRIC_RMSE, HPAC_METRIC_MCR = 0, 1, 2
@@ -107,6 +108,10 @@ SIGNATURES = {
                                C.POINTER(hpac_quality_result), _P]),
     "hpac_quality_noalloc": (C.c_int, [C.c_int32, C.c_int64, _P, _P, C.c_int32,
                                        C.POINTER(hpac_quality_result), _P]),
+    "hpac_region_set_aux": (C.c_int, [_P, _P]),
+    "hpac_kmeans_workspace_bytes": (C.c_size_t, [C.c_int32]),
+    "hpac_kmeans_update": (C.c_int, [C.c_int64, C.c_int32, _P, C.c_int64, _P, _P, _P, _P,
+                                     C.POINTER(C.c_int64), _P]),
     "hpac_hydro_init": (C.c_int, [C.POINTER(hpac_hydro_state), _P]),
     "hpac_hydro_step": (C.c_int, [C.POINTER(hpac_hydro_state), _P, C.c_int32, _P, _P,
                                   C.POINTER(hpac_stats)]),
@@ -358,6 +363,11 @@ class Region:
     def reset_state(self):
         hpac_region_reset_state(self._h)
 
+    def set_aux(self, aux):
+        """K-Means: the centroids (K, 8) float32 CUDA tensor later runs read."""
+        self._aux = aux
+        _check(load().hpac_region_set_aux(self._h, _ptr(aux)), "hpac_region_set_aux")
+
     def _check_io(self, x, out, mask=None, stat=None):
         if x.dtype != self.dtype or out.dtype != self.dtype:
             raise TypeError("dtype mismatch")
@@ -400,6 +410,25 @@ class Region:
                             C.cast(sc, C.POINTER(C.c_double)) if sc is not None else None)
         st = hpac_run_iact(self._h, k, _ptr(x), _ptr(out), _ptr(mask), _ptr(stat), stats)
         return st.as_dict() if st is not None else None
+
+
+def kmeans_update(x, assign, cent, work, prev=None, stream=None, changed=True):
+    """One exact centroid update (hpac_kmeans_update) on CUDA tensors: x (8,
+    stride) float32, assign / prev float32 ids, cent (K, 8) float32 updated in
+    place, work a device buffer of hpac_kmeans_workspace_bytes(K) bytes.
+    Returns the number of changed assignments (waits) when changed, else None."""
+    ch = C.c_int64(0)
+    _check(load().hpac_kmeans_update(int(assign.numel()), int(cent.shape[0]), _ptr(x), int(x.shape[1]),
+                                     _ptr(assign), _ptr(prev), _ptr(cent), _ptr(work),
+                                     C.byref(ch) if changed else None, _stream_handle(stream)),
+           "hpac_kmeans_update")
+    return int(ch.value) if changed else None
+
+
+def kmeans_workspace(clusters, device=None):
+    import torch
+    nbytes = load().hpac_kmeans_workspace_bytes(int(clusters))
+    return torch.zeros(nbytes // 8, dtype=torch.float64, device=device or "cuda")
 
 
 def quality(exact, approx, metric, stream=None):
