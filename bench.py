@@ -480,6 +480,71 @@ def bench_binomial(hpac, torch, dev, stream, members=4096, time_points=64, steps
             "table": rows}
 
 
+def bench_kmeans(hpac, torch, dev, stream, n=1 << 22, clusters=16, max_iter=300):
+    """K-Means (Table 1; the distance kernel is the approximated region,
+    Section 4.2): 4M observations of 8 features from 16 overlapping blobs,
+    started from the first 16 observations, iterated until no observation
+    changes cluster. Exact, TAF and iACT with kernel-scoped state (T = N/8),
+    TAF and iACT with state kept across iterations (T = N: one logical thread
+    per observation, so a window holds that observation's recent ids), and
+    herded perforation (a skipped observation keeps its previous id). Reported:
+    iterations, time to convergence (assignment + update + the changed-count
+    read every iteration), and MCR of the final ids against the exact run's."""
+    x, labels, _ = W.kmeans_blobs(n, clusters, spread=2.0)
+    xd = torch.from_numpy(x).to(dev)
+    init = torch.from_numpy(np.ascontiguousarray(x[:, :clusters].T)).to(dev)
+    sc = W.iact_scale(x, n)
+    work = hpac.kmeans_workspace(clusters, dev)
+    cent = init.clone()
+    a = torch.zeros(n, dtype=torch.float32, device=dev)
+    prev = torch.zeros(n, dtype=torch.float32, device=dev)
+    regions = {T: hpac.Region(hpac.HPAC_REGION_KMEANS, xd, arg=clusters, logical_threads=T,
+                              block_threads=256, stream=stream) for T in (n // 8, n)}
+    for R in regions.values():
+        R.set_aux(cent)
+    variants = {
+        "exact": (n // 8, False, lambda R: R.run_exact(xd, a)),
+        "taf_h2p4": (n // 8, False, lambda R: R.run_taf(xd, a, 2, 4, 0.01, 0)),
+        "taf_persistent_h2p4": (n, True, lambda R: R.run_taf(xd, a, 2, 4, 0.01, 0)),
+        "taf_persistent_h3p8": (n, True, lambda R: R.run_taf(xd, a, 3, 8, 0.01, 0)),
+        "taf_persistent_h8p1": (n, True, lambda R: R.run_taf(xd, a, 8, 1, 0.01, 0)),
+        "iact_t8": (n // 8, False, lambda R: R.run_iact(xd, a, 8, 32, 0.02, 0, in_scale=sc)),
+        "iact_persistent_t4": (n, True, lambda R: R.run_iact(xd, a, 4, 32, 0.01, 0, in_scale=sc)),
+        "perfo_small2": (n // 8, False, lambda R: R.run_perfo(xd, a, hpac.HPAC_PERFO_SMALL, 2, herded=True)),
+        "perfo_small4": (n // 8, False, lambda R: R.run_perfo(xd, a, hpac.HPAC_PERFO_SMALL, 4, herded=True)),
+    }
+    res, ref = {}, None
+    for name, (T, persist, run) in variants.items():
+        R = regions[T]
+        for rep in range(2):                           # the first run warms up
+            cent.copy_(init)
+            a.zero_()
+            R.set_persistent(persist)
+            R.reset_state()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for it in range(1, max_iter + 1):
+                run(R)
+                ch = hpac.kmeans_update(xd, a, cent, work, prev=prev if it > 1 else None, stream=stream)
+                if it > 1 and ch == 0:
+                    break
+                prev.copy_(a)
+            torch.cuda.synchronize()
+            ms = (time.perf_counter() - t0) * 1e3
+        row = {"iterations": it, "ms": ms, "converged": it < max_iter}
+        if name == "exact":
+            ref = a.clone()
+        else:
+            row["mcr_vs_exact"] = hpac.quality(ref.double(), a, hpac.HPAC_METRIC_MCR, stream=stream)["value"]
+            row["speedup_vs_exact"] = res["exact"]["ms"] / ms
+            row["convergence_speedup"] = res["exact"]["iterations"] / it
+        res[name] = row
+        R.set_persistent(False)
+    for R in regions.values():
+        R.close()
+    return {"observations": n, "features": 8, "clusters": clusters, "runs": res}
+
+
 def calibrate_floor(pred, exact, target=0.01, q=0.99):
     """Smallest price floor tau such that, among predictions >= tau, the q-th
     quantile of the relative error |pred - exact| / |exact| is at most target."""
@@ -791,6 +856,7 @@ def main(argv=None):
     ap.add_argument("--no-persistent", action="store_true")
     ap.add_argument("--no-search", action="store_true")
     ap.add_argument("--no-binomial", action="store_true")
+    ap.add_argument("--no-kmeans", action="store_true")
     args = ap.parse_args(argv)
     if args.impl == "reference":
         return run_reference(args)
@@ -981,6 +1047,7 @@ def main(argv=None):
     sweep = None if args.no_sweep else bench_sweep(hpac, torch, dev, stream)
     knob_search = None if args.no_search else bench_search(hpac, torch, dev, stream)
     binomial = None if args.no_binomial else bench_binomial(hpac, torch, dev, stream)
+    kmeans = None if args.no_kmeans else bench_kmeans(hpac, torch, dev, stream)
     surrogate = None if args.no_surrogate else bench_surrogate(hpac, torch, dev, stream)
     large = None if args.no_hydro_large else bench_hydro_large(hpac, torch, dev, stream)
     persistent = None if args.no_persistent else bench_persistent(hpac, torch, dev, stream)
@@ -1017,6 +1084,7 @@ def main(argv=None):
             "sweep": sweep,
             "search": knob_search,
             "binomial": binomial,
+            "kmeans": kmeans,
             "surrogate": surrogate,
             "hydro_large": large,
             "persistent_state": persistent,
