@@ -121,15 +121,13 @@ static float binomial_call_f32(float S0, float X, float T, float sig, double r, 
   float puA = (float)(pu / a), pdA = (float)(pd / a), uf = (float)u;
   for (int j = 0; j <= N; ++j) {
     S[j] = (float)((double)S0 * exp(v * (double)(2 * j - N)));
-    float ex = S[j] - X;
-    V[j] = ex > 0.0f ? ex : 0.0f;
+    V[j] = fmaxf(S[j] - X, 0.0f);
   }
   for (int n = N - 1; n >= 0; --n)
     for (int j = 0; j <= n; ++j) {
       float cont = fmaf(puA, V[j + 1], pdA * V[j]);
       S[j] = S[j] * uf;
-      float ex = S[j] - X;
-      V[j] = cont > ex ? cont : ex;
+      V[j] = fmaxf(cont, S[j] - X);
     }
   return V[0];
 }

@@ -54,19 +54,33 @@ __device__ __forceinline__ float team_price(float S0, float X, float Tm, float s
     const float Sj = j <= N ? (float)Sd : 0.0f;
     Sd *= step;
     S[s] = Sj;
-    const float ex = __fsub_rn(Sj, X);
-    V[s] = ex > 0.0f ? ex : 0.0f;
+    V[s] = fmaxf(__fsub_rn(Sj, X), 0.0f);
   }
   for (int n = N - 1; n >= 0; --n) {
+    // slots in groups of four with one warp-uniform test per group (the level
+    // has nodes 0..n; up to three slots past it are computed and never read),
+    // so the four shuffles of a group issue back to back
 #pragma unroll
-    for (int s = 0; s < NPL; ++s) {
-      if (32 * s > n) break;  // warp-uniform: the level has nodes 0..n
-      const float send = lane == 0 ? (s + 1 < NPL ? V[s + 1] : 0.0f) : V[s];
-      const float up = __shfl_sync(kFull, send, (lane + 1) & 31);
-      const float cont = __fmaf_rn(c.puA, up, __fmul_rn(c.pdA, V[s]));
-      S[s] = __fmul_rn(S[s], c.uf);
-      const float ex = __fsub_rn(S[s], X);
-      V[s] = cont > ex ? cont : ex;
+    for (int s0 = 0; s0 < NPL; s0 += 4) {
+      if (32 * s0 > n) break;
+      float up[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int s = s0 + q;
+        if (s < NPL) {
+          const float send = lane == 0 ? (s + 1 < NPL ? V[s + 1] : 0.0f) : V[s];
+          up[q] = __shfl_sync(kFull, send, (lane + 1) & 31);
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int s = s0 + q;
+        if (s < NPL) {
+          const float cont = __fmaf_rn(c.puA, up[q], __fmul_rn(c.pdA, V[s]));
+          S[s] = __fmul_rn(S[s], c.uf);
+          V[s] = fmaxf(cont, __fsub_rn(S[s], X));  // early exercise
+        }
+      }
     }
   }
   return __shfl_sync(kFull, V[0], 0);
