@@ -50,7 +50,9 @@ __host__ __device__ inline size_t warp_table_bytes(int tsize, int D, int g) {
 // DC: the number of inputs when fixed by the region (4 for Black-Scholes and
 // the EOS), so that the distance loops are fully unrolled; 0 reads P.D.
 // COUNT: the caller asked for counters.
-template <class R, int LEVEL, int DC, bool COUNT>
+// PERSIST: the warp's tables are loaded from and saved to st (persistent
+// state), in a separate instantiation so the plain kernels carry none of it.
+template <class R, int LEVEL, int DC, bool COUNT, bool PERSIST = false>
 __global__ void __launch_bounds__(1024) iact_kernel(R reg, const typename R::T *__restrict__ in,
                                                     int64_t stride, typename R::T *__restrict__ out,
                                                     uint8_t *__restrict__ mask,
@@ -78,7 +80,7 @@ __global__ void __launch_bounds__(1024) iact_kernel(R reg, const typename R::T *
   // logical warp of this physical warp; with persistent state (st, one table
   // image of wbytes per logical warp) its tables resume from the last call
   const int64_t gwarp = ((int64_t)blockIdx.x * blockDim.x) / 32 + warp;
-  const bool has_state = st != nullptr && gwarp * 32 < T;
+  const bool has_state = PERSIST && gwarp * 32 < T;
   uint32_t *wst = has_state ? st + (size_t)gwarp * (wbytes / 4) : nullptr;
   if (has_state) {
     uint32_t *dst = reinterpret_cast<uint32_t *>(base);
@@ -252,21 +254,27 @@ hpac_status launch(hpac_region *r, R reg, const hpac_iact_knobs *k, const void *
   constexpr int kDC = R::kReads == 4 ? 4 : 0;
   switch (k->level) {
     case HPAC_LEVEL_THREAD: {
-      auto fn = counters ? iact_kernel<R, HPAC_LEVEL_THREAD, kDC, true> : iact_kernel<R, HPAC_LEVEL_THREAD, kDC, false>;
+      auto fn = st_words ? (counters ? iact_kernel<R, HPAC_LEVEL_THREAD, kDC, true, true>
+                                     : iact_kernel<R, HPAC_LEVEL_THREAD, kDC, false, true>)
+                         : (counters ? iact_kernel<R, HPAC_LEVEL_THREAD, kDC, true> : iact_kernel<R, HPAC_LEVEL_THREAD, kDC, false>);
       HPAC_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
       fn<<<(unsigned)blocks, B, smem, r->stream>>>(reg, x, d.in_stride, o, mask, st, d.n, T, P, counters,
                                                    st_words);
       break;
     }
     case HPAC_LEVEL_WARP: {
-      auto fn = counters ? iact_kernel<R, HPAC_LEVEL_WARP, kDC, true> : iact_kernel<R, HPAC_LEVEL_WARP, kDC, false>;
+      auto fn = st_words ? (counters ? iact_kernel<R, HPAC_LEVEL_WARP, kDC, true, true>
+                                     : iact_kernel<R, HPAC_LEVEL_WARP, kDC, false, true>)
+                         : (counters ? iact_kernel<R, HPAC_LEVEL_WARP, kDC, true> : iact_kernel<R, HPAC_LEVEL_WARP, kDC, false>);
       HPAC_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
       fn<<<(unsigned)blocks, B, smem, r->stream>>>(reg, x, d.in_stride, o, mask, st, d.n, T, P, counters,
                                                    st_words);
       break;
     }
     default: {
-      auto fn = counters ? iact_kernel<R, HPAC_LEVEL_BLOCK, kDC, true> : iact_kernel<R, HPAC_LEVEL_BLOCK, kDC, false>;
+      auto fn = st_words ? (counters ? iact_kernel<R, HPAC_LEVEL_BLOCK, kDC, true, true>
+                                     : iact_kernel<R, HPAC_LEVEL_BLOCK, kDC, false, true>)
+                         : (counters ? iact_kernel<R, HPAC_LEVEL_BLOCK, kDC, true> : iact_kernel<R, HPAC_LEVEL_BLOCK, kDC, false>);
       HPAC_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
       fn<<<(unsigned)blocks, B, smem, r->stream>>>(reg, x, d.in_stride, o, mask, st, d.n, T, P, counters,
                                                    st_words);

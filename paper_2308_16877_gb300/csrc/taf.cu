@@ -21,7 +21,10 @@ namespace {
 // in registers (shifted on insertion, oldest first), so the statistic is two
 // unrolled passes over registers. KH = 0: the window is in shared memory and h
 // is a run-time argument.
-template <class R, int LEVEL, int KH>
+// PERSIST: the window and owed predictions are read from and written back to
+// st_* (persistent state); a separate instantiation so that the plain kernels
+// carry none of its registers. Persistent runs use the shared-memory window.
+template <class R, int LEVEL, int KH, bool PERSIST = false>
 __global__ void __launch_bounds__(1024) taf_kernel(R reg, const typename R::T *__restrict__ in,
                                                    int64_t stride, typename R::T *__restrict__ out,
                                                    uint8_t *__restrict__ mask,
@@ -59,7 +62,7 @@ __global__ void __launch_bounds__(1024) taf_kernel(R reg, const typename R::T *_
   int pred = 0;  // predictions still owed
   unsigned long long n_apx = 0, n_border = 0;
   // persistent state (st_vals[j * T + t], oldest first, j < cnt): resume
-  if (st_cnt && t < T) {
+  if (PERSIST && t < T) {
     cnt = st_cnt[t];
     pred = st_pred[t];
     if (KH > 0) {
@@ -144,7 +147,7 @@ __global__ void __launch_bounds__(1024) taf_kernel(R reg, const typename R::T *_
       }
     }
   }
-  if (st_cnt && t < T) {  // persistent state: save where this thread stopped
+  if (PERSIST && t < T) {  // persistent state: save where this thread stopped
     st_cnt[t] = cnt;
     st_pred[t] = pred;
     if (KH > 0) {
@@ -186,7 +189,8 @@ hpac_status launch(hpac_region *r, R reg, const hpac_taf_knobs *k, const void *i
   int *st_pred = sb ? reinterpret_cast<int *>(sb + b_vals + b_int) : nullptr;
   const int B = d.block_threads;
   const int h = k->hsize;
-  const int kh = (h == 2 || h == 4 || h == 8) ? h : 0;  // register-window sizes
+  // register-window sizes; persistent state runs the shared-memory window
+  const int kh = !sb && (h == 2 || h == 4 || h == 8) ? h : 0;
   const size_t smem = kh ? 0 : (size_t)h * B * sizeof(V);
   const int limit = max_dyn_smem(r->device);
   if ((int64_t)smem > limit)
@@ -207,7 +211,10 @@ hpac_status launch(hpac_region *r, R reg, const hpac_taf_knobs *k, const void *i
        taf_kernel<R, HPAC_LEVEL_WARP, 4>, taf_kernel<R, HPAC_LEVEL_WARP, 8>},
       {taf_kernel<R, HPAC_LEVEL_BLOCK, 0>, taf_kernel<R, HPAC_LEVEL_BLOCK, 2>,
        taf_kernel<R, HPAC_LEVEL_BLOCK, 4>, taf_kernel<R, HPAC_LEVEL_BLOCK, 8>}};
-  const Fn fn = table[lvl][kh == 0 ? 0 : kh == 2 ? 1 : kh == 4 ? 2 : 3];
+  static const Fn persistent[3] = {taf_kernel<R, HPAC_LEVEL_THREAD, 0, true>,
+                                   taf_kernel<R, HPAC_LEVEL_WARP, 0, true>,
+                                   taf_kernel<R, HPAC_LEVEL_BLOCK, 0, true>};
+  const Fn fn = sb ? persistent[lvl] : table[lvl][kh == 0 ? 0 : kh == 2 ? 1 : kh == 4 ? 2 : 3];
   if (smem > 0)
     HPAC_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   fn<<<(unsigned)blocks, B, smem, r->stream>>>(reg, x, d.in_stride, o, mask, st, d.n, T, h, k->psize,
