@@ -56,11 +56,12 @@ IACT = dict(tsize=8, tperwarp=32, thresh=1e-3, level=0)
 IACT_SCALE = (1.0 / W.HYDRO_E0, 1.0, 10.0, 1.0 / ((GAMMA - 1.0) * W.HYDRO_E0))
 
 # FP64 operations of the element kernel per element, each add, multiply or FMA
-# one issue slot of the FP64 pipe: 21 corner-pair cross products (126), 135
-# signed accumulations, 21 relative-position subtractions, 21 corner-0 sums,
-# 8 for the volume, 1 for dv; the division V / V0 counts as one. Its ceiling is
-# the measured FMA rate in the same unit (FMA per second).
-ELEM_OPS = 126 + 135 + 21 + 21 + 8 + 1 + 1
+# one issue slot of the FP64 pipe: 15 shared corner-pair cross products (90),
+# their 42 scatters less 7 first assignments (105 adds), 3 single-use pairs as
+# fused multiply-adds (18), 21 relative-position subtractions, 18 corner-0
+# sums, 8 for the volume, 1 for dv; the division V / V0 counts as one. Its
+# ceiling is the measured FMA rate in the same unit (FMA per second).
+ELEM_OPS = 90 + 105 + 18 + 21 + 18 + 8 + 1 + 1
 
 BS_N = 1 << 24
 BS_TAF = dict(hsize=4, psize=8, thresh=0.005, level=0)

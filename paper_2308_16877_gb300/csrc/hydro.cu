@@ -23,10 +23,9 @@
 // of s times the cross product of the other two corners (oriented as in the
 // determinant), and corner 0 gets minus the sum of the others. The kernel
 // stores 12 dV/dP_c (the 1/12 is applied where the gradient is used).
-// Cost per element: 45 cross products (270 FP64 multiply / FMA), 135 signed
-// accumulations (FMA), 21 subtractions for the relative positions, 21 sums for
-// corner 0 and 7 FMA for the volume: about 460 FP64 instructions (734 flops
-// counting an FMA as two), the bulk of the step on GB300's narrow FP64 pipe.
+// Cost per element: the 15 triples share 18 corner-pair cross products, formed
+// once each and scattered to their corners (hex_grad12): 260 FP64 operations
+// with the relative positions, the bulk of the step on GB300's narrow FP64 pipe.
 #include <math.h>
 
 #include "hpac_internal.cuh"
@@ -37,12 +36,39 @@ namespace {
 constexpr double kCq = 2.0;   // quadratic viscosity coefficient
 constexpr double kCl = 0.5;   // linear viscosity coefficient
 
-// The 15 corner triples (a < b < c, all > 0) with their signs s_abc.
-struct Tri { int a, b, c, s; };
-__device__ constexpr Tri kTri[15] = {
-    {1, 2, 3, 1}, {1, 3, 5, 1}, {1, 3, 7, 1}, {1, 4, 5, -1}, {1, 5, 7, -1},
-    {2, 3, 6, -1}, {2, 3, 7, -1}, {2, 4, 6, 1}, {2, 6, 7, 1}, {3, 5, 7, -1},
-    {3, 6, 7, 1}, {4, 5, 6, 1}, {4, 5, 7, 1}, {4, 6, 7, -1}, {5, 6, 7, -1}};
+// The 15 corner triples (a < b < c, all > 0) with signs s_abc hold 18
+// distinct corner pairs. Triple (a, b, c) adds s P_b x P_c to 12 dV/dP_a,
+// -s P_a x P_c to 12 dV/dP_b and s P_a x P_b to 12 dV/dP_c, so each pair's cross
+// product C_ij = P_i x P_j is formed once and scattered to the corners that use
+// it. kPairs lists the 15 pairs used two to four times (corner k, sign, and
+// whether it is the corner's first term, which assigns instead of adding), in
+// an order that touches every corner 1..7 before any single-use pair;
+// kSingle the 3 pairs used once, added with two fused multiply-adds per
+// component instead of a cross product and an add.
+struct PairUse {
+  int i, j, n;
+  int k[4], s[4], first[4];
+};
+__device__ constexpr PairUse kPairs[15] = {
+    {1, 3, 3, {2, 5, 7, 0}, {-1, 1, 1, 0}, {1, 1, 1, 0}},
+    {1, 5, 3, {3, 4, 7, 0}, {-1, 1, -1, 0}, {1, 1, 0, 0}},
+    {1, 7, 2, {3, 5, 0, 0}, {-1, 1, 0, 0}, {0, 0, 0, 0}},
+    {2, 3, 3, {1, 6, 7, 0}, {1, -1, -1, 0}, {1, 1, 0, 0}},
+    {2, 6, 3, {3, 4, 7, 0}, {1, -1, 1, 0}, {0, 0, 0, 0}},
+    {2, 7, 2, {3, 6, 0, 0}, {1, -1, 0, 0}, {0, 0, 0, 0}},
+    {3, 5, 2, {1, 7, 0, 0}, {1, -1, 0, 0}, {0, 0, 0, 0}},
+    {3, 6, 2, {2, 7, 0, 0}, {-1, 1, 0, 0}, {0, 0, 0, 0}},
+    {3, 7, 4, {1, 2, 5, 6}, {1, -1, 1, -1}, {0, 0, 0, 0}},
+    {4, 5, 3, {1, 6, 7, 0}, {-1, 1, 1, 0}, {0, 0, 0, 0}},
+    {4, 6, 3, {2, 5, 7, 0}, {1, -1, -1, 0}, {0, 0, 0, 0}},
+    {4, 7, 2, {5, 6, 0, 0}, {-1, 1, 0, 0}, {0, 0, 0, 0}},
+    {5, 6, 2, {4, 7, 0, 0}, {1, -1, 0, 0}, {0, 0, 0, 0}},
+    {5, 7, 4, {1, 3, 4, 6}, {-1, -1, 1, 1}, {0, 0, 0, 0}},
+    {6, 7, 4, {2, 3, 4, 5}, {1, 1, -1, -1}, {0, 0, 0, 0}}};
+struct SingleUse {
+  int i, j, k, s;
+};
+__device__ constexpr SingleUse kSingle[3] = {{1, 2, 3, 1}, {1, 4, 5, -1}, {2, 4, 6, 1}};
 
 __device__ __forceinline__ void cross3(double ax, double ay, double az, double bx, double by,
                                        double bz, double &cx, double &cy, double &cz) {
@@ -52,36 +78,49 @@ __device__ __forceinline__ void cross3(double ax, double ay, double az, double b
 }
 
 // 12 dV/dP_c for the corners (relative to corner 0) and the volume V.
+// FP64 operations: 15 cross products (90), 42 scatters less the 7 first
+// assignments (105 adds), 3 fused single-use pairs (18), corner 0 (18), the
+// volume (8): 239, plus the 21 subtractions of the relative positions.
 __device__ __forceinline__ double hex_grad12(const double (&X)[8], const double (&Y)[8],
                                              const double (&Z)[8], double (&gx)[8], double (&gy)[8],
                                              double (&gz)[8]) {
 #pragma unroll
-  for (int c = 0; c < 8; ++c) gx[c] = gy[c] = gz[c] = 0.0;
-#pragma unroll
-  for (int t = 0; t < 15; ++t) {
-    const int a = kTri[t].a, b = kTri[t].b, c = kTri[t].c;
-    const double s = (double)kTri[t].s;
+  for (int p = 0; p < 15; ++p) {
+    const PairUse &u = kPairs[p];
     double cx, cy, cz;
-    cross3(X[b], Y[b], Z[b], X[c], Y[c], Z[c], cx, cy, cz);  // d/dP_a det = P_b x P_c
-    gx[a] = fma(s, cx, gx[a]);
-    gy[a] = fma(s, cy, gy[a]);
-    gz[a] = fma(s, cz, gz[a]);
-    cross3(X[c], Y[c], Z[c], X[a], Y[a], Z[a], cx, cy, cz);  // d/dP_b det = P_c x P_a
-    gx[b] = fma(s, cx, gx[b]);
-    gy[b] = fma(s, cy, gy[b]);
-    gz[b] = fma(s, cz, gz[b]);
-    cross3(X[a], Y[a], Z[a], X[b], Y[b], Z[b], cx, cy, cz);  // d/dP_c det = P_a x P_b
-    gx[c] = fma(s, cx, gx[c]);
-    gy[c] = fma(s, cy, gy[c]);
-    gz[c] = fma(s, cz, gz[c]);
+    cross3(X[u.i], Y[u.i], Z[u.i], X[u.j], Y[u.j], Z[u.j], cx, cy, cz);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      if (q >= u.n) break;
+      const int k = u.k[q];
+      const double sx = u.s[q] > 0 ? cx : -cx, sy = u.s[q] > 0 ? cy : -cy, sz = u.s[q] > 0 ? cz : -cz;
+      if (u.first[q]) {
+        gx[k] = sx;
+        gy[k] = sy;
+        gz[k] = sz;
+      } else {
+        gx[k] += sx;
+        gy[k] += sy;
+        gz[k] += sz;
+      }
+    }
+  }
+#pragma unroll
+  for (int p = 0; p < 3; ++p) {
+    const SingleUse &u = kSingle[p];
+    const double sg = (double)u.s;
+    // g_k += s (P_i x P_j), one component at a time in two fused steps
+    gx[u.k] = fma(-sg * Z[u.i], Y[u.j], fma(sg * Y[u.i], Z[u.j], gx[u.k]));
+    gy[u.k] = fma(-sg * X[u.i], Z[u.j], fma(sg * Z[u.i], X[u.j], gy[u.k]));
+    gz[u.k] = fma(-sg * Y[u.i], X[u.j], fma(sg * X[u.i], Y[u.j], gz[u.k]));
   }
   double sx = 0.0, sy = 0.0, sz = 0.0, v12 = 0.0;
 #pragma unroll
   for (int c = 1; c < 8; ++c) {
-    sx += gx[c];
-    sy += gy[c];
-    sz += gz[c];
-    v12 = fma(X[c], gx[c], v12);  // V is linear in the x coordinates
+    sx = c == 1 ? gx[c] : sx + gx[c];
+    sy = c == 1 ? gy[c] : sy + gy[c];
+    sz = c == 1 ? gz[c] : sz + gz[c];
+    v12 = c == 1 ? X[c] * gx[c] : fma(X[c], gx[c], v12);  // V is linear in the x coordinates
   }
   gx[0] = -sx;
   gy[0] = -sy;
