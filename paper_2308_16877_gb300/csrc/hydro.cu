@@ -233,7 +233,7 @@ __global__ void __launch_bounds__(256) node_kernel(hpac_hydro_state s) {
 }
 
 // New volume and gradient, viscosity, and the EOS region's inputs.
-__global__ void __launch_bounds__(128) elem_kernel(hpac_hydro_state s) {
+__global__ void __launch_bounds__(96) elem_kernel(hpac_hydro_state s) {
   const int n = s.n;
   const int64_t E = (int64_t)n * n * n;
   const double dt = s.dt, gamma = s.gamma;
@@ -336,7 +336,11 @@ extern "C" hpac_status hpac_hydro_elements(const hpac_hydro_state *s, void *cuda
   int dev = 0;
   HPAC_CUDA_TRY(cudaGetDevice(&dev));
   const int64_t E = (int64_t)s->n * s->n * s->n;
-  elem_kernel<<<grid_for(E, 128, dev), 128, 0, (cudaStream_t)cuda_stream>>>(*s);
+  // 96 threads: six blocks (18 warps) per SM fit at 108 registers, against
+  // four of 128; one element per thread, so the 64^3 mesh is three full waves
+  const int64_t blocks = (E + 95) / 96;
+  elem_kernel<<<(unsigned)(blocks < 0x7fffffffLL ? blocks : 0x7fffffffLL), 96, 0,
+                (cudaStream_t)cuda_stream>>>(*s);
   HPAC_CUDA_TRY(cudaGetLastError());
   return HPAC_OK;
 }
