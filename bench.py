@@ -546,6 +546,57 @@ def bench_kmeans(hpac, torch, dev, stream, n=1 << 22, clusters=16, max_iter=300)
     return {"observations": n, "features": 8, "clusters": clusters, "runs": res}
 
 
+def bench_levels(hpac, torch, dev, stream, n=1 << 22, clusters=64, reps=5):
+    """Decision hierarchy (Section 3.3; the paper's Fig. 7 contrast): the
+    K-Means assignment region (64 centroids, ~1.5 k instructions per call) on
+    observations whose logical threads each follow one cluster with 5%
+    outliers from random clusters, T = N/16. TAF and iACT at thread, warp and
+    block level against the exact region: time, share approximated and MCR of
+    the ids. At thread level an outlier lane makes its whole warp run the
+    distance loop; warp and block majorities keep the group together."""
+    T = n // 16
+    x, labels, cent = W.kmeans_coherent(n, clusters, T)
+    xd = torch.from_numpy(x).to(dev)
+    cd = torch.from_numpy(cent).to(dev)
+    sc = W.iact_scale(x, n)
+    out = torch.zeros(n, dtype=torch.float32, device=dev)
+    exact = torch.zeros(n, dtype=torch.float32, device=dev)
+    R = hpac.Region(hpac.HPAC_REGION_KMEANS, xd, arg=clusters, logical_threads=T, block_threads=256,
+                    stream=stream)
+    R.set_aux(cd)
+
+    def timed(f):
+        f()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            f()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    exact_ms = timed(lambda: R.run_exact(xd, exact))
+    ref = exact.double()
+    rows = []
+    for tech in ("taf", "iact"):
+        for level in (hpac.HPAC_LEVEL_THREAD, hpac.HPAC_LEVEL_WARP, hpac.HPAC_LEVEL_BLOCK):
+            if tech == "taf":
+                f = lambda: R.run_taf(xd, out, 2, 8, 0.01, level)
+                st = R.run_taf(xd, out, 2, 8, 0.01, level, stats=True)
+            else:
+                f = lambda: R.run_iact(xd, out, 8, 32, 0.3, level, in_scale=sc)
+                st = R.run_iact(xd, out, 8, 32, 0.3, level, in_scale=sc, stats=True)
+            mcr = hpac.quality(ref, out, hpac.HPAC_METRIC_MCR, stream=stream)["value"]
+            ms = timed(f)
+            rows.append({"technique": tech, "level": ["thread", "warp", "block"][level], "ms": ms,
+                         "speedup_vs_exact": exact_ms / ms, "approximated": st["approximated"] / n,
+                         "mcr": mcr})
+    R.close()
+    return {"region": "K-Means assignment, 64 centroids", "observations": n, "logical_threads": T,
+            "knobs": {"taf": "h2 p8 0.01", "iact": "t8 private tables, distance 0.3 (scaled)"},
+            "exact_ms": exact_ms, "table": rows}
+
+
 def calibrate_floor(pred, exact, target=0.01, q=0.99):
     """Smallest price floor tau such that, among predictions >= tau, the q-th
     quantile of the relative error |pred - exact| / |exact| is at most target."""
@@ -858,6 +909,7 @@ def main(argv=None):
     ap.add_argument("--no-search", action="store_true")
     ap.add_argument("--no-binomial", action="store_true")
     ap.add_argument("--no-kmeans", action="store_true")
+    ap.add_argument("--no-levels", action="store_true")
     args = ap.parse_args(argv)
     if args.impl == "reference":
         return run_reference(args)
@@ -1052,6 +1104,7 @@ def main(argv=None):
     knob_search = None if args.no_search else bench_search(hpac, torch, dev, stream)
     binomial = None if args.no_binomial else bench_binomial(hpac, torch, dev, stream)
     kmeans = None if args.no_kmeans else bench_kmeans(hpac, torch, dev, stream)
+    levels = None if args.no_levels else bench_levels(hpac, torch, dev, stream)
     surrogate = None if args.no_surrogate else bench_surrogate(hpac, torch, dev, stream)
     large = None if args.no_hydro_large else bench_hydro_large(hpac, torch, dev, stream)
     persistent = None if args.no_persistent else bench_persistent(hpac, torch, dev, stream)
@@ -1092,6 +1145,7 @@ def main(argv=None):
             "search": knob_search,
             "binomial": binomial,
             "kmeans": kmeans,
+            "levels": levels,
             "surrogate": surrogate,
             "hydro_large": large,
             "persistent_state": persistent,

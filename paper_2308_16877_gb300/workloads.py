@@ -257,6 +257,24 @@ def kmeans_blobs(n: int, clusters: int, seed: int = DEFAULT_SEED, spread: float 
     return np.ascontiguousarray(x), labels, np.ascontiguousarray(x[:, first].T)
 
 
+def kmeans_coherent(n: int, clusters: int, threads: int, outliers: float = 0.05,
+                    seed: int = DEFAULT_SEED, spread: float = 1.0):
+    """K-Means observations laid out for the logical schedule: observation
+    i = t + k * threads belongs to blob (t mod clusters) except for a share
+    `outliers` drawn from a random blob, so a logical thread's successive
+    invocations mostly come from one cluster (the temporal locality TAF and
+    iACT exploit) while neighbouring lanes see different clusters. Returns
+    (x (8, n) float32, labels, centres (clusters, 8) float32)."""
+    g = _rng(seed, 13)
+    centres = g.uniform(-10.0, 10.0, size=(clusters, 8))
+    t = np.arange(n) % threads
+    labels = t % clusters
+    out = g.random(n) < outliers
+    labels[out] = g.integers(0, clusters, size=int(out.sum()))
+    x = (centres[labels] + spread * g.standard_normal((n, 8))).T.astype(np.float32)
+    return np.ascontiguousarray(x), labels, centres.astype(np.float32)
+
+
 def hydro_dt(n: int, gamma: float = 5.0 / 3.0, e0: float = HYDRO_E0, cfl: float = 0.1) -> float:
     """Fixed time step of the hydro run: cfl * h / c0 with h = 1/n and c0 the
     ideal-gas sound speed of the initial corner element at unit density."""
