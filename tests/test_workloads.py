@@ -45,3 +45,14 @@ def test_hydro_initial():
     g = x.reshape(5, 5, 5)
     assert np.all(g[:, :, 0] == 0) and np.all(g[:, :, 4] == 1.0)
     assert np.max(np.abs(g - np.arange(5) / 4.0)) <= 0.05 / 4 + 1e-15
+
+
+def test_kmeans_coherent_layout():
+    """Logical thread t's observations come from blob t mod K, but for the
+    outlier share; generated deterministically."""
+    n, K, T = 1 << 14, 16, 1024
+    x, labels, cent = W.kmeans_coherent(n, K, T, outliers=0.05, seed=4)
+    assert x.shape == (8, n) and x.dtype == np.float32 and cent.shape == (K, 8)
+    own = labels == (np.arange(n) % T) % K
+    assert 0.93 < own.mean() < 0.98
+    assert np.array_equal(W.kmeans_coherent(n, K, T, outliers=0.05, seed=4)[0], x)
