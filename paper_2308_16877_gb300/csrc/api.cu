@@ -36,6 +36,26 @@ int max_dyn_smem(int device) {
   return cached[device];
 }
 
+int sm_count(int device) {
+  static int cached[64] = {0};
+  if (device < 0 || device >= 64) return 148;
+  if (!cached[device]) {
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || v <= 0)
+      v = 148;
+    cached[device] = v;
+  }
+  return cached[device];
+}
+
+int balanced_block(int64_t threads, int b, int device) {
+  const int64_t want = (int64_t)sm_count(device) * 8;
+  int64_t per = (threads + want - 1) / want;
+  per = (per + 31) / 32 * 32;
+  if (per < 32) per = 32;
+  return per < b ? (int)per : b;
+}
+
 static hpac_status check_desc(const hpac_region_desc *d) {
   if (!d) return set_error(HPAC_EINVAL, "descriptor is NULL");
   if (d->n < 0) return set_error(HPAC_EINVAL, "n = %lld < 0", (long long)d->n);

@@ -49,8 +49,9 @@ __device__ __forceinline__ void store_vec(T *p, const T (&v)[V]) {
   __stcs(reinterpret_cast<VT *>(p), x);
 }
 
-// Invocations [0, n) in groups of V; group g covers [g*V, g*V + V).
-template <class R, int V>
+// Invocations [0, n) in groups of V; group g covers [g*V, g*V + V). The
+// accurate path (PERFO false) carries no drop rule.
+template <class R, int V, bool PERFO>
 __global__ void __launch_bounds__(256) map_kernel(R reg, const typename R::T *__restrict__ in,
                                                   int64_t stride, typename R::T *__restrict__ out,
                                                   uint8_t *__restrict__ mask, int64_t n,
@@ -63,10 +64,19 @@ __global__ void __launch_bounds__(256) map_kernel(R reg, const typename R::T *__
   unsigned long long n_drop = 0;
   const int64_t groups = n / V;
   const int64_t gstride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < groups; g += gstride) {
+  const int64_t g0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  DropWalk<V> walk;
+  if (PERFO) walk.init(rule, g0 * V, gstride * V);
+  for (int64_t g = g0; g < groups; g += gstride) {
     const int64_t i0 = g * V;
     bool drop[V];
-    rule.drops<V>(i0, drop);
+    if (PERFO) {
+      walk.drops(rule, i0, drop);
+      walk.advance(rule);
+    } else {
+#pragma unroll
+      for (int j = 0; j < V; ++j) drop[j] = false;
+    }
     bool all_drop = true, none_drop = true;
 #pragma unroll
     for (int j = 0; j < V; ++j) {
@@ -114,8 +124,8 @@ __global__ void __launch_bounds__(256) map_kernel(R reg, const typename R::T *__
   if (blockIdx.x == 0) {
     const int64_t i = groups * V + threadIdx.x;
     if (threadIdx.x < V && i < n) {
-      bool drop[1];
-      rule.drops<1>(i, drop);
+      bool drop[1] = {false};
+      if (PERFO) rule.drops<1>(i, drop);
       if (mask) mask[i] = drop[0] ? HPAC_MASK_SKIPPED : HPAC_MASK_EXACT;
       n_drop += drop[0] ? 1 : 0;
       if (!drop[0]) {
@@ -133,18 +143,6 @@ __global__ void __launch_bounds__(256) map_kernel(R reg, const typename R::T *__
   }
 }
 
-int sm_count(int device) {
-  static int cached[64] = {0};
-  if (device < 0 || device >= 64) return 148;
-  if (!cached[device]) {
-    int v = 0;
-    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || v <= 0)
-      v = 148;
-    cached[device] = v;
-  }
-  return cached[device];
-}
-
 template <class R>
 hpac_status launch_map(const hpac_region *r, R reg, const void *in_, void *out_, uint8_t *mask,
                        const DropRule &rule, unsigned long long *counters) {
@@ -156,20 +154,16 @@ hpac_status launch_map(const hpac_region *r, R reg, const void *in_, void *out_,
   constexpr int VW = 16 / sizeof(T);
   const bool vec_ok = (r->d.in_stride % VW == 0) && ((uintptr_t)in % 16 == 0) &&
                       ((uintptr_t)out % 16 == 0) && (mask == nullptr || (uintptr_t)mask % 4 == 0);
-  const int threads = 256;
-  const int64_t per_block_max = (int64_t)sm_count(r->device) * 8;
-  if (vec_ok) {
-    const int64_t groups = n / VW;
-    int64_t blocks = (groups + threads - 1) / threads;
-    blocks = blocks < 1 ? 1 : (blocks > per_block_max ? per_block_max : blocks);
-    map_kernel<R, VW><<<(unsigned)blocks, threads, 0, r->stream>>>(reg, in, r->d.in_stride, out,
-                                                                   mask, n, rule, counters);
-  } else {
-    int64_t blocks = (n + threads - 1) / threads;
-    blocks = blocks < 1 ? 1 : (blocks > per_block_max ? per_block_max : blocks);
-    map_kernel<R, 1><<<(unsigned)blocks, threads, 0, r->stream>>>(reg, in, r->d.in_stride, out,
-                                                                  mask, n, rule, counters);
-  }
+  const bool perfo = rule.kind >= 0;
+  const int vw = vec_ok ? VW : 1;
+  const int threads = balanced_block(n / vw, 256, r->device);
+  const int64_t per_block_max = (int64_t)sm_count(r->device) * 2048 / threads;
+  int64_t blocks = (n / vw + threads - 1) / threads;
+  blocks = blocks < 1 ? 1 : (blocks > per_block_max ? per_block_max : blocks);
+  auto kern = vec_ok ? (perfo ? map_kernel<R, VW, true> : map_kernel<R, VW, false>)
+                     : (perfo ? map_kernel<R, 1, true> : map_kernel<R, 1, false>);
+  kern<<<(unsigned)blocks, threads, 0, r->stream>>>(reg, in, r->d.in_stride, out, mask, n, rule,
+                                                     counters);
   HPAC_CUDA_TRY(cudaGetLastError());
   return HPAC_OK;
 }

@@ -61,6 +61,18 @@ inline size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 // Largest dynamic shared memory a block of this device may use.
 int max_dyn_smem(int device);
 
+// Number of SMs of the device.
+int sm_count(int device);
+
+// Physical block size (a multiple of 32, at most b) for a launch of `threads`
+// threads whose block is not part of the semantics (plain maps, thread- and
+// warp-level decisions): small enough to give every SM about eight blocks.
+// The work of a region is often uneven along the invocation index (a shock
+// front, a run of approximations), and double-precision work runs at a small
+// fraction of the single-precision rate, so a few large blocks left on a few
+// SMs would set the kernel time.
+int balanced_block(int64_t threads, int b, int device);
+
 }  // namespace hpac
 
 #define HPAC_CUDA_TRY(call)                                   \

@@ -99,6 +99,14 @@ __global__ void __launch_bounds__(1024) iact_kernel(R reg, const typename R::T *
 
   if (t_lead < T) {
     int k3 = 0;
+    // Every invocation reads its inputs, so the next one's are loaded while
+    // this one scans its table and computes (one invocation ahead).
+    V xn[KD];
+    if (t < T && t < n) {
+#pragma unroll
+      for (int d = 0; d < KD; ++d)
+        if (d < D) xn[d] = in[d * stride + t];
+    }
     for (int64_t i = t; t_lead + (i - t) < n; i += T) {
       const bool act = (t < T) && (i < n);
       // ---- read phase
@@ -109,9 +117,15 @@ __global__ void __launch_bounds__(1024) iact_kernel(R reg, const typename R::T *
       int near = 0;
       if (act) {
 #pragma unroll
+        for (int d = 0; d < KD; ++d) x[d] = xn[d];
+        if (i + T < n) {
+#pragma unroll
+          for (int d = 0; d < KD; ++d)
+            if (d < D) xn[d] = in[d * stride + i + T];
+        }
+#pragma unroll
         for (int d = 0; d < KD; ++d) {
           if (d < D) {
-            x[d] = in[d * stride + i];
             if (sizeof(V) == 4)
               z[d] = __fmul_rn(P.scale_f[d], (float)x[d]);
             else
@@ -232,9 +246,11 @@ hpac_status launch(hpac_region *r, R reg, const hpac_iact_knobs *k, const void *
   const size_t wbytes = warp_table_bytes<V>(P.tsize, P.D, P.g);
   const int limit = max_dyn_smem(r->device);
   // At thread and warp level only the warp is semantic, so the physical block
-  // may shrink to fit the tables; at block level B is part of the semantics.
+  // may shrink, to spread the warps over all SMs and to fit the tables; at
+  // block level B is part of the semantics.
   int B = d.block_threads;
   if (k->level != HPAC_LEVEL_BLOCK) {
+    B = balanced_block(T, B, r->device);
     while (B > 32 && (size_t)(B / 32) * wbytes > (size_t)limit) B -= 32;
   }
   const size_t smem = (size_t)(B / 32) * wbytes;

@@ -66,4 +66,85 @@ struct DropRule {
   }
 };
 
+// drops<V> for a thread that visits the groups i0, i0 + G, i0 + 2G, ... of a
+// grid-stride loop. The step k = i0 / T of a herded pattern and the residues
+// modulo M of the small and large patterns are carried from one group to the
+// next by additions, so the loop divides only once per thread, at its start.
+template <int V>
+struct DropWalk {
+  int64_t k, r;      // herded: i0 = k T + r with 0 <= r < T
+  int64_t dk, dr;
+  int res;           // small / large: k mod M (herded) or i0 mod M (per invocation)
+  int dres, m;
+
+  __device__ __forceinline__ void init(const DropRule &R, int64_t i0, int64_t G) {
+    k = r = res = dk = dr = dres = 0;
+    m = (R.kind == HPAC_PERFO_SMALL || R.kind == HPAC_PERFO_LARGE) ? (int)R.m : 1;
+    if (R.kind < 0 || R.kind == HPAC_PERFO_INI || R.kind == HPAC_PERFO_FINI) return;
+    if (R.herded) {
+      k = i0 / R.T;
+      r = i0 - k * R.T;
+      dk = G / R.T;
+      dr = G - dk * R.T;
+      res = (int)(k % m);
+      dres = (int)(dk % m);
+    } else {
+      res = (int)(i0 % m);
+      dres = (int)(G % m);
+    }
+  }
+  __device__ __forceinline__ void advance(const DropRule &R) {
+    if (R.herded) {
+      k += dk;
+      r += dr;
+      res += dres;
+      if (r >= R.T) {
+        r -= R.T;
+        ++k;
+        ++res;
+      }
+    } else {
+      res += dres;
+    }
+    if (res >= m) res -= m;  // res < 2M here (M < 2^31)
+  }
+  __device__ __forceinline__ bool drop_res(const DropRule &R, int q) const {
+    return R.kind == HPAC_PERFO_SMALL ? q == m - 1 : q != 0;
+  }
+  __device__ __forceinline__ void drops(const DropRule &R, int64_t i0, bool (&d)[V]) const {
+    const bool modm = R.kind == HPAC_PERFO_SMALL || R.kind == HPAC_PERFO_LARGE;
+    if (R.kind < 0 || R.kind == HPAC_PERFO_INI || R.kind == HPAC_PERFO_FINI ||
+        (!R.herded && !modm)) {
+      R.drops<V>(i0, d);  // no division on these paths
+      return;
+    }
+    if (R.herded) {
+      if (r + V <= R.T) {
+        const bool dd = modm ? drop_res(R, res) : R.drop_key(k);
+#pragma unroll
+        for (int j = 0; j < V; ++j) d[j] = dd;
+      } else {  // the group straddles steps: walk them invocation by invocation
+        int64_t rr = r, kk = k;
+        int q = res;
+#pragma unroll
+        for (int j = 0; j < V; ++j) {
+          d[j] = modm ? drop_res(R, q) : R.drop_key(kk);
+          if (++rr == R.T) {
+            rr = 0;
+            ++kk;
+            q = q + 1 == m ? 0 : q + 1;
+          }
+        }
+      }
+      return;
+    }
+    int q = res;
+#pragma unroll
+    for (int j = 0; j < V; ++j) {
+      d[j] = drop_res(R, q);
+      q = q + 1 == m ? 0 : q + 1;
+    }
+  }
+};
+
 }  // namespace hpac

@@ -235,6 +235,66 @@ __device__ __forceinline__ bool rsd_below_fast(const T *win, int ld, int oldest,
   return rsd_below_moments(mu, acc, h, thr, inv_h);
 }
 
+// Decision RSD(w) < thr for a double-precision window of compile-time size KH
+// (2, 4 or 8) settled, where it is clear, in single precision from the copy
+// wf[j] = (float)w[j]; GB300 issues double-precision arithmetic at a small
+// fraction of its single-precision rate. With u = 2^-24 and M = max |wf_j|
+// (in [1e-10, 1e15]), the single-precision mean m = fl(sum wf_j) / KH and
+// standard deviation sqrt(var), var = fl(sum fl(wf_j - m)^2) / KH, are within
+// (KH + 1) u M and (2 KH + 3) u M of the exact mean and standard deviation of
+// w (rounding of the copy, of the KH-term sums and of the squares; the
+// deviation is at most 2 M). The test widens those bounds to Em = 4 (KH + 1) u M
+// and Es = 8 (KH + 2) u M, so that the double-precision statistic's own
+// rounding (relative 2^-53) also lies inside, takes the threshold 1e-5
+// relative further (rounding of thr to single precision and of the test's own
+// few operations) and decides only when the whole interval is on one side:
+// below when sqrt(var) < thr (|m| - Em) - Es, not below when
+// sqrt(var) > thr (|m| + Em) + Es, compared as squares. The subtraction is
+// used only while Es is at most half of thr (|m| - Em), which keeps its
+// relative rounding error within 5u. Returns 1 (below), 0 (not below) or -1
+// (the double-precision test decides): always -1 for a window with a NaN or
+// an infinity or outside the magnitude range, and for thresholds outside
+// [1e-7, 1e12] (the caller passes thr_ok). An all-zero window has statistic 0
+// and is decided exactly.
+template <int KH>
+__device__ __forceinline__ int rsd_below_f32(const float (&wf)[KH], const double (&w)[KH], float thr,
+                                             bool thr_ok) {
+  if (!thr_ok) return -1;
+  float M = 0.0f;
+#pragma unroll
+  for (int j = 0; j < KH; ++j) M = fmaxf(M, fabsf(wf[j]));
+  if (M == 0.0f) {
+    bool zero = true;  // exact test on the double-precision values (+0 or -0)
+#pragma unroll
+    for (int j = 0; j < KH; ++j) zero &= (__double_as_longlong(w[j]) << 1) == 0;
+    return zero ? 1 : -1;
+  }
+  if (!(M >= 1e-10f && M <= 1e15f)) return -1;
+  float S = 0.0f;
+#pragma unroll
+  for (int j = 0; j < KH; ++j) S = __fadd_rn(S, wf[j]);
+  const float m = __fmul_rn(S, 1.0f / KH);
+  float a = 0.0f;
+#pragma unroll
+  for (int j = 0; j < KH; ++j) {
+    const float d = __fsub_rn(wf[j], m);
+    a = __fadd_rn(a, __fmul_rn(d, d));
+  }
+  const float var = __fmul_rn(a, 1.0f / KH);
+  constexpr float u = 5.9604644775390625e-8f;  // 2^-24
+  const float Es = __fmul_rn((float)(8 * (KH + 2)) * u, M);
+  const float Em = __fmul_rn((float)(4 * (KH + 1)) * u, M);
+  const float am = fabsf(m);
+  const float xlo = __fmul_rn(thr, __fsub_rn(am, Em));
+  if (Es <= 0.5f * xlo) {
+    const float t = __fsub_rn(xlo, Es);
+    if (t >= 1e-15f && t <= 1e15f && var < __fmul_rn(__fmul_rn(t, t), 1.0f - 1e-5f)) return 1;
+  }
+  const float t = __fadd_rn(__fmul_rn(thr, __fadd_rn(am, Em)), Es);
+  if (t >= 1e-15f && t <= 1e15f && var > __fmul_rn(__fmul_rn(t, t), 1.0f + 1e-5f)) return 0;
+  return -1;
+}
+
 // The window held in registers, oldest first (compile-time size): the same
 // two IEEE passes in the same order as window_rsd.
 template <typename T, int KH>

@@ -44,6 +44,16 @@ __global__ void __launch_bounds__(1024) taf_kernel(R reg, const typename R::T *_
   V w[KH > 0 ? KH : 1];  // register window (KH > 0), defined from the start
 #pragma unroll
   for (int j = 0; j < (KH > 0 ? KH : 1); ++j) w[j] = (V)0;
+  // double-precision register windows of 2 or 4 values also keep a
+  // single-precision copy for the single-precision decision test
+  // (rsd_below_f32); windows of 8 stay within the 64 registers of
+  // 1024-thread blocks without it
+  constexpr bool F32T = KH > 0 && KH <= 4 && sizeof(V) == 8;
+  float wf[F32T ? KH : 1];
+#pragma unroll
+  for (int j = 0; j < (F32T ? KH : 1); ++j) wf[j] = 0.0f;
+  const float thr_f = (float)thr;
+  const bool thr_ok = F32T && !thr_inf && (double)thr >= 1e-7 && (double)thr <= 1e12;
   if (KH > 0) h = KH;
   const V inv_h = (V)1 / (V)h;
   const int ld = blockDim.x;
@@ -100,6 +110,11 @@ __global__ void __launch_bounds__(1024) taf_kernel(R reg, const typename R::T *_
 #pragma unroll
             for (int j = 0; j + 1 < KH; ++j) w[j] = w[j + 1];
             w[KH > 0 ? KH - 1 : 0] = y;
+            if (F32T) {
+#pragma unroll
+              for (int j = 0; j + 1 < (F32T ? KH : 1); ++j) wf[j] = wf[j + 1];
+              wf[F32T ? KH - 1 : 0] = (float)y;
+            }
           } else {
             win[pos * ld + threadIdx.x] = y;
             pos = (pos + 1 == h) ? 0 : pos + 1;
@@ -108,11 +123,19 @@ __global__ void __launch_bounds__(1024) taf_kernel(R reg, const typename R::T *_
           decided = true;
           if (cnt == h) {
             V mu = (V)0, acc = (V)0;
-            if (KH > 0) reg_window_moments(w, inv_h, mu, acc);
             if (stat == nullptr && counters == nullptr && !thr_inf) {
-              wants = KH > 0 ? rsd_below_moments(mu, acc, h, thr, inv_h)
-                             : rsd_below_fast<V>(win + threadIdx.x, ld, pos, h, thr, inv_h);
+              int f = -1;
+              if constexpr (F32T) f = rsd_below_f32<KH>(wf, w, thr_f, thr_ok);
+              if (f >= 0) {
+                wants = f == 1;
+              } else if (KH > 0) {
+                reg_window_moments(w, inv_h, mu, acc);
+                wants = rsd_below_moments(mu, acc, h, thr, inv_h);
+              } else {
+                wants = rsd_below_fast<V>(win + threadIdx.x, ld, pos, h, thr, inv_h);
+              }
             } else {
+              if (KH > 0) reg_window_moments(w, inv_h, mu, acc);
               const V s = KH > 0 ? rsd_from_moments(mu, acc, h, inv_h)
                                  : window_rsd<V>(win + threadIdx.x, ld, pos, h, inv_h);
               if (stat) stat[i] = s;
@@ -187,7 +210,9 @@ hpac_status launch(hpac_region *r, R reg, const hpac_taf_knobs *k, const void *i
   V *st_vals = reinterpret_cast<V *>(sb);
   int *st_cnt = sb ? reinterpret_cast<int *>(sb + b_vals) : nullptr;
   int *st_pred = sb ? reinterpret_cast<int *>(sb + b_vals + b_int) : nullptr;
-  const int B = d.block_threads;
+  // the block is part of the semantics at block level only
+  const int B = k->level == HPAC_LEVEL_BLOCK ? d.block_threads
+                                             : balanced_block(T, d.block_threads, r->device);
   const int h = k->hsize;
   // register-window sizes; persistent state runs the shared-memory window
   const int kh = !sb && (h == 2 || h == 4 || h == 8) ? h : 0;

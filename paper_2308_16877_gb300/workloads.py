@@ -119,6 +119,38 @@ def identity_inputs(n: int, d: int = 1, seed: int = DEFAULT_SEED, dtype=np.float
     return x
 
 
+def identity_near_threshold(n: int, T: int, rsd: float, seed: int = DEFAULT_SEED) -> np.ndarray:
+    """Double-precision identity inputs, shape (1, n), whose TAF windows sit
+    next to a relative standard deviation of `rsd`. Logical thread t (of T)
+    draws a magnitude 10^U(-12, 14) and a sign; at its step k it reads
+    magnitude * (1 + (-1)^k rsd (1 + e)) for 10 of 16 threads (every window of
+    even size over values of alternating parity has relative standard
+    deviation rsd (1 + e); e is within 1e-2 .. 1e-9 of zero, either sign),
+    magnitude * (1 + rsd z) with z standard normal for 4 of 16, and special
+    values (signed zeros, subnormals, values beyond the single-precision
+    range, infinities, NaN, repeats) for the rest."""
+    g = _rng(seed, 11)
+    x = np.zeros((1, n), dtype=np.float64)
+    if n == 0:
+        return x
+    T = max(1, T)
+    i = np.arange(n)
+    t, k = i % T, i // T
+    mag = 10.0 ** g.uniform(-12, 14, T) * g.choice([-1.0, 1.0], T)
+    e = 10.0 ** g.uniform(-9, -2, T) * g.choice([-1.0, 1.0], T)
+    alt = np.where(k % 2 == 0, 1.0, -1.0)
+    v = mag[t] * (1.0 + alt * rsd * (1.0 + e[t]))
+    cls = t % 16
+    rnd = (cls >= 10) & (cls < 14)
+    v[rnd] = mag[t[rnd]] * (1.0 + rsd * g.normal(size=int(rnd.sum())))
+    special = np.array([0.0, -0.0, 1e-310, 5e-324, 1e-45, 1e-39, 1e-12, 1.0, 4e38, 1e300, np.inf,
+                        -np.inf, np.nan, 1.5])
+    odd = cls >= 14
+    v[odd] = g.choice(special, size=int(odd.sum()))
+    x[0] = v
+    return x
+
+
 def iact_scale(x: np.ndarray, n: int) -> np.ndarray:
     """Per-dimension input scale 1/max|x_d| (1 where the column is all zero).
 

@@ -120,6 +120,30 @@ def test_perforation(H, orc, kind, dt, pk, m, rate, herded, n, T):
     assert st["skipped"] == int(skip.sum()) == cnt[2]
 
 
+@pytest.mark.parametrize("dt", [np.float32, np.float64])
+@pytest.mark.parametrize("pk,m,rate", [(0, 4, 0.0), (0, 3, 0.0), (1, 5, 0.0), (4, 0, 0.3), (3, 20, 0.0)])
+@pytest.mark.parametrize("herded", [1, 0])
+@pytest.mark.parametrize("T", [3, 1001, 1000003, 5000000])
+def test_perforation_grid_stride_walk(H, orc, dt, pk, m, rate, herded, T):
+    """Regions several grid strides long (a thread visits its groups with the
+    step and residues carried by additions), logical-thread counts below the
+    vector width, not a multiple of it, below and above the grid stride."""
+    n = 3_000_017
+    x, param = inputs(3, n, dt, d=1)
+    tdt = torch.float32 if dt == np.float32 else torch.float64
+    out = torch.full((n,), float("nan"), dtype=tdt, device="cuda")
+    mask = torch.full((n,), 255, dtype=torch.uint8, device="cuda")
+    with H.Region(3, dev(x), param=param, logical_threads=T) as R:
+        st = R.run_perfo(dev(x), out, pk, m, rate, seed=5, herded=bool(herded), mask=mask, stats=True)
+    g, gm = host(out), host(mask)
+    ref, om, cnt = orc.run_perfo(3, x, param, pk, m, rate, 5, herded, threads=T,
+                                 out=np.full(n, np.nan, dtype=dt))
+    assert np.array_equal(gm, om)
+    skip = om == 2
+    assert np.all(np.isnan(g[skip])) and np.array_equal(g[~skip], ref[~skip])
+    assert st["skipped"] == int(skip.sum()) == cnt[2]
+
+
 # ---------------------------------------------------------------- TAF
 
 def taf_case(H, orc, kind, dt, n, T, B, h, p, thr, level, ikind="walk", seed=2308):
@@ -177,6 +201,33 @@ def test_taf_reset_on_exit_bitexact(H, orc, dt, level, h, p, thr):
     assert np.array_equal(host(stat), os_, equal_nan=True)
     assert np.array_equal(host(fast_mask), om) and np.array_equal(host(fast_out), o)
     assert st["approximated"] == cnt[1] > 0
+
+
+@pytest.mark.parametrize("level", [0, 1, 2])
+@pytest.mark.parametrize("h", [2, 4, 8])
+@pytest.mark.parametrize("thr", [1e-4, 5e-3, 0.05, 0.5])
+def test_taf_f64_single_precision_decisions(H, orc, level, h, thr):
+    """Double-precision register windows settle clear decisions in single
+    precision inside a proven error band: on windows next to the threshold,
+    over magnitudes 1e-12 .. 1e14 with zeros, subnormals, out-of-range values,
+    infinities and NaNs, the masks and outputs equal the oracle's and the
+    IEEE-statistic path's bit for bit."""
+    n, T, B, p = 48000, 1500, 128, 2
+    x = W.identity_near_threshold(n, T, thr, seed=h)
+    xd = dev(x)
+    with H.Region(3, xd, logical_threads=T, block_threads=B) as R:
+        o1 = torch.zeros(n, dtype=torch.float64, device="cuda")
+        m1 = torch.zeros(n, dtype=torch.uint8, device="cuda")
+        R.run_taf(xd, o1, h, p, thr, level, mask=m1)
+        o2 = torch.zeros(n, dtype=torch.float64, device="cuda")
+        m2 = torch.zeros(n, dtype=torch.uint8, device="cuda")
+        s2 = torch.zeros(n, dtype=torch.float64, device="cuda")
+        R.run_taf(xd, o2, h, p, thr, level, mask=m2, stat=s2, stats=True)
+    o, om, _, cnt = orc.run_taf(3, x, 0.0, h, p, thr, level=level, threads=T, block=B)
+    g1, gm1 = host(o1), host(m1)
+    assert np.array_equal(gm1, om) and np.array_equal(host(m2), om)
+    assert np.array_equal(g1, o, equal_nan=True) and np.array_equal(host(o2), o, equal_nan=True)
+    assert 0 < cnt[1] < n
 
 
 @pytest.mark.parametrize("kind,dt", [(0, np.float32), (0, np.float64), (1, np.float64)])
