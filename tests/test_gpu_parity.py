@@ -317,6 +317,37 @@ def test_iact(H, orc, kind, dt, d, level, g, ts):
         assert cnt[1] > 0
 
 
+@pytest.mark.parametrize("dt", [np.float32, np.float64])
+@pytest.mark.parametrize("level", [0, 1])
+@pytest.mark.parametrize("T", [40000, 100003, 400000])
+def test_taf_iact_physical_block_sizes(H, orc, dt, level, T):
+    """At thread and warp level the physical block shrinks with T (about eight
+    blocks per SM, 32..B threads): logical-thread counts giving physical blocks
+    of 64, 96 and 256 threads (the last ragged), with the register window
+    (h = 4) and the shared-memory window (h = 3), and iACT with private and
+    shared tables; masks and outputs equal the oracle's."""
+    n, B = 8 * T + 1234, 256
+    x, param = inputs(3, n, dt, d=2, ikind="levels")
+    tdt = torch.float32 if dt == np.float32 else torch.float64
+    xd = dev(x)
+    sc = W.iact_scale(x, n)
+    with H.Region(3, xd, param=param, logical_threads=T, block_threads=B) as R:
+        for h in (3, 4):
+            out = torch.full((n,), float("nan"), dtype=tdt, device="cuda")
+            mask = torch.full((n,), 255, dtype=torch.uint8, device="cuda")
+            R.run_taf(xd, out, h, 2, 0.2, level, mask=mask)
+            o, om, _, cnt = orc.run_taf(3, x, param, h, 2, 0.2, level=level, threads=T, block=B)
+            assert np.array_equal(host(mask), om) and np.array_equal(host(out), o)
+            assert cnt[1] > 0
+        for g in (32, 4):
+            out = torch.full((n,), float("nan"), dtype=tdt, device="cuda")
+            mask = torch.full((n,), 255, dtype=torch.uint8, device="cuda")
+            R.run_iact(xd, out, 4, g, 0.05, level, in_scale=sc, mask=mask)
+            o, om, _, cnt = orc.run_iact(3, x, param, 4, g, 0.05, level=level, in_scale=sc, threads=T, block=B)
+            assert np.array_equal(host(mask), om) and np.array_equal(host(out), o)
+            assert cnt[1] > 0
+
+
 # ---------------------------------------------------------------- quality
 
 @pytest.mark.parametrize("metric", [0, 1, 2])
