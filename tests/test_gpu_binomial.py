@@ -120,6 +120,34 @@ def test_perforation_per_team(H, orc, kind, m, rate, herded):
     assert np.all(np.abs(g[keep].astype(np.float64) - o[keep]) <= price_tol(x)[keep])
 
 
+def test_portfolio_workload_sampled(H, orc):
+    """The benchmark's workload (4096 members x 64 time points = 262,144
+    American calls on 1024-step trees, one team per member) in its launch:
+    exact prices of 256 sampled options against the oracle's tree, and a
+    TAF run (h1 p2, per team) whose predicted outputs repeat the team's last
+    exact price and whose exact ones equal the exact run's."""
+    M, K, steps = 4096, 64, 1024
+    x = W.binomial_portfolio(M, K)
+    n = x.shape[1]
+    xd = dev(x)
+    exact = torch.zeros(n, device="cuda")
+    out = torch.zeros(n, device="cuda")
+    mask = torch.zeros(n, dtype=torch.uint8, device="cuda")
+    with H.Region(H.HPAC_REGION_BINOMIAL, xd, param=W.BS_RATE, arg=steps, logical_threads=M) as R:
+        R.run_exact(xd, exact)
+        st = R.run_taf(xd, out, 1, 2, 0.05, H.HPAC_LEVEL_BLOCK, mask=mask, stats=True)
+    g, o, m = host(exact), host(out), host(mask)
+    idx = np.concatenate([np.random.default_rng(4).choice(n, 254, replace=False), [0, n - 1]])
+    xs = np.ascontiguousarray(x[:, idx])
+    ref = orc.run_exact(orc.BINOMIAL, xs, W.BS_RATE, steps=steps).astype(np.float64)
+    assert np.all(np.abs(g[idx].astype(np.float64) - ref) <= price_tol(xs))
+    assert 0 < st["approximated"] == int((m == 1).sum()) < n
+    assert np.array_equal(o[m == 0], g[m == 0])
+    # a predicted option repeats its team's previous output (column i - M)
+    pred = np.nonzero(m == 1)[0]
+    assert np.all(pred >= M) and np.array_equal(o[pred], o[pred - M])
+
+
 def test_rejected_configurations(H):
     x = dev(W.binomial_portfolio(64, 2))
     n = x.shape[1]

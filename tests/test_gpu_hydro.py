@@ -180,6 +180,44 @@ def test_workload_64_cubed_100_steps(H, orc):
     G.close()
 
 
+def test_workload_256_cubed_launch_configuration(H, orc):
+    """The large hydro workload's mesh (256^3 elements, 16.8M) in the
+    benchmark's launch configuration (T = E/8 logical threads, blocks of 256):
+    three exact steps, then one step with the EOS under TAF (h4 p8 0.5%) and
+    one under iACT (t8, private tables, 1e-3); after each, masks agree with the
+    oracle's and the fields agree (everywhere for the nodes, where the masks
+    agree for the elements)."""
+    n = 256
+    E = n ** 3
+    T = E // 8
+    S, G = pair(H, orc, n, T=T, B=256)
+    dt = W.hydro_dt(n)
+    for _ in range(3):
+        S.step(dt)
+    G.run(3, H.HYDRO_EXACT)
+    sc = (1.0 / W.HYDRO_E0, 1.0, 10.0, 1e-6)
+    scale = (H.C.c_double * 4)(*sc)
+    steps = [
+        (orc.eos_knobs(orc.EOS_TAF, hsize=4, psize=8, thresh=5e-3, threads=T, block=256),
+         H.hpac_taf_knobs(4, 8, 5e-3, 0, 0), H.HYDRO_TAF),
+        (orc.eos_knobs(orc.EOS_IACT, tsize=8, tperwarp=32, thresh=1e-3, threads=T, block=256, in_scale=sc),
+         H.hpac_iact_knobs(8, 32, 1e-3, 0, 0, H.C.cast(scale, H.C.POINTER(H.C.c_double))), H.HYDRO_IACT)]
+    mask = torch.full((E,), 255, dtype=torch.uint8, device="cuda")
+    for ok, gk, t in steps:
+        _, om, _ = S.step(dt, ok)
+        G.step(t, gk, mask=mask)
+        torch.cuda.synchronize()
+        gm = mask.cpu().numpy()
+        agree = gm == om
+        assert agree.mean() >= 0.999, (t, agree.mean())
+        assert (gm == 1).sum() > E // 4
+        for f in NODE:
+            close(G[f].cpu(), getattr(S, f), 1e-12, (t, f))
+        for f in ("p", "e"):
+            close(G[f].cpu().numpy()[agree], getattr(S, f)[agree], 1e-12, (t, f))
+    G.close()
+
+
 def test_state_arrays_checkpoint_and_resume(H, orc):
     """The library keeps no state: copying the arrays and resuming gives the
     same run bit for bit."""

@@ -47,6 +47,19 @@ def test_exact_assignment(H, orc, n, K):
         assert np.array_equal(host(out), orc.run_exact(orc.KMEANS, x, cent))
 
 
+def test_assignment_at_4M_observations(H, orc):
+    """The K-Means workload's size (4M observations, 16 clusters) in the
+    benchmark's launch (T = N/8): every id against the oracle's nearest
+    centroid (integer work, bit-exact)."""
+    n, K = 1 << 22, 16
+    x, _, _ = W.kmeans_blobs(n, K, spread=2.0)
+    cent = np.ascontiguousarray(x[:, :K].T)
+    out = torch.full((n,), float("nan"), device="cuda")
+    with region(H, dev(x), dev(cent), T=n // 8) as R:
+        R.run_exact(dev(x), out)
+    assert np.array_equal(host(out), orc.run_exact(orc.KMEANS, x, cent))
+
+
 @pytest.mark.parametrize("level", [0, 1, 2])
 @pytest.mark.parametrize("h,p,thr", [(2, 4, 0.1), (4, 8, 0.5), (3, 2, np.inf)])
 def test_taf_on_ids(H, orc, level, h, p, thr):

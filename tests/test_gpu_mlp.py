@@ -136,6 +136,48 @@ def test_training_reduces_loss_and_fallback_is_exact(H, orc):
     S.close()
 
 
+def test_inference_at_16M_options_sampled(H, orc):
+    """The surrogate workload's inference size (2^24 options) with the
+    calibrated fallback, in the benchmark's launch: sampled predictions within
+    the bfloat16 forward bound of the oracle's network, the mask exactly the
+    rule prediction < tau, sampled fallback outputs within the exact region's
+    bar, approximated outputs equal to the plain predictions."""
+    desc = H.blackscholes_desc(64)
+    n = 1 << 24
+    x = W.blackscholes_inputs(n, seed=25)
+    xd = torch.from_numpy(x).cuda()
+    S = H.Surrogate(desc, seed=9)
+    m_tr = 1 << 18
+    tgt = torch.zeros(m_tr, dtype=torch.float32, device="cuda")
+    xt = xd[:, :m_tr].contiguous()
+    with H.Region(H.HPAC_REGION_BLACKSCHOLES, xt, param=W.BS_RATE) as R:
+        R.run_exact(xt, tgt)
+    S.train(xt, tgt, W.BS_RATE, batch=4096, epochs=1, lr=3e-3)
+    pred = torch.zeros(n, dtype=torch.float32, device="cuda")
+    S.infer(xd, pred, W.BS_RATE)
+    out = torch.zeros(n, dtype=torch.float32, device="cuda")
+    mask = torch.zeros(n, dtype=torch.uint8, device="cuda")
+    tau = 1.0
+    st = S.infer(xd, out, W.BS_RATE, fallback_below=tau, mask=mask, stats=True)
+    pr, o, m = pred.cpu().numpy(), out.cpu().numpy(), mask.cpu().numpy()
+    assert np.array_equal(m == 0, pr < tau)
+    assert st["approximated"] == int((m == 1).sum()) and 0 < st["approximated"] < n
+    assert np.array_equal(o[m == 1], pr[m == 1])
+    rng = np.random.default_rng(3)
+    idx = np.concatenate([rng.choice(n, 4096, replace=False), [0, n - 1]])
+    p = S.params()
+    xs = np.ascontiguousarray(x[:, idx])
+    ref, _, _ = M.forward(p, dd(desc), 0, xs, W.BS_RATE)
+    bound = forward_bound(p, dd(desc), xs, W.BS_RATE) * desc.out_scale * xs[0].astype(np.float64)
+    assert np.all(np.abs(pr[idx].astype(np.float64) - ref) <= bound + 1e-6 * np.abs(ref))
+    from tolerances import blackscholes_tol
+    fb = np.nonzero(m == 0)[0]
+    fb = fb[rng.choice(fb.size, min(fb.size, 4096), replace=False)]
+    exact = orc.run_exact(orc.BLACKSCHOLES, x[:, fb].astype(np.float64), W.BS_RATE)
+    assert np.all(np.abs(o[fb] - exact) <= blackscholes_tol(x[:, fb], W.BS_RATE))
+    S.close()
+
+
 def test_adjoint_blackscholes_textbook_and_finite_differences(H, orc):
     rows = [l.split() for l in open(os.path.join(GOLD, "blackscholes_hull.txt"))
             if l.strip() and not l.startswith("#")]
