@@ -93,6 +93,7 @@ __global__ void identity_adjoint(int64_t n, int D, T *__restrict__ g) {
 using namespace hpac;
 
 extern "C" hpac_status hpac_region_adjoint(hpac_region *r, const void *d_in, void *d_grad) {
+  TraceRange trace_("hpac_region_adjoint");
   if (!r) return set_error(HPAC_EINVAL, "region is NULL");
   const hpac_region_desc &d = r->d;
   if (d.n == 0) return HPAC_OK;

@@ -234,6 +234,7 @@ hpac_status hpac_region_set_stream(hpac_region *r, void *cuda_stream) {
 }
 
 hpac_status hpac_run_exact(hpac_region *r, const void *d_in, void *d_out) {
+  TraceRange trace_("hpac_run_exact");
   hpac_status s = check_call(r, d_in, d_out);
   if (s != HPAC_OK) return s;
   if (r->d.kind == HPAC_REGION_BINOMIAL)
@@ -243,6 +244,7 @@ hpac_status hpac_run_exact(hpac_region *r, const void *d_in, void *d_out) {
 
 hpac_status hpac_run_perfo(hpac_region *r, const hpac_perfo_knobs *k, const void *d_in, void *d_out,
                            uint8_t *d_mask, hpac_stats *h_stats) {
+  TraceRange trace_("hpac_run_perfo");
   hpac_status s = check_call(r, d_in, d_out);
   if (s != HPAC_OK) return s;
   if (!k) return set_error(HPAC_EINVAL, "knobs are NULL");
@@ -282,6 +284,7 @@ hpac_status hpac_run_perfo(hpac_region *r, const hpac_perfo_knobs *k, const void
 
 hpac_status hpac_run_taf(hpac_region *r, const hpac_taf_knobs *k, const void *d_in, void *d_out,
                          uint8_t *d_mask, void *d_stat, hpac_stats *h_stats) {
+  TraceRange trace_("hpac_run_taf");
   hpac_status s = check_call(r, d_in, d_out);
   if (s != HPAC_OK) return s;
   if (!k) return set_error(HPAC_EINVAL, "knobs are NULL");
@@ -309,6 +312,7 @@ hpac_status hpac_run_taf(hpac_region *r, const hpac_taf_knobs *k, const void *d_
 
 hpac_status hpac_run_iact(hpac_region *r, const hpac_iact_knobs *k, const void *d_in, void *d_out,
                           uint8_t *d_mask, void *d_stat, hpac_stats *h_stats) {
+  TraceRange trace_("hpac_run_iact");
   hpac_status s = check_call(r, d_in, d_out);
   if (s != HPAC_OK) return s;
   if (!k) return set_error(HPAC_EINVAL, "knobs are NULL");

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include "hpac.h"
@@ -57,6 +58,16 @@ hpac_status launch_binomial(hpac_region *r, int technique, const void *knobs, co
 hpac_status region_state(hpac_region *r, const int64_t (&key)[6], size_t bytes, void **out);
 
 inline size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+// A named NVTX range around a library call, for timeline tools (Nsight
+// Systems, ncu --nvtx); without a tool attached the push and pop return at
+// once.
+struct TraceRange {
+  explicit TraceRange(const char *name) { nvtxRangePushA(name); }
+  ~TraceRange() { nvtxRangePop(); }
+  TraceRange(const TraceRange &) = delete;
+  TraceRange &operator=(const TraceRange &) = delete;
+};
 
 // Largest dynamic shared memory a block of this device may use.
 int max_dyn_smem(int device);

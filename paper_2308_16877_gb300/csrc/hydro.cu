@@ -306,6 +306,7 @@ hpac_status check_state(const hpac_hydro_state *s) {
 using namespace hpac;
 
 extern "C" hpac_status hpac_hydro_init(const hpac_hydro_state *s, void *cuda_stream) {
+  TraceRange trace_("hpac_hydro_init");
   hpac_status st = check_state(s);
   if (st != HPAC_OK) return st;
   int dev = 0;
@@ -320,6 +321,7 @@ extern "C" hpac_status hpac_hydro_init(const hpac_hydro_state *s, void *cuda_str
 }
 
 extern "C" hpac_status hpac_hydro_nodes(const hpac_hydro_state *s, void *cuda_stream) {
+  TraceRange trace_("hpac_hydro_nodes");
   hpac_status st = check_state(s);
   if (st != HPAC_OK) return st;
   int dev = 0;
@@ -331,6 +333,7 @@ extern "C" hpac_status hpac_hydro_nodes(const hpac_hydro_state *s, void *cuda_st
 }
 
 extern "C" hpac_status hpac_hydro_elements(const hpac_hydro_state *s, void *cuda_stream) {
+  TraceRange trace_("hpac_hydro_elements");
   hpac_status st = check_state(s);
   if (st != HPAC_OK) return st;
   int dev = 0;
@@ -346,6 +349,7 @@ extern "C" hpac_status hpac_hydro_elements(const hpac_hydro_state *s, void *cuda
 }
 
 extern "C" hpac_status hpac_hydro_finalize(const hpac_hydro_state *s, void *cuda_stream) {
+  TraceRange trace_("hpac_hydro_finalize");
   hpac_status st = check_state(s);
   if (st != HPAC_OK) return st;
   int dev = 0;
@@ -359,6 +363,7 @@ extern "C" hpac_status hpac_hydro_finalize(const hpac_hydro_state *s, void *cuda
 extern "C" hpac_status hpac_hydro_step(const hpac_hydro_state *s, hpac_region *eos,
                                        int32_t technique, const void *knobs, uint8_t *d_mask,
                                        hpac_stats *h_stats) {
+  TraceRange trace_("hpac_hydro_step");
   hpac_status st = check_state(s);
   if (st != HPAC_OK) return st;
   if (!eos) return set_error(HPAC_EINVAL, "EOS region is NULL");
@@ -402,6 +407,7 @@ extern "C" hpac_status hpac_hydro_step(const hpac_hydro_state *s, hpac_region *e
 
 extern "C" hpac_status hpac_hydro_run(const hpac_hydro_state *s, hpac_region *eos, int32_t steps,
                                       int32_t technique, const void *knobs) {
+  TraceRange trace_("hpac_hydro_run");
   if (steps < 0) return set_error(HPAC_EINVAL, "steps < 0");
   for (int32_t k = 0; k < steps; ++k) {
     hpac_status st = hpac_hydro_step(s, eos, technique, knobs, nullptr, nullptr);

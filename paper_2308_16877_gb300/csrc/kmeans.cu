@@ -66,6 +66,7 @@ extern "C" hpac_status hpac_kmeans_update(int64_t n, int32_t clusters, const flo
                                           int64_t stride, const float *d_assign,
                                           const float *d_prev, float *d_cent, void *d_work,
                                           int64_t *h_changed, void *cuda_stream) {
+  TraceRange trace_("hpac_kmeans_update");
   if (n < 0 || clusters < 1 || clusters > kMaxClusters || stride < n)
     return set_error(HPAC_EINVAL, "K-Means update: bad n, clusters or stride");
   if (!d_cent || !d_work || (n > 0 && (!d_x || !d_assign)))

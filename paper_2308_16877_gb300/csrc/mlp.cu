@@ -742,6 +742,7 @@ extern "C" hpac_status hpac_mlp_set_params(hpac_mlp *m, const float *h_params) {
 extern "C" hpac_status hpac_mlp_infer(hpac_mlp *m, int64_t n, const void *d_in, int64_t in_stride,
                                       double param, void *d_out_, float fallback_below,
                                       uint8_t *d_mask, hpac_stats *h_stats) {
+  TraceRange trace_("hpac_mlp_infer");
   hpac_status s = check_io(m, n, d_in, in_stride);
   if (s != HPAC_OK) return s;
   float *d_out = static_cast<float *>(d_out_);
@@ -770,6 +771,7 @@ extern "C" hpac_status hpac_mlp_infer(hpac_mlp *m, int64_t n, const void *d_in, 
 extern "C" hpac_status hpac_mlp_grad(hpac_mlp *m, int64_t n, const void *d_in, int64_t in_stride,
                                      double param, const float *d_target, float *d_grad,
                                      float *h_loss) {
+  TraceRange trace_("hpac_mlp_grad");
   hpac_status s = check_io(m, n, d_in, in_stride);
   if (s != HPAC_OK) return s;
   if (n < 1 || !d_target) return set_error(HPAC_EINVAL, "empty batch or NULL targets");
@@ -796,6 +798,7 @@ extern "C" hpac_status hpac_mlp_grad(hpac_mlp *m, int64_t n, const void *d_in, i
 extern "C" hpac_status hpac_mlp_train(hpac_mlp *m, int64_t n, const void *d_in, int64_t in_stride,
                                       double param, const float *d_target, int32_t batch,
                                       int32_t epochs, float lr, float *h_loss) {
+  TraceRange trace_("hpac_mlp_train");
   hpac_status s = check_io(m, n, d_in, in_stride);
   if (s != HPAC_OK) return s;
   if (n < 1 || !d_target || batch < 16 || epochs < 0 || !(lr > 0.f))
@@ -831,6 +834,7 @@ extern "C" hpac_status hpac_mlp_train(hpac_mlp *m, int64_t n, const void *d_in, 
 
 extern "C" hpac_status hpac_mlp_input_grad(hpac_mlp *m, int64_t n, const void *d_in,
                                            int64_t in_stride, double param, float *d_grad) {
+  TraceRange trace_("hpac_mlp_input_grad");
   hpac_status s = check_io(m, n, d_in, in_stride);
   if (s != HPAC_OK) return s;
   if (n > 0 && !d_grad) return set_error(HPAC_EINVAL, "output is NULL");

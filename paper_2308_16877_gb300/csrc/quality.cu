@@ -152,6 +152,7 @@ using namespace hpac;
 extern "C" hpac_status hpac_quality(int32_t approx_dtype, int64_t n, const double *d_exact,
                                     const void *d_approx, int32_t metric,
                                     hpac_quality_result *h_result, void *cuda_stream) {
+  TraceRange trace_("hpac_quality");
   if (!h_result) return set_error(HPAC_EINVAL, "h_result is NULL");
   if (n < 0) return set_error(HPAC_EINVAL, "n < 0");
   if (metric < HPAC_METRIC_MAPE || metric > HPAC_METRIC_MCR)
@@ -235,6 +236,7 @@ hpac_status static_scratch(int dev, Partial **out) {
 extern "C" hpac_status hpac_quality_noalloc(int32_t approx_dtype, int64_t n, const double *d_exact,
                                             const void *d_approx, int32_t metric,
                                             hpac_quality_result *h_result, void *cuda_stream) {
+  TraceRange trace_("hpac_quality_noalloc");
   if (!h_result) return set_error(HPAC_EINVAL, "h_result is NULL");
   if (n < 0) return set_error(HPAC_EINVAL, "n < 0");
   if (n > kStaticMaxN)

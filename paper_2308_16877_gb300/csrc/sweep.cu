@@ -561,6 +561,7 @@ extern "C" hpac_status hpac_sweep_create(int32_t n_configs, const hpac_sweep_con
 }
 
 extern "C" hpac_status hpac_sweep_run(hpac_sweep *p) {
+  TraceRange trace_("hpac_sweep_run");
   if (!p) return set_error(HPAC_EINVAL, "sweep is NULL");
   HPAC_CUDA_TRY(cudaGraphLaunch(p->exec, p->user_stream));
   return HPAC_OK;
