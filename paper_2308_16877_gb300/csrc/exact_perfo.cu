@@ -146,11 +146,60 @@ __device__ __forceinline__ void map_body(R reg, const typename R::T *__restrict_
 // the perforation kernel's registers at five 256-thread blocks per SM, the
 // accurate map's occupancy, made the Black-Scholes stream slower: 59.4 against
 // 57.6 us for 2^24 options at small:4.)
+// The accurate map takes U groups per iteration (two for single-precision
+// regions), so that all their loads are in flight before any of them computes.
 template <class R, int V>
 __global__ void __launch_bounds__(256) map_kernel(R reg, const typename R::T *__restrict__ in,
                                                   int64_t stride, typename R::T *__restrict__ out,
                                                   int64_t n) {
-  map_body<R, V, false>(reg, in, stride, out, nullptr, n, DropRule{}, nullptr);
+  using T = typename R::T;
+  constexpr int U = sizeof(T) == 4 ? 2 : 1;
+  const int64_t groups = n / V;
+  const int64_t gstride = (int64_t)gridDim.x * blockDim.x;
+  int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  for (; g + (U - 1) * gstride < groups; g += U * gstride) {
+    T x[U][R::kReads][V];
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+      for (int d = 0; d < R::kReads; ++d) load_vec<T, V>(in + d * stride + (g + u * gstride) * V, x[u][d]);
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      T y[V];
+#pragma unroll
+      for (int j = 0; j < V; ++j) {
+        T xi[R::kReads];
+#pragma unroll
+        for (int d = 0; d < R::kReads; ++d) xi[d] = x[u][d][j];
+        y[j] = reg(xi);
+      }
+      store_vec<T, V>(out + (g + u * gstride) * V, y);
+    }
+  }
+  for (; g < groups; g += gstride) {  // at most U - 1 groups left
+    T x[R::kReads][V];
+#pragma unroll
+    for (int d = 0; d < R::kReads; ++d) load_vec<T, V>(in + d * stride + g * V, x[d]);
+    T y[V];
+#pragma unroll
+    for (int j = 0; j < V; ++j) {
+      T xi[R::kReads];
+#pragma unroll
+      for (int d = 0; d < R::kReads; ++d) xi[d] = x[d][j];
+      y[j] = reg(xi);
+    }
+    store_vec<T, V>(out + g * V, y);
+  }
+  // tail [groups*V, n): one invocation per thread of block 0
+  if (blockIdx.x == 0) {
+    const int64_t i = groups * V + threadIdx.x;
+    if (threadIdx.x < V && i < n) {
+      T xi[R::kReads];
+#pragma unroll
+      for (int d = 0; d < R::kReads; ++d) xi[d] = in[d * stride + i];
+      out[i] = reg(xi);
+    }
+  }
 }
 
 template <class R, int V>
