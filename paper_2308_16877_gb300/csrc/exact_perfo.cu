@@ -49,10 +49,10 @@ __device__ __forceinline__ void store_vec(T *p, const T (&v)[V]) {
   __stcs(reinterpret_cast<VT *>(p), x);
 }
 
-// Invocations [0, n) in groups of V; group g covers [g*V, g*V + V). The
-// accurate path (PERFO false) carries no drop rule.
-template <class R, int V, bool PERFO>
-__device__ __forceinline__ void map_body(R reg, const typename R::T *__restrict__ in, int64_t stride,
+// Perforation over invocations [0, n) in groups of V; group g covers
+// [g*V, g*V + V).
+template <class R, int V>
+__device__ __forceinline__ void perfo_body(R reg, const typename R::T *__restrict__ in, int64_t stride,
                                          typename R::T *__restrict__ out,
                                          uint8_t *__restrict__ mask, int64_t n, DropRule rule,
                                          unsigned long long *__restrict__ counters) {
@@ -65,17 +65,12 @@ __device__ __forceinline__ void map_body(R reg, const typename R::T *__restrict_
   const int64_t gstride = (int64_t)gridDim.x * blockDim.x;
   const int64_t g0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   DropWalk<V> walk;
-  if (PERFO) walk.init(rule, g0 * V, gstride * V);
+  walk.init(rule, g0 * V, gstride * V);
   for (int64_t g = g0; g < groups; g += gstride) {
     const int64_t i0 = g * V;
     bool drop[V];
-    if (PERFO) {
-      walk.drops(rule, i0, drop);
-      walk.advance(rule);
-    } else {
-#pragma unroll
-      for (int j = 0; j < V; ++j) drop[j] = false;
-    }
+    walk.drops(rule, i0, drop);
+    walk.advance(rule);
     bool all_drop = true, none_drop = true;
 #pragma unroll
     for (int j = 0; j < V; ++j) {
@@ -124,7 +119,7 @@ __device__ __forceinline__ void map_body(R reg, const typename R::T *__restrict_
     const int64_t i = groups * V + threadIdx.x;
     if (threadIdx.x < V && i < n) {
       bool drop[1] = {false};
-      if (PERFO) rule.drops<1>(i, drop);
+      rule.drops<1>(i, drop);
       if (mask) mask[i] = drop[0] ? HPAC_MASK_SKIPPED : HPAC_MASK_EXACT;
       n_drop += drop[0] ? 1 : 0;
       if (!drop[0]) {
@@ -208,7 +203,7 @@ __global__ void __launch_bounds__(256) perfo_kernel(R reg, const typename R::T *
                                                     uint8_t *__restrict__ mask, int64_t n,
                                                     DropRule rule,
                                                     unsigned long long *__restrict__ counters) {
-  map_body<R, V, true>(reg, in, stride, out, mask, n, rule, counters);
+  perfo_body<R, V>(reg, in, stride, out, mask, n, rule, counters);
 }
 
 template <class R>
