@@ -421,6 +421,14 @@ hpac_status hpac_sweep_destroy(hpac_sweep *sweep);
  * ------------------------------------------------------------------------ */
 hpac_status hpac_region_adjoint(hpac_region *region, const void *d_in, void *d_grad);
 
+/* Vector-Jacobian product of the exact region (the backward pass of a
+ * differentiable region call): d_grad[d * n + i] = d_gout[i] * d out_i / d in_{d,i}.
+ * d_gout: n values of the region dtype (device), the derivative of a scalar
+ * loss with respect to each output. Same regions, layout and errors as
+ * hpac_region_adjoint; HPAC_EINVAL if d_gout is NULL for n > 0. Asynchronous
+ * on the region's stream. */
+hpac_status hpac_region_vjp(hpac_region *region, const void *d_in, const void *d_gout, void *d_grad);
+
 /* ------------------------------------------------------------------------
  * Learned surrogate of a region (not from the paper): an MLP
  * n_feat -> hidden -> hidden -> 1 with GELU (tanh form), BF16 weights and
@@ -496,6 +504,27 @@ hpac_status hpac_mlp_train(hpac_mlp *mlp, int64_t n, const void *d_in, int64_t i
  * 4 x n floats, row d at d_grad[d * n + i]. */
 hpac_status hpac_mlp_input_grad(hpac_mlp *mlp, int64_t n, const void *d_in, int64_t in_stride,
                                 double param, float *d_grad);
+
+/* Vector-Jacobian products of the surrogate's region output as hpac_mlp_infer
+ * returns it without fallback (the backward pass of a differentiable surrogate
+ * call): given d_gout (n floats, device: the derivative of a scalar loss with
+ * respect to each output), d_grad_params (nullable; n_params floats, device,
+ * overwritten) receives sum_i gout_i d out_i / d params with the bfloat16
+ * rounding of weights and activations passed through as the identity, and
+ * d_grad_in (nullable; 4 x n floats, row d at d_grad_in[d * n + i])
+ * receives gout_i d out_i / d in_{d,i}. An EOS output clamped at zero has zero
+ * derivative. Asynchronous on the surrogate's stream. Errors: HPAC_EINVAL
+ * (NULL surrogate, inputs or d_gout, n < 0, stride < n), HPAC_ECUDA. */
+hpac_status hpac_mlp_vjp(hpac_mlp *mlp, int64_t n, const void *d_in, int64_t in_stride,
+                         double param, const float *d_gout, float *d_grad_params,
+                         float *d_grad_in);
+
+/* Replace the surrogate's parameters from device memory (n_params floats in
+ * the layout of hpac_mlp_get_params): an asynchronous device-to-device copy on
+ * the surrogate's stream, so a caller can keep the parameters as its own
+ * tensor (for example a framework's trainable parameter) and load them before
+ * each call. */
+hpac_status hpac_mlp_set_params_device(hpac_mlp *mlp, const float *d_params);
 
 /* Measured double-precision FMA rate of the current device in TFLOP/s
  * (2 flops per FMA), from a kernel of independent FMA chains on every SM: the

@@ -140,6 +140,40 @@ def input_grad(p, desc, kind, x, param):
     return xt.grad.numpy()
 
 
+def vjp(p, desc, kind, x, param, gout):
+    """Vector-Jacobian products of the region output (the EOS output clamped at
+    zero, as served) of the unrounded network with bf16 weights: the gradient
+    of sum_i gout_i out_i with respect to the parameters (the weights' bf16
+    rounding passed through as the identity, as in loss_and_grad) and to the
+    region inputs (4, n)."""
+    D, H = desc["n_feat"], desc["hidden"]
+    leaves = [t.clone().requires_grad_(True) for t in unpack(p, D, H)]
+    xt = torch.as_tensor(np.asarray(x, dtype=np.float64)).clone().requires_grad_(True)
+    if kind == 0:
+        S, K, T, sig = xt[0], xt[1], xt[2], xt[3]
+        d1 = (torch.log(S / K) + (param + 0.5 * sig * sig) * T) / (sig * torch.sqrt(T))
+        f = torch.stack([torch.log(S / K), sig * torch.sqrt(T), param * T,
+                         torch.clamp(d1, -10.0, 10.0), sig], dim=1)
+        mult = S
+    else:
+        f = xt[:4].T
+        e, v1, dv, q = xt[0], xt[1], xt[2], xt[3]
+        mult = (param - 1.0) * torch.clamp(e - dv * q, min=0.0) / v1
+    W1, b1, W2, b2, W3, b3 = leaves
+    fn = (f - torch.tensor(desc["feat_shift"][:D], dtype=torch.float64)) * \
+        torch.tensor(desc["feat_scale"][:D], dtype=torch.float64)
+    w1 = W1 + (bf16(W1) - W1).detach()
+    w2 = W2 + (bf16(W2) - W2).detach()
+    w3 = W3 + (bf16(W3) - W3).detach()
+    y = gelu(gelu(fn @ w1.T + b1) @ w2.T + b2) @ w3 + b3
+    out = mult * (desc["out_shift"] + desc["out_scale"] * y)
+    if kind == 1:
+        out = torch.clamp(out, min=0.0)
+    g = torch.as_tensor(np.asarray(gout, dtype=np.float64))
+    (out * g).sum().backward()
+    return torch.cat([l.grad.reshape(-1) for l in leaves]).numpy(), xt.grad.numpy()
+
+
 def adam(p, g, m, v, step, lr, b1=0.9, b2=0.999, eps=1e-8):
     """One Adam update (Kingma & Ba 2014) in float64; returns (p, m, v)."""
     m = b1 * m + (1 - b1) * g

@@ -12,7 +12,7 @@ namespace {
 // dC/dS = N(d1), dC/dK = -e^{-rT} N(d2),
 // dC/dT = S phi(d1) sigma / (2 sqrt T) + r K e^{-rT} N(d2), dC/dsigma = S phi(d1) sqrt T.
 __global__ void bs32_adjoint(const float *__restrict__ in, int64_t stride, int64_t n, float r,
-                             float *__restrict__ g) {
+                             const float *__restrict__ gout, float *__restrict__ g) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     const float S = in[i], K = in[stride + i], Tm = in[2 * stride + i], sig = in[3 * stride + i];
@@ -22,15 +22,16 @@ __global__ void bs32_adjoint(const float *__restrict__ in, int64_t stride, int64
     const float disc = __expf(-r * Tm);
     const float phi1 = 0.3989422804014327f * __expf(-0.5f * d1 * d1);
     const float n2 = normal_cdf(d2);
-    g[i] = normal_cdf(d1);
-    g[n + i] = -disc * n2;
-    g[2 * n + i] = S * phi1 * sig * 0.5f / sq + r * K * disc * n2;
-    g[3 * n + i] = S * phi1 * sq;
+    const float w = gout ? gout[i] : 1.0f;
+    g[i] = w * normal_cdf(d1);
+    g[n + i] = w * (-disc * n2);
+    g[2 * n + i] = w * (S * phi1 * sig * 0.5f / sq + r * K * disc * n2);
+    g[3 * n + i] = w * (S * phi1 * sq);
   }
 }
 
 __global__ void bs64_adjoint(const double *__restrict__ in, int64_t stride, int64_t n, double r,
-                             double *__restrict__ g) {
+                             const double *__restrict__ gout, double *__restrict__ g) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     const double S = in[i], K = in[stride + i], Tm = in[2 * stride + i], sig = in[3 * stride + i];
@@ -41,10 +42,11 @@ __global__ void bs64_adjoint(const double *__restrict__ in, int64_t stride, int6
     const double phi1 = 0.39894228040143267794 * exp(-0.5 * d1 * d1);
     const double n1 = 0.5 * erfc(-0.70710678118654752440 * d1);
     const double n2 = 0.5 * erfc(-0.70710678118654752440 * d2);
-    g[i] = n1;
-    g[n + i] = -disc * n2;
-    g[2 * n + i] = S * phi1 * sig * 0.5 / sq + r * K * disc * n2;
-    g[3 * n + i] = S * phi1 * sq;
+    const double w = gout ? gout[i] : 1.0;
+    g[i] = w * n1;
+    g[n + i] = w * (-disc * n2);
+    g[2 * n + i] = w * (S * phi1 * sig * 0.5 / sq + r * K * disc * n2);
+    g[3 * n + i] = w * (S * phi1 * sq);
   }
 }
 
@@ -52,7 +54,7 @@ __global__ void bs64_adjoint(const double *__restrict__ in, int64_t stride, int6
 // Dn = v1 + (g-1) dv / 2 (the closed form of the implicit update times v1);
 // zero where num < 0 (the energy clamp).
 __global__ void eos_adjoint(const double *__restrict__ in, int64_t stride, int64_t n, double gamma,
-                            double *__restrict__ g) {
+                            const double *__restrict__ gout, double *__restrict__ g) {
   const double g1 = gamma - 1.0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
@@ -73,18 +75,19 @@ __global__ void eos_adjoint(const double *__restrict__ in, int64_t stride, int64
       dv1 = g1 * (num_v1 * Dn - num) * inv * inv;
       ddv = g1 * (num_dv * Dn - 0.5 * g1 * num) * inv * inv;
     }
-    g[i] = de;
-    g[n + i] = dv1;
-    g[2 * n + i] = ddv;
-    g[3 * n + i] = dq;
+    const double w = gout ? gout[i] : 1.0;
+    g[i] = w * de;
+    g[n + i] = w * dv1;
+    g[2 * n + i] = w * ddv;
+    g[3 * n + i] = w * dq;
   }
 }
 
 template <typename T>
-__global__ void identity_adjoint(int64_t n, int D, T *__restrict__ g) {
+__global__ void identity_adjoint(int64_t n, int D, const T *__restrict__ gout, T *__restrict__ g) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
-    for (int d = 0; d < D; ++d) g[d * n + i] = d == 0 ? (T)1 : (T)0;
+    for (int d = 0; d < D; ++d) g[d * n + i] = d == 0 ? (gout ? gout[i] : (T)1) : (T)0;
 }
 
 }  // namespace
@@ -92,8 +95,9 @@ __global__ void identity_adjoint(int64_t n, int D, T *__restrict__ g) {
 
 using namespace hpac;
 
-extern "C" hpac_status hpac_region_adjoint(hpac_region *r, const void *d_in, void *d_grad) {
-  TraceRange trace_("hpac_region_adjoint");
+namespace {
+
+hpac_status adjoint_launch(hpac_region *r, const void *d_in, const void *d_gout, void *d_grad) {
   if (!r) return set_error(HPAC_EINVAL, "region is NULL");
   const hpac_region_desc &d = r->d;
   if (d.n == 0) return HPAC_OK;
@@ -104,25 +108,47 @@ extern "C" hpac_status hpac_region_adjoint(hpac_region *r, const void *d_in, voi
   if (blocks > (int64_t)sms * 8) blocks = (int64_t)sms * 8;
   if (d.kind == HPAC_REGION_BINOMIAL || d.kind == HPAC_REGION_KMEANS)
     return set_error(HPAC_EUNSUPPORTED, "no adjoint of region kind %d", d.kind);
+  const bool f32 = d.dtype == HPAC_F32;
+  const float *gf = static_cast<const float *>(d_gout);
+  const double *gd = static_cast<const double *>(d_gout);
   switch (d.kind) {
     case HPAC_REGION_BLACKSCHOLES:
-      if (d.dtype == HPAC_F32)
+      if (f32)
         bs32_adjoint<<<(unsigned)blocks, 256, 0, r->stream>>>(
-            static_cast<const float *>(d_in), d.in_stride, d.n, (float)d.param, static_cast<float *>(d_grad));
+            static_cast<const float *>(d_in), d.in_stride, d.n, (float)d.param, gf,
+            static_cast<float *>(d_grad));
       else
         bs64_adjoint<<<(unsigned)blocks, 256, 0, r->stream>>>(
-            static_cast<const double *>(d_in), d.in_stride, d.n, d.param, static_cast<double *>(d_grad));
+            static_cast<const double *>(d_in), d.in_stride, d.n, d.param, gd,
+            static_cast<double *>(d_grad));
       break;
     case HPAC_REGION_EOS:
       eos_adjoint<<<(unsigned)blocks, 256, 0, r->stream>>>(
-          static_cast<const double *>(d_in), d.in_stride, d.n, d.param, static_cast<double *>(d_grad));
+          static_cast<const double *>(d_in), d.in_stride, d.n, d.param, gd,
+          static_cast<double *>(d_grad));
       break;
     default:
-      if (d.dtype == HPAC_F32)
-        identity_adjoint<float><<<(unsigned)blocks, 256, 0, r->stream>>>(d.n, d.n_in, static_cast<float *>(d_grad));
+      if (f32)
+        identity_adjoint<float><<<(unsigned)blocks, 256, 0, r->stream>>>(d.n, d.n_in, gf,
+                                                                         static_cast<float *>(d_grad));
       else
-        identity_adjoint<double><<<(unsigned)blocks, 256, 0, r->stream>>>(d.n, d.n_in, static_cast<double *>(d_grad));
+        identity_adjoint<double><<<(unsigned)blocks, 256, 0, r->stream>>>(d.n, d.n_in, gd,
+                                                                          static_cast<double *>(d_grad));
   }
   HPAC_CUDA_TRY(cudaGetLastError());
   return HPAC_OK;
+}
+
+}  // namespace
+
+extern "C" hpac_status hpac_region_adjoint(hpac_region *r, const void *d_in, void *d_grad) {
+  TraceRange trace_("hpac_region_adjoint");
+  return adjoint_launch(r, d_in, nullptr, d_grad);
+}
+
+extern "C" hpac_status hpac_region_vjp(hpac_region *r, const void *d_in, const void *d_gout,
+                                       void *d_grad) {
+  TraceRange trace_("hpac_region_vjp");
+  if (r && r->d.n > 0 && !d_gout) return set_error(HPAC_EINVAL, "upstream gradient is NULL");
+  return adjoint_launch(r, d_in, d_gout, d_grad);
 }

@@ -98,6 +98,9 @@ struct MlpArgs {
   float *loss;
   unsigned long long *counters;  // [0] fallbacks
   float inv_n;          // MODE_GRAD: 1 / total samples of the batch
+  const float *gout;    // vector-Jacobian products: per-sample d(loss)/d(region output);
+                        // MODE_GRAD takes it instead of the squared error, MODE_INPUT_GRAD
+                        // multiplies each input derivative by it (nullable)
 };
 
 // Features of one invocation (FP32) and the output multiplier of the region.
@@ -316,7 +319,22 @@ __global__ void __launch_bounds__(H * 2) mlp_kernel(MlpArgs a, hpac_mlp_desc d) 
 
     // ---- backward: dy per row
     float dy0, dy1;
-    if (MODE == MODE_GRAD) {
+    // d(region output)/d(net) of each row, for the vector-Jacobian products:
+    // mult out_scale, and 0 where the EOS output is clamped at zero
+    float go0 = 0.f, go1 = 0.f;
+    if (a.gout) {
+      const float o0 = m0 * fmaf(d.out_scale, y0, d.out_shift);
+      const float o1 = m1 * fmaf(d.out_scale, y1, d.out_shift);
+      const bool k0 = v0 && (KIND != HPAC_REGION_EOS || o0 > 0.f);
+      const bool k1 = v1 && (KIND != HPAC_REGION_EOS || o1 > 0.f);
+      go0 = k0 ? a.gout[r0] : 0.f;
+      go1 = k1 ? a.gout[r1] : 0.f;
+    }
+    if (MODE == MODE_GRAD && a.gout) {
+      dy0 = go0 * m0 * d.out_scale;
+      dy1 = go1 * m1 * d.out_scale;
+      if (t == 0) atomicAdd(&g_b3, dy0 + dy1);
+    } else if (MODE == MODE_GRAD) {
       // rows whose multiplier is 0 (an untouched EOS element) carry no target
       const bool u0 = v0 && m0 != 0.f, u1 = v1 && m1 != 0.f;
       const float t0 = u0 ? (a.target[r0] / m0 - d.out_shift) / d.out_scale : 0.f;
@@ -450,6 +468,11 @@ __global__ void __launch_bounds__(H * 2) mlp_kernel(MlpArgs a, hpac_mlp_desc d) 
 #pragma unroll
             for (int k = 0; k < 4; ++k) gin[k] = ratio * dm[k] + m * d.out_scale * df[k];
           }
+          if (a.gout) {
+            const float go = h ? go1 : go0;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) gin[k] *= go;
+          }
 #pragma unroll
           for (int k = 0; k < 4; ++k) a.out[k * a.n + i] = gin[k];
         }
@@ -532,7 +555,7 @@ __global__ void __launch_bounds__(H * 2) mlp_kernel(MlpArgs a, hpac_mlp_desc d) 
     }
     if (threadIdx.x == 0) {
       atomicAdd(&a.grad[ob3], g_b3);
-      atomicAdd(a.loss, g_loss);
+      if (a.loss) atomicAdd(a.loss, g_loss);
     }
   }
   if (MODE == MODE_INFER) {
@@ -843,6 +866,41 @@ extern "C" hpac_status hpac_mlp_input_grad(hpac_mlp *m, int64_t n, const void *d
   a.in = d_in, a.stride = in_stride, a.n = n, a.param = param, a.out = d_grad;
   a.params = m->params;
   return launch<MODE_INPUT_GRAD>(m, a);
+}
+
+extern "C" hpac_status hpac_mlp_vjp(hpac_mlp *m, int64_t n, const void *d_in, int64_t in_stride,
+                                    double param, const float *d_gout, float *d_grad_params,
+                                    float *d_grad_in) {
+  TraceRange trace_("hpac_mlp_vjp");
+  hpac_status s = check_io(m, n, d_in, in_stride);
+  if (s != HPAC_OK) return s;
+  if (n > 0 && !d_gout) return set_error(HPAC_EINVAL, "upstream gradient is NULL");
+  if (d_grad_params) {
+    HPAC_CUDA_TRY(cudaMemsetAsync(d_grad_params, 0, sizeof(float) * m->n_params, m->stream));
+    if (n > 0) {
+      MlpArgs a{};
+      a.in = d_in, a.stride = in_stride, a.n = n, a.param = param, a.gout = d_gout;
+      a.params = m->params;
+      a.grad = d_grad_params;
+      s = launch<MODE_GRAD>(m, a);
+      if (s != HPAC_OK) return s;
+    }
+  }
+  if (d_grad_in && n > 0) {
+    MlpArgs a{};
+    a.in = d_in, a.stride = in_stride, a.n = n, a.param = param, a.out = d_grad_in, a.gout = d_gout;
+    a.params = m->params;
+    s = launch<MODE_INPUT_GRAD>(m, a);
+    if (s != HPAC_OK) return s;
+  }
+  return HPAC_OK;
+}
+
+extern "C" hpac_status hpac_mlp_set_params_device(hpac_mlp *m, const float *d_params) {
+  if (!m || !d_params) return set_error(HPAC_EINVAL, "NULL argument");
+  HPAC_CUDA_TRY(cudaMemcpyAsync(m->params, d_params, sizeof(float) * m->n_params,
+                                cudaMemcpyDeviceToDevice, m->stream));
+  return HPAC_OK;
 }
 
 extern "C" hpac_status hpac_mlp_fit_normalization(hpac_mlp *m, int64_t n, const void *d_in,

@@ -127,6 +127,7 @@ SIGNATURES = {
     "hpac_sweep_results": (C.c_int, [_P, C.POINTER(hpac_sweep_stats)]),
     "hpac_sweep_destroy": (C.c_int, [_P]),
     "hpac_region_adjoint": (C.c_int, [_P, _P, _P]),
+    "hpac_region_vjp": (C.c_int, [_P, _P, _P, _P]),
     "hpac_mlp_create": (C.c_int, [C.POINTER(hpac_mlp_desc), _P, C.c_uint64, _P, C.POINTER(_P)]),
     "hpac_mlp_destroy": (C.c_int, [_P]),
     "hpac_mlp_num_params": (C.c_int32, [_P]),
@@ -139,6 +140,8 @@ SIGNATURES = {
     "hpac_mlp_train": (C.c_int, [_P, C.c_int64, _P, C.c_int64, C.c_double, _P, C.c_int32, C.c_int32,
                                  C.c_float, C.POINTER(C.c_float)]),
     "hpac_mlp_input_grad": (C.c_int, [_P, C.c_int64, _P, C.c_int64, C.c_double, _P]),
+    "hpac_mlp_vjp": (C.c_int, [_P, C.c_int64, _P, C.c_int64, C.c_double, _P, _P, _P]),
+    "hpac_mlp_set_params_device": (C.c_int, [_P, _P]),
     "hpac_mlp_fit_normalization": (C.c_int, [_P, C.c_int64, _P, C.c_int64, C.c_double, _P]),
     "hpac_mlp_get_desc": (C.c_int, [_P, C.POINTER(hpac_mlp_desc)]),
     "hpac_last_error": (C.c_char_p, []),
@@ -571,6 +574,79 @@ def region_adjoint(region, x, grad):
     return grad
 
 
+def region_vjp(region, x, gout, grad):
+    """gout_i d out_i / d in_{d,i} of the exact region (hpac_region_vjp) into grad (D, n)."""
+    _check(load().hpac_region_vjp(region._h, _ptr(x), _ptr(gout), _ptr(grad)), "hpac_region_vjp")
+    return grad
+
+
+def _autograd():
+    import torch
+
+    class RegionFn(torch.autograd.Function):
+        """The exact region as a differentiable function of its inputs: forward
+        hpac_run_exact, backward hpac_region_vjp."""
+
+        @staticmethod
+        def forward(ctx, x, region):
+            out = torch.empty(region.n, dtype=x.dtype, device=x.device)
+            region.run_exact(x, out)
+            ctx.region = region
+            ctx.save_for_backward(x)
+            return out
+
+        @staticmethod
+        def backward(ctx, gout):
+            (x,) = ctx.saved_tensors
+            R = ctx.region
+            g = torch.empty(R.d_in, R.n, dtype=x.dtype, device=x.device)
+            region_vjp(R, x, gout.to(x.dtype).contiguous(), g)
+            gx = torch.zeros_like(x)
+            gx[:, :R.n] = g
+            return gx, None
+
+    class SurrogateFn(torch.autograd.Function):
+        """The surrogate as a differentiable function of the region inputs and
+        of its parameters (a float32 CUDA tensor of n_params values, loaded
+        into the surrogate before the forward and the backward): forward
+        hpac_mlp_infer, backward hpac_mlp_vjp."""
+
+        @staticmethod
+        def forward(ctx, x, weights, surrogate, param):
+            surrogate.set_params_device(weights)
+            eos = surrogate.desc.kind == HPAC_REGION_EOS
+            n = x.shape[1]
+            out = torch.empty(n, dtype=torch.float64 if eos else torch.float32, device=x.device)
+            surrogate.infer(x, out, param)
+            ctx.surrogate, ctx.param = surrogate, param
+            ctx.save_for_backward(x, weights)
+            return out
+
+        @staticmethod
+        def backward(ctx, gout):
+            x, weights = ctx.saved_tensors
+            S = ctx.surrogate
+            S.set_params_device(weights)
+            n = x.shape[1]
+            gp = torch.empty(S.n_params, dtype=torch.float32, device=x.device) \
+                if ctx.needs_input_grad[1] else None
+            gi = torch.empty(4, n, dtype=torch.float32, device=x.device) \
+                if ctx.needs_input_grad[0] else None
+            S.vjp(x, gout.to(torch.float32).contiguous(), ctx.param, gp, gi)
+            gx = None
+            if gi is not None:
+                gx = torch.zeros_like(x)
+                gx[:4] = gi.to(x.dtype)
+            return gx, gp, None, None
+
+    return RegionFn, SurrogateFn
+
+
+def differentiable(region, x):
+    """out = region(x) with autograd: d(loss)/dx comes from hpac_region_vjp."""
+    return _autograd()[0].apply(x, region)
+
+
 class Surrogate:
     """The learned surrogate of a region (hpac_mlp_*). desc: hpac_mlp_desc."""
 
@@ -637,6 +713,25 @@ class Surrogate:
         _check(load().hpac_mlp_input_grad(self._h, n, _ptr(x), x.shape[1], float(param), _ptr(out)),
                "hpac_mlp_input_grad")
         return out
+
+    def vjp(self, x, gout, param, grad_params=None, grad_in=None, n=None):
+        """hpac_mlp_vjp: sum_i gout_i d out_i / d params into grad_params and
+        gout_i d out_i / d in_{d,i} into grad_in (4, n); either may be None."""
+        n = x.shape[1] if n is None else n
+        _check(load().hpac_mlp_vjp(self._h, n, _ptr(x), x.shape[1], float(param), _ptr(gout),
+                                   _ptr(grad_params), _ptr(grad_in)), "hpac_mlp_vjp")
+
+    def set_params_device(self, weights):
+        """Load the parameters from a float32 CUDA tensor (hpac_mlp_set_params_device)."""
+        import torch
+        if (weights.dtype != torch.float32 or not weights.is_cuda or not weights.is_contiguous()
+                or weights.numel() != self.n_params):
+            raise ValueError("weights must be a contiguous float32 CUDA tensor of n_params values")
+        _check(load().hpac_mlp_set_params_device(self._h, _ptr(weights)), "hpac_mlp_set_params_device")
+
+    def apply(self, x, weights, param):
+        """out = surrogate(x; weights) with autograd through hpac_mlp_vjp."""
+        return _autograd()[1].apply(x, weights, self, param)
 
     def close(self):
         if self._h:

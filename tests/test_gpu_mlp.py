@@ -283,3 +283,82 @@ def test_eos_surrogate_forward_gradient_and_training(H):
     l1 = S.train(xd, yf, 5 / 3, batch=1024, epochs=20, lr=2e-3)
     assert l1 < 0.2 * l0, (l0, l1)
     S.close()
+
+
+@pytest.mark.parametrize("kind", [0, 1])
+def test_differentiable_exact_region(H, kind):
+    """The exact region behind torch.autograd (forward hpac_run_exact, backward
+    hpac_region_vjp): torch.autograd.gradcheck in double precision against
+    central differences of the region itself, and the vector-Jacobian product
+    equal to the adjoint times the upstream gradient."""
+    n = 12
+    if kind == 0:
+        x = W.blackscholes_inputs(n, seed=31).astype(np.float64)
+        param = W.BS_RATE
+    else:
+        x = W.eos_inputs(n, seed=31)
+        x[0] += 1e3           # away from the energy clamp, where p is not differentiable
+        param = 5.0 / 3.0
+    xd = torch.from_numpy(np.ascontiguousarray(x)).cuda().requires_grad_(True)
+    with H.Region(kind, xd.detach(), param=param) as R:
+        f = lambda t: H.differentiable(R, t)
+        if kind == 0:
+            assert torch.autograd.gradcheck(f, (xd,), eps=1e-6, atol=1e-6, rtol=1e-4)
+        else:
+            # inputs of very different scales (e ~ 1e5, dv ~ 1e-2): central
+            # differences with a step relative to each input row's magnitude
+            (gx,) = torch.autograd.grad(f(xd).sum(), xd)
+            for d in range(4):
+                hstep = 1e-6 * max(float(xd.detach()[d].abs().max()), 1e-3)
+                xp, xm = xd.detach().clone(), xd.detach().clone()
+                xp[d] += hstep
+                xm[d] -= hstep
+                fd = (f(xp) - f(xm)) / (2 * hstep)
+                assert torch.allclose(gx[d], fd, rtol=1e-5, atol=1e-9 * float(fd.abs().max())), d
+        w = torch.randn(n, dtype=torch.float64, device="cuda")
+        (f(xd) * w).sum().backward()
+        adj = torch.zeros(4, n, dtype=torch.float64, device="cuda")
+        H.region_adjoint(R, xd.detach(), adj)
+    assert torch.allclose(xd.grad, adj * w, rtol=1e-12, atol=1e-300)
+
+
+@pytest.mark.parametrize("kind,hidden", [(0, 64), (1, 128)])
+def test_differentiable_surrogate(H, kind, hidden):
+    """The surrogate behind torch.autograd with its parameters as a torch
+    tensor (forward hpac_mlp_infer, backward hpac_mlp_vjp): the parameter and
+    input gradients of sum_i w_i out_i against the oracle's, within the
+    bfloat16 rounding of the activations (cosine > 0.999, < 3% relative)."""
+    if kind == 0:
+        desc = H.blackscholes_desc(hidden)
+        n = 4096
+        x = W.blackscholes_inputs(n, seed=32)
+        param = W.BS_RATE
+    else:
+        desc = H.eos_desc(hidden)
+        n = 4096
+        x = W.eos_inputs(n, seed=32)
+        param = 5.0 / 3.0
+    S = H.Surrogate(desc, seed=12)
+    p0 = S.params()
+    xd = torch.from_numpy(np.ascontiguousarray(x)).cuda().requires_grad_(True)
+    weights = torch.from_numpy(p0).cuda().requires_grad_(True)
+    rng = np.random.default_rng(5)
+    w = rng.normal(size=n)
+    out = S.apply(xd, weights, param)
+    (out * torch.from_numpy(w).cuda().to(out.dtype)).sum().backward()
+    gp_ref, gx_ref = M.vjp(p0, dd(S.get_desc()), kind, x.astype(np.float64), param, w)
+    gp = weights.grad.cpu().numpy().astype(np.float64)
+    cos = float(gp @ gp_ref / (np.linalg.norm(gp) * np.linalg.norm(gp_ref)))
+    assert cos > 0.999, cos
+    assert np.linalg.norm(gp - gp_ref) / np.linalg.norm(gp_ref) < 0.03
+    gx = xd.grad.cpu().numpy().astype(np.float64)
+    for d in range(4):
+        err = np.linalg.norm(gx[d] - gx_ref[d]) / max(np.linalg.norm(gx_ref[d]), 1e-300)
+        assert err < 0.03, (d, err)
+    # the parameters are the caller's: a changed tensor changes the output
+    with torch.no_grad():
+        w2 = weights.detach().clone()
+        w2[-1] += 0.5
+    out2 = S.apply(xd.detach(), w2, param)
+    assert not torch.equal(out2, out.detach())
+    S.close()

@@ -91,3 +91,69 @@ def test_first_adam_step_closed_form():
     p1, m, v = M.adam(p, g, np.zeros(4), np.zeros(4), 1, lr=0.01)
     # bias-corrected moments equal g and g^2 after one step: update = lr g / (|g| + eps)
     assert np.allclose(p1, -0.01 * g / (np.abs(g) + 1e-8), rtol=1e-12)
+
+
+EOS_DESC = {"n_feat": 4, "hidden": 8, "feat_shift": [1e5, 1.0, 0.0, 0.0, 0, 0, 0, 0],
+            "feat_scale": [1e-5, 1.0, 10.0, 1e-4, 0, 0, 0, 0], "out_shift": 1.0, "out_scale": 0.1}
+
+
+@pytest.mark.parametrize("kind", [0, 1])
+def test_vjp_matches_finite_differences(kind):
+    """sum_i gout_i out_i: its parameter gradient (bf16-valued weights perturbed)
+    and its input gradient against central differences of the unrounded
+    forward, Black-Scholes and EOS (with the output clamp)."""
+    desc = DESC if kind == 0 else EOS_DESC
+    D, H = desc["n_feat"], desc["hidden"]
+    rng = np.random.default_rng(11 + kind)
+    p = rng.uniform(-0.5, 0.5, M.n_params(D, H))
+    if kind == 0:
+        x = W.blackscholes_inputs(6, seed=4).astype(np.float64)
+        param = W.BS_RATE
+    else:
+        n = 6
+        x = np.stack([rng.uniform(1e4, 3e5, n), rng.uniform(0.8, 1.2, n), rng.uniform(-0.05, 0.05, n),
+                      rng.uniform(0.0, 2e3, n)])
+        param = 5.0 / 3.0
+    gout = rng.normal(size=x.shape[1])
+    gp, gx = M.vjp(p, desc, kind, x, param, gout)
+    base = [M.bf16(t) if i in (0, 2, 4) else t.clone() for i, t in enumerate(M.unpack(p, D, H))]
+    flat = np.concatenate([t.reshape(-1).numpy() for t in base])
+
+    def F(pp, xx):
+        out, _, _ = M.forward(pp, desc, kind, xx, param, round_act=False)
+        return float(np.dot(gout, out))
+
+    h = 1e-6
+    # the forward rounds weights to bf16 again; perturbing W1/W2/W3 entries of
+    # bf16 values by 1e-6 would be rounded away, so the check perturbs biases
+    # (not rounded) and compares the weights' gradient through the bias identity
+    sizes = [H * D, H, H * H, H, H, 1]
+    starts = np.cumsum([0] + sizes)
+    for seg in (1, 3, 5):
+        for off in range(0, sizes[seg], max(1, sizes[seg] // 3)):
+            fi = starts[seg] + off
+            pp, pm = flat.copy(), flat.copy()
+            pp[fi] += h
+            pm[fi] -= h
+            fd = (F(pp, x) - F(pm, x)) / (2 * h)
+            assert gp[fi] == pytest.approx(fd, rel=1e-5, abs=1e-7), (seg, off)
+    # weight gradients: the layer-3 weight gradient is the sum over rows of
+    # gout_i mult_i out_scale h2_i (h2 from the unrounded network)
+    params = [t for t in base]
+    f, mult = M.features(kind, x, param)
+    _, (fn, z1, h1, z2, h2) = M.net(params, desc, f, round_act=False)
+    dout = torch.as_tensor(gout) * mult * desc["out_scale"]
+    if kind == 1:
+        out, _, _ = M.forward(p, desc, kind, x, param, round_act=False)
+        dout = dout * torch.as_tensor(out > 0)
+    w3g = (dout[:, None] * h2).sum(dim=0).numpy()
+    assert np.allclose(gp[starts[4]:starts[5]], w3g, rtol=1e-9, atol=1e-12)
+    for d in range(4):
+        xp, xm = x.copy(), x.copy()
+        step = h * max(1.0, np.abs(x[d]).max())
+        xp[d] += step
+        xm[d] -= step
+        fd = (F(flat, xp) - F(flat, xm)) / (2 * step)
+        # F sums over rows, each row depends on its own inputs only: compare the
+        # directional derivative along the all-ones perturbation of row d
+        assert gx[d].sum() == pytest.approx(fd, rel=1e-5, abs=1e-8), d
