@@ -176,7 +176,7 @@ def measured_hbm():
 
 # ---------------------------------------------------------------- CPU oracle
 
-def hydro_cpu(n=HYDRO_N, steps=25):
+def hydro_cpu(n=HYDRO_N, steps=25, single_steps=0):
     """The oracle on the same mesh: exact, TAF and iACT runs of `steps` time
     steps (a bounded sample of the 100-step workload)."""
     import oracle
@@ -190,16 +190,28 @@ def hydro_cpu(n=HYDRO_N, steps=25):
              oracle.eos_knobs(oracle.EOS_IACT, tsize=IACT["tsize"], tperwarp=IACT["tperwarp"],
                               thresh=IACT["thresh"], level=IACT["level"], threads=T, block=256,
                               in_scale=IACT_SCALE)]
-    t0 = time.perf_counter()
-    for k in knobs:
-        S = oracle.HydroState(n, x, y, z, e)
-        for _ in range(steps):
-            S.step(dt, k)
-    dt_s = time.perf_counter() - t0
-    return {"value": 3 * E * steps / dt_s, "unit": "elements/s", "cores": oracle.num_threads(),
-            "kind": "oracle",
-            "sample": f"{n}^3 mesh, exact + TAF + iACT runs of {steps} time steps each",
-            "seconds": dt_s}
+    def timed(nsteps):
+        t0 = time.perf_counter()
+        for k in knobs:
+            S = oracle.HydroState(n, x, y, z, e)
+            for _ in range(nsteps):
+                S.step(dt, k)
+        return time.perf_counter() - t0
+
+    cores = oracle.num_threads()
+    dt_s = timed(steps)
+    out = {"value": 3 * E * steps / dt_s, "unit": "elements/s", "cores": cores, "kind": "oracle",
+           "sample": f"{n}^3 mesh, exact + TAF + iACT runs of {steps} time steps each",
+           "seconds": dt_s}
+    if single_steps:
+        oracle.set_threads(1)
+        try:
+            t1 = timed(single_steps)
+        finally:
+            oracle.set_threads(cores)
+        out["single_thread"] = {"value": 3 * E * single_steps / t1, "unit": "elements/s",
+                                "sample": f"exact + TAF + iACT runs of {single_steps} time steps each"}
+    return out
 
 
 def run_reference(args):
@@ -1110,7 +1122,7 @@ def main(argv=None):
     persistent = None if args.no_persistent else bench_persistent(hpac, torch, dev, stream)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = hydro_cpu()
+        cpu = hydro_cpu(single_steps=2)
         cpu.pop("seconds", None)
 
     if rank == 0:

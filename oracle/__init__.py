@@ -56,6 +56,8 @@ def lib() -> C.CDLL:
         L.orc_kmeans_update.argtypes = [I64, I32, P, I64, P, P, P, P]
         L.orc_kmeans_update.restype = C.c_int
         L.orc_num_threads.restype = C.c_int
+        L.orc_set_threads.argtypes = [I32]
+        L.orc_set_threads.restype = None
         for f in ("orc_run_exact", "orc_run_perfo", "orc_run_taf", "orc_replay_taf", "orc_run_iact",
                   "orc_quality", "orc_run_taf_persist", "orc_run_iact_persist"):
             getattr(L, f).restype = C.c_int
@@ -89,6 +91,11 @@ def _ptr(a):
 
 def num_threads() -> int:
     return int(lib().orc_num_threads())
+
+
+def set_threads(n: int) -> None:
+    """OpenMP threads of the oracle's parallel loops (n < 1: one per processor)."""
+    lib().orc_set_threads(int(n))
 
 
 def _region(kind, x, n, param, threads, block, arg=0):

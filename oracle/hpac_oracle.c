@@ -838,3 +838,12 @@ int orc_num_threads(void) {
   return 1;
 #endif
 }
+
+/* Threads of the following parallel regions (n < 1: one per processor). */
+void orc_set_threads(int n) {
+#ifdef _OPENMP
+  omp_set_num_threads(n > 0 ? n : omp_get_num_procs());
+#else
+  (void)n;
+#endif
+}
