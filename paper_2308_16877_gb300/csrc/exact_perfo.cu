@@ -50,8 +50,10 @@ __device__ __forceinline__ void store_vec(T *p, const T (&v)[V]) {
 }
 
 // Perforation over invocations [0, n) in groups of V; group g covers
-// [g*V, g*V + V).
-template <class R, int V>
+// [g*V, g*V + V). UNIFORM: every group is kept or dropped as a whole
+// (DropWalk::uniform), so a group costs one decision and no per-invocation
+// selects.
+template <class R, int V, bool UNIFORM>
 __device__ __forceinline__ void perfo_body(R reg, const typename R::T *__restrict__ in, int64_t stride,
                                          typename R::T *__restrict__ out,
                                          uint8_t *__restrict__ mask, int64_t n, DropRule rule,
@@ -66,7 +68,39 @@ __device__ __forceinline__ void perfo_body(R reg, const typename R::T *__restric
   const int64_t g0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   DropWalk<V> walk;
   walk.init(rule, g0 * V, gstride * V);
-  for (int64_t g = g0; g < groups; g += gstride) {
+  if (UNIFORM) {
+    for (int64_t g = g0; g < groups; g += gstride) {
+      const int64_t i0 = g * V;
+      const bool dd = walk.uniform(rule, i0);
+      walk.advance(rule);
+      if (mask) {
+        const uint8_t mv = dd ? HPAC_MASK_SKIPPED : HPAC_MASK_EXACT;
+        if (V == 4) {
+          *reinterpret_cast<uchar4 *>(mask + i0) = make_uchar4(mv, mv, mv, mv);
+        } else {
+#pragma unroll
+          for (int j = 0; j < V; ++j) mask[i0 + j] = mv;
+        }
+      }
+      if (dd) {
+        n_drop += V;
+        continue;
+      }
+      T x[R::kReads][V];
+#pragma unroll
+      for (int d = 0; d < R::kReads; ++d) load_vec<T, V>(in + d * stride + i0, x[d]);
+      T y[V];
+#pragma unroll
+      for (int j = 0; j < V; ++j) {
+        T xi[R::kReads];
+#pragma unroll
+        for (int d = 0; d < R::kReads; ++d) xi[d] = x[d][j];
+        y[j] = reg(xi);
+      }
+      store_vec<T, V>(out + i0, y);
+    }
+  }
+  for (int64_t g = g0; g < groups && !UNIFORM; g += gstride) {
     const int64_t i0 = g * V;
     bool drop[V];
     walk.drops(rule, i0, drop);
@@ -197,13 +231,13 @@ __global__ void __launch_bounds__(256) map_kernel(R reg, const typename R::T *__
   }
 }
 
-template <class R, int V>
+template <class R, int V, bool UNIFORM>
 __global__ void __launch_bounds__(256) perfo_kernel(R reg, const typename R::T *__restrict__ in,
                                                     int64_t stride, typename R::T *__restrict__ out,
                                                     uint8_t *__restrict__ mask, int64_t n,
                                                     DropRule rule,
                                                     unsigned long long *__restrict__ counters) {
-  perfo_body<R, V>(reg, in, stride, out, mask, n, rule, counters);
+  perfo_body<R, V, UNIFORM>(reg, in, stride, out, mask, n, rule, counters);
 }
 
 template <class R>
@@ -227,7 +261,12 @@ hpac_status launch_map(const hpac_region *r, R reg, const void *in_, void *out_,
     auto kern = vec_ok ? map_kernel<R, VW> : map_kernel<R, 1>;
     kern<<<(unsigned)blocks, threads, 0, r->stream>>>(reg, in, r->d.in_stride, out, n);
   } else {
-    auto kern = vec_ok ? perfo_kernel<R, VW> : perfo_kernel<R, 1>;
+    const bool range = rule.kind == HPAC_PERFO_INI || rule.kind == HPAC_PERFO_FINI;
+    // (groups cover [0, n - n % VW); the tail runs per invocation, so hi = n splits none)
+    const bool uniform = vec_ok && (range ? (rule.lo % VW == 0 && (rule.hi % VW == 0 || rule.hi == n))
+                                          : (rule.herded && rule.T % VW == 0));
+    auto kern = uniform ? perfo_kernel<R, VW, true>
+                        : (vec_ok ? perfo_kernel<R, VW, false> : perfo_kernel<R, 1, false>);
     kern<<<(unsigned)blocks, threads, 0, r->stream>>>(reg, in, r->d.in_stride, out, mask, n, rule,
                                                        counters);
   }

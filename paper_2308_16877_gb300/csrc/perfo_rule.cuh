@@ -108,6 +108,14 @@ struct DropWalk {
     }
     if (res >= m) res -= m;  // res < 2M here (M < 2^31)
   }
+  // The whole group's decision when it is the same for its V invocations: a
+  // herded pattern with T a multiple of V (no group straddles two steps), or
+  // ini / fini with no group straddling an end of the kept range.
+  __device__ __forceinline__ bool uniform(const DropRule &R, int64_t i0) const {
+    if (R.kind == HPAC_PERFO_INI || R.kind == HPAC_PERFO_FINI) return i0 < R.lo || i0 >= R.hi;
+    return (R.kind == HPAC_PERFO_SMALL || R.kind == HPAC_PERFO_LARGE) ? drop_res(R, res)
+                                                                      : R.drop_key(k);
+  }
   __device__ __forceinline__ bool drop_res(const DropRule &R, int q) const {
     return R.kind == HPAC_PERFO_SMALL ? q == m - 1 : q != 0;
   }

@@ -121,13 +121,16 @@ def test_perforation(H, orc, kind, dt, pk, m, rate, herded, n, T):
 
 
 @pytest.mark.parametrize("dt", [np.float32, np.float64])
-@pytest.mark.parametrize("pk,m,rate", [(0, 4, 0.0), (0, 3, 0.0), (1, 5, 0.0), (4, 0, 0.3), (3, 20, 0.0)])
+@pytest.mark.parametrize("pk,m,rate", [(0, 4, 0.0), (0, 3, 0.0), (1, 5, 0.0), (4, 0, 0.3), (3, 20, 0.0),
+                                      (2, 25, 0.0)])
 @pytest.mark.parametrize("herded", [1, 0])
-@pytest.mark.parametrize("T", [3, 1001, 1000003, 5000000])
+@pytest.mark.parametrize("T", [3, 1001, 1000003, 5000000, 600000])
 def test_perforation_grid_stride_walk(H, orc, dt, pk, m, rate, herded, T):
     """Regions several grid strides long (a thread visits its groups with the
     step and residues carried by additions), logical-thread counts below the
-    vector width, not a multiple of it, below and above the grid stride."""
+    vector width, not a multiple of it, below and above the grid stride, and
+    multiples of it (whole groups kept or dropped: the uniform path, also ini
+    at 25% whose kept range starts on a group boundary)."""
     n = 3_000_017
     x, param = inputs(3, n, dt, d=1)
     tdt = torch.float32 if dt == np.float32 else torch.float64
