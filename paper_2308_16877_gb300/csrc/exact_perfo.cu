@@ -69,6 +69,8 @@ __device__ __forceinline__ void perfo_body(R reg, const typename R::T *__restric
   DropWalk<V> walk;
   walk.init(rule, g0 * V, gstride * V);
   if (UNIFORM) {
+    // (two groups per iteration, as in the accurate map, took 74 registers
+    // here and ran slower: 62.9 against 55.0 us for 2^24 options)
     for (int64_t g = g0; g < groups; g += gstride) {
       const int64_t i0 = g * V;
       const bool dd = walk.uniform(rule, i0);
@@ -176,13 +178,14 @@ __device__ __forceinline__ void perfo_body(R reg, const typename R::T *__restric
 // accurate map's occupancy, made the Black-Scholes stream slower: 59.4 against
 // 57.6 us for 2^24 options at small:4.)
 // The accurate map takes U groups per iteration (two for single-precision
-// regions), so that all their loads are in flight before any of them computes.
+// regions of up to four inputs), so that all their loads are in flight before
+// any of them computes.
 template <class R, int V>
 __global__ void __launch_bounds__(256) map_kernel(R reg, const typename R::T *__restrict__ in,
                                                   int64_t stride, typename R::T *__restrict__ out,
                                                   int64_t n) {
   using T = typename R::T;
-  constexpr int U = sizeof(T) == 4 ? 2 : 1;
+  constexpr int U = sizeof(T) == 4 && R::kReads <= 4 ? 2 : 1;
   const int64_t groups = n / V;
   const int64_t gstride = (int64_t)gridDim.x * blockDim.x;
   int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
