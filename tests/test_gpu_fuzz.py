@@ -93,3 +93,51 @@ def test_random_configuration(H, orc, case):
         assert np.array_equal(np.isnan(g), np.isnan(o)) and np.array_equal(g[~np.isnan(o)], o[~np.isnan(o)])
     else:
         assert np.array_equal(g, o), c
+
+
+@pytest.mark.parametrize("case", range(48))
+def test_random_persistent_sequence(H, orc, case):
+    """Seeded random sequences of 2 to 5 calls on one region with state kept
+    across calls (TAF or iACT on the identity region): a random length (rarely
+    a multiple of T), knobs, level and block size, new inputs every call and a
+    random reset between calls; every call's masks and outputs equal the
+    oracle's persistent call."""
+    rng = np.random.default_rng(5000 + case)
+    tech = ["taf", "iact"][case % 2]
+    dt = [np.float32, np.float64][int(rng.integers(0, 2))]
+    T = int(rng.integers(1, 3000))
+    B = 32 * int(rng.integers(1, 17))
+    level = int(rng.integers(0, 3))
+    thr = float(10.0 ** rng.uniform(-2, 0.3))
+    h, p = int(rng.integers(1, 9)), int(rng.integers(1, 17))
+    ts, g = int(rng.integers(1, 9)), int(rng.choice([1, 4, 16, 32]))
+    calls = int(rng.integers(2, 6))
+    n = int(rng.integers(1, 4 * T + 50))
+    x = W.identity_inputs(n * calls, d=2, dtype=dt, kind="walk", seed=case)
+    tdt = torch.float32 if dt == np.float32 else torch.float64
+    fresh = lambda: orc.taf_state(T, h) if tech == "taf" else orc.iact_state(T, ts, g, 2)
+    st = fresh()
+    sc = W.iact_scale(x, x.shape[1])
+    with H.Region(3, dev_(x[:, :n]), param=0.0, logical_threads=T, block_threads=B) as R:
+        R.set_persistent(True)
+        for c in range(calls):
+            xs = np.ascontiguousarray(x[:, c * n:(c + 1) * n])
+            if c > 0 and rng.random() < 0.25:
+                R.reset_state()
+                st = fresh()
+            out = torch.full((n,), float("nan"), dtype=tdt, device="cuda")
+            mask = torch.full((n,), 255, dtype=torch.uint8, device="cuda")
+            if tech == "taf":
+                R.run_taf(dev_(xs), out, h, p, thr, level, mask=mask)
+                o, m, _, _ = orc.run_taf(3, xs, 0.0, h, p, thr, level=level, threads=T, block=B, state=st)
+            else:
+                R.run_iact(dev_(xs), out, ts, g, thr, level, in_scale=sc, mask=mask)
+                o, m, _, _ = orc.run_iact(3, xs, 0.0, ts, g, thr, level=level, in_scale=sc, threads=T,
+                                          block=B, state=st)
+            torch.cuda.synchronize()
+            assert np.array_equal(mask.cpu().numpy(), m), c
+            assert np.array_equal(out.cpu().numpy(), o), c
+
+
+def dev_(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
