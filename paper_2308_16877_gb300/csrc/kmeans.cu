@@ -1,15 +1,21 @@
 // K-Means centroid update, the exact step between two (approximated)
 // assignments (Table 1, K-Means: iterate until no observation changes
-// cluster). One pass over the observations: each block accumulates the
-// per-cluster feature sums (double) and counts in shared memory, then adds
-// them to the workspace with one atomic per value; a second tiny kernel
-// divides. Changed assignments are counted in the same pass.
+// cluster). One pass over the observations: each warp accumulates the
+// per-cluster feature sums (double) and counts in its own shared-memory copy,
+// each block adds its copies and then the workspace with one atomic per
+// value; a second tiny kernel divides. Changed assignments are counted in the
+// same pass.
 #include "hpac_internal.cuh"
 
 namespace hpac {
 namespace {
 
 constexpr int kThreads = 256;
+
+// Each warp accumulates into its own copy of the per-cluster sums, so the
+// shared-memory double-precision atomics of one instruction collide only among
+// lanes of the same warp and cluster; the copies are then added once per block.
+constexpr int kWarps = kThreads / 32;
 
 __global__ void __launch_bounds__(kThreads) kmeans_sums(const float *__restrict__ x, int64_t stride,
                                                         int64_t n, int K,
@@ -18,30 +24,41 @@ __global__ void __launch_bounds__(kThreads) kmeans_sums(const float *__restrict_
                                                         double *__restrict__ sum,
                                                         unsigned long long *__restrict__ cnt,
                                                         unsigned long long *__restrict__ changed) {
-  __shared__ double s_sum[kMaxClusters * 8];
-  __shared__ unsigned long long s_cnt[kMaxClusters];
-  for (int j = threadIdx.x; j < K * 8; j += blockDim.x) s_sum[j] = 0.0;
-  for (int j = threadIdx.x; j < K; j += blockDim.x) s_cnt[j] = 0;
+  __shared__ double s_sum[kWarps][kMaxClusters * 8];
+  __shared__ unsigned s_cnt[kWarps][kMaxClusters];
+  const int warp = threadIdx.x >> 5;
+  for (int j = threadIdx.x; j < kWarps * K * 8; j += blockDim.x) s_sum[j / (K * 8)][j % (K * 8)] = 0.0;
+  for (int j = threadIdx.x; j < kWarps * K; j += blockDim.x) s_cnt[j / K][j % K] = 0;
   __syncthreads();
+  double *ws = s_sum[warp];
+  unsigned *wc = s_cnt[warp];
   unsigned ch = 0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     const float a = assign[i];
     const int k = (int)a;
     if (k >= 0 && k < K) {  // ids are produced in range; anything else is left out
-      atomicAdd(&s_cnt[k], 1ull);
+      atomicAdd(&wc[k], 1u);
 #pragma unroll
-      for (int d = 0; d < 8; ++d) atomicAdd(&s_sum[k * 8 + d], (double)x[d * stride + i]);
+      for (int d = 0; d < 8; ++d) atomicAdd(&ws[k * 8 + d], (double)x[d * stride + i]);
     }
     if (prev && prev[i] != a) ++ch;
   }
   ch = __reduce_add_sync(0xffffffffu, ch);
   if ((threadIdx.x & 31) == 0 && ch) atomicAdd(changed, (unsigned long long)ch);
   __syncthreads();
-  for (int j = threadIdx.x; j < K * 8; j += blockDim.x)
-    if (s_sum[j] != 0.0) atomicAdd(&sum[j], s_sum[j]);
-  for (int j = threadIdx.x; j < K; j += blockDim.x)
-    if (s_cnt[j]) atomicAdd(&cnt[j], s_cnt[j]);
+  for (int j = threadIdx.x; j < K * 8; j += blockDim.x) {
+    double v = 0.0;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) v += s_sum[w][j];
+    if (v != 0.0) atomicAdd(&sum[j], v);
+  }
+  for (int j = threadIdx.x; j < K; j += blockDim.x) {
+    unsigned long long c = 0;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) c += s_cnt[w][j];
+    if (c) atomicAdd(&cnt[j], c);
+  }
 }
 
 __global__ void kmeans_divide(int K, const double *__restrict__ sum,
