@@ -61,6 +61,51 @@ __global__ void __launch_bounds__(kThreads) kmeans_sums(const float *__restrict_
   }
 }
 
+// For up to 32 clusters: every thread keeps its own column of per-cluster
+// sums and counts in shared memory ([cluster * 8 + d][thread], conflict-free),
+// so the pass needs no atomics; the block then adds its columns (each thread
+// starting at its own column, so the reads spread over the banks) and the
+// workspace gets one atomic per value.
+template <int L>
+__global__ void __launch_bounds__(L) kmeans_sums_private(const float *__restrict__ x, int64_t stride,
+                                                         int64_t n, int K,
+                                                         const float *__restrict__ assign,
+                                                         const float *__restrict__ prev,
+                                                         double *__restrict__ sum,
+                                                         unsigned long long *__restrict__ cnt,
+                                                         unsigned long long *__restrict__ changed) {
+  extern __shared__ __align__(16) double s_acc[];             // [K * 8][L]
+  unsigned *s_n = reinterpret_cast<unsigned *>(s_acc + K * 8 * L);  // [K][L]
+  const int tid = threadIdx.x;
+  for (int j = 0; j < K * 8; ++j) s_acc[j * L + tid] = 0.0;
+  for (int j = 0; j < K; ++j) s_n[j * L + tid] = 0;
+  unsigned ch = 0;
+  for (int64_t i = (int64_t)blockIdx.x * L + tid; i < n; i += (int64_t)gridDim.x * L) {
+    const float a = assign[i];
+    const int k = (int)a;
+    if (k >= 0 && k < K) {  // ids are produced in range; anything else is left out
+      s_n[k * L + tid] += 1;
+      double *col = s_acc + (size_t)k * 8 * L + tid;
+#pragma unroll
+      for (int d = 0; d < 8; ++d) col[d * L] += (double)x[d * stride + i];
+    }
+    if (prev && prev[i] != a) ++ch;
+  }
+  ch = __reduce_add_sync(0xffffffffu, ch);
+  if ((tid & 31) == 0 && ch) atomicAdd(changed, (unsigned long long)ch);
+  __syncthreads();
+  for (int j = tid; j < K * 8; j += L) {
+    double v = 0.0;
+    for (int l = 0; l < L; ++l) v += s_acc[j * L + ((l + tid) & (L - 1))];
+    if (v != 0.0) atomicAdd(&sum[j], v);
+  }
+  for (int j = tid; j < K; j += L) {
+    unsigned long long c = 0;
+    for (int l = 0; l < L; ++l) c += s_n[j * L + ((l + tid) & (L - 1))];
+    if (c) atomicAdd(&cnt[j], c);
+  }
+}
+
 __global__ void kmeans_divide(int K, const double *__restrict__ sum,
                               const unsigned long long *__restrict__ cnt, float *__restrict__ cent) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
@@ -97,11 +142,25 @@ extern "C" hpac_status hpac_kmeans_update(int64_t n, int32_t clusters, const flo
   int dev = 0, sms = 148;
   HPAC_CUDA_TRY(cudaGetDevice(&dev));
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  int64_t blocks = (n + kThreads - 1) / kThreads;
-  const int64_t cap = (int64_t)sms * 4;
-  blocks = blocks < 1 ? 1 : blocks > cap ? cap : blocks;
-  kmeans_sums<<<(unsigned)blocks, kThreads, 0, s>>>(d_x, stride, n, clusters, d_assign, d_prev, sum,
-                                                      cnt, changed);
+  if (clusters <= 32) {
+    // thread-private columns: 64 threads per block up to 16 clusters, 32 up to 32
+    const int L = clusters <= 16 ? 64 : 32;
+    const size_t smem = (size_t)clusters * 8 * L * sizeof(double) + (size_t)clusters * L * sizeof(unsigned);
+    auto fn = L == 64 ? kmeans_sums_private<64> : kmeans_sums_private<32>;
+    HPAC_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 1;
+    HPAC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, L, smem));
+    int64_t blocks = (n + L - 1) / L;
+    const int64_t cap = (int64_t)sms * (per_sm < 1 ? 1 : per_sm);
+    blocks = blocks < 1 ? 1 : blocks > cap ? cap : blocks;
+    fn<<<(unsigned)blocks, L, smem, s>>>(d_x, stride, n, clusters, d_assign, d_prev, sum, cnt, changed);
+  } else {
+    int64_t blocks = (n + kThreads - 1) / kThreads;
+    const int64_t cap = (int64_t)sms * 4;
+    blocks = blocks < 1 ? 1 : blocks > cap ? cap : blocks;
+    kmeans_sums<<<(unsigned)blocks, kThreads, 0, s>>>(d_x, stride, n, clusters, d_assign, d_prev, sum,
+                                                        cnt, changed);
+  }
   HPAC_CUDA_TRY(cudaGetLastError());
   kmeans_divide<<<(clusters * 8 + 255) / 256, 256, 0, s>>>(clusters, sum, cnt, d_cent);
   HPAC_CUDA_TRY(cudaGetLastError());

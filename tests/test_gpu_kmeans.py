@@ -108,11 +108,15 @@ def test_perforation_keeps_previous_ids(H, orc):
     assert np.array_equal(host(mask), m) and np.array_equal(host(out), o)
 
 
-def test_update_and_changed_count(H, orc):
-    n, K = 100000, 12
+@pytest.mark.parametrize("K", [12, 24, 48, 64])
+def test_update_and_changed_count(H, orc, K):
+    """Centroid sums with thread-private columns (K <= 16: 64 threads per
+    block, K <= 32: 32) and with per-warp shared atomics (K > 32); cluster
+    K - 1 left empty keeps its centroid."""
+    n = 100000
     x, labels, init = W.kmeans_blobs(n, K, seed=12)
     a = labels.astype(np.float32)
-    a[a == 11] = 0                                   # cluster 11 empty
+    a[a == K - 1] = 0                                # cluster K - 1 empty
     prev = np.roll(a, 1)
     cent = dev(init)
     work = H.kmeans_workspace(K)
@@ -121,7 +125,7 @@ def test_update_and_changed_count(H, orc):
     assert ch == wch
     g = host(cent)
     assert np.all(np.abs(g - want) <= np.abs(want) * 2 ** -23 + 1e-7)
-    assert np.array_equal(g[11], init[11])
+    assert np.array_equal(g[K - 1], init[K - 1])
 
 
 def test_whole_run_matches_the_oracle(H, orc):
