@@ -74,3 +74,27 @@ def test_enum_values_match_header():
                  "HPAC_REGION_IDENTITY", "HPAC_REGION_BINOMIAL", "HPAC_PERFO_RANDOM", "HPAC_MASK_SKIPPED", "HPAC_METRIC_MCR"):
         m = re.search(rf"\b{name}\s*=\s*(\d+)", src)
         assert m and int(m.group(1)) == getattr(hpac, name), name
+
+
+def test_invalid_arguments_are_rejected_before_any_device_work():
+    """NULL handles and out-of-range arguments return HPAC_EINVAL with a
+    message, without a device (every check precedes the first CUDA call)."""
+    from paper_2308_16877_gb300 import hpac
+    L = hpac.load()
+    EINVAL = hpac.HPAC_EINVAL
+    calls = [
+        ("hpac_run_exact", (None, None, None)),
+        ("hpac_region_adjoint", (None, None, None)),
+        ("hpac_region_vjp", (None, None, None, None)),
+        ("hpac_mlp_vjp", (None, 10, None, 10, 0.0, None, None, None)),
+        ("hpac_mlp_set_params_device", (None, None)),
+        ("hpac_mlp_input_grad", (None, 10, None, 10, 0.0, None)),
+        ("hpac_kmeans_update", (10, 0, None, 10, None, None, None, None, None, None)),
+        ("hpac_hydro_step", (None, None, 0, None, None, None)),
+    ]
+    for name, args in calls:
+        status = getattr(L, name)(*args)
+        assert status == EINVAL, (name, status)
+        assert hpac.hpac_last_error(), name
+    # destroying NULL is a no-op, as free(NULL)
+    assert L.hpac_region_destroy(None) == hpac.HPAC_OK
