@@ -2,10 +2,29 @@
 3.1.4; read/write phases, farthest-lane writer and round-robin replacement,
 Section 3.3) against closed forms, a nearest-neighbour brute force and an
 independent small-case simulation written in Python (no GPU)."""
+import os
+
 import numpy as np
 import pytest
 
 from paper_2308_16877_gb300 import workloads as W
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def test_worked_example_two_entry_table(orc):
+    """tests/golden/iact_worked_t2.txt, worked by hand: reuse below the
+    threshold, exact computation and a round-robin write otherwise."""
+    rows = [l.split() for l in open(os.path.join(GOLD, "iact_worked_t2.txt"))
+            if l.strip() and not l.startswith("#")]
+    x = np.array([[float(r[0]) for r in rows]], dtype=np.float32)
+    out, mask, stat, cnt = orc.run_iact(orc.IDENTITY, x, 0.0, 2, 32, 0.1, in_scale=[1.0], threads=1,
+                                        block=32)
+    assert np.array_equal(out, np.array([float(r[1]) for r in rows], dtype=np.float32))
+    assert np.array_equal(mask, np.array([int(r[2]) for r in rows], dtype=np.uint8))
+    want = np.array([float(r[3]) for r in rows])
+    assert np.isinf(stat[0]) and np.allclose(stat[1:], want[1:], rtol=0, atol=2e-6)
+    assert cnt[1] == 4
 
 
 @pytest.mark.parametrize("kind", [0, 1, 3])
