@@ -351,6 +351,24 @@ def test_taf_iact_physical_block_sizes(H, orc, dt, level, T):
             assert cnt[1] > 0
 
 
+def test_taf_worked_example(H):
+    """The hand-worked TAF example of tests/golden (h = p = 2) on the GPU, on
+    the statistic path and on the fast decision path."""
+    import os
+    rows = [l.split() for l in open(os.path.join(os.path.dirname(__file__), "golden", "taf_worked_h2p2.txt"))
+            if l.strip() and not l.startswith("#")]
+    x = np.array([[float(r[0]) for r in rows]], dtype=np.float32)
+    n = x.shape[1]
+    xd = dev(x)
+    for stats in (True, False):
+        out = torch.full((n,), float("nan"), device="cuda")
+        mask = torch.full((n,), 255, dtype=torch.uint8, device="cuda")
+        with H.Region(3, xd, logical_threads=1, block_threads=32) as R:
+            R.run_taf(xd, out, 2, 2, 0.1, 0, mask=mask, stats=stats)
+        assert np.array_equal(host(out), np.array([float(r[1]) for r in rows], dtype=np.float32))
+        assert np.array_equal(host(mask), np.array([int(r[2]) for r in rows], dtype=np.uint8))
+
+
 def test_iact_worked_example(H):
     """The hand-worked two-entry iACT example of tests/golden on the GPU."""
     import os
