@@ -351,6 +351,27 @@ def test_taf_iact_physical_block_sizes(H, orc, dt, level, T):
             assert cnt[1] > 0
 
 
+def test_perforation_worked_masks(H):
+    """The hand-worked perforation masks of tests/golden on the GPU (scalar and
+    vector paths: the float input is 16-byte aligned, T = 4)."""
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "perfo_worked.txt")
+    xd = dev(np.arange(12, dtype=np.float32)[None, :])
+    for line in open(path):
+        if not line.strip() or line.startswith("#"):
+            continue
+        kind, m, herded, want = line.split()
+        out = torch.full((12,), float("nan"), device="cuda")
+        mask = torch.full((12,), 255, dtype=torch.uint8, device="cuda")
+        with H.Region(3, xd, logical_threads=4) as R:
+            st = R.run_perfo(xd, out, int(kind), int(m), 0.0, 0, bool(int(herded)), mask=mask, stats=True)
+        assert "".join(str(v) for v in host(mask)) == want, line
+        assert st["skipped"] == want.count("2")
+        o = host(out)
+        keep = np.array([c == "0" for c in want])
+        assert np.array_equal(o[keep], np.arange(12, dtype=np.float32)[keep]) and np.all(np.isnan(o[~keep]))
+
+
 def test_taf_worked_example(H):
     """The hand-worked TAF example of tests/golden (h = p = 2) on the GPU, on
     the statistic path and on the fast decision path."""

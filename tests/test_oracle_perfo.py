@@ -113,3 +113,18 @@ def test_rejects_bad_knobs(orc):
     for args in ((0, 0, 0.0), (1, 0, 0.0), (2, 101, 0.0), (3, -1, 0.0), (4, 0, 1.5), (7, 1, 0.0)):
         with pytest.raises(ValueError):
             orc.run_perfo(orc.IDENTITY, x, 0.0, args[0], args[1], rate=args[2])
+
+
+def test_worked_masks(orc):
+    """tests/golden/perfo_worked.txt: the masks of each pattern worked by hand."""
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "perfo_worked.txt")
+    x = np.arange(12, dtype=np.float32)[None, :]
+    for line in open(path):
+        if not line.strip() or line.startswith("#"):
+            continue
+        kind, m, herded, want = line.split()
+        _, mask, cnt = orc.run_perfo(orc.IDENTITY, x, 0.0, int(kind), int(m), 0.0, 0, int(herded), threads=4,
+                                     out=np.zeros(12, dtype=np.float32))
+        assert "".join(str(v) for v in mask) == want, line
+        assert cnt[2] == want.count("2")
