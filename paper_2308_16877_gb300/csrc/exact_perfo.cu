@@ -9,7 +9,9 @@
 //
 // Memory: structure-of-arrays inputs are read with 16-byte vector loads
 // (4 floats / 2 doubles per input row per thread), outputs written with
-// 16-byte vector stores; grids are a multiple of the SM count and grid-stride.
+// 16-byte vector stores; grid-stride loops over a grid of at most 2048 threads
+// per SM, in blocks small enough that every SM gets about eight
+// (balanced_block).
 #include <stdio.h>
 
 #include "hpac_internal.cuh"

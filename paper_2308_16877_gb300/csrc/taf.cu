@@ -2,9 +2,10 @@
 // (Section 3.1.3, Figure 3(d); runtime Section 3.3; majority rules Section 3.3).
 //
 // One physical thread per logical thread t, walking its grid-stride sequence
-// i = t + k*T. Its window of the last hsize accurate outputs lives in shared
-// memory (Section 3.1.1), column-major so that the lanes of a warp touch
-// consecutive words: win[slot * blockDim.x + threadIdx.x]. A predicting
+// i = t + k*T. Its window of the last hsize accurate outputs lives in
+// registers for hsize 2, 4 and 8, otherwise in shared memory (Section 3.1.1),
+// column-major so that the lanes of a warp touch consecutive words:
+// win[slot * blockDim.x + threadIdx.x]. A predicting
 // thread stores the newest window value and issues no input load, so
 // prediction removes the region's input bytes and arithmetic. At warp level the
 // decision is a ballot + popcount over the lanes that computed this step; at
