@@ -1,5 +1,7 @@
 // Adjoint (input derivatives) of the exact regions: the derivative targets of
-// the learned surrogate. One thread per invocation, grid-stride.
+// the learned surrogate, and, scaled by an upstream gradient, the backward
+// pass of a differentiable region call (vector-Jacobian product). One thread
+// per invocation, grid-stride.
 #include <math.h>
 
 #include "hpac_internal.cuh"
