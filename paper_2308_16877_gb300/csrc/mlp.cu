@@ -18,7 +18,10 @@
 // 16 output rows of dW2 / dW1, accumulated in registers across the whole
 // persistent loop with transposed ldmatrix loads feeding mma.sync. Bias and
 // layer-3 gradients go through shared-memory atomics; everything reaches the
-// global gradient with one atomic add per value per block.
+// global gradient with one atomic add per value per block. The same pass with a
+// caller's per-sample d(loss)/d(output) in place of the squared error's gives
+// the parameter half of a vector-Jacobian product; the input half scales the
+// input-derivative pass by it.
 #include <cuda_bf16.h>
 #include <math.h>
 #include <stdlib.h>
