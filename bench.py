@@ -60,8 +60,14 @@ IACT_SCALE = (1.0 / W.HYDRO_E0, 1.0, 10.0, 1.0 / ((GAMMA - 1.0) * W.HYDRO_E0))
 # their 42 scatters less 7 first assignments (105 adds), 3 single-use pairs as
 # fused multiply-adds (18), 21 relative-position subtractions, 18 corner-0
 # sums, 8 for the volume, 1 for dv; the division V / V0 counts as one. Its
-# ceiling is the measured FMA rate in the same unit (FMA per second).
+# ceiling, in the same unit (FP64 instructions per lane per second), is the
+# FP64 issue rate of the part: the nominal 1.25 TFLOP/s of GB300 at 152 SMs and
+# 2070 MHz is 1.25e12 / (2 x 152 x 2.07e9) = 1.99, i.e. 2 FP64 FMA per SM per
+# clock, taken at the SM count of the device and the median SM clock sampled
+# under load. The FMA rate that the library's probe measures in the same run is
+# reported beside it.
 ELEM_OPS = 90 + 105 + 18 + 21 + 18 + 8 + 1 + 1
+FP64_FMA_PER_SM_CLK = 2
 
 BS_N = 1 << 24
 BS_TAF = dict(hsize=4, psize=8, thresh=0.005, level=0)
@@ -1089,12 +1095,20 @@ def main(argv=None):
     del ref_mid
 
     fp64_tflops = hpac.hpac_device_fp64_rate(sh)
-    peak = fp64_tflops / 2.0                      # FMA instructions per second, 1e12
+    measured = fp64_tflops / 2.0                  # FMA instructions per second, 1e12
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    clk_now = clk.summary()
+    mhz = clk_now["sm_mhz"] or clk_now["sm_max_mhz"] or 2070.0
+    peak = FP64_FMA_PER_SM_CLK * sms * mhz * 1e6 / 1e12
     achieved = ELEM_OPS * E / (elem_ms * 1e-3) / 1e12
     roofline = {"bound": "alu", "kernel": "elem_kernel (FP64 volume gradient)", "achieved": achieved,
                 "peak": peak, "unit": "T FP64-ops/s", "frac": achieved / peak,
-                "peak_source": "measured FP64 FMA rate of this GPU in the same run "
-                               f"(hpac_device_fp64_rate: {fp64_tflops:.3f} TFLOP/s = {peak:.3f} T FMA/s)",
+                "peak_source": f"derived: {FP64_FMA_PER_SM_CLK} FP64 FMA per SM per clock (the nominal "
+                               f"1.25 TFLOP/s at 152 SMs x 2070 MHz) x {sms} SMs x {mhz:.0f} MHz "
+                               "(median SM clock sampled under load)",
+                "measured_peak": measured, "frac_of_measured": achieved / measured,
+                "measured_peak_source": "FP64 FMA rate of this GPU measured in the same run "
+                                        f"(hpac_device_fp64_rate: {fp64_tflops:.3f} TFLOP/s)",
                 "ops_per_element": ELEM_OPS,
                 "traffic": dram_traffic("elem_kernel", E), "launch_ms": elem_ms}
 
