@@ -311,19 +311,29 @@ typedef struct {
   double *V0;                /* element reference volumes (= masses, density 1)    */
   double *grad;              /* 24 n^3 scratch: 12 dV/dx per corner (x, y, z rows) */
   double *eos_in;            /* 4 n^3: the EOS region's inputs of the last step    */
+  double *pq;                /* n^3: p + q of the last step (init, finalize)        */
+  double *rmass;             /* (n+1)^3: 1 / (12 m) per node (init)                */
 } hpac_hydro_state;
 
 /* From x, y, z and e (initial state): V0, node masses, p = (gamma-1) e,
- * q = 0, v = 1, zero velocities and the volume gradients. Enqueued on
- * cuda_stream. Errors: HPAC_EINVAL (state), HPAC_ECUDA. */
+ * q = 0, v = 1, zero velocities, the volume gradients and the derived arrays
+ * pq and rmass. Enqueued on cuda_stream. Errors: HPAC_EINVAL (state),
+ * HPAC_ECUDA. */
 hpac_status hpac_hydro_init(const hpac_hydro_state *s, void *cuda_stream);
+
+/* Recompute the derived arrays from the state (pq = p + q, rmass = 1 / (12
+ * mnode)): for a caller that has overwritten p, q or mnode, e.g. restored a
+ * checkpoint of the other arrays. Enqueued on cuda_stream. Errors as
+ * hpac_hydro_init. */
+hpac_status hpac_hydro_derive(const hpac_hydro_state *s, void *cuda_stream);
 
 /* The three non-region phases of a time step, each one kernel on cuda_stream,
  * for callers that run the EOS region themselves between them:
- * nodes (forces from p + q and the stored gradients, velocity, position,
- * symmetry planes), elements (volume and gradient at the new positions,
- * viscosity, the EOS inputs in eos_in), finalize (e = p v_{n+1} / (gamma - 1),
- * v = v_{n+1}). hpac_hydro_step is nodes, elements, the region, finalize. */
+ * nodes (forces from pq = p + q and the stored gradients, velocity,
+ * position, symmetry planes), elements (volume and gradient at the new
+ * positions, viscosity, the EOS inputs in eos_in), finalize (e = p v_{n+1} /
+ * (gamma - 1), v = v_{n+1}, pq = p + q). hpac_hydro_step is nodes, elements,
+ * the region, finalize. */
 hpac_status hpac_hydro_nodes(const hpac_hydro_state *s, void *cuda_stream);
 hpac_status hpac_hydro_elements(const hpac_hydro_state *s, void *cuda_stream);
 hpac_status hpac_hydro_finalize(const hpac_hydro_state *s, void *cuda_stream);

@@ -4,13 +4,14 @@
 // the same one the CPU oracle restates).
 //
 // Per time step, on the EOS region's stream:
-//   node kernel     forces from the stored volume gradients, velocity and
-//                   position update, symmetry planes x = 0, y = 0, z = 0;
+//   node kernel     forces from the stored volume gradients and the stored
+//                   p + q, velocity and position update (1 / (12 m) stored at
+//                   init), symmetry planes x = 0, y = 0, z = 0;
 //   element kernel  exact trilinear-hexahedron volume and its gradient at the
 //                   new positions, relative volume, artificial viscosity, the
 //                   EOS inputs (e, v_{n+1}, dv, q_{n+1});
 //   EOS region      exact, TAF, iACT or perforation through the region API;
-//   finalize        e = p v / (gamma - 1), v = v_{n+1}.
+//   finalize        e = p v / (gamma - 1), v = v_{n+1}, pq = p + q.
 //
 // Volume of a trilinear hexahedron. With corners P_c in lexicographic order
 // (c = a + 2b + 4d for offsets a, b, d), the integral of det J over the
@@ -170,6 +171,7 @@ __global__ void __launch_bounds__(128) init_elem_kernel(hpac_hydro_state s) {
     s.vrel[e] = 1.0;
     s.p[e] = gm1 * s.e[e];
     s.q[e] = 0.0;
+    s.pq[e] = s.p[e];
   }
 }
 
@@ -187,6 +189,7 @@ __global__ void __launch_bounds__(256) init_node_kernel(hpac_hydro_state s) {
           m += 0.125 * s.V0[(ek * n + ej) * n + ei];
         }
     s.mnode[nd] = m;
+    s.rmass[nd] = 1.0 / (12.0 * m);
     s.u[nd] = s.v[nd] = s.w[nd] = 0.0;
   }
 }
@@ -210,13 +213,15 @@ __global__ void __launch_bounds__(256) node_kernel(hpac_hydro_state s) {
           if (ei < 0 || ej < 0 || ek < 0 || ei >= n || ej >= n || ek >= n) continue;
           const int64_t el = (ek * n + ej) * n + ei;
           const int c = di + 2 * dj + 4 * dk;  // corner of this node in element el
-          const double pq = s.p[el] + s.q[el];
+          const double pq = s.pq[el];
           fx = fma(pq, s.grad[(0 * 8 + c) * E + el], fx);
           fy = fma(pq, s.grad[(1 * 8 + c) * E + el], fy);
           fz = fma(pq, s.grad[(2 * 8 + c) * E + el], fz);
         }
-    // the stored gradients are 12 dV/dx: the 1/12 joins dt / m in one factor
-    const double sc = dt * (1.0 / 12.0) / s.mnode[nd];
+    // the stored gradients are 12 dV/dx: rmass = 1 / (12 m), formed once at
+    // init (a double division per node and step would cost a fifth of the
+    // kernel's FP64 work)
+    const double sc = dt * s.rmass[nd];
     double un = fma(fx, sc, s.u[nd]);
     double vn = fma(fy, sc, s.v[nd]);
     double wn = fma(fz, sc, s.w[nd]);
@@ -276,6 +281,18 @@ __global__ void __launch_bounds__(256) finalize_kernel(hpac_hydro_state s, doubl
     const double v1 = s.eos_in[E + e];
     s.e[e] = s.p[e] * v1 * inv_gm1;
     s.vrel[e] = v1;
+    s.pq[e] = s.p[e] + s.q[e];  // the next step's nodal forces use p + q
+  }
+}
+
+// The derived arrays from the state: pq = p + q per element, rmass = 1 / (12 m)
+// per node.
+__global__ void __launch_bounds__(256) derive_kernel(hpac_hydro_state s) {
+  const int64_t E = (int64_t)s.n * s.n * s.n, n1 = s.n + 1, Nn = n1 * n1 * n1;
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < (E > Nn ? E : Nn);
+       j += (int64_t)gridDim.x * blockDim.x) {
+    if (j < E) s.pq[j] = s.p[j] + s.q[j];
+    if (j < Nn) s.rmass[j] = 1.0 / (12.0 * s.mnode[j]);
   }
 }
 
@@ -294,7 +311,7 @@ hpac_status check_state(const hpac_hydro_state *s) {
   if (!(s->dt > 0.0) || !isfinite(s->dt)) return set_error(HPAC_EINVAL, "hydro dt must be > 0");
   if (!(s->gamma > 1.0) || !isfinite(s->gamma)) return set_error(HPAC_EINVAL, "gamma must be > 1");
   const void *ptrs[] = {s->x, s->y, s->z, s->u, s->v, s->w, s->mnode, s->e, s->p, s->q, s->vrel,
-                        s->V0, s->grad, s->eos_in};
+                        s->V0, s->grad, s->eos_in, s->pq, s->rmass};
   for (const void *p : ptrs)
     if (!p) return set_error(HPAC_EINVAL, "a hydro state array is NULL");
   return HPAC_OK;
@@ -316,6 +333,18 @@ extern "C" hpac_status hpac_hydro_init(const hpac_hydro_state *s, void *cuda_str
   init_elem_kernel<<<grid_for(E, 128, dev), 128, 0, stream>>>(*s);
   HPAC_CUDA_TRY(cudaGetLastError());
   init_node_kernel<<<grid_for(Nn, 256, dev), 256, 0, stream>>>(*s);
+  HPAC_CUDA_TRY(cudaGetLastError());
+  return HPAC_OK;
+}
+
+extern "C" hpac_status hpac_hydro_derive(const hpac_hydro_state *s, void *cuda_stream) {
+  TraceRange trace_("hpac_hydro_derive");
+  hpac_status st = check_state(s);
+  if (st != HPAC_OK) return st;
+  int dev = 0;
+  HPAC_CUDA_TRY(cudaGetDevice(&dev));
+  const int64_t Nn = (int64_t)(s->n + 1) * (s->n + 1) * (s->n + 1);
+  derive_kernel<<<grid_for(Nn, 256, dev), 256, 0, (cudaStream_t)cuda_stream>>>(*s);
   HPAC_CUDA_TRY(cudaGetLastError());
   return HPAC_OK;
 }

@@ -67,7 +67,7 @@ class hpac_hydro_state(C.Structure):
     _fields_ = [("n", C.c_int32), ("reserved0", C.c_int32), ("gamma", C.c_double),
                 ("dt", C.c_double), ("x", _D), ("y", _D), ("z", _D), ("u", _D), ("v", _D),
                 ("w", _D), ("mnode", _D), ("e", _D), ("p", _D), ("q", _D), ("vrel", _D),
-                ("V0", _D), ("grad", _D), ("eos_in", _D)]
+                ("V0", _D), ("grad", _D), ("eos_in", _D), ("pq", _D), ("rmass", _D)]
 
 
 class hpac_sweep_config(C.Structure):
@@ -113,6 +113,7 @@ SIGNATURES = {
     "hpac_kmeans_update": (C.c_int, [C.c_int64, C.c_int32, _P, C.c_int64, _P, _P, _P, _P,
                                      C.POINTER(C.c_int64), _P]),
     "hpac_hydro_init": (C.c_int, [C.POINTER(hpac_hydro_state), _P]),
+    "hpac_hydro_derive": (C.c_int, [C.POINTER(hpac_hydro_state), _P]),
     "hpac_hydro_step": (C.c_int, [C.POINTER(hpac_hydro_state), _P, C.c_int32, _P, _P,
                                   C.POINTER(hpac_stats)]),
     "hpac_hydro_nodes": (C.c_int, [C.POINTER(hpac_hydro_state), _P]),
@@ -259,6 +260,10 @@ def hpac_quality_noalloc(dtype, n, d_exact, d_approx, metric, stream=None):
 
 def hpac_hydro_init(state, stream=None):
     _check(load().hpac_hydro_init(C.byref(state), stream or None), "hpac_hydro_init")
+
+
+def hpac_hydro_derive(state, stream=None):
+    _check(load().hpac_hydro_derive(C.byref(state), stream or None), "hpac_hydro_derive")
 
 
 def hpac_hydro_step(state, eos, technique, knobs=None, d_mask=None, want_stats=False):
@@ -474,15 +479,19 @@ class Hydro:
             self.t[k] = torch.zeros(E, **f64)
         self.t["grad"] = torch.zeros(24 * E, **f64)
         self.t["eos_in"] = torch.zeros(4, E, **f64)
+        self.t["pq"] = torch.zeros(E, **f64)
+        self.t["rmass"] = torch.zeros(Nn, **f64)
         self.state = self._state()
         self.eos = Region(HPAC_REGION_EOS, self.t["eos_in"], param=self.gamma,
                           logical_threads=logical_threads, block_threads=block_threads, stream=stream)
+        self._stream = stream
         hpac_hydro_init(self.state, _stream_handle(stream))
 
     def _state(self):
         ptr = lambda k: C.cast(C.c_void_p(self.t[k].data_ptr()), _D)
         return hpac_hydro_state(self.n, 0, self.gamma, self.dt, *[ptr(k) for k in (
-            "x", "y", "z", "u", "v", "w", "mnode", "e", "p", "q", "vrel", "V0", "grad", "eos_in")])
+            "x", "y", "z", "u", "v", "w", "mnode", "e", "p", "q", "vrel", "V0", "grad", "eos_in", "pq",
+            "rmass")])
 
     def __getitem__(self, k):
         return self.t[k]
@@ -490,10 +499,13 @@ class Hydro:
     def load_state(self, fields):
         """Overwrite node/element fields (a checkpoint) from host or device arrays;
         the volume gradients are recomputed by the next step's element kernel only,
-        so the gradient field must be supplied too (key 'grad') or left as is."""
+        so the gradient field must be supplied too (key 'grad') or left as is. The
+        derived arrays (pq, rmass) are recomputed from the loaded state."""
         import torch
         for k, v in fields.items():
             self.t[k].copy_(torch.as_tensor(v, dtype=torch.float64).reshape(self.t[k].shape))
+        torch.cuda.current_stream().synchronize()   # the copies land before the derive kernel
+        hpac_hydro_derive(self.state, _stream_handle(self._stream))
 
     def step(self, technique=HYDRO_EXACT, knobs=None, mask=None, stats=False):
         st = hpac_hydro_step(self.state, self.eos._h, technique, knobs, _ptr(mask), stats)
