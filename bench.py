@@ -59,14 +59,15 @@ IACT_SCALE = (1.0 / W.HYDRO_E0, 1.0, 10.0, 1.0 / ((GAMMA - 1.0) * W.HYDRO_E0))
 # one issue slot of the FP64 pipe: 15 shared corner-pair cross products (90),
 # their 42 scatters less 7 first assignments (105 adds), 3 single-use pairs as
 # fused multiply-adds (18), 21 relative-position subtractions, 18 corner-0
-# sums, 8 for the volume, 1 for dv; the division V / V0 counts as one. Its
+# sums, 8 for the volume, 1 for dv, and 2 for v = V / V0 formed as a comparison
+# with V0 and a product with the stored 1 / V0. Its
 # ceiling, in the same unit (FP64 instructions per lane per second), is the
 # FP64 issue rate of the part: the nominal 1.25 TFLOP/s of GB300 at 152 SMs and
 # 2070 MHz is 1.25e12 / (2 x 152 x 2.07e9) = 1.99, i.e. 2 FP64 FMA per SM per
 # clock, taken at the SM count of the device and the median SM clock sampled
 # under load. The FMA rate that the library's probe measures in the same run is
 # reported beside it.
-ELEM_OPS = 90 + 105 + 18 + 21 + 18 + 8 + 1 + 1
+ELEM_OPS = 90 + 105 + 18 + 21 + 18 + 8 + 1 + 2
 FP64_FMA_PER_SM_CLK = 2
 
 BS_N = 1 << 24

@@ -313,18 +313,20 @@ typedef struct {
   double *eos_in;            /* 4 n^3: the EOS region's inputs of the last step    */
   double *pq;                /* n^3: p + q of the last step (init, finalize)        */
   double *rmass;             /* (n+1)^3: 1 / (12 m) per node (init)                */
+  double *rV0;               /* n^3: 1 / V0 per element (init)                      */
 } hpac_hydro_state;
 
 /* From x, y, z and e (initial state): V0, node masses, p = (gamma-1) e,
  * q = 0, v = 1, zero velocities, the volume gradients and the derived arrays
- * pq and rmass. Enqueued on cuda_stream. Errors: HPAC_EINVAL (state),
- * HPAC_ECUDA. */
+ * pq, rmass and rV0. Relative volumes are formed as 1 where V = V0 and as
+ * V rV0 otherwise (within a rounding of V / V0). Enqueued on cuda_stream.
+ * Errors: HPAC_EINVAL (state), HPAC_ECUDA. */
 hpac_status hpac_hydro_init(const hpac_hydro_state *s, void *cuda_stream);
 
 /* Recompute the derived arrays from the state (pq = p + q, rmass = 1 / (12
- * mnode)): for a caller that has overwritten p, q or mnode, e.g. restored a
- * checkpoint of the other arrays. Enqueued on cuda_stream. Errors as
- * hpac_hydro_init. */
+ * mnode), rV0 = 1 / V0): for a caller that has overwritten p, q, mnode or V0,
+ * e.g. restored a checkpoint of the other arrays. Enqueued on cuda_stream.
+ * Errors as hpac_hydro_init. */
 hpac_status hpac_hydro_derive(const hpac_hydro_state *s, void *cuda_stream);
 
 /* The three non-region phases of a time step, each one kernel on cuda_stream,

@@ -168,6 +168,7 @@ __global__ void __launch_bounds__(128) init_elem_kernel(hpac_hydro_state s) {
       s.grad[(2 * 8 + c) * E + e] = gz[c];
     }
     s.V0[e] = V;
+    s.rV0[e] = 1.0 / V;
     s.vrel[e] = 1.0;
     s.p[e] = gm1 * s.e[e];
     s.q[e] = 0.0;
@@ -253,7 +254,11 @@ __global__ void __launch_bounds__(96) elem_kernel(hpac_hydro_state s) {
       s.grad[(1 * 8 + c) * E + e] = gy[c];
       s.grad[(2 * 8 + c) * E + e] = gz[c];
     }
-    const double v1 = V / s.V0[e];
+    // v1 = V / V0 without a division per element and step: exactly 1 for an
+    // element at its reference volume (so an unmoved element keeps dv = 0),
+    // else V times the stored 1 / V0 (within a rounding of the quotient)
+    const double V0e = s.V0[e];
+    const double v1 = V == V0e ? 1.0 : V * s.rV0[e];
     const double dv = v1 - s.vrel[e];
     double qn = 0.0;
     if (dv < 0.0) {
@@ -285,13 +290,16 @@ __global__ void __launch_bounds__(256) finalize_kernel(hpac_hydro_state s, doubl
   }
 }
 
-// The derived arrays from the state: pq = p + q per element, rmass = 1 / (12 m)
-// per node.
+// The derived arrays from the state: pq = p + q and rV0 = 1 / V0 per element,
+// rmass = 1 / (12 m) per node.
 __global__ void __launch_bounds__(256) derive_kernel(hpac_hydro_state s) {
   const int64_t E = (int64_t)s.n * s.n * s.n, n1 = s.n + 1, Nn = n1 * n1 * n1;
   for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < (E > Nn ? E : Nn);
        j += (int64_t)gridDim.x * blockDim.x) {
-    if (j < E) s.pq[j] = s.p[j] + s.q[j];
+    if (j < E) {
+      s.pq[j] = s.p[j] + s.q[j];
+      s.rV0[j] = 1.0 / s.V0[j];
+    }
     if (j < Nn) s.rmass[j] = 1.0 / (12.0 * s.mnode[j]);
   }
 }
@@ -311,7 +319,7 @@ hpac_status check_state(const hpac_hydro_state *s) {
   if (!(s->dt > 0.0) || !isfinite(s->dt)) return set_error(HPAC_EINVAL, "hydro dt must be > 0");
   if (!(s->gamma > 1.0) || !isfinite(s->gamma)) return set_error(HPAC_EINVAL, "gamma must be > 1");
   const void *ptrs[] = {s->x, s->y, s->z, s->u, s->v, s->w, s->mnode, s->e, s->p, s->q, s->vrel,
-                        s->V0, s->grad, s->eos_in, s->pq, s->rmass};
+                        s->V0, s->grad, s->eos_in, s->pq, s->rmass, s->rV0};
   for (const void *p : ptrs)
     if (!p) return set_error(HPAC_EINVAL, "a hydro state array is NULL");
   return HPAC_OK;

@@ -67,7 +67,7 @@ class hpac_hydro_state(C.Structure):
     _fields_ = [("n", C.c_int32), ("reserved0", C.c_int32), ("gamma", C.c_double),
                 ("dt", C.c_double), ("x", _D), ("y", _D), ("z", _D), ("u", _D), ("v", _D),
                 ("w", _D), ("mnode", _D), ("e", _D), ("p", _D), ("q", _D), ("vrel", _D),
-                ("V0", _D), ("grad", _D), ("eos_in", _D), ("pq", _D), ("rmass", _D)]
+                ("V0", _D), ("grad", _D), ("eos_in", _D), ("pq", _D), ("rmass", _D), ("rV0", _D)]
 
 
 class hpac_sweep_config(C.Structure):
@@ -481,6 +481,7 @@ class Hydro:
         self.t["eos_in"] = torch.zeros(4, E, **f64)
         self.t["pq"] = torch.zeros(E, **f64)
         self.t["rmass"] = torch.zeros(Nn, **f64)
+        self.t["rV0"] = torch.zeros(E, **f64)
         self.state = self._state()
         self.eos = Region(HPAC_REGION_EOS, self.t["eos_in"], param=self.gamma,
                           logical_threads=logical_threads, block_threads=block_threads, stream=stream)
@@ -491,7 +492,7 @@ class Hydro:
         ptr = lambda k: C.cast(C.c_void_p(self.t[k].data_ptr()), _D)
         return hpac_hydro_state(self.n, 0, self.gamma, self.dt, *[ptr(k) for k in (
             "x", "y", "z", "u", "v", "w", "mnode", "e", "p", "q", "vrel", "V0", "grad", "eos_in", "pq",
-            "rmass")])
+            "rmass", "rV0")])
 
     def __getitem__(self, k):
         return self.t[k]
@@ -500,7 +501,7 @@ class Hydro:
         """Overwrite node/element fields (a checkpoint) from host or device arrays;
         the volume gradients are recomputed by the next step's element kernel only,
         so the gradient field must be supplied too (key 'grad') or left as is. The
-        derived arrays (pq, rmass) are recomputed from the loaded state."""
+        derived arrays (pq, rmass, rV0) are recomputed from the loaded state."""
         import torch
         for k, v in fields.items():
             self.t[k].copy_(torch.as_tensor(v, dtype=torch.float64).reshape(self.t[k].shape))
