@@ -362,3 +362,71 @@ def test_differentiable_surrogate(H, kind, hidden):
     out2 = S.apply(xd.detach(), w2, param)
     assert not torch.equal(out2, out.detach())
     S.close()
+
+
+def test_surrogate_gains_over_taf_and_iact_at_one_percent(H):
+    """What the trained network adds to the method: on the same Black-Scholes
+    options, at the same quality bar (NRMSE <= 1% against the FP64 exact
+    prices), the surrogate with its calibrated exact fallback replaces far more
+    invocations than the best TAF or iACT configuration of a small knob sweep
+    (independent random options give TAF windows no temporal stability and
+    iACT tables no nearby inputs). Trained by the library's kernels on 4M
+    exact pairs, calibrated on 1M held-out options, scored on another 1M."""
+    dev = "cuda"
+
+    def exact(x, dtype, T=0):
+        out = torch.zeros(x.shape[1], dtype=dtype, device=dev)
+        xx = x if dtype == torch.float32 else x.double().contiguous()
+        with H.Region(H.HPAC_REGION_BLACKSCHOLES, xx, param=W.BS_RATE, logical_threads=T) as R:
+            R.run_exact(xx, out)
+        return out
+
+    xt = torch.from_numpy(W.blackscholes_inputs(1 << 22, seed=31)).to(dev)
+    yt = exact(xt, torch.float32)
+    S = H.Surrogate(H.blackscholes_desc(64), seed=2308)
+    S.fit_normalization(xt, yt, W.BS_RATE)
+    S.train(xt, yt, W.BS_RATE, batch=8192, epochs=24, lr=3e-3)
+    # calibration: the smallest price floor above which the 99th percentile of
+    # the surrogate's relative error is within 1%
+    xc = torch.from_numpy(W.blackscholes_inputs(1 << 20, seed=32)).to(dev)
+    pc = torch.zeros(xc.shape[1], dtype=torch.float32, device=dev)
+    S.infer(xc, pc, W.BS_RATE)
+    p = pc.cpu().numpy().astype(np.float64)
+    yc = exact(xc, torch.float64).cpu().numpy()
+    order = np.argsort(p)[::-1]
+    rel = np.abs(p[order] - yc[order]) / np.maximum(np.abs(yc[order]), 1e-30)
+    tau = float("inf")
+    for frac in np.linspace(0.02, 1.0, 50):
+        k = max(1, int(frac * len(order)))
+        if np.quantile(rel[:k], 0.99) <= 0.01:
+            tau = float(p[order][k - 1])
+    assert np.isfinite(tau), "no calibrated floor reaches the 1% bar"
+
+    n = 1 << 20
+    xs = W.blackscholes_inputs(n, seed=33)
+    xi = torch.from_numpy(xs).to(dev)
+    ref = exact(xi, torch.float64).cpu().numpy()
+    rms = float(np.sqrt(np.mean(ref * ref)))
+    nrmse = lambda o: float(np.sqrt(np.mean((o.cpu().numpy().astype(np.float64) - ref) ** 2)) / rms)
+
+    out = torch.zeros(n, dtype=torch.float32, device=dev)
+    st = S.infer(xi, out, W.BS_RATE, fallback_below=tau, stats=True)
+    sur_frac, sur_q = st["approximated"] / n, nrmse(out)
+    S.close()
+    assert sur_q <= 0.01 and sur_frac >= 0.25, (sur_q, sur_frac, tau)
+
+    best = {}
+    sc = W.iact_scale(xs, n)
+    with H.Region(H.HPAC_REGION_BLACKSCHOLES, xi, param=W.BS_RATE, logical_threads=n // 8) as R:
+        for thr in (0.005, 0.02, 0.1):
+            o = torch.zeros(n, dtype=torch.float32, device=dev)
+            s = R.run_taf(xi, o, 4, 8, thr, H.HPAC_LEVEL_THREAD, stats=True)
+            if nrmse(o) <= 0.01:
+                best["taf"] = max(best.get("taf", 0.0), s["approximated"] / n)
+        for thr in (1e-3, 1e-2, 5e-2):
+            o = torch.zeros(n, dtype=torch.float32, device=dev)
+            s = R.run_iact(xi, o, 8, 32, thr, H.HPAC_LEVEL_THREAD, in_scale=sc, stats=True)
+            if nrmse(o) <= 0.01:
+                best["iact"] = max(best.get("iact", 0.0), s["approximated"] / n)
+    method = max(best.values(), default=0.0)
+    assert sur_frac > 10 * method, (sur_frac, best)
