@@ -222,7 +222,8 @@ hpac_status hpac_region_reset_state(hpac_region *region);
 
 /* KMEANS regions: the centroids every later run reads (device pointer, K x 8
  * floats, caller-owned, may change between runs; must stay valid while a run
- * using it is in flight). HPAC_EINVAL for other kinds or NULL. */
+ * using it is in flight; 16-byte aligned). HPAC_EINVAL for other kinds, NULL
+ * or a pointer that is not 16-byte aligned. */
 hpac_status hpac_region_set_aux(hpac_region *region, const void *d_aux);
 
 /* K-Means centroid update, the exact step between two assignments: centroid k

@@ -217,6 +217,7 @@ hpac_status hpac_region_set_aux(hpac_region *r, const void *d_aux) {
   if (!r) return set_error(HPAC_EINVAL, "region is NULL");
   if (r->d.kind != HPAC_REGION_KMEANS) return set_error(HPAC_EINVAL, "region kind %d takes no aux", r->d.kind);
   if (!d_aux) return set_error(HPAC_EINVAL, "aux is NULL");
+  if ((uintptr_t)d_aux % 16) return set_error(HPAC_EINVAL, "centroids not 16-byte aligned");
   r->aux = d_aux;
   return HPAC_OK;
 }

@@ -80,16 +80,40 @@ __global__ void __launch_bounds__(L) kmeans_sums_private(const float *__restrict
   for (int j = 0; j < K * 8; ++j) s_acc[j * L + tid] = 0.0;
   for (int j = 0; j < K; ++j) s_n[j * L + tid] = 0;
   unsigned ch = 0;
-  for (int64_t i = (int64_t)blockIdx.x * L + tid; i < n; i += (int64_t)gridDim.x * L) {
-    const float a = assign[i];
+  // the next observation's id and features are loaded before this one's
+  // additions, so each thread keeps two observations' loads in flight (the
+  // columns leave room for few threads per SM)
+  const int64_t step = (int64_t)gridDim.x * L;
+  int64_t i = (int64_t)blockIdx.x * L + tid;
+  float a = 0.0f, pa = 0.0f, xv[8];
+  if (i < n) {
+    a = assign[i];
+    if (prev) pa = prev[i];
+#pragma unroll
+    for (int d = 0; d < 8; ++d) xv[d] = x[d * stride + i];
+  }
+  while (i < n) {
+    const int64_t nx = i + step;
+    float an = 0.0f, pn = 0.0f, xn[8];
+    if (nx < n) {
+      an = assign[nx];
+      if (prev) pn = prev[nx];
+#pragma unroll
+      for (int d = 0; d < 8; ++d) xn[d] = x[d * stride + nx];
+    }
     const int k = (int)a;
     if (k >= 0 && k < K) {  // ids are produced in range; anything else is left out
       s_n[k * L + tid] += 1;
       double *col = s_acc + (size_t)k * 8 * L + tid;
 #pragma unroll
-      for (int d = 0; d < 8; ++d) col[d * L] += (double)x[d * stride + i];
+      for (int d = 0; d < 8; ++d) col[d * L] += (double)xv[d];
     }
-    if (prev && prev[i] != a) ++ch;
+    if (prev && pa != a) ++ch;
+    a = an;
+    pa = pn;
+#pragma unroll
+    for (int d = 0; d < 8; ++d) xv[d] = xn[d];
+    i = nx;
   }
   ch = __reduce_add_sync(0xffffffffu, ch);
   if ((tid & 31) == 0 && ch) atomicAdd(changed, (unsigned long long)ch);

@@ -105,11 +105,16 @@ struct KMeans32 {
   __device__ __forceinline__ float operator()(const float *x) const {
     int best = 0;
     float bd = 0.0f;
+    // a centroid is two 16-byte loads (the pointer is 16-byte aligned, checked
+    // when it is set); the distance sums d = 0..7 in order, as defined
+    const float4 *c4 = reinterpret_cast<const float4 *>(cent);
     for (int k = 0; k < K; ++k) {
+      const float4 lo = __ldg(c4 + 2 * k), hi = __ldg(c4 + 2 * k + 1);
+      const float c[8] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
       float acc = 0.0f;
 #pragma unroll
       for (int d = 0; d < 8; ++d) {
-        const float df = __fsub_rn(x[d], __ldg(cent + k * 8 + d));
+        const float df = __fsub_rn(x[d], c[d]);
         acc = __fadd_rn(acc, __fmul_rn(df, df));
       }
       if (k == 0 || acc < bd) {

@@ -47,6 +47,21 @@ def test_exact_assignment(H, orc, n, K):
         assert np.array_equal(host(out), orc.run_exact(orc.KMEANS, x, cent))
 
 
+def test_misaligned_centroids_are_rejected(H):
+    """Centroids are read as 16-byte vectors: a pointer off that boundary is
+    refused when it is set, before any launch."""
+    x = torch.zeros((8, 64), dtype=torch.float32, device="cuda")
+    buf = torch.zeros(4 * 8 + 1, dtype=torch.float32, device="cuda")
+    R = H.Region(H.HPAC_REGION_KMEANS, x, arg=4, logical_threads=0, block_threads=256)
+    try:
+        with pytest.raises(H.HpacError) as e:
+            R.set_aux(buf[1:])
+        assert e.value.status == H.HPAC_EINVAL
+        R.set_aux(buf[:32])
+    finally:
+        R.close()
+
+
 def test_assignment_at_4M_observations(H, orc):
     """The K-Means workload's size (4M observations, 16 clusters) in the
     benchmark's launch (T = N/8): every id against the oracle's nearest
