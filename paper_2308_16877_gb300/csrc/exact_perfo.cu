@@ -94,13 +94,7 @@ __device__ __forceinline__ void perfo_body(R reg, const typename R::T *__restric
 #pragma unroll
       for (int d = 0; d < R::kReads; ++d) load_vec<T, V>(in + d * stride + i0, x[d]);
       T y[V];
-#pragma unroll
-      for (int j = 0; j < V; ++j) {
-        T xi[R::kReads];
-#pragma unroll
-        for (int d = 0; d < R::kReads; ++d) xi[d] = x[d][j];
-        y[j] = reg(xi);
-      }
+      eval_group<R, V>(reg, x, y);
       store_vec<T, V>(out + i0, y);
     }
   }
@@ -200,13 +194,7 @@ __global__ void __launch_bounds__(256) map_kernel(R reg, const typename R::T *__
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       T y[V];
-#pragma unroll
-      for (int j = 0; j < V; ++j) {
-        T xi[R::kReads];
-#pragma unroll
-        for (int d = 0; d < R::kReads; ++d) xi[d] = x[u][d][j];
-        y[j] = reg(xi);
-      }
+      eval_group<R, V>(reg, x[u], y);
       store_vec<T, V>(out + (g + u * gstride) * V, y);
     }
   }
@@ -215,13 +203,7 @@ __global__ void __launch_bounds__(256) map_kernel(R reg, const typename R::T *__
 #pragma unroll
     for (int d = 0; d < R::kReads; ++d) load_vec<T, V>(in + d * stride + g * V, x[d]);
     T y[V];
-#pragma unroll
-    for (int j = 0; j < V; ++j) {
-      T xi[R::kReads];
-#pragma unroll
-      for (int d = 0; d < R::kReads; ++d) xi[d] = x[d][j];
-      y[j] = reg(xi);
-    }
+    eval_group<R, V>(reg, x, y);
     store_vec<T, V>(out + g * V, y);
   }
   // tail [groups*V, n): one invocation per thread of block 0

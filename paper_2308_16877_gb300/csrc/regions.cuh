@@ -97,9 +97,36 @@ struct Eos64 {
 // distance kernel): the nearest of K centroids (cent[k * 8 + d], read-only
 // cache) in squared Euclidean distance over 8 features, summed over d in order
 // in IEEE single precision, ties to the lowest index; the id as a float.
+// Packed single-precision pairs (one IEEE round-to-nearest operation per
+// half): two observations' distances advance in one instruction.
+__device__ __forceinline__ unsigned long long f32x2_pack(float lo, float hi) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ void f32x2_unpack(unsigned long long v, float &lo, float &hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ unsigned long long f32x2_sub(unsigned long long a, unsigned long long b) {
+  unsigned long long r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ unsigned long long f32x2_mul(unsigned long long a, unsigned long long b) {
+  unsigned long long r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ unsigned long long f32x2_add(unsigned long long a, unsigned long long b) {
+  unsigned long long r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+
 struct KMeans32 {
   using T = float;
   static constexpr int kReads = 8;
+  static constexpr bool kGroup4 = true;  // has group4()
   const float *cent;
   int K;
   __device__ __forceinline__ float operator()(const float *x) const {
@@ -124,7 +151,71 @@ struct KMeans32 {
     }
     return (float)best;
   }
+  // Four observations at once (x[d][j]: feature d of observation j), each
+  // with exactly the operations and order of operator(): the pairs (0, 1) and
+  // (2, 3) share every packed subtract, square and add.
+  __device__ __forceinline__ void group4(const float (&x)[8][4], float (&y)[4]) const {
+    unsigned long long xp[8][2];
+#pragma unroll
+    for (int d = 0; d < 8; ++d) {
+      xp[d][0] = f32x2_pack(x[d][0], x[d][1]);
+      xp[d][1] = f32x2_pack(x[d][2], x[d][3]);
+    }
+    int best[4] = {0, 0, 0, 0};
+    float bd[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    const float4 *c4 = reinterpret_cast<const float4 *>(cent);
+    for (int k = 0; k < K; ++k) {
+      const float4 lo = __ldg(c4 + 2 * k), hi = __ldg(c4 + 2 * k + 1);
+      const float c[8] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
+      unsigned long long acc0 = 0ull, acc1 = 0ull;  // (+0, +0)
+#pragma unroll
+      for (int d = 0; d < 8; ++d) {
+        const unsigned long long cc = f32x2_pack(c[d], c[d]);
+        const unsigned long long d0 = f32x2_sub(xp[d][0], cc), d1 = f32x2_sub(xp[d][1], cc);
+        acc0 = f32x2_add(acc0, f32x2_mul(d0, d0));
+        acc1 = f32x2_add(acc1, f32x2_mul(d1, d1));
+      }
+      float a[4];
+      f32x2_unpack(acc0, a[0], a[1]);
+      f32x2_unpack(acc1, a[2], a[3]);
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        if (k == 0 || a[j] < bd[j]) {
+          bd[j] = a[j];
+          best[j] = k;
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) y[j] = (float)best[j];
+  }
 };
+
+// Regions that evaluate a vector group of four invocations in one call
+// (group4) use it in the maps; the others are called once per invocation.
+template <class R, class = void>
+struct HasGroup4 {
+  static constexpr bool value = false;
+};
+template <class R>
+struct HasGroup4<R, decltype(void(R::kGroup4))> {
+  static constexpr bool value = R::kGroup4;
+};
+
+template <class R, int V>
+__device__ __forceinline__ void eval_group(const R &reg, const typename R::T (&x)[R::kReads][V],
+                                           typename R::T (&y)[V]) {
+  if constexpr (V == 4 && HasGroup4<R>::value) {
+    reg.group4(x, y);
+  } else {
+#pragma unroll
+    for (int j = 0; j < V; ++j) {
+      typename R::T xi[R::kReads];
+#pragma unroll
+      for (int d = 0; d < R::kReads; ++d) xi[d] = x[d][j];
+      y[j] = reg(xi);
+    }
+  }
+}
 
 template <typename T_>
 struct Identity {
