@@ -77,8 +77,10 @@ def test_assignment_at_4M_observations(H, orc):
 
 @pytest.mark.parametrize("level", [0, 1, 2])
 @pytest.mark.parametrize("h,p,thr", [(2, 4, 0.1), (4, 8, 0.5), (3, 2, np.inf)])
-def test_taf_on_ids(H, orc, level, h, p, thr):
-    n, K, T = 40000, 8, 5000
+@pytest.mark.parametrize("K", [8, 7])
+def test_taf_on_ids(H, orc, level, h, p, thr, K):
+    """K odd takes the last centroid alone after the packed pairs."""
+    n, T = 40000, 5000
     x, labels, init = W.kmeans_blobs(n, K, seed=9)
     idx = np.argsort(labels, kind="stable")       # clustered order: windows of equal ids
     x = np.ascontiguousarray(x[:, idx])
@@ -95,8 +97,9 @@ def test_taf_on_ids(H, orc, level, h, p, thr):
 
 @pytest.mark.parametrize("level", [0, 1])
 @pytest.mark.parametrize("ts,g,thr", [(8, 32, 0.05), (4, 4, 0.1)])
-def test_iact_on_observations(H, orc, level, ts, g, thr):
-    n, K, T = 30000, 8, 3000
+@pytest.mark.parametrize("K", [8, 5])
+def test_iact_on_observations(H, orc, level, ts, g, thr, K):
+    n, T = 30000, 3000
     x, labels, init = W.kmeans_blobs(n, K, seed=10)
     sc = W.iact_scale(x, n)
     out = torch.zeros(n, device="cuda")
