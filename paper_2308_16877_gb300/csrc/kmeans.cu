@@ -1,10 +1,10 @@
 // K-Means centroid update, the exact step between two (approximated)
 // assignments (Table 1, K-Means: iterate until no observation changes
-// cluster). One pass over the observations: each warp accumulates the
-// per-cluster feature sums (double) and counts in its own shared-memory copy,
-// each block adds its copies and then the workspace with one atomic per
-// value; a second tiny kernel divides. Changed assignments are counted in the
-// same pass.
+// cluster). One pass over the observations accumulates the per-cluster
+// feature sums (double) and counts in shared memory: one column per thread up
+// to 32 clusters, one copy per warp beyond; each block adds its columns or
+// copies and then the workspace with one atomic per value; a second tiny
+// kernel divides. Changed assignments are counted in the same pass.
 #include "hpac_internal.cuh"
 
 namespace hpac {
