@@ -56,6 +56,8 @@ __device__ __forceinline__ float team_price(float S0, float X, float Tm, float s
     S[s] = Sj;
     V[s] = fmaxf(__fsub_rn(Sj, X), 0.0f);
   }
+  const unsigned long long pu2 = f32x2_pack(c.puA, c.puA), pd2 = f32x2_pack(c.pdA, c.pdA);
+  const unsigned long long uf2 = f32x2_pack(c.uf, c.uf), x2 = f32x2_pack(X, X);
   for (int n = N - 1; n >= 0; --n) {
     // slots in groups of four with one warp-uniform test per group (the level
     // has nodes 0..n; up to three slots past it are computed and never read),
@@ -72,13 +74,26 @@ __device__ __forceinline__ float team_price(float S0, float X, float Tm, float s
           up[q] = __shfl_sync(kFull, send, (lane + 1) & 31);
         }
       }
+      // two slots per packed instruction (each half rounded as the scalar
+      // operation would be): continuation, the node's price and its exercise
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
+      for (int q = 0; q < 4; q += 2) {
         const int s = s0 + q;
-        if (s < NPL) {
+        if (s + 1 < NPL) {
+          const unsigned long long cont =
+              f32x2_fma(pu2, f32x2_pack(up[q], up[q + 1]), f32x2_mul(pd2, f32x2_pack(V[s], V[s + 1])));
+          const unsigned long long sp = f32x2_mul(f32x2_pack(S[s], S[s + 1]), uf2);
+          const unsigned long long ex = f32x2_sub(sp, x2);
+          float c0, c1, e0, e1;
+          f32x2_unpack(cont, c0, c1);
+          f32x2_unpack(sp, S[s], S[s + 1]);
+          f32x2_unpack(ex, e0, e1);
+          V[s] = fmaxf(c0, e0);  // early exercise
+          V[s + 1] = fmaxf(c1, e1);
+        } else if (s < NPL) {
           const float cont = __fmaf_rn(c.puA, up[q], __fmul_rn(c.pdA, V[s]));
           S[s] = __fmul_rn(S[s], c.uf);
-          V[s] = fmaxf(cont, __fsub_rn(S[s], X));  // early exercise
+          V[s] = fmaxf(cont, __fsub_rn(S[s], X));
         }
       }
     }
