@@ -70,7 +70,7 @@ class EosKnobs(C.Structure):
     _fields_ = [("mode", C.c_int32), ("hsize", C.c_int32), ("psize", C.c_int32),
                 ("tsize", C.c_int32), ("tperwarp", C.c_int32), ("level", C.c_int32),
                 ("thresh", C.c_double), ("threads", C.c_int64), ("block", C.c_int32),
-                ("reserved", C.c_int32), ("in_scale", C.c_double * 4)]
+                ("reserved", C.c_int32), ("in_scale", C.c_double * 4), ("st", C.c_void_p * 4)]
 
 
 def _hydro_bind(L):
@@ -265,6 +265,35 @@ def quality(a, b, metric):
                                zeros_mismatch=int(aux[1]))
 
 
+def calibrate_floor(pred, exact, target=0.01, quantile=0.99):
+    """The surrogate's calibrated fallback bound, by its definition: bad_i is
+    |pred_i - exact_i| > target |exact_i| (in double precision); over the
+    distinct prediction values v, taken from the largest down, k(v) is the
+    number of predictions >= v and b(v) the bad ones among them; the floor is
+    the smallest v with b(v) <= k(v) - ceil(quantile k(v)) (at least
+    ceil(quantile k) of the k served invocations within the target: the
+    nearest-rank quantile). NaN predictions take no part; -0 equals +0.
+    Returns (floor, k at the floor), (inf, 0) when no value qualifies."""
+    y = np.asarray(pred, dtype=np.float32).ravel()
+    a = np.asarray(exact, dtype=np.float64).ravel()
+    keep = ~np.isnan(y)
+    y, a = y[keep], a[keep]
+    if y.size == 0:
+        return math.inf, 0
+    bad = np.abs(y.astype(np.float64) - a) > target * np.abs(a)
+    order = np.argsort(-y.astype(np.float64), kind="stable")   # largest prediction first
+    ys, bs = y[order], bad[order]
+    k = np.arange(1, ys.size + 1)
+    b = np.cumsum(bs)
+    last_of_value = np.r_[ys[1:] != ys[:-1], True]             # k(v) at each distinct value
+    allowed = k - np.ceil(quantile * k.astype(np.float64)).astype(np.int64)
+    ok = np.nonzero(last_of_value & (b <= allowed))[0]
+    if ok.size == 0:
+        return math.inf, 0
+    j = ok[-1]
+    return float(ys[j]), int(j + 1)
+
+
 # ---------------------------------------------------------------- hydro
 
 GAMMA = 5.0 / 3.0
@@ -334,9 +363,20 @@ class HydroState:
 
 
 def eos_knobs(mode, hsize=4, psize=8, tsize=8, tperwarp=32, level=THREAD, thresh=0.0,
-              threads=0, block=256, in_scale=(1.0, 1.0, 1.0, 1.0)):
-    return EosKnobs(mode, hsize, psize, tsize, tperwarp, level, float(thresh), threads, block, 0,
-                    (C.c_double * 4)(*in_scale))
+              threads=0, block=256, in_scale=(1.0, 1.0, 1.0, 1.0), persistent=False, n=None):
+    """EOS technique of a hydro step. persistent=True keeps the TAF windows or
+    iACT tables across steps (the state arrays of taf_state / iact_state for
+    T = threads, or n^3 elements when threads is 0; n is then required)."""
+    k = EosKnobs(mode, hsize, psize, tsize, tperwarp, level, float(thresh), threads, block, 0,
+                 (C.c_double * 4)(*in_scale))
+    if persistent and mode in (EOS_TAF, EOS_IACT):
+        T = threads if threads > 0 else n ** 3
+        st = taf_state(T, hsize) if mode == EOS_TAF else iact_state(T, tsize, tperwarp, 4)
+        keys = ("vals", "cnt", "pred") if mode == EOS_TAF else ("z", "y", "valid", "rr")
+        for j, key in enumerate(keys):
+            k.st[j] = st[key].ctypes.data
+        k._state = st                      # keeps the arrays alive with the knobs
+    return k
 
 
 __all__ = [k for k in dir() if not k.startswith("_")] + ["math"]

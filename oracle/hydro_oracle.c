@@ -53,6 +53,14 @@ int orc_run_taf(const orc_region *R, const void *in, int32_t hsize, int32_t psiz
 int orc_run_iact(const orc_region *R, const void *in, int32_t tsize, int32_t tperwarp,
                  double thr, int32_t level, const double *in_scale, void *out, uint8_t *mask,
                  void *stat, int64_t *counters);
+int orc_run_taf_persist(const orc_region *R, const void *in, int32_t hsize, int32_t psize,
+                        double thr, int32_t level, int32_t reset, double *st_vals,
+                        int32_t *st_cnt, int32_t *st_pred, void *out, uint8_t *mask, void *stat,
+                        int64_t *counters);
+int orc_run_iact_persist(const orc_region *R, const void *in, int32_t tsize, int32_t tperwarp,
+                         double thr, int32_t level, const double *in_scale, float *st_z,
+                         double *st_y, int32_t *st_valid, int32_t *st_rr, void *out,
+                         uint8_t *mask, void *stat, int64_t *counters);
 
 #define HYDRO_CQ 2.0
 #define HYDRO_CL 0.5
@@ -173,6 +181,12 @@ typedef struct {
   int32_t block;
   int32_t reserved;
   double in_scale[4];       /* iACT */
+  /* State kept across steps (NULL: each step's call starts empty, as the
+   * paper's kernel-scoped state). TAF: st[0] window values (double, [h][T]),
+   * st[1] fill counts, st[2] owed predictions (int32, [T]); iACT: st[0] scaled
+   * inputs (float), st[1] outputs (double), st[2] valid flags, st[3]
+   * round-robin slots (int32), laid out as orc_run_iact_persist reads them. */
+  void *st[4];
 } orc_eos_knobs;
 
 /* One time step. eos_in: scratch of 4E doubles (left holding the EOS inputs
@@ -272,11 +286,22 @@ int orc_hydro_step(int32_t n, double dt, double gamma, double *x, double *y, dou
     if (mask) memset(mask, 0, (size_t)E);
     if (counters) counters[0] = E, counters[1] = counters[2] = counters[3] = 0;
   } else if (mode == 1) {
-    rc = orc_run_taf(&R, eos_in, K->hsize, K->psize, K->thresh, K->level, 0, pn, mask, NULL,
-                     counters);
+    if (K->st[0])
+      rc = orc_run_taf_persist(&R, eos_in, K->hsize, K->psize, K->thresh, K->level, 0,
+                               (double *)K->st[0], (int32_t *)K->st[1], (int32_t *)K->st[2], pn,
+                               mask, NULL, counters);
+    else
+      rc = orc_run_taf(&R, eos_in, K->hsize, K->psize, K->thresh, K->level, 0, pn, mask, NULL,
+                       counters);
   } else {
-    rc = orc_run_iact(&R, eos_in, K->tsize, K->tperwarp, K->thresh, K->level, K->in_scale, pn, mask,
-                      NULL, counters);
+    if (K->st[0])
+      rc = orc_run_iact_persist(&R, eos_in, K->tsize, K->tperwarp, K->thresh, K->level,
+                                K->in_scale, (float *)K->st[0], (double *)K->st[1],
+                                (int32_t *)K->st[2], (int32_t *)K->st[3], pn, mask, NULL,
+                                counters);
+    else
+      rc = orc_run_iact(&R, eos_in, K->tsize, K->tperwarp, K->thresh, K->level, K->in_scale, pn,
+                        mask, NULL, counters);
   }
   if (rc) {
     free(pn);

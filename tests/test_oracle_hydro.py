@@ -115,9 +115,16 @@ def test_axis_permutation_symmetry(orc):
         assert np.allclose(e, e.transpose(perm), rtol=1e-10, atol=1e-6 * e.max())
 
 
-def test_energy_converges_under_time_step_refinement(orc):
-    """Total energy (internal + kinetic) drifts by a time-discretization error
-    that shrinks at least linearly when dt is halved at equal physical time."""
+def test_energy_conservation_in_the_limit_of_small_time_steps(orc):
+    """Total energy (internal + kinetic) is not conserved step by step: the
+    nodal forces use p + q of the step's start and the old and new velocities'
+    mean, while the energy update charges the trapezoid pressure and the new
+    viscosity against the volume change, which differ by O(dt) per unit of
+    work. So the drift at equal physical time is first order in dt, and its
+    Richardson extrapolation to dt -> 0 (2 D(dt/2) - D(dt)) vanishes at second
+    order: what an exactly consistent force and work pair gives. A force or
+    work term scaled by 1 + eps adds eps times the work done (here ~40% of the
+    energy becomes kinetic) at every dt, which the extrapolation exposes."""
     n = 10
     drift = []
     for scale, steps in ((1.0, 40), (0.5, 80), (0.25, 160)):
@@ -127,9 +134,15 @@ def test_energy_converges_under_time_step_refinement(orc):
         dt = W.hydro_dt(n) * scale
         for _ in range(steps):
             S.step(dt)
-        drift.append(abs(sum(S.energies()) - e0) / e0)
-    assert drift[0] < 0.05
-    assert drift[1] < 0.6 * drift[0] and drift[2] < 0.6 * drift[1]
+        ie, ke = S.energies()
+        assert ke > 0.3 * e0                      # the blast did work
+        drift.append((ie + ke - e0) / e0)
+    d = np.array(drift)
+    assert abs(d[0]) < 1e-2
+    assert 0.45 < d[1] / d[0] < 0.55 and 0.45 < d[2] / d[1] < 0.55   # first order
+    r = 2 * d[1:] - d[:-1]                        # extrapolated to dt -> 0
+    assert abs(r[0]) < 0.1 * abs(d[1]) and abs(r[1]) < 0.35 * abs(r[0])  # second order
+    assert abs(r[1]) < 5e-5
 
 
 def test_step_is_deterministic_and_resumable(orc):
