@@ -554,12 +554,20 @@ hpac_status hpac_device_fp64_rate(double *h_tflops, void *cuda_stream);
  *  - Scratch is a fixed array inside the library (about 656 KB on every device
  *    that loads it, held until the process exits), so n must not exceed
  *    134,217,728 elements; larger n returns HPAC_EINVAL with a message.
- *  - The first call on a device looks up that array's device address (with the
- *    device current) and caches it; make that first call before any stream
- *    capture begins on the device.
+ *  - The first call on a device, made with that device current, finds the
+ *    array's device address and caches it. A call with n = 0 does that set-up
+ *    and also makes the CUDA runtime load the call's kernels (with lazy
+ *    module loading, the default, a kernel's code is loaded, into newly
+ *    allocated device memory, at its first use), then returns without
+ *    launching anything. Make one such call per device before the caller
+ *    reserves that device's memory; later calls then allocate nothing.
+ *  - Like hpac_quality, the call copies its result to the host and waits for
+ *    it, so it must not be made on a stream that is being captured.
  *  - Every call on a device uses the same array. A call waits for its own
  *    result, but calls issued from several host threads whose work overlaps on
- *    the GPU race on the array: serialize them. */
+ *    the GPU race on the array: serialize them.
+ *  - The cached address belongs to the device's primary context: resetting
+ *    the device (cudaDeviceReset) while the library is in use invalidates it. */
 hpac_status hpac_quality_noalloc(int32_t approx_dtype, int64_t n, const double *d_exact,
                                  const void *d_approx, int32_t metric,
                                  hpac_quality_result *h_result, void *cuda_stream);

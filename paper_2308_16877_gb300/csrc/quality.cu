@@ -1,11 +1,20 @@
 // Quality loss against an exact reference (Section 4): MAPE (Eq. 1), RMSE and
 // the misclassification rate MCR (Eq. 2), accumulated in double precision.
 //
-// Two deterministic passes: a fixed grid of kBlocks blocks reduces grid-stride
-// slices to per-block partials (a tree inside each block), then one block
-// reduces the partials in index order. The partials live in a device buffer
-// allocated once per device and kept for the life of the process; a host
-// mutex serializes calls, which wait for their result before returning.
+// Two deterministic passes: a grid of blocks reduces grid-stride slices to
+// per-block partials (a tree inside each block), then one block reduces the
+// partials in index order. Two entry points differ only in where the partials
+// live:
+//  - hpac_quality: a device buffer of kBlocks + 1 partials, allocated with
+//    cudaMalloc on a device's first call and kept for the life of the process;
+//    a host mutex serializes calls, which wait for their result.
+//  - hpac_quality_noalloc: a fixed static __device__ array of kStaticPartials
+//    + 1 partials compiled into the library, addressed through a per-device
+//    cache of its device address; no lock (callers serialize overlapping
+//    calls themselves, see hpac.h).
+// Both per-device caches hold device addresses of the primary context: they
+// assume that context is not reset (cudaDeviceReset) while the process uses
+// the library.
 #include <math.h>
 #include <mutex>
 
@@ -250,12 +259,21 @@ extern "C" hpac_status hpac_quality_noalloc(int32_t approx_dtype, int64_t n, con
     return set_error(HPAC_EINVAL, "dtype %d", approx_dtype);
   if (n > 0 && (!d_exact || !d_approx)) return set_error(HPAC_EINVAL, "NULL data pointer");
   *h_result = hpac_quality_result{0.0, 0.0, 0, 0, 0};
-  if (n == 0) return HPAC_OK;
   int dev = 0;
   HPAC_CUDA_TRY(cudaGetDevice(&dev));
   Partial *scr = nullptr;
   hpac_status s = static_scratch(dev, &scr);
   if (s != HPAC_OK) return s;
+  if (n == 0) {
+    // The warm-up call: besides the address lookup above, make the runtime
+    // load the three kernels now (with lazy module loading they would load,
+    // and allocate device memory for their code, at their first launch).
+    cudaFuncAttributes fa;
+    HPAC_CUDA_TRY(cudaFuncGetAttributes(&fa, quality_partial<float>));
+    HPAC_CUDA_TRY(cudaFuncGetAttributes(&fa, quality_partial<double>));
+    HPAC_CUDA_TRY(cudaFuncGetAttributes(&fa, quality_final));
+    return HPAC_OK;
+  }
   cudaStream_t st = (cudaStream_t)cuda_stream;
   // Every partial slot the final kernel reads is written earlier in this call,
   // so nothing left in the shared array by a previous call is used.

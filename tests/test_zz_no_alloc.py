@@ -8,6 +8,11 @@ give the same result as hpac_quality on the same inputs, including on a second
 call right after the first (the array keeps the previous call's contents), and
 it must refuse inputs larger than its fixed scratch can reduce.
 
+Beyond the comparison with hpac_quality, the tests pin it to the CPU oracle's
+quality function on a small case, run it once at its fixed limit (every slot of
+the array written), and check that after the n = 0 warm-up call a repeated call
+leaves the device's free memory unchanged.
+
 This file is collected last so that a run stopping at the first failure has
 already run every other test; it also passes on its own in a fresh process.
 """
@@ -82,3 +87,64 @@ def test_rejects_inputs_beyond_the_fixed_scratch(H):
                                        H.C.c_void_p(b.data_ptr()), 0, H.C.byref(res), None)
     assert st == H.HPAC_EINVAL
     assert "limit" in H.hpac_last_error()
+
+
+def test_warm_up_then_calls_allocate_nothing(H):
+    # n = 0 finds the array and loads the kernels without launching anything;
+    # after it (and one call that launches), further calls must not change the
+    # device's free memory
+    a, b = _pair(1 << 20, np.float32, seed=3)
+    a64, b64 = _pair(1 << 20, np.float64, seed=4)
+    res = H.hpac_quality_result()
+    assert H.load().hpac_quality_noalloc(H.HPAC_F32, 0, None, None, 0, H.C.byref(res), None) == H.HPAC_OK
+    assert res.used == 0
+    _call(H, H.hpac_quality_noalloc, a, b, 0)
+    _call(H, H.hpac_quality_noalloc, a64, b64, 1)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for metric in (0, 1, 2):
+        _call(H, H.hpac_quality_noalloc, a, b, metric)
+        _call(H, H.hpac_quality_noalloc, a64, b64, metric)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+
+
+@pytest.mark.parametrize("metric", [0, 1, 2])
+def test_small_case_matches_the_oracle(H, metric):
+    import oracle
+    rng = np.random.default_rng(40 + metric)
+    n = 70_001
+    a = rng.uniform(0.05, 3.0, n)
+    a[rng.random(n) < 0.1] = 0.0
+    b = (a * (1.0 + rng.normal(0.0, 0.02, n))).astype(np.float32)
+    b[rng.random(n) < 0.05] = 0.5
+    if metric == 2:                       # ids for the misclassification rate
+        a = np.floor(a * 3.0)
+        b = np.where(rng.random(n) < 0.07, a + 1.0, a).astype(np.float32)
+    r = _call(H, H.hpac_quality_noalloc, torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda(),
+              metric)
+    val, aux = oracle.quality(a, b.astype(np.float64), metric)
+    assert r["value"] == pytest.approx(val, rel=1e-6, abs=1e-300)
+    if metric == 0:
+        assert r["zeros"] == aux["zeros"] and r["zeros_mismatch"] == aux["zeros_mismatch"]
+        assert r["zero_max_abs"] == aux["zero_max_abs"]
+
+
+def test_at_the_fixed_limit(H):
+    # n = 134,217,728 fills all 16,384 partial slots (the last one next to the
+    # result slot) with exactly 32 elements per thread
+    n = NOALLOC_MAX_N
+    g = torch.Generator(device="cuda").manual_seed(5)
+    a = torch.rand(n, dtype=torch.float64, device="cuda", generator=g) + 0.1
+    a[: n // 16] = 0.0
+    b = (a * (1.0 + 0.01 * torch.randn(n, dtype=torch.float64, device="cuda", generator=g))).float()
+    b[n // 32: n // 16] = 0.0
+    for metric in (0, 1):
+        first = _call(H, H.hpac_quality_noalloc, a, b, metric)
+        again = _call(H, H.hpac_quality_noalloc, a, b, metric)
+        ref = _call(H, H.hpac_quality, a, b, metric)
+        _same(first, ref)
+        _same(again, ref)
+    del a, b
+    torch.cuda.empty_cache()
