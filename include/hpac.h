@@ -499,6 +499,24 @@ hpac_status hpac_mlp_infer(hpac_mlp *mlp, int64_t n, const void *d_in, int64_t i
                            double param, void *d_out, float fallback_below, uint8_t *d_mask,
                            hpac_stats *h_stats);
 
+/* Calibrated fallback bound of a surrogate (the exact region as judge of its
+ * error; not in the paper). On n held-out invocations with surrogate
+ * predictions d_pred (floats) and exact region outputs d_exact (doubles, both
+ * device), an invocation is bad when |pred - exact| > target |exact|. The
+ * floor is the smallest prediction value v such that, among the k predictions
+ * >= v, at most k - ceil(quantile k) are bad: the nearest-rank quantile of
+ * the relative error over the invocations the surrogate would serve is
+ * within target. -0 and +0 count as one value; NaN predictions are never at
+ * or above a floor. *h_floor gets the floor (+inf when no v qualifies, so the
+ * exact region serves everything; pass it as hpac_mlp_infer's fallback_below)
+ * and *h_kept (nullable) the k at that floor. target >= 0 and finite,
+ * quantile in (0, 1], 0 <= n <= 2^31. Waits for the result; allocates about
+ * 12 bytes per invocation (rounded up to a power of two, at least 2048) of
+ * device memory for the call. Errors: HPAC_EINVAL, HPAC_ECUDA. */
+hpac_status hpac_calibrate_floor(int64_t n, const float *d_pred, const double *d_exact,
+                                 double target, double quantile, float *h_floor,
+                                 int64_t *h_kept, void *cuda_stream);
+
 /* Gradient of the mean squared error over n invocations with targets d_target
  * (region outputs, n floats) into d_grad (num_params floats, overwritten; NULL:
  * the surrogate's internal buffer). h_loss (nullable, synchronous): the loss. */

@@ -108,6 +108,8 @@ SIGNATURES = {
                                C.POINTER(hpac_quality_result), _P]),
     "hpac_quality_noalloc": (C.c_int, [C.c_int32, C.c_int64, _P, _P, C.c_int32,
                                        C.POINTER(hpac_quality_result), _P]),
+    "hpac_calibrate_floor": (C.c_int, [C.c_int64, _P, _P, C.c_double, C.c_double, C.POINTER(C.c_float),
+                                       C.POINTER(C.c_int64), _P]),
     "hpac_region_set_aux": (C.c_int, [_P, _P]),
     "hpac_kmeans_workspace_bytes": (C.c_size_t, [C.c_int32]),
     "hpac_kmeans_update": (C.c_int, [C.c_int64, C.c_int32, _P, C.c_int64, _P, _P, _P, _P,
@@ -256,6 +258,25 @@ def hpac_quality_noalloc(dtype, n, d_exact, d_approx, metric, stream=None):
     _check(load().hpac_quality_noalloc(dtype, n, d_exact, d_approx, metric, C.byref(res),
                                        stream or None), "hpac_quality_noalloc")
     return res
+
+
+def hpac_calibrate_floor(n, d_pred, d_exact, target, quantile, stream=None):
+    """(floor, kept): the surrogate's calibrated fallback bound (see hpac.h)."""
+    fl = C.c_float()
+    kept = C.c_int64()
+    _check(load().hpac_calibrate_floor(n, d_pred, d_exact, float(target), float(quantile), C.byref(fl),
+                                       C.byref(kept), stream or None), "hpac_calibrate_floor")
+    return float(fl.value), int(kept.value)
+
+
+def calibrate_floor(pred, exact, target=0.01, quantile=0.99, stream=None):
+    """Floor for Surrogate.infer's fallback_below from predictions (float32)
+    and exact outputs (float64) of the same held-out invocations (CUDA tensors)."""
+    import torch
+    if pred.dtype != torch.float32 or exact.dtype != torch.float64 or pred.numel() != exact.numel():
+        raise ValueError("pred must be float32 and exact float64 of the same length")
+    return hpac_calibrate_floor(pred.numel(), _ptr(pred.contiguous()), _ptr(exact.contiguous()), target,
+                                quantile, _stream_handle(stream))
 
 
 def hpac_hydro_init(state, stream=None):

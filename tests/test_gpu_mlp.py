@@ -386,20 +386,12 @@ def test_surrogate_gains_over_taf_and_iact_at_one_percent(H):
     S = H.Surrogate(H.blackscholes_desc(64), seed=2308)
     S.fit_normalization(xt, yt, W.BS_RATE)
     S.train(xt, yt, W.BS_RATE, batch=8192, epochs=24, lr=3e-3)
-    # calibration: the smallest price floor above which the 99th percentile of
-    # the surrogate's relative error is within 1%
+    # calibration (hpac_calibrate_floor): the smallest price floor above which
+    # the 99th percentile of the surrogate's relative error is within 1%
     xc = torch.from_numpy(W.blackscholes_inputs(1 << 20, seed=32)).to(dev)
     pc = torch.zeros(xc.shape[1], dtype=torch.float32, device=dev)
     S.infer(xc, pc, W.BS_RATE)
-    p = pc.cpu().numpy().astype(np.float64)
-    yc = exact(xc, torch.float64).cpu().numpy()
-    order = np.argsort(p)[::-1]
-    rel = np.abs(p[order] - yc[order]) / np.maximum(np.abs(yc[order]), 1e-30)
-    tau = float("inf")
-    for frac in np.linspace(0.02, 1.0, 50):
-        k = max(1, int(frac * len(order)))
-        if np.quantile(rel[:k], 0.99) <= 0.01:
-            tau = float(p[order][k - 1])
+    tau, _ = H.calibrate_floor(pc, exact(xc, torch.float64), 0.01, 0.99)
     assert np.isfinite(tau), "no calibrated floor reaches the 1% bar"
 
     n = 1 << 20
