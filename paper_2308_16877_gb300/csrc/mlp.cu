@@ -567,6 +567,252 @@ __global__ void __launch_bounds__(H * 2) mlp_kernel(MlpArgs a, hpac_mlp_desc d) 
   }
 }
 
+// ---------------------------------------------------------------------------
+// Inference on the fifth-generation tensor cores (tcgen05, accumulators in
+// tensor memory). One thread owns one invocation of a 128-invocation tile:
+// features, layer 1 and GELU in FP32 on the CUDA cores, the BF16 activations
+// written as row `thread` of the layer-2 A operand in shared memory; one
+// elected thread issues the H x H product (M = 128 rows, N = H, K = H in
+// steps of 16) into an FP32 accumulator of H tensor-memory columns and
+// commits it to an mbarrier; every thread then reads its own row back
+// (tcgen05.ld, 32 lanes per warp) for bias, GELU and the layer-3 dot product.
+//
+// Operands in shared memory use the canonical no-swizzle K-major layout of
+// 8-row x 16-byte core matrices: element (r, k) of an R x H BF16 matrix at
+// byte (r / 8) * 16 H + (k / 8) * 128 + (r % 8) * 16 + (k % 8) * 2, so the
+// leading-dimension offset (between core matrices along K) is 128 bytes and
+// the stride offset (between 8-row groups) 16 H bytes. A is the tile's
+// activations (128 x H), B is W2 as stored, [out][in] (N x K, K-major).
+//
+// Every wait on the mbarrier is bounded: after kWaitLimit polls the block
+// sets the status word (counters[2] = 1), waits once more (bounded) for the
+// product in flight, frees its tensor memory and returns; hpac_mlp_infer
+// reports HPAC_ETIMEOUT at its next synchronizing call.
+// ---------------------------------------------------------------------------
+constexpr int kTile = 128;
+constexpr int kWaitLimit = 1 << 20;
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// Shared-memory matrix descriptor: start address, leading and stride byte
+// offsets (all in 16-byte units), descriptor version 1 (bits 46-47), no
+// swizzle (bits 61-63 = 0).
+__device__ __forceinline__ uint64_t umma_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((addr >> 4) & 0x3fff) | ((uint64_t)((lbo >> 4) & 0x3fff) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3fff) << 32) | (1ull << 46);
+}
+
+// Instruction descriptor of kind::f16: FP32 accumulator (bits 4-5 = 1), BF16
+// A and B (bits 7-9 = 1, 10-12 = 1), both K-major (bits 15, 16 = 0), N / 8 at
+// bits 17-22, M / 16 at bits 24-28.
+template <int N>
+__host__ __device__ constexpr uint32_t umma_idesc_bf16_m128() {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(kTile >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                          uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(done)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity) {
+  for (int it = 0; it < kWaitLimit; ++it)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
+// 32 consecutive FP32 accumulator columns of this warp's 32 lanes.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+        "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+        "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+        "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+template <int H>
+struct TcLayout {
+  static constexpr int kA = 0;                        // 128 x H BF16 activations
+  static constexpr int kB = kTile * H * 2;            // H x H BF16 W2 [out][in]
+  static constexpr int kW1 = kB + H * H * 2;          // H x 8 floats
+  static constexpr int kB1 = kW1 + H * 8 * 4;
+  static constexpr int kB2 = kB1 + H * 4;
+  static constexpr int kW3 = kB2 + H * 4;
+  static constexpr int kB3 = kW3 + H * 4;
+  static constexpr int kBar = (kB3 + 4 + 7) & ~7;     // mbarrier (8 bytes)
+  static constexpr int kSlot = kBar + 8;              // tensor-memory address
+  static constexpr int kBytes = kSlot + 8;
+};
+
+// Byte offset of element (r, k) in the canonical K-major layout of an
+// R x H BF16 operand (8-element chunk k / 8).
+template <int H>
+__device__ __forceinline__ int kmajor_off(int r, int k) {
+  return (r >> 3) * (16 * H) + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2;
+}
+
+template <int H, int KIND>
+__global__ void __launch_bounds__(kTile) mlp_tc_infer(MlpArgs a, hpac_mlp_desc d) {
+  using L = TcLayout<H>;
+  extern __shared__ __align__(1024) unsigned char sm[];
+  float *w1 = reinterpret_cast<float *>(sm + L::kW1);
+  float *b1 = reinterpret_cast<float *>(sm + L::kB1);
+  float *b2 = reinterpret_cast<float *>(sm + L::kB2);
+  float *w3 = reinterpret_cast<float *>(sm + L::kW3);
+  float *b3 = reinterpret_cast<float *>(sm + L::kB3);
+  const uint32_t bar = smem_u32(sm + L::kBar);
+  uint32_t *slot = reinterpret_cast<uint32_t *>(sm + L::kSlot);
+  __shared__ unsigned long long fallbacks;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int D = d.n_feat;
+  {
+    const float *p = a.params;
+    const int oW1 = 0, ob1 = H * D, oW2 = ob1 + H, ob2 = oW2 + H * H, oW3 = ob2 + H, ob3 = oW3 + H;
+    for (int j = tid; j < H * H; j += kTile) {
+      const int o = j / H, k = j % H;
+      *reinterpret_cast<__nv_bfloat16 *>(sm + L::kB + kmajor_off<H>(o, k)) = __float2bfloat16_rn(p[oW2 + j]);
+    }
+    for (int j = tid; j < H * 8; j += kTile) {
+      const int u = j / 8, k = j % 8;
+      w1[j] = k < D ? bf16r(p[oW1 + u * D + k]) : 0.f;
+    }
+    for (int j = tid; j < H; j += kTile) {
+      b1[j] = p[ob1 + j];
+      b2[j] = p[ob2 + j];
+      w3[j] = bf16r(p[oW3 + j]);
+    }
+    if (tid == 0) {
+      *b3 = p[ob3];
+      fallbacks = 0;
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar));
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {  // H columns of tensor memory (a power of two >= 32)
+      asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)),
+                   "r"(H));
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+  }
+  // W2 was written by the generic proxy; the tensor core reads it through the
+  // async proxy
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *slot;
+  const uint64_t adesc = umma_desc(smem_u32(sm + L::kA), 128, 16 * H);
+  const uint64_t bdesc = umma_desc(smem_u32(sm + L::kB), 128, 16 * H);
+  constexpr uint32_t idesc = umma_idesc_bf16_m128<H>();
+  uint32_t parity = 0;
+  bool failed = false;
+  const int64_t tiles = (a.n + kTile - 1) / kTile;
+  for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+    const int64_t i = tile * kTile + tid;
+    const bool valid = i < a.n;
+    float f[8], mult = 0.f, raw[4];
+    features<KIND>(a.in, a.stride, valid ? i : 0, a.param, d, f, mult, raw);
+    // layer 1 and GELU into row tid of A, 8 units (16 bytes) at a time
+#pragma unroll 2
+    for (int kc = 0; kc < H / 8; ++kc) {
+      uint32_t pk[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int u0 = 8 * kc + 2 * q, u1 = u0 + 1;
+        float z0 = b1[u0], z1 = b1[u1];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          if (k < D) {
+            z0 = fmaf(w1[u0 * 8 + k], f[k], z0);
+            z1 = fmaf(w1[u1 * 8 + k], f[k], z1);
+          }
+        }
+        pk[q] = pack_bf16(gelu(z0), gelu(z1));
+      }
+      *reinterpret_cast<uint4 *>(sm + L::kA + kmajor_off<H>(tid, 8 * kc)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (tid == 0) {
+#pragma unroll
+      for (int ks = 0; ks < H / 16; ++ks)  // K = 16 per product: two core matrices (256 bytes) along K
+        umma_bf16(tmem, adesc + (uint64_t)((ks * 256) >> 4), bdesc + (uint64_t)((ks * 256) >> 4), idesc,
+                  ks > 0 ? 1u : 0u);
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                   : "memory");
+    }
+    const bool ok = mbar_wait_bounded(bar, parity);
+    if (__syncthreads_or(!ok)) {
+      failed = true;
+      break;
+    }
+    parity ^= 1u;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    // row tid of the accumulator: lane 32 warp + (tid % 32) of this warp's quarter
+    float y = 0.f;
+#pragma unroll
+    for (int c = 0; c < H; c += 32) {
+      float v[32];
+      tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, v);
+#pragma unroll
+      for (int j = 0; j < 32; ++j) y = fmaf(bf16r(gelu(v[j] + b2[c + j])), w3[c + j], y);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    y += *b3;
+    if (valid) {
+      const float pred = mult * fmaf(d.out_scale, y, d.out_shift);
+      float o = pred;
+      uint8_t mk = HPAC_MASK_APPROX;
+      if (pred < a.fallback_below) {  // calibrated exact fallback (NaN never falls back)
+        if (KIND == HPAC_REGION_BLACKSCHOLES) o = BlackScholes32{(float)a.param}(raw);
+        mk = HPAC_MASK_EXACT;
+        atomicAdd(&fallbacks, 1ull);
+      }
+      if (KIND == HPAC_REGION_EOS)  // the region's own dtype; pressure is non-negative
+        reinterpret_cast<double *>(a.out)[i] = (double)fmaxf(o, 0.f);
+      else
+        a.out[i] = o;
+      if (a.mask) a.mask[i] = mk;
+    }
+  }
+  if (failed) {
+    // the product in flight must land before its tensor memory is freed
+    mbar_wait_bounded(bar, parity);
+    if (tid == 0 && a.counters) atomicExch(&a.counters[2], 1ull);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(H));
+  if (tid == 0 && fallbacks && a.counters) atomicAdd(&a.counters[0], fallbacks);
+}
+
 // Sums of the features, their squares and the per-invocation targets
 // (region output / multiplier) for the normalisation statistics.
 template <int KIND>
@@ -642,6 +888,37 @@ hpac_status launch_t(hpac_mlp *m, const MlpArgs &a) {
   return HPAC_OK;
 }
 
+// The tensor-core inference: persistent blocks of 128 threads, as many per
+// SM as shared memory allows while their tensor-memory columns (H each) fit
+// in the SM's 512 (extra shared memory is requested until they do, so no
+// block ever waits for columns another resident block holds).
+template <int H, int KIND>
+hpac_status launch_tc_infer(hpac_mlp *m, const MlpArgs &a) {
+  auto fn = mlp_tc_infer<H, KIND>;
+  int smem = TcLayout<H>::kBytes;
+  int per_sm = 0;
+  for (;;) {
+    HPAC_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    HPAC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kTile, smem));
+    if (per_sm * H <= 512 || per_sm <= 1) break;
+    smem += 1024;
+  }
+  if (per_sm < 1) return set_error(HPAC_EUNSUPPORTED, "surrogate inference kernel does not fit an SM");
+  const int64_t tiles = (a.n + kTile - 1) / kTile;
+  int64_t blocks = (int64_t)sm_count(m->device) * per_sm;
+  if (blocks > tiles) blocks = tiles < 1 ? 1 : tiles;
+  fn<<<(unsigned)blocks, kTile, smem, m->stream>>>(a, m->d);
+  HPAC_CUDA_TRY(cudaGetLastError());
+  return HPAC_OK;
+}
+
+hpac_status launch_infer(hpac_mlp *m, const MlpArgs &a) {
+  const bool bs = m->d.kind == HPAC_REGION_BLACKSCHOLES;
+  if (m->d.hidden == 64)
+    return bs ? launch_tc_infer<64, HPAC_REGION_BLACKSCHOLES>(m, a) : launch_tc_infer<64, HPAC_REGION_EOS>(m, a);
+  return bs ? launch_tc_infer<128, HPAC_REGION_BLACKSCHOLES>(m, a) : launch_tc_infer<128, HPAC_REGION_EOS>(m, a);
+}
+
 template <int MODE>
 hpac_status launch(hpac_mlp *m, const MlpArgs &a) {
   const bool bs = m->d.kind == HPAC_REGION_BLACKSCHOLES;
@@ -693,6 +970,7 @@ extern "C" hpac_status hpac_mlp_create(const hpac_mlp_desc *desc, const float *h
   if (e == cudaSuccess) e = cudaMalloc(&m->v, pb);
   if (e == cudaSuccess) e = cudaMalloc(&m->loss, sizeof(float));
   if (e == cudaSuccess) e = cudaMalloc(&m->counters, 4 * sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMemset(m->counters, 0, 4 * sizeof(unsigned long long));
   if (e != cudaSuccess) {
     hpac_mlp_destroy(m);
     return cuda_error(e, "hpac_mlp_create");
@@ -782,14 +1060,19 @@ extern "C" hpac_status hpac_mlp_infer(hpac_mlp *m, int64_t n, const void *d_in, 
     a.fallback_below = fallback_below;
     a.params = m->params;
     a.counters = m->counters;
-    s = launch<MODE_INFER>(m, a);
+    s = launch_infer(m, a);
     if (s != HPAC_OK) return s;
   }
   if (h_stats) {
-    unsigned long long fb = 0;
-    HPAC_CUDA_TRY(cudaMemcpyAsync(&fb, m->counters, sizeof(fb), cudaMemcpyDeviceToHost, m->stream));
+    unsigned long long c[3] = {0, 0, 0};
+    HPAC_CUDA_TRY(cudaMemcpyAsync(c, m->counters, sizeof(c), cudaMemcpyDeviceToHost, m->stream));
     HPAC_CUDA_TRY(cudaStreamSynchronize(m->stream));
-    *h_stats = hpac_stats{n, n - (int64_t)fb, 0, 0};
+    if (c[2]) {
+      HPAC_CUDA_TRY(cudaMemsetAsync(m->counters + 2, 0, sizeof(unsigned long long), m->stream));
+      return set_error(HPAC_ETIMEOUT, "surrogate inference: a tensor-core product did not complete "
+                                      "within the kernel's wait limit");
+    }
+    *h_stats = hpac_stats{n, n - (int64_t)c[0], 0, 0};
   }
   return HPAC_OK;
 }
