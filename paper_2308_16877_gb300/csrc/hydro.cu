@@ -129,6 +129,33 @@ __device__ __forceinline__ double hex_grad12(const double (&X)[8], const double 
   return v12 * (1.0 / 12.0);
 }
 
+// Division of a 32-bit index by a fixed divisor with one multiply-high, an
+// add and two shifts (Granlund and Montgomery, "Division by invariant
+// integers using multiplication", PLDI 1994): with l = ceil(log2 d) and
+// m = floor(2^32 (2^l - d) / d) + 1, x / d = (t + ((x - t) >> s1)) >> s2,
+// t = umulhi(m, x), s1 = min(l, 1), s2 = max(l - 1, 0), for every 32-bit x
+// and d >= 1. Mesh indices stay below 2^31 (n <= 1024: (n + 1)^3 < 1.1e9), so
+// the kernels split them with it instead of 64-bit divisions.
+struct FastDiv {
+  uint32_t d, m, s1, s2;
+};
+
+FastDiv make_fastdiv(uint32_t d) {
+  uint32_t l = 0;
+  while ((1ull << l) < d) ++l;
+  FastDiv f;
+  f.d = d;
+  f.m = (uint32_t)((((1ull << l) - d) << 32) / d + 1);
+  f.s1 = l > 0 ? 1 : 0;
+  f.s2 = l > 0 ? l - 1 : 0;
+  return f;
+}
+
+__device__ __forceinline__ uint32_t fdiv(uint32_t x, const FastDiv &f) {
+  const uint32_t t = __umulhi(f.m, x);
+  return (t + ((x - t) >> f.s1)) >> f.s2;
+}
+
 __device__ __forceinline__ void gather_rel(int n, int64_t e, const double *__restrict__ x,
                                            const double *__restrict__ y,
                                            const double *__restrict__ z, double (&X)[8],
@@ -136,6 +163,32 @@ __device__ __forceinline__ void gather_rel(int n, int64_t e, const double *__res
   const int64_t n1 = n + 1;
   const int64_t i = e % n, j = (e / n) % n, k = e / ((int64_t)n * n);
   const int64_t base = (k * n1 + j) * n1 + i;
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    const int64_t nd = base + ((c >> 2) & 1) * n1 * n1 + ((c >> 1) & 1) * n1 + (c & 1);
+    X[c] = x[nd];
+    Y[c] = y[nd];
+    Z[c] = z[nd];
+  }
+#pragma unroll
+  for (int c = 1; c < 8; ++c) {
+    X[c] -= X[0];
+    Y[c] -= Y[0];
+    Z[c] -= Z[0];
+  }
+  X[0] = Y[0] = Z[0] = 0.0;
+}
+
+// The same gather for the time-step kernel: element e split by the fixed
+// divisor n, node offsets in 32 bits.
+__device__ __forceinline__ void gather_rel32(uint32_t e, const FastDiv &fn, const double *__restrict__ x,
+                                             const double *__restrict__ y,
+                                             const double *__restrict__ z, double (&X)[8],
+                                             double (&Y)[8], double (&Z)[8]) {
+  const uint32_t n = fn.d, n1 = n + 1;
+  const uint32_t jk = fdiv(e, fn), i = e - jk * n;
+  const uint32_t k = fdiv(jk, fn), j = jk - k * n;
+  const uint32_t base = (k * n1 + j) * n1 + i;
 #pragma unroll
   for (int c = 0; c < 8; ++c) {
     const int64_t nd = base + ((c >> 2) & 1) * n1 * n1 + ((c >> 1) & 1) * n1 + (c & 1);
@@ -196,13 +249,16 @@ __global__ void __launch_bounds__(256) init_node_kernel(hpac_hydro_state s) {
 }
 
 // Forces at x^n from (p + q) and the stored gradients; velocity and position.
-__global__ void __launch_bounds__(256) node_kernel(hpac_hydro_state s) {
+// Node indices are split by the fixed divisor n + 1 (fn1) in 32 bits.
+__global__ void __launch_bounds__(256) node_kernel(hpac_hydro_state s, FastDiv fn1) {
   const int n = s.n;
-  const int64_t n1 = n + 1, Nn = n1 * n1 * n1, E = (int64_t)n * n * n;
+  const uint32_t n1 = fn1.d, Nn = n1 * n1 * n1;
+  const int64_t E = (int64_t)n * n * n;
   const double dt = s.dt;
-  for (int64_t nd = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; nd < Nn;
-       nd += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = nd % n1, j = (nd / n1) % n1, k = nd / (n1 * n1);
+  for (uint32_t nd = blockIdx.x * blockDim.x + threadIdx.x; nd < Nn; nd += gridDim.x * blockDim.x) {
+    const uint32_t jk = fdiv(nd, fn1), i_ = nd - jk * n1;
+    const uint32_t k_ = fdiv(jk, fn1), j_ = jk - k_ * n1;
+    const int i = (int)i_, j = (int)j_, k = (int)k_;
     double fx = 0.0, fy = 0.0, fz = 0.0;
 #pragma unroll
     for (int dk = 1; dk >= 0; --dk)
@@ -210,9 +266,9 @@ __global__ void __launch_bounds__(256) node_kernel(hpac_hydro_state s) {
       for (int dj = 1; dj >= 0; --dj)
 #pragma unroll
         for (int di = 1; di >= 0; --di) {
-          const int64_t ei = i - di, ej = j - dj, ek = k - dk;
+          const int ei = i - di, ej = j - dj, ek = k - dk;
           if (ei < 0 || ej < 0 || ek < 0 || ei >= n || ej >= n || ek >= n) continue;
-          const int64_t el = (ek * n + ej) * n + ei;
+          const int64_t el = (int64_t)(((uint32_t)ek * n + (uint32_t)ej) * n + (uint32_t)ei);
           const int c = di + 2 * dj + 4 * dk;  // corner of this node in element el
           const double pq = s.pq[el];
           fx = fma(pq, s.grad[(0 * 8 + c) * E + el], fx);
@@ -238,15 +294,16 @@ __global__ void __launch_bounds__(256) node_kernel(hpac_hydro_state s) {
   }
 }
 
-// New volume and gradient, viscosity, and the EOS region's inputs.
-__global__ void __launch_bounds__(96) elem_kernel(hpac_hydro_state s) {
+// New volume and gradient, viscosity, and the EOS region's inputs. Element
+// indices are split by the fixed divisor n (fn) in 32 bits.
+__global__ void __launch_bounds__(96) elem_kernel(hpac_hydro_state s, FastDiv fn) {
   const int n = s.n;
   const int64_t E = (int64_t)n * n * n;
   const double dt = s.dt, gamma = s.gamma;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < E;
        e += (int64_t)gridDim.x * blockDim.x) {
     double X[8], Y[8], Z[8], gx[8], gy[8], gz[8];
-    gather_rel(n, e, s.x, s.y, s.z, X, Y, Z);
+    gather_rel32((uint32_t)e, fn, s.x, s.y, s.z, X, Y, Z);
     const double V = hex_grad12(X, Y, Z, gx, gy, gz);
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
@@ -364,7 +421,7 @@ extern "C" hpac_status hpac_hydro_nodes(const hpac_hydro_state *s, void *cuda_st
   int dev = 0;
   HPAC_CUDA_TRY(cudaGetDevice(&dev));
   const int64_t Nn = (int64_t)(s->n + 1) * (s->n + 1) * (s->n + 1);
-  node_kernel<<<grid_for(Nn, 256, dev), 256, 0, (cudaStream_t)cuda_stream>>>(*s);
+  node_kernel<<<grid_for(Nn, 256, dev), 256, 0, (cudaStream_t)cuda_stream>>>(*s, make_fastdiv(s->n + 1));
   HPAC_CUDA_TRY(cudaGetLastError());
   return HPAC_OK;
 }
@@ -380,7 +437,7 @@ extern "C" hpac_status hpac_hydro_elements(const hpac_hydro_state *s, void *cuda
   // four of 128; one element per thread, so the 64^3 mesh is three full waves
   const int64_t blocks = (E + 95) / 96;
   elem_kernel<<<(unsigned)(blocks < 0x7fffffffLL ? blocks : 0x7fffffffLL), 96, 0,
-                (cudaStream_t)cuda_stream>>>(*s);
+                (cudaStream_t)cuda_stream>>>(*s, make_fastdiv(s->n));
   HPAC_CUDA_TRY(cudaGetLastError());
   return HPAC_OK;
 }
