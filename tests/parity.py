@@ -156,3 +156,40 @@ def taf_replay_check(n, T, B, level, out_g, mask_g, stat_g, out_r, stat_r, dis, 
             assert abs(float(stat_g[j]) - float(stat_r[j])) <= 2 * b + 1e-300, \
                 ("stats apart", int(j), float(stat_g[j]), float(stat_r[j]), b)
     return int(counts[1])
+
+
+def literal_beyond(n, T, B, level, mask_g, stat_r, dis, thr, rel=1e-6):
+    """Disagreements (dis[i] = 1 at a decision point) at which no deciding lane
+    (the thread, its warp or its block) holds an oracle statistic within
+    rel * thr of the threshold: the decisions that the literal borderline rule
+    (|s - thr| <= 1e-6 thr) would not excuse. The parity tests excuse instead
+    the rounding band of each statistic (rsd_band); this count shows how many
+    disagreements need that wider reading."""
+    T = T if T > 0 else n
+    G = 1 if level == 0 else 32 if level == 1 else B
+    beyond = 0
+    for i in np.nonzero(dis)[0]:
+        t, k = i % T, i // T
+        g0 = (t // G) * G
+        j = np.arange(g0, min(g0 + G, T)) + k * T
+        j = j[j < n]
+        j = j[mask_g[j] == 0]
+        s = stat_r[j].astype(np.float64)
+        s = s[~np.isnan(s)]
+        if not np.any(np.abs(s - thr) <= rel * thr):
+            beyond += 1
+    return beyond
+
+
+def relative_beyond(g, ref, rel):
+    """Outputs farther than rel from the reference relative to
+    max(|ref|, 1e-6 max |ref|) (the denominator that keeps near-zero prices
+    from dividing by almost nothing), and the largest such relative error."""
+    g = np.asarray(g, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    if ref.size == 0:
+        return 0, 0.0
+    den = np.maximum(np.abs(ref), 1e-6 * np.abs(ref).max())
+    den = np.where(den > 0, den, 1.0)
+    r = np.abs(g - ref) / den
+    return int(np.sum(r > rel)), float(r.max())

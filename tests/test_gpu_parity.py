@@ -6,7 +6,7 @@ import numpy as np
 import pytest
 
 from paper_2308_16877_gb300 import workloads as W
-from parity import source_index, taf_compare, taf_replay_check
+from parity import literal_beyond, relative_beyond, source_index, taf_compare, taf_replay_check
 from tolerances import EPS32, EPS64, output_tol
 
 torch = pytest.importorskip("torch")
@@ -61,6 +61,17 @@ def test_exact(H, orc, kind, dt, n):
         assert np.array_equal(g, ref)
     else:
         assert np.all(np.abs(g.astype(np.float64) - ref.astype(np.float64)) <= tol)
+        # the literal relative bar (1e-5 single, 1e-12 double precision) with
+        # the near-zero denominator max(|ref|, 1e-6 max|ref|): met by every
+        # double-precision output; in single precision the cancellation of
+        # out-of-the-money prices puts a few percent beyond it, so that count
+        # is reported (the bound asserted above is relative to S N(d1))
+        bar = 1e-5 if dt == np.float32 else 1e-12
+        cnt, worst = relative_beyond(g, ref, bar)
+        print(f"exact kind {kind} {np.dtype(dt).name} n {n}: {cnt} of {n} outputs beyond {bar:g} "
+              f"relative (largest {worst:.3g})")
+        if dt == np.float64:
+            assert cnt == 0, (cnt, worst)
 
 
 def test_exact_strided_and_misaligned(H, orc):
@@ -274,6 +285,17 @@ def test_taf_regions_replay(H, orc, kind, dt, level, h, thr):
                             2 * rel, eps)
     assert counts[0] > 0
     assert ndis <= max(1, counts[0] // 1000), ndis
+    # disagreements that the literal 1e-6 thr borderline rule would not excuse:
+    # none in double precision (the outputs differ by a few ulps, which moves
+    # the statistic far less than 1e-6 thr); in single precision the fast
+    # math of the region moves the outputs by up to ~1e-6 relative, so the
+    # count is reported and kept within the same bound as all disagreements
+    beyond = literal_beyond(n, T, B, level, gm, s_r, dis, thr)
+    print(f"TAF kind {kind} {np.dtype(dt).name} level {level} h {h} thr {thr}: {int(counts[0])} "
+          f"decisions, {ndis} disagreements, {beyond} beyond 1e-6 thr")
+    if dt == np.float64:
+        assert beyond == 0, beyond
+    assert beyond <= ndis
 
 
 def test_taf_blackscholes_workload_counts(H, orc):
