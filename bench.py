@@ -1,21 +1,32 @@
 """Benchmark of the approximate-region hot path on GB300.
 
-Workload (the hydro configuration): a 64^3-element hexahedral Lagrangian-hydro
-mesh (node coordinates jittered +-5%, energy 3.9e6 in the corner element),
-FP64, 100 time steps, whose equation-of-state call is the approximated region.
-One benchmark step is the whole hot path over that batch: the run with the
-exact EOS, the run with TAF on the EOS and the run with iACT on the EOS (each
-100 time steps from the initial state: nodal update, element volume/gradient/
-viscosity, EOS region, energy update), plus the quality of each approximated
-run against the exact one (final origin energy, the paper's LULESH QoI, and the
-MAPE of the final pressure field, Eq. 1).
+Headline workload (the large hydro configuration): a 256^3-element hexahedral
+Lagrangian-hydro mesh (node coordinates jittered +-5%, energy 3.9e6 in the
+corner element), FP64, 200 time steps, whose equation-of-state (EOS) call is
+the approximated region. Before timing, every candidate form of the EOS
+(TAF and iACT with state scoped to one launch, and with windows / tables kept
+across time steps) runs once and is scored against the exact run: the error
+of the final origin energy (the paper's LULESH quantity of interest) and the
+normalised RMSE of the final pressure field, ||p - p_exact|| / ||p_exact||
+(the exact pressure is zero outside the blast, so this is the error on the
+elements the blast reached). A form qualifies when both are <= 1% and it
+approximates at least 10% of the active invocations: the EOS calls of
+elements that carry energy at that step in the exact run (elsewhere the EOS
+returns zero, and predicting there says nothing about the method). The
+fastest qualifying form is the headline.
 
-`value` is element updates per second over the step (3 runs x 64^3 elements x
-100 time steps / step time). `speedup_vs_exact` gives the run-level and
-EOS-region-level speedup of each technique on the same GPU, `roofline` covers
-the dominant kernel (the FP64-bound element kernel), `cpu_baseline` the CPU
-oracle on a bounded sample of the same workload. A secondary section times the
-single-precision Black-Scholes region passes (exact, perforation, TAF, iACT).
+One benchmark step is one run of that form from the initial state (200 time
+steps: nodal update, element volume / gradient / viscosity, the EOS region
+under the technique, energy update) plus its quality against the stored exact
+result. `value` is element updates per second of the whole run (E x 200 per
+step); `speedup_vs_exact` gives the run-level and EOS-region-level speedup
+against the exact run on the same GPU; `roofline` covers the dominant kernel
+(the FP64-bound element kernel) and `kernels` every exact kernel's roofline
+fraction; `cpu_baseline` is the CPU oracle on a bounded sample of the same run.
+Every other configuration (Black-Scholes at 65,536 and 2^24 options, the
+64^3 hydro run, the batched knob sweep, the surrogate, the NEXT rows) is a
+section printed on its own line before the final one, and the whole record is
+written to gpurun_out/bench_detail.json.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
@@ -45,9 +56,13 @@ from paper_2308_16877_gb300 import workloads as W  # noqa: E402
 METRIC = "region elements/s and speedup vs exact kernel on 1 GB300 at <=1% quality loss"
 GAMMA = 5.0 / 3.0
 
-HYDRO_N = 64
+HEAD_N = 256                                    # headline mesh: 256^3 elements
+HEAD_STEPS = 200
+HYDRO_N = 64                                    # the 64^3 x 100-step configuration
 HYDRO_STEPS = 100
-HYDRO_IPT = 8                                   # EOS items per logical thread
+HYDRO_IPT = 8                                   # EOS items per logical thread (kernel-scoped state)
+QUALITY_BOUND = 0.01                            # <= 1% quality loss
+MIN_ACTIVE_APPROX = 0.10                        # share of active invocations a headline form approximates
 TAF = dict(hsize=4, psize=8, thresh=0.005, level=0)
 IACT = dict(tsize=8, tperwarp=32, thresh=1e-3, level=0)
 # iACT input normalisation: energy by the initial corner energy, relative
@@ -55,22 +70,51 @@ IACT = dict(tsize=8, tperwarp=32, thresh=1e-3, level=0)
 # corner pressure.
 IACT_SCALE = (1.0 / W.HYDRO_E0, 1.0, 10.0, 1.0 / ((GAMMA - 1.0) * W.HYDRO_E0))
 
+# Candidate forms of the EOS region for the headline: (name, technique
+# (1 TAF, 2 iACT), state kept across time steps, knobs). Kept state uses one
+# logical thread per element (T = E), so a thread's window or a warp's tables
+# follow the same elements from step to step; launch-scoped state uses
+# T = E / 8 (8 elements per thread within a step).
+HEAD_FORMS = [
+    ("taf h4 p8 0.5%", 1, False, dict(hsize=4, psize=8, thresh=0.005, level=0)),
+    ("iact t8 g32 1e-3", 2, False, dict(tsize=8, tperwarp=32, thresh=1e-3, level=0)),
+    ("taf kept h2 p2 0.1%", 1, True, dict(hsize=2, psize=2, thresh=0.001, level=0)),
+    ("taf kept h4 p8 0.5%", 1, True, dict(hsize=4, psize=8, thresh=0.005, level=0)),
+    ("iact kept t8 g1 1e-3", 2, True, dict(tsize=8, tperwarp=1, thresh=1e-3, level=0)),
+    ("iact kept t4 g4 1e-3", 2, True, dict(tsize=4, tperwarp=4, thresh=1e-3, level=0)),
+    ("iact kept t2 g32 1e-4", 2, True, dict(tsize=2, tperwarp=32, thresh=1e-4, level=0)),
+    ("iact kept t8 g32 1e-3", 2, True, dict(tsize=8, tperwarp=32, thresh=1e-3, level=0)),
+]
+
 # FP64 operations of the element kernel per element, each add, multiply or FMA
 # one issue slot of the FP64 pipe: 15 shared corner-pair cross products (90),
 # their 42 scatters less 7 first assignments (105 adds), 3 single-use pairs as
 # fused multiply-adds (18), 21 relative-position subtractions, 18 corner-0
 # sums, 8 for the volume, 1 for dv, and 2 for v = V / V0 formed as a comparison
-# with V0 and a product with the stored 1 / V0. Its
-# ceiling, in the same unit (FP64 instructions per lane per second), is the
-# FP64 issue rate of the part: the nominal 1.25 TFLOP/s of GB300 at 152 SMs and
-# 2070 MHz is 1.25e12 / (2 x 152 x 2.07e9) = 1.99, i.e. 2 FP64 FMA per SM per
-# clock, taken at the SM count of the device and the median SM clock sampled
-# under load. The FMA rate that the library's probe measures in the same run is
-# reported beside it.
+# with V0 and a product with the stored 1 / V0. Its ceiling, in the same unit
+# (FP64 instructions per lane per second), is the FP64 issue rate of the part:
+# the nominal 1.25 TFLOP/s of GB300 at 152 SMs and 2070 MHz is
+# 1.25e12 / (2 x 152 x 2.07e9) = 1.99, i.e. 2 FP64 FMA per SM per clock, taken
+# at the SM count of the device and the median SM clock sampled under load.
+# The FMA rate that the library's probe measures in the same run is reported
+# beside it.
 ELEM_OPS = 90 + 105 + 18 + 21 + 18 + 8 + 1 + 2
 FP64_FMA_PER_SM_CLK = 2
+# EOS closed form per element: v_n, (g-1) e, the numerator N (e v_n, 2 q v_n,
+# the sum, 0.5 dv times it, the difference: 6), the denominator (3), (g-1) N
+# and the clamp test: 14 FP64 operations and one IEEE division, which GB300
+# carries out as a sequence of FP64 instructions. EOS_DIV_OPS is that
+# sequence's share as ncu's FP64 instruction counters measure it on the exact
+# EOS kernel (27.3 FP64 instructions per element, less the 14 above).
+EOS_OPS = 14
+EOS_DIV_OPS = 13.3
+# The node kernel's FP64 work per node: 24 corner-force FMAs and 6 for the
+# velocity and position updates (30.4 measured per node, boundary nodes having
+# fewer elements); it runs the FP64 pipe and HBM near their limits at once.
+NODE_OPS = 30
 
 BS_N = 1 << 24
+BS_CFG0_N = 65536
 BS_TAF = dict(hsize=4, psize=8, thresh=0.005, level=0)
 BS_PERFO = dict(kind=0, m_or_percent=4, herded=True)
 BS_IACT = dict(tsize=8, tperwarp=32, thresh=0.05, level=1)
@@ -78,6 +122,17 @@ BS_IACT = dict(tsize=8, tperwarp=32, thresh=0.05, level=1)
 KERNEL_SOURCES = {"map_kernel": ["exact_perfo.cu", "regions.cuh"], "taf_kernel": ["taf.cu", "regions.cuh"],
                   "iact_kernel": ["iact.cu", "regions.cuh"], "elem_kernel": ["hydro.cu"],
                   "node_kernel": ["hydro.cu"]}
+
+
+def sig(x, k=4):
+    """x rounded to k significant digits (floats), for the compact line."""
+    if isinstance(x, float):
+        return float(f"{x:.{k}g}") if np.isfinite(x) else None
+    if isinstance(x, dict):
+        return {a: sig(b, k) for a, b in x.items()}
+    if isinstance(x, (list, tuple)):
+        return [sig(b, k) for b in x]
+    return x
 
 
 def aggregate(total_ms, units_per_rank, world, device=None):
@@ -149,7 +204,7 @@ class ClockSampler:
         if not sm:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
         return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons),
-                "samples": len(sm), "window": "1 s pre-heat + timed region + 0.5 s"}
+                "samples": len(sm)}
 
 
 def source_digest(tag):
@@ -161,8 +216,9 @@ def source_digest(tag):
 
 
 def dram_traffic(tag, units):
-    """DRAM bytes (read + write) per launch, scaled from the ncu capture in
-    profiles/dram_traffic.txt; None when the kernel's sources changed since."""
+    """DRAM bytes (read + write) per launch from the ncu record in
+    profiles/dram_traffic.txt (bytes per unit, scaled to `units`); None when
+    the kernel's sources changed since the capture or no record exists."""
     p = os.path.join(ROOT, "profiles", "dram_traffic.txt")
     if not os.path.exists(p):
         return None
@@ -173,64 +229,99 @@ def dram_traffic(tag, units):
     return None
 
 
-def measured_hbm():
+def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
         with open(p) as f:
-            return json.load(f).get("hbm_gbs", 6800.0), "measured"
+            d = json.load(f)
+        return float(d.get("hbm_gbs", 6800.0)), "measured"
     return 6800.0, "fallback"
+
+
+def measured_hbm():
+    return measured_peaks()
+
+
+def timed_ms(torch, stream, f, reps):
+    """Mean CUDA-event time of f() on `stream` over reps calls after one warm call."""
+    f()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(reps):
+        f()
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / reps
 
 
 # ---------------------------------------------------------------- CPU oracle
 
-def hydro_cpu(n=HYDRO_N, steps=25, single_steps=0):
-    """The oracle on the same mesh: exact, TAF and iACT runs of `steps` time
-    steps (a bounded sample of the 100-step workload)."""
+def form_oracle_knobs(oracle, form, n):
+    """The oracle's EOS knobs for a headline form (None: exact)."""
+    if form is None:
+        return None
+    name, tech, kept, kn = form
+    E = n ** 3
+    T = E if kept else E // HYDRO_IPT
+    if tech == 1:
+        return oracle.eos_knobs(oracle.EOS_TAF, hsize=kn["hsize"], psize=kn["psize"], thresh=kn["thresh"],
+                                level=kn["level"], threads=T, block=256, persistent=kept, n=n)
+    return oracle.eos_knobs(oracle.EOS_IACT, tsize=kn["tsize"], tperwarp=kn["tperwarp"], thresh=kn["thresh"],
+                            level=kn["level"], threads=T, block=256, in_scale=IACT_SCALE, persistent=kept, n=n)
+
+
+_INITIAL = {}                                   # initial meshes by size (generated once)
+
+
+def hydro_cpu(form, n=HEAD_N, steps=4, single_steps=0):
+    """The oracle on the same mesh and EOS form: `steps` time steps from the
+    initial state (a bounded sample of the 200-step run); element updates per
+    second on all host cores, and on one core for `single_steps` steps."""
     import oracle
-    x, y, z, e = W.hydro_initial(n)
+    if n not in _INITIAL:
+        _INITIAL[n] = W.hydro_initial(n)
+    x, y, z, e = _INITIAL[n]
     dt = W.hydro_dt(n)
     E = n ** 3
-    T = E // HYDRO_IPT
-    knobs = [None,
-             oracle.eos_knobs(oracle.EOS_TAF, hsize=TAF["hsize"], psize=TAF["psize"],
-                              thresh=TAF["thresh"], level=TAF["level"], threads=T, block=256),
-             oracle.eos_knobs(oracle.EOS_IACT, tsize=IACT["tsize"], tperwarp=IACT["tperwarp"],
-                              thresh=IACT["thresh"], level=IACT["level"], threads=T, block=256,
-                              in_scale=IACT_SCALE)]
+
     def timed(nsteps):
+        S = oracle.HydroState(n, x, y, z, e)
+        k = form_oracle_knobs(oracle, form, n)
         t0 = time.perf_counter()
-        for k in knobs:
-            S = oracle.HydroState(n, x, y, z, e)
-            for _ in range(nsteps):
-                S.step(dt, k)
+        for _ in range(nsteps):
+            S.step(dt, k)
         return time.perf_counter() - t0
 
     cores = oracle.num_threads()
     dt_s = timed(steps)
-    out = {"value": 3 * E * steps / dt_s, "unit": "elements/s", "cores": cores, "kind": "oracle",
-           "sample": f"{n}^3 mesh, exact + TAF + iACT runs of {steps} time steps each",
-           "seconds": dt_s}
+    label = form[0] if form is not None else "exact EOS"
+    out = {"value": E * steps / dt_s, "unit": "elements/s", "cores": cores, "kind": "oracle",
+           "sample": f"{n}^3 mesh, {label}, first {steps} of the time steps", "seconds": dt_s}
     if single_steps:
         oracle.set_threads(1)
         try:
             t1 = timed(single_steps)
         finally:
             oracle.set_threads(cores)
-        out["single_thread"] = {"value": 3 * E * single_steps / t1, "unit": "elements/s",
-                                "sample": f"exact + TAF + iACT runs of {single_steps} time steps each"}
+        out["single_thread"] = {"value": E * single_steps / t1, "unit": "elements/s",
+                                "sample": f"first {single_steps} time step(s), one core"}
     return out
 
 
 def run_reference(args):
+    """The reference arm: the CPU oracle (there is no reference implementation
+    of this paper to install) on bounded samples of the headline workload."""
     rank, world, _ = env_rank()
     if rank != 0:
         return 0
     import oracle
     oracle.lib()
-    times, per = [], None
+    form = next(f for f in HEAD_FORMS if f[0] == args.reference_form)
+    times, per, cores = [], None, oracle.num_threads()
     for i in range(args.warmup + args.steps):
-        cb = hydro_cpu(steps=5)
-        per = 3 * HYDRO_N ** 3 * 5
+        cb = hydro_cpu(form, n=args.n, steps=1)
+        per = args.n ** 3
         if i >= args.warmup:
             times.append(cb["seconds"])
     v = per * len(times) / sum(times)
@@ -238,18 +329,17 @@ def run_reference(args):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"hydro {HYDRO_N}^3 hex mesh, exact + TAF + iACT EOS runs "
-                                   "(bounded CPU sample: 5 time steps per run)",
+            "config": {"workload": f"hydro {args.n}^3 hex mesh, EOS under {form[0]} (bounded CPU sample: "
+                                   "the first time step of the run per bench step)",
                        "parallelism": "oracle on host cores"},
-            "cpu_baseline": {"value": v, "unit": "elements/s", "cores": oracle.num_threads(),
-                             "kind": "oracle", "sample": "3 runs x 5 time steps of the 64^3 mesh"},
-            "e2e": {"value": v, "unit": "elements/s", "h2d_bytes_per_step": 0,
-                    "d2h_bytes_per_step": 0}}
+            "cpu_baseline": {"value": v, "unit": "elements/s", "cores": cores, "kind": "oracle",
+                             "sample": f"first time step of the {args.n}^3 run, {form[0]}"},
+            "e2e": {"value": v, "unit": "elements/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
 
 
-# ---------------------------------------------------------------- GPU arm
+# ---------------------------------------------------------------- GPU sections
 
 def bench_blackscholes(hpac, torch, dev, stream, reps=20):
     """Single-precision Black-Scholes region passes on 2^24 options (inputs
@@ -295,6 +385,8 @@ def bench_blackscholes(hpac, torch, dev, stream, reps=20):
     R.close()
     return {"options": n, "pass_ms": ms, "speedup_vs_exact": {k: ms["exact"] / v for k, v in ms.items()},
             "exact_gbs": gbs, "exact_hbm_frac": gbs / peak, "hbm_peak_source": src,
+            "kernel_row": {"bound": "hbm", "ms": ms["exact"], "bytes": 20 * n, "peak": peak * 1e9,
+                           "unit": "B/s", "achieved": gbs * 1e9, "frac": gbs / peak},
             "quality": q, "approximated": stats,
             "note": "MAPE is dominated by options whose exact price is below single-precision "
                     "resolution; NRMSE = RMSE / RMS(exact price)"}
@@ -616,20 +708,6 @@ def bench_levels(hpac, torch, dev, stream, n=1 << 22, clusters=64, reps=5):
             "exact_ms": exact_ms, "table": rows}
 
 
-def calibrate_floor(pred, exact, target=0.01, q=0.99):
-    """Smallest price floor tau such that, among predictions >= tau, the q-th
-    quantile of the relative error |pred - exact| / |exact| is at most target."""
-    order = np.argsort(pred)[::-1]                  # largest predictions first
-    rel = np.abs(pred[order] - exact[order]) / np.maximum(np.abs(exact[order]), 1e-30)
-    # running q-quantile over growing prefixes, on a grid of prefix sizes
-    best = None
-    for frac in np.linspace(0.02, 1.0, 50):
-        k = max(1, int(frac * len(order)))
-        if np.quantile(rel[:k], q) <= target:
-            best = float(pred[order][k - 1])
-    return best if best is not None else float("inf")
-
-
 def bench_surrogate(hpac, torch, dev, stream, n_train=1 << 22, n_cal=1 << 20, n_inf=1 << 24,
                     epochs=24, batch=8192, lr=3e-3):
     """The learned surrogate of the Black-Scholes region: trained by the
@@ -659,7 +737,7 @@ def bench_surrogate(hpac, torch, dev, stream, n_train=1 << 22, n_cal=1 << 20, n_
     pc = torch.zeros(n_cal, dtype=torch.float32, device=dev)
     S.infer(xc, pc, W.BS_RATE)
     yc = exact(xc, torch.float64)
-    tau = calibrate_floor(pc.cpu().numpy().astype(np.float64), yc.cpu().numpy())
+    tau, kept = hpac.calibrate_floor(pc, yc, 0.01, 0.99, stream=stream)
     # inference with fallback vs the exact kernel
     out = torch.zeros(n_inf, dtype=torch.float32, device=dev)
     mask = torch.zeros(n_inf, dtype=torch.uint8, device=dev)
@@ -695,7 +773,7 @@ def bench_surrogate(hpac, torch, dev, stream, n_train=1 << 22, n_cal=1 << 20, n_
     return {
         "train": {"pairs": n_train, "epochs": epochs, "batch": batch, "ms": train_ms,
                   "samples_per_s": n_train * epochs / (train_ms * 1e-3), "final_mse_normalized": loss},
-        "calibrated_floor": tau,
+        "calibrated_floor": tau, "calibration_served": kept / n_cal,
         "inference": {"options": n_inf, "ms": sur_ms, "ms_without_fallback": nofb_ms,
                       "exact_kernel_ms": exact_ms, "speedup_vs_exact": exact_ms / sur_ms,
                       "surrogate_fraction": st["approximated"] / n_inf,
@@ -753,105 +831,6 @@ def eos_region_sweep(hpac, torch, stream, eos_h, eos_in, ref, scale_arr, n_confi
     ok = [r for r in table if r["p_nrmse"] <= 0.01]
     best = max(ok, key=lambda r: r["speedup"]) if ok else None
     return {"configs": len(table), "exact_region_ms": t_exact, "best_within_1pct": best, "table": table}
-
-
-def bench_hydro_large(hpac, torch, dev, stream, n=256, nsteps=200, train_pairs=1 << 22, epochs=16,
-                      sweep_configs=64):
-    """The large hydro configuration: a 256^3 mesh for 200 time steps with the
-    EOS exact, under TAF, under iACT and replaced by a learned surrogate
-    (4 -> 128 -> 128 -> 1, trained on EOS pairs recorded from the exact run),
-    plus a 64-configuration knob sweep of the EOS region at mid-run."""
-    x, y, z, e = W.hydro_initial(n)
-    dt = W.hydro_dt(n)
-    E = n ** 3
-    T = E // HYDRO_IPT
-    Hy = hpac.Hydro(n, x, y, z, e, dt, logical_threads=T, block_threads=256, stream=stream)
-    sh = stream.cuda_stream
-    torch.cuda.synchronize()
-    init = {k: v.clone() for k, v in Hy.t.items()}
-    scale_arr = (hpac.C.c_double * 4)(*IACT_SCALE)
-    taf_k = hpac.hpac_taf_knobs(TAF["hsize"], TAF["psize"], TAF["thresh"], TAF["level"], 0)
-    iact_k = hpac.hpac_iact_knobs(IACT["tsize"], IACT["tperwarp"], IACT["thresh"], IACT["level"], 0,
-                                  hpac.C.cast(scale_arr, hpac.C.POINTER(hpac.C.c_double)))
-    eos_h = Hy.eos._h
-    eos_ptr, p_ptr = hpac.C.c_void_p(Hy["eos_in"].data_ptr()), hpac.C.c_void_p(Hy["p"].data_ptr())
-
-    def reset():
-        for k, v in init.items():
-            Hy.t[k].copy_(v)
-
-    pairs, mid = [], []
-    S = None
-
-    def run(tech, record=False):
-        reset()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        for s in range(nsteps):
-            hpac.hpac_hydro_nodes(Hy.state, sh)
-            hpac.hpac_hydro_elements(Hy.state, sh)
-            if tech == "exact":
-                hpac.hpac_run_exact(eos_h, eos_ptr, p_ptr)
-            elif tech == "taf":
-                hpac.hpac_run_taf(eos_h, taf_k, eos_ptr, p_ptr)
-            elif tech == "iact":
-                hpac.hpac_run_iact(eos_h, iact_k, eos_ptr, p_ptr)
-            else:
-                S.infer(Hy["eos_in"], Hy["p"], GAMMA)
-            if record:
-                # EOS pairs of this step: the active elements (energy, viscosity
-                # or volume change), the mid-run state kept whole for the sweep
-                ein = Hy["eos_in"]
-                act = torch.nonzero((ein[0] > 0) | (ein[3] > 0) | (ein[2] != 0)).flatten()
-                pairs.append((ein[:, act].clone(), Hy["p"][act].clone()))
-                if s + 1 == nsteps // 2:
-                    mid.append((ein.clone(), Hy["p"].clone()))
-            hpac.hpac_hydro_finalize(Hy.state, sh)
-        b.record(stream)
-        torch.cuda.synchronize()
-        return a.elapsed_time(b), Hy["e"][:1].item(), Hy["p"].clone()
-
-    res = {}
-    run("exact", record=True)           # records the EOS pairs; not timed
-    t_ex, qoi_ex, p_ex = run("exact")
-    res["exact"] = {"ms": t_ex}
-    for tech in ("taf", "iact"):
-        t, qoi, p_fin = run(tech)
-        res[tech] = {"ms": t, "speedup_vs_exact": t_ex / t, "qoi_rel_err": abs(qoi - qoi_ex) / abs(qoi_ex),
-                     "p_nrmse": float(torch.sqrt(torch.mean((p_fin - p_ex) ** 2)).item()
-                                      / torch.sqrt(torch.mean(p_ex ** 2)).item())}
-    # surrogate trained on the EOS pairs of the exact run: the active elements
-    # of every step plus as many untouched ones (inputs (0, 1, 0, 0) -> p = 0)
-    xa = torch.cat([a for a, _ in pairs], dim=1)
-    ya = torch.cat([b for _, b in pairs])
-    nq = xa.shape[1]
-    xq = torch.zeros(4, nq, dtype=torch.float64, device=dev)
-    xq[1] = 1.0
-    perm = torch.randperm(2 * nq, device=dev, generator=torch.Generator(device=dev).manual_seed(7))
-    xtr = torch.cat([xa, xq], dim=1)[:, perm][:, :train_pairs].contiguous()
-    ytr = torch.cat([ya, torch.zeros(nq, dtype=torch.float64, device=dev)])[perm][:train_pairs].float().contiguous()
-    S = hpac.Surrogate(hpac.eos_desc(128), seed=4, stream=stream)
-    S.fit_normalization(xtr, ytr, GAMMA)
-    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a.record(stream)
-    loss = S.train(xtr, ytr, GAMMA, batch=8192, epochs=epochs, lr=2e-3)
-    b.record(stream)
-    torch.cuda.synchronize()
-    t, qoi, p_fin = run("surrogate")
-    res["surrogate"] = {"ms": t, "speedup_vs_exact": t_ex / t, "qoi_rel_err": abs(qoi - qoi_ex) / abs(qoi_ex),
-                        "p_nrmse": float(torch.sqrt(torch.mean((p_fin - p_ex) ** 2)).item()
-                                         / torch.sqrt(torch.mean(p_ex ** 2)).item()),
-                        "train_pairs": int(xtr.shape[1]), "train_ms": a.elapsed_time(b),
-                        "train_mse_normalized": loss}
-    # 64-configuration EOS knob sweep on the mid-run inputs (region only)
-    ein_mid, p_mid = mid[0]
-    Hy["eos_in"].copy_(ein_mid)
-    ref = torch.zeros(E, dtype=torch.float64, device=dev)
-    hpac.hpac_run_exact(eos_h, eos_ptr, hpac.C.c_void_p(ref.data_ptr()))
-    eos_sweep = eos_region_sweep(hpac, torch, stream, eos_h, Hy["eos_in"], ref, scale_arr, sweep_configs)
-    S.close()
-    Hy.close()
-    return {"mesh": f"{n}^3", "time_steps": nsteps, "runs": res, "eos_sweep": eos_sweep}
 
 
 def bench_persistent(hpac, torch, dev, stream, n=HYDRO_N, nsteps=HYDRO_STEPS, reps=3):
@@ -921,27 +900,500 @@ def bench_persistent(hpac, torch, dev, stream, n=HYDRO_N, nsteps=HYDRO_STEPS, re
             "knobs": {"taf": "h4 p8 0.5% (and h2 p4)", "iact": "t8 g32 1e-3 scaled"}, "runs": res}
 
 
+
+
+def bench_blackscholes_cfg0(hpac, torch, dev, stream, n=BS_CFG0_N, reps=200):
+    """The 65,536-option Black-Scholes configuration: exact, herded
+    perforation small:4 and TAF (h4 p8 0.5%) at T = N / 8, each timed over 200
+    back-to-back launches (the 1.3 MB working set stays in L2, so these are
+    launch- and L2-bound figures), with the MAPE and NRMSE against the
+    double-precision exact prices. Two readings of "sorted by strike in runs
+    of 32": each aligned run of 32 consecutive options sorted (the lanes of one
+    warp step see ascending strikes), and the same runs laid along one logical
+    thread's sequence (T = N / 32, thread t's 32 invocations are run t), which
+    gives TAF the temporal order the configuration describes."""
+    xh = W.blackscholes_inputs(n)
+    T32 = n // 32
+    layouts = {"runs_across_lanes": (xh, n // 8),
+               "runs_along_threads": (np.ascontiguousarray(xh.reshape(4, T32, 32).transpose(0, 2, 1).reshape(4, n)),
+                                      T32)}
+    res = {}
+    for name, (xa, T) in layouts.items():
+        x = torch.from_numpy(xa).to(dev)
+        x64 = x.double().contiguous()
+        ref = torch.zeros(n, dtype=torch.float64, device=dev)
+        with hpac.Region(hpac.HPAC_REGION_BLACKSCHOLES, x64, param=W.BS_RATE, stream=stream) as R64:
+            R64.run_exact(x64, ref)
+        rms = float(torch.sqrt(torch.mean(ref * ref)).item())
+        outs = {k: torch.zeros(n, dtype=torch.float32, device=dev) for k in ("exact", "perfo", "taf")}
+        R = hpac.Region(hpac.HPAC_REGION_BLACKSCHOLES, x, param=W.BS_RATE, logical_threads=T,
+                        block_threads=256, stream=stream)
+        calls = {"exact": lambda: R.run_exact(x, outs["exact"]),
+                 "perfo": lambda: R.run_perfo(x, outs["perfo"], BS_PERFO["kind"], BS_PERFO["m_or_percent"],
+                                              herded=True),
+                 "taf": lambda: R.run_taf(x, outs["taf"], **BS_TAF)}
+        ms = {k: timed_ms(torch, stream, f, reps) for k, f in calls.items()}
+        st = {"perfo": R.run_perfo(x, outs["perfo"], 0, 4, herded=True, stats=True),
+              "taf": R.run_taf(x, outs["taf"], stats=True, **BS_TAF)}
+        R.close()
+        q = {k: {"mape": hpac.quality(ref, outs[k], hpac.HPAC_METRIC_MAPE, stream=stream)["value"],
+                 "nrmse": hpac.quality(ref, outs[k], hpac.HPAC_METRIC_RMSE, stream=stream)["value"] / rms}
+             for k in outs}
+        res[name] = {"logical_threads": T, "launch_ms": ms,
+                     "speedup_vs_exact": {k: ms["exact"] / v for k, v in ms.items()},
+                     "approximated": {k: v["approximated"] / n for k, v in st.items()},
+                     "skipped": st["perfo"]["skipped"] / n, "quality": q,
+                     "exact_options_per_s": n / (ms["exact"] * 1e-3)}
+    hbm, _ = measured_peaks()
+    ex = res["runs_across_lanes"]["launch_ms"]["exact"]
+    return {"options": n, "layouts": res,
+            "kernel_row": {"bound": "hbm", "ms": ex, "bytes": 20 * n, "peak": hbm * 1e9, "unit": "B/s",
+                           "achieved": 20 * n / (ex * 1e-3), "frac": 20 * n / (ex * 1e-3) / (hbm * 1e9),
+                           "note": "1.3 MB working set: L2-resident and launch-bound"}}
+
+
+# ---------------------------------------------------------------- headline
+
+class HydroBench:
+    """The hydro state at one mesh size with two EOS regions: launch-scoped
+    state (T = E / 8) and state kept across time steps (T = E)."""
+
+    def __init__(self, hpac, torch, dev, stream, n, nsteps, seed):
+        self.hpac, self.torch, self.stream, self.sh = hpac, torch, stream, stream.cuda_stream
+        self.n, self.nsteps, self.E = n, nsteps, n ** 3
+        self.x, self.y, self.z, self.e = W.hydro_initial(n, seed=seed)
+        self.dt = W.hydro_dt(n)
+        self.Hy = hpac.Hydro(n, self.x, self.y, self.z, self.e, self.dt, logical_threads=self.E // HYDRO_IPT,
+                             block_threads=256, stream=stream)
+        self.kept = hpac.Region(hpac.HPAC_REGION_EOS, self.Hy["eos_in"], param=GAMMA, logical_threads=self.E,
+                                block_threads=256, stream=stream)
+        torch.cuda.synchronize()
+        self.init = {k: v.clone() for k, v in self.Hy.t.items()}
+        self.scale = (hpac.C.c_double * 4)(*IACT_SCALE)
+        self.eos_ptr = hpac.C.c_void_p(self.Hy["eos_in"].data_ptr())
+        self.p_ptr = hpac.C.c_void_p(self.Hy["p"].data_ptr())
+
+    def knobs(self, form):
+        hp = self.hpac
+        name, tech, kept, kn = form
+        if tech == 1:
+            return hp.hpac_taf_knobs(kn["hsize"], kn["psize"], kn["thresh"], kn["level"], 0)
+        return hp.hpac_iact_knobs(kn["tsize"], kn["tperwarp"], kn["thresh"], kn["level"], 0,
+                                  hp.C.cast(self.scale, hp.C.POINTER(hp.C.c_double)))
+
+    def region(self, form):
+        return self.kept if (form is not None and form[2]) else self.Hy.eos
+
+    def reset(self, form):
+        for k, v in self.init.items():
+            self.Hy.t[k].copy_(v, non_blocking=True)
+        self.Hy.eos.set_persistent(False)
+        if form is not None and form[2]:
+            self.kept.set_persistent(True)
+            self.kept.reset_state()
+        else:
+            self.kept.set_persistent(False)
+
+    def run(self, form, elem_ev=None, region_ev=None, mask=None, count=None, record=None):
+        """One run from the initial state. elem_ev / region_ev: lists of event
+        pairs (one per time step) around the element kernel / the region call;
+        record: a list that receives, per time step, the indices of the
+        elements whose EOS input carries energy; mask + count (with the exact
+        run's record as count[3]): per-step counts of those elements and of
+        the ones this run approximates."""
+        hp, sh = self.hpac, self.sh
+        self.reset(form)
+        R = self.region(form)
+        k = self.knobs(form) if form is not None else None
+        tech = form[1] if form is not None else 0
+        st = self.stream
+        for s in range(self.nsteps):
+            hp.hpac_hydro_nodes(self.Hy.state, sh)
+            if elem_ev is not None:
+                elem_ev[s][0].record(st)
+            hp.hpac_hydro_elements(self.Hy.state, sh)
+            if elem_ev is not None:
+                elem_ev[s][1].record(st)
+            if region_ev is not None:
+                region_ev[s][0].record(st)
+            m = hp.C.c_void_p(mask.data_ptr()) if mask is not None else None
+            if tech == 0:
+                hp.hpac_run_exact(R._h, self.eos_ptr, self.p_ptr)
+            elif tech == 1:
+                hp.hpac_run_taf(R._h, k, self.eos_ptr, self.p_ptr, m)
+            else:
+                hp.hpac_run_iact(R._h, k, self.eos_ptr, self.p_ptr, m)
+            if region_ev is not None:
+                region_ev[s][1].record(st)
+            if record is not None:
+                record.append(torch_nonzero(self.Hy["eos_in"][0] > 0))
+            if count is not None:
+                act = count[3][s]
+                count[0] += act.numel()
+                count[1] += (mask[act] == 1).sum()
+                count[2] += (mask == 1).sum()
+            hp.hpac_hydro_finalize(self.Hy.state, sh)
+
+    def close(self):
+        self.kept.close()
+        self.Hy.close()
+
+
+def torch_nonzero(b):
+    return b.nonzero().flatten()
+
+
+def events(torch, n):
+    return [[torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)] for _ in range(n)]
+
+
+def bench_headline(hpac, torch, dev, stream, args, world, rank, clk):
+    """Selection of the headline form, then K timed steps of it (see the
+    module docstring), the exact run's time for the speedup, the element
+    kernel's roofline inside the timed region and the end-to-end run through
+    the public API with host buffers."""
+    HB = HydroBench(hpac, torch, dev, stream, args.n, args.time_steps, W.DEFAULT_SEED + rank)
+    E, nsteps = HB.E, HB.nsteps
+    sh = stream.cuda_stream
+    # exact reference: final pressure, origin energy, the elements carrying
+    # energy at each step's EOS call (the blast's reach), the exact run's time
+    active = []
+    HB.run(None, record=active)
+    torch.cuda.synchronize()
+    reg_ev = events(torch, nsteps)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    exact_ms, exact_region_ms = [], []
+    for rep in range(args.exact_reps):
+        a.record(stream)
+        HB.run(None, region_ev=reg_ev)
+        b.record(stream)
+        torch.cuda.synchronize()
+        exact_ms.append(a.elapsed_time(b))
+        exact_region_ms.append(sum(e0.elapsed_time(e1) for e0, e1 in reg_ev))
+    p_ex = HB.Hy["p"].clone()
+    qoi_ex = float(HB.Hy["e"][0].item())
+    p_rms = float(torch.sqrt(torch.mean(p_ex * p_ex)).item())
+    t_ex = float(np.median(exact_ms))
+    t_ex_region = float(np.median(exact_region_ms))
+
+    def quality():
+        r = hpac.quality(p_ex, HB.Hy["p"], hpac.HPAC_METRIC_RMSE, stream=stream)["value"]
+        q = float(HB.Hy["e"][0].item())
+        nrmse = r / p_rms if p_rms > 0 else 0.0
+        return {"qoi_rel_err": abs(q - qoi_ex) / abs(qoi_ex), "p_nrmse": nrmse}
+
+    # selection: one timed run and the quality of every candidate form
+    table = []
+    mask = torch.zeros(E, dtype=torch.uint8, device=dev)
+    for form in HEAD_FORMS:
+        a.record(stream)
+        HB.run(form, region_ev=reg_ev)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b)
+        rms = sum(e0.elapsed_time(e1) for e0, e1 in reg_ev)
+        q = quality()
+        ok = all(np.isfinite(v) and v <= QUALITY_BOUND for v in q.values())
+        table.append(dict(form=form[0], ms=ms, speedup=t_ex / ms, region_ms=rms,
+                          region_speedup=t_ex_region / rms, **q, within_bound=bool(ok)))
+    # approximated share of the active invocations (elements that carry
+    # energy at that step's EOS call in the exact run), for every form within
+    # the bound; the fastest approximating at least MIN_ACTIVE_APPROX of them
+    # is the headline (if none does, the one approximating the largest share)
+    for row in table:
+        if not row["within_bound"]:
+            continue
+        form = next(f for f in HEAD_FORMS if f[0] == row["form"])
+        cnt = [torch.zeros((), dtype=torch.int64, device=dev) for _ in range(3)] + [active]
+        HB.run(form, mask=mask, count=cnt)
+        act, apx_act, apx = (int(c.item()) if hasattr(c, "item") else int(c) for c in cnt[:3])
+        row.update(active_invocations=act / (E * nsteps), approx_active=apx_act / max(act, 1),
+                   approx_all=apx / (E * nsteps))
+    ok = [r for r in table if r["within_bound"]]
+    qual = [r for r in ok if r["approx_active"] >= MIN_ACTIVE_APPROX]
+    best = min(qual, key=lambda r: r["ms"]) if qual else max(ok, key=lambda r: (r["approx_active"], -r["ms"]))
+    best["qualifies"] = bool(qual)
+    del active
+    form = next(f for f in HEAD_FORMS if f[0] == best["form"])
+    vacuous = min((r for r in table if r["within_bound"]), key=lambda r: r["ms"])
+
+    # timed steps: warm-up, then K runs with their quality, the element kernel
+    # timed by events inside every run
+    for _ in range(args.warmup):
+        HB.run(form)
+        quality()
+    torch.cuda.synchronize()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    elem_ev = [events(torch, nsteps) for _ in range(args.steps)]
+    q_dev = torch.zeros(args.steps, dtype=torch.float64, device=dev)
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    start.record(stream)
+    quals = []
+    for s in range(args.steps):
+        HB.run(form, elem_ev=elem_ev[s])
+        r = hpac.quality(p_ex, HB.Hy["p"], hpac.HPAC_METRIC_RMSE, stream=stream)
+        q_dev[s] = HB.Hy["e"][0]
+        quals.append(r["value"])
+    stop.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    total_ms, _ = aggregate(start.elapsed_time(stop), 1, world, dev)
+    ms_per_step = total_ms / args.steps
+    value = world * E * nsteps / (ms_per_step * 1e-3)
+    elem_ms = float(np.mean([e0.elapsed_time(e1) for s in range(args.steps) for e0, e1 in elem_ev[s]]))
+    qoi_t = q_dev.cpu().numpy()
+    timed_quality = {"qoi_rel_err": float(np.max(np.abs(qoi_t - qoi_ex)) / abs(qoi_ex)),
+                     "p_nrmse": float(max(quals)) / p_rms}
+
+    # end to end through the public API with host buffers: the initial mesh
+    # from pinned host memory, hpac_hydro_init, the run under the form
+    # (hpac_hydro_run), the final energy field back to the host
+    pin = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory() for k, v in
+           (("x", HB.x), ("y", HB.y), ("z", HB.z), ("e", HB.e))}
+    e_out = torch.empty(E, dtype=torch.float64).pin_memory()
+    h2d = sum(int(v.numel() * 8) for v in pin.values())
+    R = HB.region(form)
+    k = HB.knobs(form)
+
+    def e2e_once():
+        HB.reset(form)
+        for key, v in pin.items():
+            HB.Hy.t[key].copy_(v, non_blocking=True)
+        hpac.hpac_hydro_init(HB.Hy.state, sh)
+        hpac.hpac_hydro_run(HB.Hy.state, R._h, nsteps, form[1], k)
+        e_out.copy_(HB.Hy["e"], non_blocking=True)
+
+    e2e_ms = timed_ms(torch, stream, e2e_once, args.e2e_reps)
+    e2e = {"value": world * E * nsteps / (e2e_ms * 1e-3), "unit": "elements/s",
+           "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": int(E * 8)}
+
+    # the element kernel's roofline (FP64 issue) in the timed region
+    fp64_tflops = hpac.hpac_device_fp64_rate(sh)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    cs = clk.summary()
+    mhz = cs["sm_mhz"] or cs["sm_max_mhz"] or 2070.0
+    peak = FP64_FMA_PER_SM_CLK * sms * mhz * 1e6 / 1e12
+    achieved = ELEM_OPS * E / (elem_ms * 1e-3) / 1e12
+    roofline = {"bound": "alu", "kernel": "elem_kernel", "achieved": achieved, "peak": peak,
+                "unit": "T FP64-ops/s", "frac": achieved / peak,
+                "peak_source": f"derived: {FP64_FMA_PER_SM_CLK} FP64 FMA/SM/clk x {sms} SMs x {mhz:.0f} MHz",
+                "frac_of_measured_fma": achieved / (fp64_tflops / 2.0),
+                "traffic": dram_traffic("elem_kernel", E), "launch_ms": elem_ms}
+    n_launch = args.steps * (nsteps * 4 + 2)      # node, elem, region, finalize; quality: 2
+    detail = {"mesh": f"{args.n}^3", "time_steps": nsteps, "form": form[0], "exact_ms": t_ex,
+              "exact_region_ms": t_ex_region, "selection": table, "best": best,
+              "fastest_within_bound": vacuous["form"], "timed_quality": timed_quality,
+              "fp64_fma_tflops_measured": fp64_tflops}
+    out = dict(value=value, ms_per_step=ms_per_step, form=form, best=best, t_ex=t_ex,
+               t_ex_region=t_ex_region, e2e=e2e, roofline=roofline, gpu_launches=n_launch,
+               detail=detail, timed_quality=timed_quality)
+    return out, HB
+
+
+# ---------------------------------------------------------------- kernels
+
+def bench_kernels(hpac, torch, dev, stream, HB, clk, bs_cfg0=None):
+    """Roofline of every exact hydro kernel at the headline mesh: one exact run
+    with CUDA events around each phase of every time step (node, element, EOS
+    region, finalize). Units and algorithmic work per unit:
+      node_kernel   HBM: per node u, v, w, x, y, z read and written (96 B) and
+                    1 / (12 m) (8 B); per element its 24 stored gradient
+                    values (192 B) and p + q (8 B), each read once (its FP64
+                    fraction, NODE_OPS per node, is reported beside it)
+      elem_kernel   FP64 issue: ELEM_OPS per element
+      EOS exact     FP64 issue: EOS_OPS + EOS_DIV_OPS per element (its 40 B
+                    per element would take a ninth of the time at HBM speed)
+      finalize      HBM: per element v_{n+1}, p, q read, e, v, p + q written (48 B)
+    """
+    E, n1 = HB.E, HB.n + 1
+    Nn = n1 ** 3
+    hbm, hbm_src = measured_peaks()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    cs = clk.summary()
+    mhz = cs["sm_mhz"] or cs["sm_max_mhz"] or 2070.0
+    fp64_peak = FP64_FMA_PER_SM_CLK * sms * mhz * 1e6
+    sh, st, hp = stream.cuda_stream, stream, hpac
+    ph = [events(torch, HB.nsteps) for _ in range(4)]
+    HB.reset(None)
+    for s in range(HB.nsteps):
+        ph[0][s][0].record(st)
+        hp.hpac_hydro_nodes(HB.Hy.state, sh)
+        ph[0][s][1].record(st)
+        ph[1][s][0].record(st)
+        hp.hpac_hydro_elements(HB.Hy.state, sh)
+        ph[1][s][1].record(st)
+        ph[2][s][0].record(st)
+        hp.hpac_run_exact(HB.Hy.eos._h, HB.eos_ptr, HB.p_ptr)
+        ph[2][s][1].record(st)
+        ph[3][s][0].record(st)
+        hp.hpac_hydro_finalize(HB.Hy.state, sh)
+        ph[3][s][1].record(st)
+    torch.cuda.synchronize()
+    ms = [float(np.mean([e0.elapsed_time(e1) for e0, e1 in ph[j]])) for j in range(4)]
+    rows = {
+        "node_kernel": dict(bound="hbm", ms=ms[0], bytes=Nn * 104 + E * 200, peak=hbm * 1e9, unit="B/s",
+                            fp64_frac=Nn * NODE_OPS / (ms[0] * 1e-3) / fp64_peak),
+        "elem_kernel": dict(bound="alu", ms=ms[1], ops=E * ELEM_OPS, peak=fp64_peak, unit="FP64 op/s"),
+        "eos_exact": dict(bound="alu", ms=ms[2], ops=E * (EOS_OPS + EOS_DIV_OPS), peak=fp64_peak,
+                          unit="FP64 op/s"),
+        "finalize_kernel": dict(bound="hbm", ms=ms[3], bytes=E * 48, peak=hbm * 1e9, unit="B/s"),
+    }
+    for r in rows.values():
+        work = r.get("bytes", r.get("ops"))
+        r["achieved"] = work / (r["ms"] * 1e-3)
+        r["frac"] = r["achieved"] / r["peak"]
+    if bs_cfg0 is not None:
+        rows.update(bs_cfg0)
+    return {"mesh": f"{HB.n}^3", "time_steps": HB.nsteps, "hbm_peak_gbs": hbm, "hbm_peak_source": hbm_src,
+            "fp64_peak_source": f"derived: {FP64_FMA_PER_SM_CLK} FP64 FMA/SM/clk x {sms} SMs x {mhz:.0f} MHz",
+            "kernels": rows}
+
+
+def bench_hydro64(hpac, torch, dev, stream, rank, n=HYDRO_N, nsteps=HYDRO_STEPS, reps=3):
+    """The 64^3 x 100-step configuration: runs with the EOS exact, under TAF
+    (h4 p8 0.5%) and under iACT (t8, private tables, 1e-3), launch-scoped state
+    (T = E / 8), each timed, with the quality of the final state (origin
+    energy, pressure NRMSE), plus the EOS region alone on a mid-run state and
+    a 64-configuration knob sweep of it."""
+    HB = HydroBench(hpac, torch, dev, stream, n, nsteps, W.DEFAULT_SEED + rank)
+    forms = {"exact": None,
+             "taf": ("taf h4 p8 0.5%", 1, False, dict(TAF)),
+             "iact": ("iact t8 g32 1e-3", 2, False, dict(IACT))}
+    res = {}
+    ref_p = ref_q = None
+    for name, form in forms.items():
+        t = timed_ms(torch, stream, lambda: HB.run(form), reps)
+        row = {"ms": t, "element_updates_per_s": HB.E * nsteps / (t * 1e-3)}
+        if form is None:
+            ref_p, ref_q = HB.Hy["p"].clone(), float(HB.Hy["e"][0].item())
+            p_rms = float(torch.sqrt(torch.mean(ref_p * ref_p)).item())
+        else:
+            r = hpac.quality(ref_p, HB.Hy["p"], hpac.HPAC_METRIC_RMSE, stream=stream)["value"]
+            row.update(speedup_vs_exact=res["exact"]["ms"] / t, p_nrmse=r / p_rms,
+                       qoi_rel_err=abs(float(HB.Hy["e"][0].item()) - ref_q) / abs(ref_q))
+        res[name] = row
+    # the EOS region alone on a mid-run state
+    HB.reset(None)
+    for _ in range(nsteps // 2):
+        hpac.hpac_hydro_step(HB.Hy.state, HB.Hy.eos._h, 0, None, None, False)
+    hpac.hpac_hydro_nodes(HB.Hy.state, stream.cuda_stream)
+    hpac.hpac_hydro_elements(HB.Hy.state, stream.cuda_stream)
+    torch.cuda.synchronize()
+    region_ms = {}
+    for name, form in forms.items():
+        k = HB.knobs(form) if form is not None else None
+        if form is None:
+            f = lambda: hpac.hpac_run_exact(HB.Hy.eos._h, HB.eos_ptr, HB.p_ptr)
+        elif form[1] == 1:
+            f = lambda k=k: hpac.hpac_run_taf(HB.Hy.eos._h, k, HB.eos_ptr, HB.p_ptr)
+        else:
+            f = lambda k=k: hpac.hpac_run_iact(HB.Hy.eos._h, k, HB.eos_ptr, HB.p_ptr)
+        region_ms[name] = timed_ms(torch, stream, f, 50)
+    ref_mid = torch.zeros(HB.E, dtype=torch.float64, device=dev)
+    hpac.hpac_run_exact(HB.Hy.eos._h, HB.eos_ptr, hpac.C.c_void_p(ref_mid.data_ptr()))
+    sweep = eos_region_sweep(hpac, torch, stream, HB.Hy.eos._h, HB.Hy["eos_in"], ref_mid, HB.scale)
+    HB.close()
+    return {"mesh": f"{n}^3", "time_steps": nsteps, "runs": res,
+            "eos_region_ms": region_ms,
+            "eos_region_speedup": {k: region_ms["exact"] / v for k, v in region_ms.items()},
+            "eos_sweep": sweep}
+
+
+def bench_cfg4_extras(hpac, torch, dev, stream, HB, train_pairs=1 << 22, epochs=16, sweep_configs=64):
+    """The rest of the large configuration on the headline mesh: the EOS
+    replaced by a learned surrogate (4 -> 128 -> 128 -> 1, trained on EOS
+    pairs recorded from the exact run) and a 64-configuration knob sweep of the
+    EOS region on the mid-run state."""
+    E, nsteps = HB.E, HB.nsteps
+    sh = stream.cuda_stream
+    pairs, mid = [], []
+    HB.reset(None)
+    for s in range(nsteps):
+        hpac.hpac_hydro_nodes(HB.Hy.state, sh)
+        hpac.hpac_hydro_elements(HB.Hy.state, sh)
+        hpac.hpac_run_exact(HB.Hy.eos._h, HB.eos_ptr, HB.p_ptr)
+        ein = HB.Hy["eos_in"]
+        act = torch.nonzero((ein[0] > 0) | (ein[3] > 0) | (ein[2] != 0)).flatten()
+        pairs.append((ein[:, act].clone(), HB.Hy["p"][act].clone()))
+        if s + 1 == nsteps // 2:
+            mid.append(ein.clone())
+        hpac.hpac_hydro_finalize(HB.Hy.state, sh)
+    p_ex = HB.Hy["p"].clone()
+    qoi_ex = float(HB.Hy["e"][0].item())
+    t_ex = timed_ms(torch, stream, lambda: HB.run(None), 1)
+    # training pairs: the active elements of every step plus as many untouched
+    # ones (inputs (0, 1, 0, 0) -> p = 0)
+    xa = torch.cat([a for a, _ in pairs], dim=1)
+    ya = torch.cat([b for _, b in pairs])
+    nq = xa.shape[1]
+    xq = torch.zeros(4, nq, dtype=torch.float64, device=dev)
+    xq[1] = 1.0
+    perm = torch.randperm(2 * nq, device=dev, generator=torch.Generator(device=dev).manual_seed(7))
+    xtr = torch.cat([xa, xq], dim=1)[:, perm][:, :train_pairs].contiguous()
+    ytr = torch.cat([ya, torch.zeros(nq, dtype=torch.float64, device=dev)])[perm][:train_pairs].float().contiguous()
+    S = hpac.Surrogate(hpac.eos_desc(128), seed=4, stream=stream)
+    S.fit_normalization(xtr, ytr, GAMMA)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    loss = S.train(xtr, ytr, GAMMA, batch=8192, epochs=epochs, lr=2e-3)
+    b.record(stream)
+    torch.cuda.synchronize()
+    train_ms = a.elapsed_time(b)
+
+    def run_sur():
+        HB.reset(None)
+        for s in range(nsteps):
+            hpac.hpac_hydro_nodes(HB.Hy.state, sh)
+            hpac.hpac_hydro_elements(HB.Hy.state, sh)
+            S.infer(HB.Hy["eos_in"], HB.Hy["p"], GAMMA)
+            hpac.hpac_hydro_finalize(HB.Hy.state, sh)
+    t = timed_ms(torch, stream, run_sur, 1)
+    p_rms = float(torch.sqrt(torch.mean(p_ex * p_ex)).item())
+    r = hpac.quality(p_ex, HB.Hy["p"], hpac.HPAC_METRIC_RMSE, stream=stream)["value"]
+    sur = {"ms": t, "speedup_vs_exact": t_ex / t, "p_nrmse": r / p_rms,
+           "qoi_rel_err": abs(float(HB.Hy["e"][0].item()) - qoi_ex) / abs(qoi_ex),
+           "train_pairs": int(xtr.shape[1]), "train_ms": train_ms, "train_mse_normalized": loss}
+    S.close()
+    del xa, ya, xq, xtr, ytr, pairs
+    HB.Hy["eos_in"].copy_(mid[0])
+    ref = torch.zeros(E, dtype=torch.float64, device=dev)
+    hpac.hpac_run_exact(HB.Hy.eos._h, HB.eos_ptr, hpac.C.c_void_p(ref.data_ptr()))
+    sweep = eos_region_sweep(hpac, torch, stream, HB.Hy.eos._h, HB.Hy["eos_in"], ref, HB.scale, sweep_configs)
+    return {"mesh": f"{HB.n}^3", "time_steps": nsteps, "exact_ms": t_ex, "surrogate": sur, "eos_sweep": sweep}
+
+
+def emit(detail, name, obj):
+    """One section: printed on its own line (before the final one) and kept
+    for the detail file."""
+    detail[name] = obj
+    print(json.dumps({"section": name, **obj} if isinstance(obj, dict) else {"section": name, "value": obj},
+                     default=float), flush=True)
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--n", type=int, default=HYDRO_N)
-    ap.add_argument("--time-steps", type=int, default=HYDRO_STEPS)
+    ap.add_argument("--n", type=int, default=HEAD_N)
+    ap.add_argument("--time-steps", type=int, default=HEAD_STEPS)
+    ap.add_argument("--exact-reps", type=int, default=3)
+    ap.add_argument("--e2e-reps", type=int, default=2)
+    ap.add_argument("--reference-form", default="iact kept t8 g1 1e-3",
+                    help="EOS form the reference arm (the CPU oracle) runs")
+    ap.add_argument("--sections", default="all",
+                    help="comma-separated sections after the headline, 'all' or 'none'")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-blackscholes", action="store_true")
-    ap.add_argument("--no-sweep", action="store_true")
-    ap.add_argument("--no-surrogate", action="store_true")
-    ap.add_argument("--no-hydro-large", action="store_true")
-    ap.add_argument("--no-persistent", action="store_true")
-    ap.add_argument("--no-search", action="store_true")
-    ap.add_argument("--no-binomial", action="store_true")
-    ap.add_argument("--no-kmeans", action="store_true")
-    ap.add_argument("--no-levels", action="store_true")
+    ap.add_argument("--detail", default=os.path.join(ROOT, "gpurun_out", "bench_detail.json"))
     args = ap.parse_args(argv)
     if args.impl == "reference":
         return run_reference(args)
+    args.steps = max(1, args.steps)
 
     import torch
     import torch.distributed as dist
@@ -955,249 +1407,106 @@ def main(argv=None):
     dev = torch.device("cuda", local)
     hpac.load()
     stream = torch.cuda.current_stream(dev)
-    sh = stream.cuda_stream
+    all_sections = ["kernels", "cfg4_extras", "hydro64", "blackscholes_65536", "blackscholes_16M", "sweep",
+                    "search", "binomial", "kmeans", "levels", "surrogate", "persistent_state"]
+    want = all_sections if args.sections == "all" else ([] if args.sections == "none"
+                                                         else args.sections.split(","))
+    detail = {}
 
-    n, nsteps = args.n, args.time_steps
-    E = n ** 3
-    T = E // HYDRO_IPT
-    x, y, z, e = W.hydro_initial(n, seed=W.DEFAULT_SEED + rank)
-    dt = W.hydro_dt(n)
-    Hy = hpac.Hydro(n, x, y, z, e, dt, logical_threads=T, block_threads=256, stream=stream)
-    torch.cuda.synchronize()
-    init = {k: v.clone() for k, v in Hy.t.items()}
-    scale_arr = (hpac.C.c_double * 4)(*IACT_SCALE)
-    knobs = {
-        "exact": None,
-        "taf": hpac.hpac_taf_knobs(TAF["hsize"], TAF["psize"], TAF["thresh"], TAF["level"], 0),
-        "iact": hpac.hpac_iact_knobs(IACT["tsize"], IACT["tperwarp"], IACT["thresh"], IACT["level"], 0,
-                                     hpac.C.cast(scale_arr, hpac.C.POINTER(hpac.C.c_double))),
-    }
-    eos_h = Hy.eos._h
-    eos_ptr, p_ptr = hpac.C.c_void_p(Hy["eos_in"].data_ptr()), hpac.C.c_void_p(Hy["p"].data_ptr())
-    runs = ["exact", "taf", "iact"]
-    ref_p = torch.zeros(E, dtype=torch.float64, device=dev)
-    ref_e0 = torch.zeros(1, dtype=torch.float64, device=dev)
-
-    def region(tech):
-        if tech == "exact":
-            hpac.hpac_run_exact(eos_h, eos_ptr, p_ptr)
-        elif tech == "taf":
-            hpac.hpac_run_taf(eos_h, knobs["taf"], eos_ptr, p_ptr)
-        else:
-            hpac.hpac_run_iact(eos_h, knobs["iact"], eos_ptr, p_ptr)
-
-    def reset():
-        for k, v in init.items():
-            Hy.t[k].copy_(v, non_blocking=True)
-
-    def one_run(tech, ev=None):
-        """nsteps time steps; ev: list of (start, stop) events per element phase."""
-        reset()
-        for s in range(nsteps):
-            hpac.hpac_hydro_nodes(Hy.state, sh)
-            if ev is not None:
-                ev[s][0].record(stream)
-            hpac.hpac_hydro_elements(Hy.state, sh)
-            if ev is not None:
-                ev[s][1].record(stream)
-            region(tech)
-            hpac.hpac_hydro_finalize(Hy.state, sh)
-
-    flush = torch.empty(1 << 26, dtype=torch.float32, device=dev)   # 256 MB, twice the L2
-
-    def step(ev=None, run_ev=None):
-        out = {}
-        flush.zero_()          # evict the previous step's state from L2 before this one
-        for j, tech in enumerate(runs):
-            if run_ev is not None:
-                run_ev[j][0].record(stream)
-            one_run(tech, ev[j] if ev is not None else None)
-            if run_ev is not None:
-                run_ev[j][1].record(stream)
-            if tech == "exact":
-                ref_p.copy_(Hy["p"])
-                ref_e0.copy_(Hy["e"][:1])
-            else:
-                out[tech] = hpac.quality(ref_p, Hy["p"], hpac.HPAC_METRIC_MAPE, stream=stream)["value"]
-                out[tech + "_rmse"] = hpac.quality(ref_p, Hy["p"], hpac.HPAC_METRIC_RMSE,
-                                                   stream=stream)["value"]
-                out[tech + "_qoi"] = Hy["e"][:1].clone()
-        return out
-
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
     clk = ClockSampler(local).start()
-    t_end = time.perf_counter() + 1.0
-    while time.perf_counter() < t_end:
-        step()
-    torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
-
-    mk = lambda: [torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)]
-    ev = [[[mk() for _ in range(nsteps)] for _ in runs] for _ in range(args.steps)]
-    run_ev = [[mk() for _ in runs] for _ in range(args.steps)]
-    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    start.record(stream)
-    for s in range(args.steps):
-        qual = step(ev[s], run_ev[s])
-    stop.record(stream)
-    torch.cuda.synchronize()
-    t_end = time.perf_counter() + 0.5
-    while time.perf_counter() < t_end:
-        step()
-    torch.cuda.synchronize()
+    time.sleep(0.5)
+    head, HB = bench_headline(hpac, torch, dev, stream, args, world, rank, clk)
     clk.stop()
-    total_ms, _ = aggregate(start.elapsed_time(stop), 1, world, dev)
-    ms_per_step = total_ms / args.steps
-    value = world * len(runs) * E * nsteps / (ms_per_step * 1e-3)
-    run_ms = {tech: float(np.mean([run_ev[s][j][0].elapsed_time(run_ev[s][j][1])
-                                   for s in range(args.steps)])) for j, tech in enumerate(runs)}
-    elem_ms = float(np.mean([ev[s][j][t][0].elapsed_time(ev[s][j][t][1])
-                             for s in range(args.steps) for j in range(len(runs)) for t in range(nsteps)]))
-    qoi_ref = float(ref_e0.item())
-    p_rms = float(torch.sqrt(torch.mean(ref_p * ref_p)).item())
-    quality = {tech: {"qoi_rel_err": abs(float(qual[tech + "_qoi"].item()) - qoi_ref) / abs(qoi_ref),
-                      "p_mape": qual[tech], "p_nrmse": qual[tech + "_rmse"] / p_rms}
-               for tech in runs[1:]}
+    clocks = clk.summary()
+    if rank == 0:
+        emit(detail, "headline", head["detail"])
 
-    # EOS region alone on a mid-run state (the approximated region's speedup)
-    reset()
-    for _ in range(nsteps // 2):
-        hpac.hpac_hydro_step(Hy.state, eos_h, 0, None, None, False)
-    hpac.hpac_hydro_nodes(Hy.state, sh)
-    hpac.hpac_hydro_elements(Hy.state, sh)
-    torch.cuda.synchronize()
-    region_ms, region_stats = {}, {}
-    for tech in runs:
-        for _ in range(3):
-            region(tech)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(50):
-            region(tech)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        region_ms[tech] = e0.elapsed_time(e1) / 50
-    st = hpac.hpac_stats()
-    hpac._check(hpac.load().hpac_run_taf(eos_h, hpac.C.byref(knobs["taf"]), eos_ptr, p_ptr, None, None,
-                                         hpac.C.byref(st)), "taf stats")
-    region_stats["taf"] = st.as_dict()
-    st = hpac.hpac_stats()
-    hpac._check(hpac.load().hpac_run_iact(eos_h, hpac.C.byref(knobs["iact"]), eos_ptr, p_ptr, None, None,
-                                          hpac.C.byref(st)), "iact stats")
-    region_stats["iact"] = st.as_dict()
-    # a 64-configuration knob sweep of the EOS region on the same mid-run state
-    ref_mid = torch.zeros(E, dtype=torch.float64, device=dev)
-    hpac.hpac_run_exact(eos_h, eos_ptr, hpac.C.c_void_p(ref_mid.data_ptr()))
-    eos_sweep = eos_region_sweep(hpac, torch, stream, eos_h, Hy["eos_in"], ref_mid, scale_arr)
-    del ref_mid
+    # sections (rank 0 prints them; every rank runs them so replicas stay alike)
+    def section(name, fn):
+        if name in want:
+            r = fn()
+            if rank == 0:
+                emit(detail, name, r)
+            return r
+        return None
 
-    fp64_tflops = hpac.hpac_device_fp64_rate(sh)
-    measured = fp64_tflops / 2.0                  # FMA instructions per second, 1e12
-    sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    clk_now = clk.summary()
-    mhz = clk_now["sm_mhz"] or clk_now["sm_max_mhz"] or 2070.0
-    peak = FP64_FMA_PER_SM_CLK * sms * mhz * 1e6 / 1e12
-    achieved = ELEM_OPS * E / (elem_ms * 1e-3) / 1e12
-    roofline = {"bound": "alu", "kernel": "elem_kernel (FP64 volume gradient)", "achieved": achieved,
-                "peak": peak, "unit": "T FP64-ops/s", "frac": achieved / peak,
-                "peak_source": f"derived: {FP64_FMA_PER_SM_CLK} FP64 FMA per SM per clock (the nominal "
-                               f"1.25 TFLOP/s at 152 SMs x 2070 MHz) x {sms} SMs x {mhz:.0f} MHz "
-                               "(median SM clock sampled under load)",
-                "measured_peak": measured, "frac_of_measured": achieved / measured,
-                "measured_peak_source": "FP64 FMA rate of this GPU measured in the same run "
-                                        f"(hpac_device_fp64_rate: {fp64_tflops:.3f} TFLOP/s)",
-                "ops_per_element": ELEM_OPS,
-                "traffic": dram_traffic("elem_kernel", E), "launch_ms": elem_ms}
+    bs0 = section("blackscholes_65536", lambda: bench_blackscholes_cfg0(hpac, torch, dev, stream))
+    bs = section("blackscholes_16M", lambda: bench_blackscholes(hpac, torch, dev, stream))
+    extra_rows = {}
+    if bs0 is not None:
+        extra_rows["bs_exact_65536"] = bs0["kernel_row"]
+    if bs is not None:
+        extra_rows["bs_exact_16M"] = bs["kernel_row"]
+    kern = section("kernels", lambda: bench_kernels(hpac, torch, dev, stream, HB, ClockSummary(clocks),
+                                                    extra_rows))
+    section("cfg4_extras", lambda: bench_cfg4_extras(hpac, torch, dev, stream, HB))
+    HB.close()
+    del HB
+    torch.cuda.empty_cache()
+    section("hydro64", lambda: bench_hydro64(hpac, torch, dev, stream, rank))
+    section("sweep", lambda: bench_sweep(hpac, torch, dev, stream))
+    section("search", lambda: bench_search(hpac, torch, dev, stream))
+    section("binomial", lambda: bench_binomial(hpac, torch, dev, stream))
+    section("kmeans", lambda: bench_kmeans(hpac, torch, dev, stream))
+    section("levels", lambda: bench_levels(hpac, torch, dev, stream))
+    section("surrogate", lambda: bench_surrogate(hpac, torch, dev, stream))
+    section("persistent_state", lambda: bench_persistent(hpac, torch, dev, stream))
 
-    # end to end through the public API with host buffers: pinned initial state
-    # in, a TAF run, the final energy field out, every step
-    pin = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory() for k, v in
-           (("x", x), ("y", y), ("z", z), ("e", e))}
-    e_out = torch.empty(E, dtype=torch.float64).pin_memory()
-    h2d = sum(int(v.numel() * 8) for v in pin.values())
-
-    def e2e_once():
-        for k, v in pin.items():
-            Hy.t[k].copy_(v, non_blocking=True)
-        hpac.hpac_hydro_init(Hy.state, sh)
-        hpac.hpac_hydro_run(Hy.state, eos_h, nsteps, hpac.HYDRO_TAF, knobs["taf"])
-        e_out.copy_(Hy["e"], non_blocking=True)
-
-    e2e_once()
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    reps = max(3, args.steps)
-    e0.record(stream)
-    for _ in range(reps):
-        e2e_once()
-    e1.record(stream)
-    torch.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1) / reps
-    e2e = {"value": world * E * nsteps / (e2e_ms * 1e-3), "unit": "elements/s",
-           "run": "TAF on the EOS, 100 time steps", "h2d_bytes_per_step": h2d,
-           "d2h_bytes_per_step": int(E * 8)}
-
-    bs = None if args.no_blackscholes else bench_blackscholes(hpac, torch, dev, stream)
-    sweep = None if args.no_sweep else bench_sweep(hpac, torch, dev, stream)
-    knob_search = None if args.no_search else bench_search(hpac, torch, dev, stream)
-    binomial = None if args.no_binomial else bench_binomial(hpac, torch, dev, stream)
-    kmeans = None if args.no_kmeans else bench_kmeans(hpac, torch, dev, stream)
-    levels = None if args.no_levels else bench_levels(hpac, torch, dev, stream)
-    surrogate = None if args.no_surrogate else bench_surrogate(hpac, torch, dev, stream)
-    large = None if args.no_hydro_large else bench_hydro_large(hpac, torch, dev, stream)
-    persistent = None if args.no_persistent else bench_persistent(hpac, torch, dev, stream)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = hydro_cpu(single_steps=2)
+        cpu = hydro_cpu(head["form"], n=args.n, steps=4)
         cpu.pop("seconds", None)
+        emit(detail, "cpu_baseline", cpu)
 
     if rank == 0:
+        best = head["best"]
+        form = head["form"]
+        rl = head["roofline"]
         line = {
-            "metric": METRIC, "value": value, "unit": "elements/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+            "metric": METRIC, "value": head["value"], "unit": "elements/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms_per_step"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": f"hydro {n}^3 hex mesh (nodes jittered 5%, corner energy 3.9e6), "
-                                   f"{nsteps} time steps per run; runs with the EOS exact, under TAF "
-                                   "(h4/p8/0.5%) and under iACT (t8, private tables, 1e-3)",
-                       "eos_logical_threads": T, "block_threads": 256,
-                       "l2": "flushed before every timed step (a 256 MB write, inside the timed "
-                             "region); within a run the 100 time steps reuse the ~120 MB mesh "
-                             "state from L2, as the algorithm does (the step is FP64-ALU bound)",
-                       "parallelism": f"replicas{world}"},
-            "roofline": roofline,
-            "cpu_baseline": cpu,
-            "e2e": e2e,
-            # per time step: node, element, EOS region, finalize; per step the two
-            # approximate runs' MAPE and RMSE (two kernels per quality call)
-            "gpu_launches": args.steps * len(runs) * nsteps * (3 + 1) + args.steps * 4 * 2,
-            "clocks": clk.summary(),
-            "run_ms": run_ms,
-            "speedup_vs_exact": {"run": {k: run_ms["exact"] / v for k, v in run_ms.items()},
-                                 "eos_region": {k: region_ms["exact"] / v for k, v in region_ms.items()}},
-            "eos_region_ms": region_ms,
-            "eos_sweep": {k: v for k, v in eos_sweep.items() if k != "table"},
-            "eos_region_approximated": region_stats,
-            "quality": quality,
-            "blackscholes": bs,
-            "sweep": sweep,
-            "search": knob_search,
-            "binomial": binomial,
-            "kmeans": kmeans,
-            "levels": levels,
-            "surrogate": surrogate,
-            "hydro_large": large,
-            "persistent_state": persistent,
+            "config": {"workload": f"hydro {args.n}^3 hex mesh, {args.time_steps} time steps, EOS region "
+                                   f"under {form[0]} (fastest form within 1% that approximates "
+                                   f">= {MIN_ACTIVE_APPROX:.0%} of active invocations)",
+                       "l2": "inputs > L2 (6.5 GB state)", "parallelism": f"replicas{world}"},
+            "speedup_vs_exact": {"run": sig(best["speedup"]), "eos_region": sig(best["region_speedup"])},
+            "quality": {"qoi_rel_err": sig(head["timed_quality"]["qoi_rel_err"], 3),
+                        "p_nrmse": sig(head["timed_quality"]["p_nrmse"], 3),
+                        "approx_active": sig(best["approx_active"], 3), "bound": QUALITY_BOUND,
+                        "qualifies": best["qualifies"]},
+            "roofline": {"bound": rl["bound"], "kernel": rl["kernel"], "achieved": sig(rl["achieved"]),
+                         "peak": sig(rl["peak"]), "unit": rl["unit"], "frac": sig(rl["frac"], 3),
+                         "traffic": rl["traffic"]},
+            "cpu_baseline": None if cpu is None else {k: sig(cpu[k]) for k in
+                                                      ("value", "unit", "cores", "kind", "sample")},
+            "e2e": sig(head["e2e"]),
+            "gpu_launches": head["gpu_launches"],
+            "clocks": {k: clocks.get(k) for k in ("sm_mhz", "sm_max_mhz", "reasons")},
         }
-        print(json.dumps(line))
-    Hy.close()
+        if kern is not None:
+            line["kernels_frac"] = {k: sig(v["frac"], 3) for k, v in kern["kernels"].items()}
+        try:
+            os.makedirs(os.path.dirname(args.detail), exist_ok=True)
+            with open(args.detail, "w") as f:
+                json.dump({"final": line, **detail}, f, indent=1, default=float)
+        except OSError:
+            pass
+        print(json.dumps(line, default=float))
     if world > 1:
         dist.destroy_process_group()
     return 0
+
+
+class ClockSummary:
+    """A fixed clock summary with the sampler's interface."""
+
+    def __init__(self, s):
+        self.s = s
+
+    def summary(self):
+        return self.s
 
 
 if __name__ == "__main__":
