@@ -82,6 +82,18 @@ __global__ void __launch_bounds__(1024) iact_kernel(R reg, const typename R::T *
   const int64_t gwarp = ((int64_t)blockIdx.x * blockDim.x) / 32 + warp;
   const bool has_state = PERSIST && gwarp * 32 < T;
   uint32_t *wst = has_state ? st + (size_t)gwarp * (wbytes / 4) : nullptr;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t t_lead = LEVEL == HPAC_LEVEL_BLOCK ? (int64_t)blockIdx.x * blockDim.x : t - lane;
+  // The first invocation's inputs are requested before the tables are read
+  // in, so that the two loads' latencies overlap; every invocation reads its
+  // inputs, and the next one's are loaded while this one scans its table and
+  // computes (one invocation ahead).
+  V xn[KD];
+  if (t_lead < T && t < T && t < n) {
+#pragma unroll
+    for (int d = 0; d < KD; ++d)
+      if (d < D) xn[d] = in[d * stride + t];
+  }
   if (has_state) {
     uint32_t *dst = reinterpret_cast<uint32_t *>(base);
     for (size_t q = lane; q < wbytes / 4; q += 32) dst[q] = wst[q];
@@ -93,20 +105,10 @@ __global__ void __launch_bounds__(1024) iact_kernel(R reg, const typename R::T *
   if (LEVEL == HPAC_LEVEL_BLOCK && threadIdx.x == 0) s_tally[0] = s_tally[1] = s_tally[2] = 0;
   __syncthreads();
 
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t t_lead = LEVEL == HPAC_LEVEL_BLOCK ? (int64_t)blockIdx.x * blockDim.x : t - lane;
   unsigned long long n_apx = 0, n_border = 0;
 
   if (t_lead < T) {
     int k3 = 0;
-    // Every invocation reads its inputs, so the next one's are loaded while
-    // this one scans its table and computes (one invocation ahead).
-    V xn[KD];
-    if (t < T && t < n) {
-#pragma unroll
-      for (int d = 0; d < KD; ++d)
-        if (d < D) xn[d] = in[d * stride + t];
-    }
     for (int64_t i = t; t_lead + (i - t) < n; i += T) {
       const bool act = (t < T) && (i < n);
       // ---- read phase

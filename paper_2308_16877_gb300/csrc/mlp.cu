@@ -658,7 +658,7 @@ template <int H>
 struct TcLayout {
   static constexpr int kA = 0;                        // 128 x H BF16 activations
   static constexpr int kB = kTile * H * 2;            // H x H BF16 W2 [out][in]
-  static constexpr int kW1 = kB + H * H * 2;          // H x 8 floats
+  static constexpr int kW1 = kB + H * H * 2;          // H / 2 unit pairs x 8 features, float pairs
   static constexpr int kB1 = kW1 + H * 8 * 4;
   static constexpr int kB2 = kB1 + H * 4;
   static constexpr int kW3 = kB2 + H * 4;
@@ -673,6 +673,19 @@ struct TcLayout {
 template <int H>
 __device__ __forceinline__ int kmajor_off(int r, int k) {
   return (r >> 3) * (16 * H) + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2;
+}
+
+// GELU of two values in packed single-precision pairs: the operations and
+// their order are those of gelu() per half (one IEEE rounding each), the
+// hyperbolic tangent per value.
+__device__ __forceinline__ unsigned long long gelu2(unsigned long long z) {
+  const unsigned long long kA2 = f32x2_pack(kGeluA, kGeluA), kB2 = f32x2_pack(kGeluB, kGeluB);
+  const unsigned long long half2 = f32x2_pack(0.5f, 0.5f), one2 = f32x2_pack(1.0f, 1.0f);
+  const unsigned long long arg = f32x2_mul(kA2, f32x2_fma(f32x2_mul(kB2, z), f32x2_mul(z, z), z));
+  float a0, a1;
+  f32x2_unpack(arg, a0, a1);
+  const unsigned long long th = f32x2_pack(tanh_fast(a0), tanh_fast(a1));
+  return f32x2_mul(f32x2_mul(half2, z), f32x2_add(one2, th));
 }
 
 template <int H, int KIND>
@@ -696,9 +709,9 @@ __global__ void __launch_bounds__(kTile) mlp_tc_infer(MlpArgs a, hpac_mlp_desc d
       const int o = j / H, k = j % H;
       *reinterpret_cast<__nv_bfloat16 *>(sm + L::kB + kmajor_off<H>(o, k)) = __float2bfloat16_rn(p[oW2 + j]);
     }
-    for (int j = tid; j < H * 8; j += kTile) {
-      const int u = j / 8, k = j % 8;
-      w1[j] = k < D ? bf16r(p[oW1 + u * D + k]) : 0.f;
+    for (int j = tid; j < H * 8; j += kTile) {  // (pair, feature, half): w1[2 pair + half][feature]
+      const int pr = j / 16, k = (j / 2) % 8, h = j % 2;
+      w1[j] = k < D ? bf16r(p[oW1 + (2 * pr + h) * D + k]) : 0.f;
     }
     for (int j = tid; j < H; j += kTile) {
       b1[j] = p[ob1 + j];
@@ -735,22 +748,29 @@ __global__ void __launch_bounds__(kTile) mlp_tc_infer(MlpArgs a, hpac_mlp_desc d
     const bool valid = i < a.n;
     float f[8], mult = 0.f, raw[4];
     features<KIND>(a.in, a.stride, valid ? i : 0, a.param, d, f, mult, raw);
-    // layer 1 and GELU into row tid of A, 8 units (16 bytes) at a time
+    // layer 1 and GELU into row tid of A, 8 units (16 bytes) at a time; two
+    // units advance together in packed pairs (the same fused multiply-adds
+    // over k in order as one unit at a time), weights read 16 bytes at once
+    unsigned long long fp[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) fp[k] = f32x2_pack(f[k], f[k]);
+    const ulonglong2 *w1v = reinterpret_cast<const ulonglong2 *>(w1);
 #pragma unroll 2
     for (int kc = 0; kc < H / 8; ++kc) {
       uint32_t pk[4];
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        const int u0 = 8 * kc + 2 * q, u1 = u0 + 1;
-        float z0 = b1[u0], z1 = b1[u1];
+        const int pr = 4 * kc + q;
+        unsigned long long z = *reinterpret_cast<const unsigned long long *>(b1 + 2 * pr);
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
-          if (k < D) {
-            z0 = fmaf(w1[u0 * 8 + k], f[k], z0);
-            z1 = fmaf(w1[u1 * 8 + k], f[k], z1);
-          }
+        for (int k2 = 0; k2 < 4; ++k2) {
+          const ulonglong2 w = w1v[pr * 4 + k2];
+          if (2 * k2 < D) z = f32x2_fma(w.x, fp[2 * k2], z);
+          if (2 * k2 + 1 < D) z = f32x2_fma(w.y, fp[2 * k2 + 1], z);
         }
-        pk[q] = pack_bf16(gelu(z0), gelu(z1));
+        float g0, g1;
+        f32x2_unpack(gelu2(z), g0, g1);
+        pk[q] = pack_bf16(g0, g1);
       }
       *reinterpret_cast<uint4 *>(sm + L::kA + kmajor_off<H>(tid, 8 * kc)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
     }
@@ -774,16 +794,32 @@ __global__ void __launch_bounds__(kTile) mlp_tc_infer(MlpArgs a, hpac_mlp_desc d
     parity ^= 1u;
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     // row tid of the accumulator: lane 32 warp + (tid % 32) of this warp's quarter
-    float y = 0.f;
+    // bias, GELU, BF16 rounding and the layer-3 dot product in packed pairs
+    // (even and odd units summed apart, then added)
+    unsigned long long y2 = 0ull;
 #pragma unroll
     for (int c = 0; c < H; c += 32) {
       float v[32];
       tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, v);
 #pragma unroll
-      for (int j = 0; j < 32; ++j) y = fmaf(bf16r(gelu(v[j] + b2[c + j])), w3[c + j], y);
+      for (int j = 0; j < 32; j += 4) {
+        const float4 bb = *reinterpret_cast<const float4 *>(b2 + c + j);
+        const float4 ww = *reinterpret_cast<const float4 *>(w3 + c + j);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const unsigned long long z =
+              f32x2_add(f32x2_pack(v[j + 2 * h], v[j + 2 * h + 1]), h ? f32x2_pack(bb.z, bb.w) : f32x2_pack(bb.x, bb.y));
+          float g0, g1;
+          f32x2_unpack(gelu2(z), g0, g1);
+          const float2 hb = __bfloat1622float2(__floats2bfloat162_rn(g0, g1));
+          y2 = f32x2_fma(f32x2_pack(hb.x, hb.y), h ? f32x2_pack(ww.z, ww.w) : f32x2_pack(ww.x, ww.y), y2);
+        }
+      }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    y += *b3;
+    float y_even, y_odd;
+    f32x2_unpack(y2, y_even, y_odd);
+    float y = (y_even + y_odd) + *b3;
     if (valid) {
       const float pred = mult * fmaf(d.out_scale, y, d.out_shift);
       float o = pred;
@@ -889,21 +925,36 @@ hpac_status launch_t(hpac_mlp *m, const MlpArgs &a) {
 }
 
 // The tensor-core inference: persistent blocks of 128 threads, as many per
-// SM as shared memory allows while their tensor-memory columns (H each) fit
-// in the SM's 512 (extra shared memory is requested until they do, so no
-// block ever waits for columns another resident block holds).
+// SM as registers, threads and shared memory allow while their tensor-memory
+// columns (H each) fit in the SM's 512; extra shared memory is requested
+// until they do, so no block waits for columns another resident block holds.
+// Residency is computed here from the function's attributes and the device
+// limits (the runtime's occupancy query reported one block per SM for this
+// kernel, a quarter of what its resources allow).
 template <int H, int KIND>
 hpac_status launch_tc_infer(hpac_mlp *m, const MlpArgs &a) {
   auto fn = mlp_tc_infer<H, KIND>;
+  cudaFuncAttributes fa;
+  HPAC_CUDA_TRY(cudaFuncGetAttributes(&fa, fn));
+  int sm_smem = 0, sm_regs = 0, sm_threads = 0, reserved = 0;
+  HPAC_CUDA_TRY(cudaDeviceGetAttribute(&sm_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, m->device));
+  HPAC_CUDA_TRY(cudaDeviceGetAttribute(&sm_regs, cudaDevAttrMaxRegistersPerMultiprocessor, m->device));
+  HPAC_CUDA_TRY(cudaDeviceGetAttribute(&sm_threads, cudaDevAttrMaxThreadsPerMultiProcessor, m->device));
+  HPAC_CUDA_TRY(cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, m->device));
+  const int regs = ((fa.numRegs + 7) / 8) * 8 * kTile;
   int smem = TcLayout<H>::kBytes;
   int per_sm = 0;
   for (;;) {
-    HPAC_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    HPAC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kTile, smem));
+    const int by_smem = sm_smem / (smem + (int)fa.sharedSizeBytes + reserved);
+    const int by_regs = regs > 0 ? sm_regs / regs : 32;
+    const int by_threads = sm_threads / kTile;
+    per_sm = by_smem < by_regs ? by_smem : by_regs;
+    per_sm = per_sm < by_threads ? per_sm : by_threads;
     if (per_sm * H <= 512 || per_sm <= 1) break;
     smem += 1024;
   }
   if (per_sm < 1) return set_error(HPAC_EUNSUPPORTED, "surrogate inference kernel does not fit an SM");
+  HPAC_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   const int64_t tiles = (a.n + kTile - 1) / kTile;
   int64_t blocks = (int64_t)sm_count(m->device) * per_sm;
   if (blocks > tiles) blocks = tiles < 1 ? 1 : tiles;
