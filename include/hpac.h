@@ -445,8 +445,13 @@ hpac_status hpac_region_vjp(hpac_region *region, const void *d_in, const void *d
 /* ------------------------------------------------------------------------
  * Learned surrogate of a region (not from the paper): an MLP
  * n_feat -> hidden -> hidden -> 1 with GELU (tanh form), BF16 weights and
- * activations and FP32 accumulation; layer 1 on FP32 features, layer 2 on the
- * tensor cores. Black-Scholes features: ln(S/K), sigma sqrt(T), r T, d1 (the
+ * activations and FP32 accumulation; layer 1 on FP32 features, layer 2 (in
+ * inference and training) and the training gradient's contractions over the
+ * samples on the tcgen05 tensor cores with tensor-memory accumulators. Their
+ * kernels bound every wait on a tensor-core product; a wait that gives up is
+ * reported as HPAC_ETIMEOUT by the next call that returns statistics or a
+ * loss (hpac_mlp_infer with h_stats, hpac_mlp_grad / hpac_mlp_train with
+ * h_loss). Black-Scholes features: ln(S/K), sigma sqrt(T), r T, d1 (the
  * Black-Scholes d1 clamped to [-10, 10]), sigma;
  * output C = S (out_shift + out_scale net). EOS features: e, v_{n+1}, dv, q
  * (as FP32); output p = m max(out_shift + out_scale net, 0) with the

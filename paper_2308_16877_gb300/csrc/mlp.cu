@@ -4,24 +4,22 @@
 // backward kernels, with the exact region as fallback. Not from the paper: it
 // stands beside TAF and iACT as a third way to skip the region's arithmetic.
 //
-// Layer 1 (D <= 8 FP32 features) runs on the CUDA cores in FP32 with BF16
-// weights; layer 2 (H x H, the bulk of the work) on the tensor cores with
-// warp-level mma.sync m16n8k16 BF16 -> FP32; layer 3 (H -> 1) is a dot product.
-// A warp owns 16 samples at a time: its layer-1 outputs land directly in the
-// accumulator layout of the m16n8 tiles, so GELU + BF16 packing turns them into
-// the A fragments of layer 2 in registers (no shared-memory round trip).
-//
-// Backward (training): dy -> dh2 = dy W3 -> dz2 = dh2 gelu'(z2) -> dh1 = dz2 W2
-// (tensor cores, W2 transposed in shared memory) -> dz1 = dh1 gelu'(z1). The
-// weight gradients dW2 = dz2^T h1 and dW1 = dz1^T f reduce over samples: the
-// block's warps stage dz2, h1, dz1, f in shared memory and each warp then owns
-// 16 output rows of dW2 / dW1, accumulated in registers across the whole
-// persistent loop with transposed ldmatrix loads feeding mma.sync. Bias and
-// layer-3 gradients go through shared-memory atomics; everything reaches the
-// global gradient with one atomic add per value per block. The same pass with a
-// caller's per-sample d(loss)/d(output) in place of the squared error's gives
-// the parameter half of a vector-Jacobian product; the input half scales the
-// input-derivative pass by it.
+// Three kernels:
+//  - inference (mlp_tc_infer): layer 2 (H x H, the contraction) as one
+//    128-row tcgen05 product per tile into tensor memory, layers 1 and 3 and
+//    the GELUs on the CUDA cores in packed single-precision pairs, one
+//    invocation per thread;
+//  - training gradient (mlp_tc_grad): the forward product, the backward
+//    product dh1 = dz2 W2, and the weight-gradient contractions over the
+//    samples (dW2 with db2, dW3, dW1 with db1) as tcgen05 products
+//    accumulated in tensor memory across a block's tiles; the same pass with
+//    a caller's per-sample d(loss)/d(output) in place of the squared error's
+//    gives the parameter half of a vector-Jacobian product;
+//  - input derivatives (mlp_input_grad_kernel): forward and backward through
+//    the network on warp-level mma.sync m16n8k16 with the fragments kept in
+//    registers, then the chain rule from the features to the region inputs
+//    (the input half of a vector-Jacobian product scales it by the caller's
+//    per-sample derivative).
 #include <cuda_bf16.h>
 #include <math.h>
 #include <stdlib.h>
@@ -78,32 +76,24 @@ __device__ __forceinline__ void mma16816(float (&d)[4], const uint32_t (&a)[4], 
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
-__device__ __forceinline__ void ldsm_x4_trans(uint32_t &r0, uint32_t &r1, uint32_t &r2, uint32_t &r3,
-                                              const void *p) {
-  const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
-  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
-               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
-               : "r"(a));
-}
 
-enum { MODE_INFER = 0, MODE_GRAD = 1, MODE_INPUT_GRAD = 2 };
 
 struct MlpArgs {
   const void *in;       // region inputs (SoA, in_stride)
   int64_t stride, n;
   double param;         // r (Black-Scholes) or gamma (EOS)
-  const float *target;  // MODE_GRAD: region outputs
-  float *out;           // MODE_INFER: region outputs; MODE_INPUT_GRAD: D x n derivatives
-  uint8_t *mask;        // MODE_INFER (nullable)
-  float fallback_below; // MODE_INFER: exact region where the prediction is below (NaN: never)
+  const float *target;  // gradient: region outputs
+  float *out;           // inference: region outputs; input gradient: D x n derivatives
+  uint8_t *mask;        // inference (nullable)
+  float fallback_below; // inference: exact region where the prediction is below (NaN: never)
   const float *params;
   float *grad;
   float *loss;
-  unsigned long long *counters;  // [0] fallbacks
-  float inv_n;          // MODE_GRAD: 1 / total samples of the batch
+  unsigned long long *counters;  // [0] fallbacks, [2] status (a tensor-core wait gave up)
+  float inv_n;          // gradient: 1 / total samples of the batch
   const float *gout;    // vector-Jacobian products: per-sample d(loss)/d(region output);
-                        // MODE_GRAD takes it instead of the squared error, MODE_INPUT_GRAD
-                        // multiplies each input derivative by it (nullable)
+                        // the gradient takes it instead of the squared error, the input
+                        // gradient multiplies each input derivative by it (nullable)
 };
 
 // Features of one invocation (FP32) and the output multiplier of the region.
@@ -148,14 +138,6 @@ struct Smem {
   float b3;
 };
 
-template <int H>
-struct Stage {  // per warp, MODE_GRAD
-  static constexpr int LD = H + 8;
-  __nv_bfloat16 dz2[16 * LD];
-  __nv_bfloat16 h1[16 * LD];
-  __nv_bfloat16 dz1[16 * LD];
-  __nv_bfloat16 f[16 * 24];         // features padded to 16 (+8)
-};
 
 template <int H>
 __device__ void load_params(Smem<H> &s, const float *p, int D) {
@@ -198,39 +180,24 @@ __device__ __forceinline__ void layer1_tile(const Smem<H> &s, int j, int t, int 
   z[0] = s00, z[1] = s01, z[2] = s10, z[3] = s11;
 }
 
-// One persistent kernel for inference, training gradients and input gradients.
-template <int H, int KIND, int MODE>
-__global__ void __launch_bounds__(H * 2) mlp_kernel(MlpArgs a, hpac_mlp_desc d) {
+// Derivatives of the surrogate's output with respect to the region inputs
+// (hpac_mlp_input_grad and the input half of hpac_mlp_vjp) on warp-level
+// mma.sync: a warp owns 16 samples at a time; its layer-1 outputs land in the
+// accumulator layout of the m16n8 tiles, so GELU and BF16 packing turn them
+// into the A fragments of layer 2 in registers, and the backward product
+// dh1 = dz2 W2 reads B from the transposed copy of W2.
+template <int H, int KIND>
+__global__ void __launch_bounds__(H * 2) mlp_input_grad_kernel(MlpArgs a, hpac_mlp_desc d) {
   constexpr int NT = H / 8;    // n-tiles of 8 hidden units
   constexpr int KS = H / 16;   // k-steps of 16 hidden units
   constexpr int W = H / 16;    // warps per block
   constexpr int LD = Smem<H>::LD;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Smem<H> &s = *reinterpret_cast<Smem<H> *>(smem_raw);
-  Stage<H> *stage = reinterpret_cast<Stage<H> *>(smem_raw + ((sizeof(Smem<H>) + 15) & ~size_t(15)));
-  __shared__ float g_b1[H], g_b2[H], g_w3[H];
-  __shared__ float g_b3, g_loss;
-  __shared__ unsigned long long g_fallback;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int g = lane >> 2, t = lane & 3;
   load_params<H>(s, a.params, d.n_feat);
-  if (MODE == MODE_GRAD) {
-    for (int j = threadIdx.x; j < H; j += blockDim.x) g_b1[j] = g_b2[j] = g_w3[j] = 0.f;
-    if (threadIdx.x == 0) g_b3 = g_loss = 0.f;
-  }
-  if (threadIdx.x == 0) g_fallback = 0;
   __syncthreads();
-
-  // MODE_GRAD register accumulators: this warp's 16 rows of dW2 (all H
-  // columns) and of dW1 (16 feature columns).
-  float acc2[NT][4];
-  float acc1[2][4];
-  if (MODE == MODE_GRAD) {
-#pragma unroll
-    for (int j = 0; j < NT; ++j) acc2[j][0] = acc2[j][1] = acc2[j][2] = acc2[j][3] = 0.f;
-#pragma unroll
-    for (int j = 0; j < 2; ++j) acc1[j][0] = acc1[j][1] = acc1[j][2] = acc1[j][3] = 0.f;
-  }
 
   const int64_t chunk = 16 * W;
   const int64_t n_chunks = (a.n + chunk - 1) / chunk;
@@ -242,7 +209,6 @@ __global__ void __launch_bounds__(H * 2) mlp_kernel(MlpArgs a, hpac_mlp_desc d) 
     float f0[8], f1[8], m0 = 0.f, m1 = 0.f, raw0[4], raw1[4];
     features<KIND>(a.in, a.stride, v0 ? r0 : 0, a.param, d, f0, m0, raw0);
     features<KIND>(a.in, a.stride, v1 ? r1 : 0, a.param, d, f1, m1, raw1);
-    Stage<H> &st = stage[warp];
     // ---- layer 1 (FP32, CUDA cores) straight into the accumulator layout of
     // n-tile j, then GELU and BF16 packing into the A fragments of layer 2
     uint32_t a2[KS][4];
@@ -255,13 +221,6 @@ __global__ void __launch_bounds__(H * 2) mlp_kernel(MlpArgs a, hpac_mlp_desc d) 
       a2[kk][1] = pack_bf16(gelu(z[0][2]), gelu(z[0][3]));
       a2[kk][2] = pack_bf16(gelu(z[1][0]), gelu(z[1][1]));
       a2[kk][3] = pack_bf16(gelu(z[1][2]), gelu(z[1][3]));
-      if (MODE == MODE_GRAD) {  // stage h1 (BF16) for dW2
-        const int col = 16 * kk + 2 * t;
-        *reinterpret_cast<uint32_t *>(&st.h1[g * LD + col]) = a2[kk][0];
-        *reinterpret_cast<uint32_t *>(&st.h1[(g + 8) * LD + col]) = a2[kk][1];
-        *reinterpret_cast<uint32_t *>(&st.h1[g * LD + col + 8]) = a2[kk][2];
-        *reinterpret_cast<uint32_t *>(&st.h1[(g + 8) * LD + col + 8]) = a2[kk][3];
-      }
     }
     // ---- layer 2 (tensor cores)
     float z2[NT][4];
@@ -292,34 +251,6 @@ __global__ void __launch_bounds__(H * 2) mlp_kernel(MlpArgs a, hpac_mlp_desc d) 
     y0 += s.b3;
     y1 += s.b3;
 
-    if (MODE == MODE_INFER) {
-      if (t == 0) {
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const bool v = h ? v1 : v0;
-          if (!v) continue;
-          const int64_t i = h ? r1 : r0;
-          const float pred = (h ? m1 : m0) * fmaf(d.out_scale, h ? y1 : y0, d.out_shift);
-          float o = pred;
-          uint8_t mk = HPAC_MASK_APPROX;
-          if (pred < a.fallback_below) {  // calibrated exact fallback (NaN never falls back)
-            float xr[4];
-#pragma unroll
-            for (int k = 0; k < 4; ++k) xr[k] = h ? raw1[k] : raw0[k];
-            if (KIND == HPAC_REGION_BLACKSCHOLES) o = BlackScholes32{(float)a.param}(xr);
-            mk = HPAC_MASK_EXACT;
-            atomicAdd(&g_fallback, 1ull);
-          }
-          if (KIND == HPAC_REGION_EOS)  // the region's own dtype; pressure is non-negative
-            reinterpret_cast<double *>(a.out)[i] = (double)fmaxf(o, 0.f);
-          else
-            a.out[i] = o;
-          if (a.mask) a.mask[i] = mk;
-        }
-      }
-      continue;
-    }
-
     // ---- backward: dy per row
     float dy0, dy1;
     // d(region output)/d(net) of each row, for the vector-Jacobian products:
@@ -333,26 +264,9 @@ __global__ void __launch_bounds__(H * 2) mlp_kernel(MlpArgs a, hpac_mlp_desc d) 
       go0 = k0 ? a.gout[r0] : 0.f;
       go1 = k1 ? a.gout[r1] : 0.f;
     }
-    if (MODE == MODE_GRAD && a.gout) {
-      dy0 = go0 * m0 * d.out_scale;
-      dy1 = go1 * m1 * d.out_scale;
-      if (t == 0) atomicAdd(&g_b3, dy0 + dy1);
-    } else if (MODE == MODE_GRAD) {
-      // rows whose multiplier is 0 (an untouched EOS element) carry no target
-      const bool u0 = v0 && m0 != 0.f, u1 = v1 && m1 != 0.f;
-      const float t0 = u0 ? (a.target[r0] / m0 - d.out_shift) / d.out_scale : 0.f;
-      const float t1 = u1 ? (a.target[r1] / m1 - d.out_shift) / d.out_scale : 0.f;
-      const float e0 = u0 ? y0 - t0 : 0.f, e1 = u1 ? y1 - t1 : 0.f;
-      dy0 = 2.f * e0 * a.inv_n;
-      dy1 = 2.f * e1 * a.inv_n;
-      if (t == 0) atomicAdd(&g_loss, e0 * e0 + e1 * e1);
-      if (t == 0) atomicAdd(&g_b3, dy0 + dy1);
-    } else {
-      dy0 = v0 ? 1.f : 0.f;  // d(net)/d(inputs)
-      dy1 = v1 ? 1.f : 0.f;
-    }
-    // dz2 = dy W3 gelu'(z2) (packed as BF16 A fragments for dh1 = dz2 W2 and
-    // staged for dW2); dW3 += dy h2; db2 += dz2
+    dy0 = v0 ? 1.f : 0.f;  // d(net)/d(inputs)
+    dy1 = v1 ? 1.f : 0.f;
+    // dz2 = dy W3 gelu'(z2), packed as BF16 A fragments for dh1 = dz2 W2
     uint32_t ad[KS][4];
 #pragma unroll
     for (int kk = 0; kk < KS; ++kk) {
@@ -365,25 +279,11 @@ __global__ void __launch_bounds__(H * 2) mlp_kernel(MlpArgs a, hpac_mlp_desc d) 
         dz[h][1] = dy0 * w1 * gelu_grad(z2[j][1]);
         dz[h][2] = dy1 * w0 * gelu_grad(z2[j][2]);
         dz[h][3] = dy1 * w1 * gelu_grad(z2[j][3]);
-        if (MODE == MODE_GRAD) {
-          const int col = 8 * j + 2 * t;
-          atomicAdd(&g_w3[col], dy0 * bf16r(gelu(z2[j][0])) + dy1 * bf16r(gelu(z2[j][2])));
-          atomicAdd(&g_w3[col + 1], dy0 * bf16r(gelu(z2[j][1])) + dy1 * bf16r(gelu(z2[j][3])));
-          atomicAdd(&g_b2[col], dz[h][0] + dz[h][2]);
-          atomicAdd(&g_b2[col + 1], dz[h][1] + dz[h][3]);
-        }
       }
       ad[kk][0] = pack_bf16(dz[0][0], dz[0][1]);
       ad[kk][1] = pack_bf16(dz[0][2], dz[0][3]);
       ad[kk][2] = pack_bf16(dz[1][0], dz[1][1]);
       ad[kk][3] = pack_bf16(dz[1][2], dz[1][3]);
-      if (MODE == MODE_GRAD) {
-        const int col = 16 * kk + 2 * t;
-        *reinterpret_cast<uint32_t *>(&st.dz2[g * LD + col]) = ad[kk][0];
-        *reinterpret_cast<uint32_t *>(&st.dz2[(g + 8) * LD + col]) = ad[kk][1];
-        *reinterpret_cast<uint32_t *>(&st.dz2[g * LD + col + 8]) = ad[kk][2];
-        *reinterpret_cast<uint32_t *>(&st.dz2[(g + 8) * LD + col + 8]) = ad[kk][3];
-      }
     }
     // dh1 = dz2 W2 (tensor cores, B from the transposed copy); dz1 = dh1 gelu'(z1)
     // with z1 recomputed from the features
@@ -406,22 +306,15 @@ __global__ void __launch_bounds__(H * 2) mlp_kernel(MlpArgs a, hpac_mlp_desc d) 
 #pragma unroll
       for (int q = 0; q < 4; ++q) dz1[q] = acc[q] * gelu_grad(z1[q]);
       const int u0 = 8 * j + 2 * t, u1 = u0 + 1;
-      if (MODE == MODE_GRAD) {
-        *reinterpret_cast<uint32_t *>(&st.dz1[g * LD + u0]) = pack_bf16(dz1[0], dz1[1]);
-        *reinterpret_cast<uint32_t *>(&st.dz1[(g + 8) * LD + u0]) = pack_bf16(dz1[2], dz1[3]);
-        atomicAdd(&g_b1[u0], dz1[0] + dz1[2]);
-        atomicAdd(&g_b1[u1], dz1[1] + dz1[3]);
-      } else {
-        // d(net)/d(features) = dz1 W1
+      // d(net)/d(features) = dz1 W1
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
-          df0[k] = fmaf(dz1[0], s.w1[u0 * 8 + k], fmaf(dz1[1], s.w1[u1 * 8 + k], df0[k]));
-          df1[k] = fmaf(dz1[2], s.w1[u0 * 8 + k], fmaf(dz1[3], s.w1[u1 * 8 + k], df1[k]));
-        }
+      for (int k = 0; k < 8; ++k) {
+        df0[k] = fmaf(dz1[0], s.w1[u0 * 8 + k], fmaf(dz1[1], s.w1[u1 * 8 + k], df0[k]));
+        df1[k] = fmaf(dz1[2], s.w1[u0 * 8 + k], fmaf(dz1[3], s.w1[u1 * 8 + k], df1[k]));
       }
     }
 
-    if (MODE == MODE_INPUT_GRAD) {
+    {
       // the chain rule from the features to the region inputs
 #pragma unroll
       for (int k = 0; k < 8; ++k) {
@@ -480,90 +373,7 @@ __global__ void __launch_bounds__(H * 2) mlp_kernel(MlpArgs a, hpac_mlp_desc d) 
           for (int k = 0; k < 4; ++k) a.out[k * a.n + i] = gin[k];
         }
       }
-      continue;
     }
-
-    // ---- MODE_GRAD: stage the features; weight-gradient GEMMs
-    if (t == 0) {  // features (zero beyond n_feat, zero rows beyond n)
-#pragma unroll
-      for (int k = 0; k < 16; ++k) {
-        st.f[g * 24 + k] = __float2bfloat16_rn(k < 8 && v0 ? f0[k & 7] : 0.f);
-        st.f[(g + 8) * 24 + k] = __float2bfloat16_rn(k < 8 && v1 ? f1[k & 7] : 0.f);
-      }
-    }
-    __syncthreads();
-    // dW2[16w .. 16w+16][:] += sum over the block's 16 W samples of dz2^T h1;
-    // dW1[16w .. 16w+16][0..16) likewise with the features
-    for (int ks = 0; ks < W; ++ks) {   // 16 samples per k-step: warp ks's tile
-      const Stage<H> &sk = stage[ks];
-      uint32_t aa[4];
-      // A = dz2^T rows 16w.., samples of tile ks: transposed 8x8 blocks
-      {
-        const int mtx = lane >> 3, r = lane & 7;
-        const int srow = (mtx >> 1) * 8 + r, ucol = 16 * warp + (mtx & 1) * 8;
-        ldsm_x4_trans(aa[0], aa[1], aa[2], aa[3], &sk.dz2[srow * LD + ucol]);
-      }
-#pragma unroll
-      for (int j = 0; j < NT; j += 2) {
-        uint32_t b0, b1, b2, b3;
-        const int mtx = lane >> 3, r = lane & 7;
-        const int srow = (mtx & 1) * 8 + r, ucol = 8 * j + (mtx >> 1) * 8;
-        ldsm_x4_trans(b0, b1, b2, b3, &sk.h1[srow * LD + ucol]);
-        mma16816(acc2[j], aa, b0, b1);
-        mma16816(acc2[j + 1], aa, b2, b3);
-      }
-      {
-        const int mtx = lane >> 3, r = lane & 7;
-        const int srow = (mtx >> 1) * 8 + r, ucol = 16 * warp + (mtx & 1) * 8;
-        ldsm_x4_trans(aa[0], aa[1], aa[2], aa[3], &sk.dz1[srow * LD + ucol]);
-        uint32_t b0, b1, b2, b3;
-        const int srow2 = (mtx & 1) * 8 + r, fcol = (mtx >> 1) * 8;
-        ldsm_x4_trans(b0, b1, b2, b3, &sk.f[srow2 * 24 + fcol]);
-        mma16816(acc1[0], aa, b0, b1);
-        mma16816(acc1[1], aa, b2, b3);
-      }
-    }
-    __syncthreads();
-  }
-
-  if (MODE == MODE_GRAD) {
-    const int D = d.n_feat;
-    const int oW1 = 0, ob1 = H * D, oW2 = ob1 + H, ob2 = oW2 + H * H, oW3 = ob2 + H, ob3 = oW3 + H;
-    // accumulator rows 16w + g (+8), columns 8j + 2t (+1)
-#pragma unroll
-    for (int j = 0; j < NT; ++j) {
-      const int row = 16 * warp + g, col = 8 * j + 2 * t;
-      atomicAdd(&a.grad[oW2 + row * H + col], acc2[j][0]);
-      atomicAdd(&a.grad[oW2 + row * H + col + 1], acc2[j][1]);
-      atomicAdd(&a.grad[oW2 + (row + 8) * H + col], acc2[j][2]);
-      atomicAdd(&a.grad[oW2 + (row + 8) * H + col + 1], acc2[j][3]);
-    }
-#pragma unroll
-    for (int j = 0; j < 2; ++j) {
-      const int row = 16 * warp + g, col = 8 * j + 2 * t;
-      if (col < D) {
-        atomicAdd(&a.grad[oW1 + row * D + col], acc1[j][0]);
-        atomicAdd(&a.grad[oW1 + (row + 8) * D + col], acc1[j][2]);
-      }
-      if (col + 1 < D) {
-        atomicAdd(&a.grad[oW1 + row * D + col + 1], acc1[j][1]);
-        atomicAdd(&a.grad[oW1 + (row + 8) * D + col + 1], acc1[j][3]);
-      }
-    }
-    __syncthreads();
-    for (int j = threadIdx.x; j < H; j += blockDim.x) {
-      atomicAdd(&a.grad[ob1 + j], g_b1[j]);
-      atomicAdd(&a.grad[ob2 + j], g_b2[j]);
-      atomicAdd(&a.grad[oW3 + j], g_w3[j]);
-    }
-    if (threadIdx.x == 0) {
-      atomicAdd(&a.grad[ob3], g_b3);
-      if (a.loss) atomicAdd(a.loss, g_loss);
-    }
-  }
-  if (MODE == MODE_INFER) {
-    __syncthreads();
-    if (threadIdx.x == 0 && g_fallback && a.counters) atomicAdd(&a.counters[0], g_fallback);
   }
 }
 
@@ -849,6 +659,395 @@ __global__ void __launch_bounds__(kTile) mlp_tc_infer(MlpArgs a, hpac_mlp_desc d
   if (tid == 0 && fallbacks && a.counters) atomicAdd(&a.counters[0], fallbacks);
 }
 
+// ---------------------------------------------------------------------------
+// Training gradients on tcgen05. One thread owns one sample of a 128-sample
+// tile; five tensor-core products per tile, all M = 128 with BF16 operands in
+// the canonical no-swizzle K-major layout and FP32 accumulators in tensor
+// memory:
+//   1. z2 = h1 W2^T            A1 = h1 (rows: samples, K = hidden), B1 = W2
+//   2. dh1 = dz2 W2            A1 = dz2, B2 = W2^T (K = the layer-2 outputs)
+//   3. [dW2 | db2] += dz2^T [h1 | 1]   A3 = dz2^T (rows: units, K = samples),
+//                                      B3 = h1^T with a row of ones
+//   4. dW3 += h2^T dy          A4 = h2^T, B4 rows 0 and 1 = dy split into its
+//                              BF16 value and the BF16 of the remainder
+//   5. [dW1 | db1] += dz1^T [f | 1]    A3 = dz1^T, B4 = the features and ones
+// Products 3-5 contract over the samples (K = 128 per tile) and accumulate in
+// tensor memory across the block's tiles; the block adds its totals to the
+// gradient once at the end. Operands with the samples along K are written
+// element by element (column `thread` of a K-major matrix). Rows beyond H of
+// A3 and A4 stay zero (H = 64). Products 1, 2 and 3-4 are each committed to
+// the block's mbarrier and waited for (bounded, as in the inference kernel);
+// 5 as well. dy, db3 and the loss are reduced in FP32 through shuffles.
+// ---------------------------------------------------------------------------
+template <int H>
+struct TcGradLayout {
+  static constexpr int kA1 = 0;                            // 128 x H: h1, then dz2
+  static constexpr int kB1 = kA1 + kTile * H * 2;          // H x H: W2 [out][in]
+  static constexpr int kB2 = kB1 + H * H * 2;              // H x H: W2^T [in][out]
+  static constexpr int kA3 = kB2 + H * H * 2;              // 128 x 128: dz2^T, then dz1^T
+  static constexpr int kA4 = kA3 + kTile * kTile * 2;      // 128 x 128: h2^T
+  static constexpr int kB3 = kA4 + kTile * kTile * 2;      // (H + 16) x 128: h1^T, ones, zeros
+  static constexpr int kB4 = kB3 + (H + 16) * kTile * 2;   // 16 x 128: dy, then features and ones
+  static constexpr int kW1 = kB4 + 16 * kTile * 2;         // unit pairs x 8 features (float pairs)
+  static constexpr int kB1v = kW1 + H * 8 * 4;
+  static constexpr int kB2v = kB1v + H * 4;
+  static constexpr int kW3 = kB2v + H * 4;
+  static constexpr int kRed = kW3 + H * 4;                 // loss, db3
+  static constexpr int kBar = (kRed + 8 + 7) & ~7;
+  static constexpr int kSlot = kBar + 8;
+  static constexpr int kBytes = kSlot + 8;
+  static constexpr int kCols = (2 * H + 48) <= 256 ? 256 : 512;  // tensor-memory columns
+};
+
+// Byte offset of element (r, s) of an R x 128 K-major operand (K = samples).
+__device__ __forceinline__ int kmajor128_off(int r, int s) {
+  return (r >> 3) * 2048 + (s >> 3) * 128 + (r & 7) * 16 + (s & 7) * 2;
+}
+
+template <int N>
+__host__ __device__ constexpr uint32_t idesc_m128() { return umma_idesc_bf16_m128<N>(); }
+
+// 16 consecutive FP32 accumulator columns of this warp's 32 lanes.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+// GELU derivative of two values in packed pairs.
+__device__ __forceinline__ unsigned long long gelu_grad2(unsigned long long z) {
+  const unsigned long long kA2 = f32x2_pack(kGeluA, kGeluA), kB2 = f32x2_pack(kGeluB, kGeluB);
+  const unsigned long long k3B2 = f32x2_pack(3.0f * kGeluB, 3.0f * kGeluB);
+  const unsigned long long half2 = f32x2_pack(0.5f, 0.5f), one2 = f32x2_pack(1.0f, 1.0f);
+  const unsigned long long zz = f32x2_mul(z, z);
+  const unsigned long long arg = f32x2_mul(kA2, f32x2_fma(f32x2_mul(kB2, z), zz, z));
+  float a0, a1;
+  f32x2_unpack(arg, a0, a1);
+  const unsigned long long th = f32x2_pack(tanh_fast(a0), tanh_fast(a1));
+  const unsigned long long t1 = f32x2_mul(half2, f32x2_add(one2, th));
+  const unsigned long long sech2 = f32x2_sub(one2, f32x2_mul(th, th));
+  const unsigned long long t2 =
+      f32x2_mul(f32x2_mul(f32x2_mul(f32x2_mul(half2, z), sech2), kA2), f32x2_fma(k3B2, zz, one2));
+  return f32x2_add(t1, t2);
+}
+
+__device__ __forceinline__ void st_bf16(unsigned char *base, int off, float v) {
+  *reinterpret_cast<__nv_bfloat16 *>(base + off) = __float2bfloat16_rn(v);
+}
+
+// Issue `steps` K = 16 products (256 bytes along K per step) and commit them.
+__device__ __forceinline__ void umma_k(uint32_t d, uint64_t adesc, uint64_t bdesc, uint32_t idesc, int steps,
+                                       bool accumulate) {
+  for (int ks = 0; ks < steps; ++ks)
+    umma_bf16(d, adesc + (uint64_t)((ks * 256) >> 4), bdesc + (uint64_t)((ks * 256) >> 4), idesc,
+              (accumulate || ks > 0) ? 1u : 0u);
+}
+
+__device__ __forceinline__ void umma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+               : "memory");
+}
+
+__device__ __forceinline__ void sync_for_umma() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+template <int H, int KIND>
+__global__ void __launch_bounds__(kTile) mlp_tc_grad(MlpArgs a, hpac_mlp_desc d) {
+  using L = TcGradLayout<H>;
+  extern __shared__ __align__(1024) unsigned char sm[];
+  float *w1 = reinterpret_cast<float *>(sm + L::kW1);
+  float *b1 = reinterpret_cast<float *>(sm + L::kB1v);
+  float *b2 = reinterpret_cast<float *>(sm + L::kB2v);
+  float *w3 = reinterpret_cast<float *>(sm + L::kW3);
+  float *red = reinterpret_cast<float *>(sm + L::kRed);
+  const uint32_t bar = smem_u32(sm + L::kBar);
+  uint32_t *slot = reinterpret_cast<uint32_t *>(sm + L::kSlot);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int D = d.n_feat;
+  const float *p = a.params;
+  const int oW1 = 0, ob1 = H * D, oW2 = ob1 + H, ob2 = oW2 + H * H, oW3 = ob2 + H, ob3 = oW3 + H;
+  // operands: W2 and its transpose, zeroed sample-major operands, the row of
+  // ones of B3, the weight vectors
+  for (int j = tid; j < H * H; j += kTile) {
+    const int o = j / H, k = j % H;
+    const __nv_bfloat16 w = __float2bfloat16_rn(p[oW2 + j]);
+    *reinterpret_cast<__nv_bfloat16 *>(sm + L::kB1 + kmajor_off<H>(o, k)) = w;
+    *reinterpret_cast<__nv_bfloat16 *>(sm + L::kB2 + kmajor_off<H>(k, o)) = w;
+  }
+  // zeros where no tile writes: rows H.. of A3 and A4 (H = 64), rows H..
+  // of B3 and all of B4 (each row group of 8 is 2048 contiguous bytes)
+  {
+    const uint4 z4 = make_uint4(0u, 0u, 0u, 0u);
+    constexpr int kPad = (kTile - H) * kTile * 2 / 16;  // 16-byte words of rows H..127
+    for (int j = tid; j < kPad; j += kTile) {
+      reinterpret_cast<uint4 *>(sm + L::kA3 + H * kTile * 2)[j] = z4;
+      reinterpret_cast<uint4 *>(sm + L::kA4 + H * kTile * 2)[j] = z4;
+    }
+    for (int j = tid; j < (16 * kTile * 2 + 16 * kTile * 2) / 16; j += kTile)
+      reinterpret_cast<uint4 *>(sm + L::kB3 + H * kTile * 2)[j] = z4;  // B3 rows H..H+15, then B4
+  }
+  __syncthreads();  // the zeros land before the row of ones is written into them
+  st_bf16(sm + L::kB3, kmajor128_off(H, tid), 1.0f);
+  for (int j = tid; j < H * 8; j += kTile) {
+    const int pr = j / 16, k = (j / 2) % 8, h = j % 2;
+    w1[j] = k < D ? bf16r(p[oW1 + (2 * pr + h) * D + k]) : 0.f;
+  }
+  for (int j = tid; j < H; j += kTile) {
+    b1[j] = p[ob1 + j];
+    b2[j] = p[ob2 + j];
+    w3[j] = bf16r(p[oW3 + j]);
+  }
+  if (tid == 0) {
+    red[0] = red[1] = 0.f;
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)),
+                 "r"(L::kCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  sync_for_umma();
+  const uint32_t tmem = *slot;
+  const uint32_t d12 = tmem, d3 = tmem + H, d4 = tmem + 2 * H + 16, d5 = tmem + 2 * H + 32;
+  const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+  const uint64_t a1 = umma_desc(smem_u32(sm + L::kA1), 128, 16 * H);
+  const uint64_t b1d = umma_desc(smem_u32(sm + L::kB1), 128, 16 * H);
+  const uint64_t b2d = umma_desc(smem_u32(sm + L::kB2), 128, 16 * H);
+  const uint64_t a3 = umma_desc(smem_u32(sm + L::kA3), 128, 2048);
+  const uint64_t a4 = umma_desc(smem_u32(sm + L::kA4), 128, 2048);
+  const uint64_t b3d = umma_desc(smem_u32(sm + L::kB3), 128, 2048);
+  const uint64_t b4d = umma_desc(smem_u32(sm + L::kB4), 128, 2048);
+  const float b3 = p[ob3];
+  uint32_t parity = 0;
+  bool failed = false, any = false;
+  const int64_t tiles = (a.n + kTile - 1) / kTile;
+  for (int64_t tile = blockIdx.x; tile < tiles && !failed; tile += gridDim.x) {
+    const int64_t i = tile * kTile + tid;
+    const bool valid = i < a.n;
+    float f[8], mult = 0.f, raw[4];
+    features<KIND>(a.in, a.stride, valid ? i : 0, a.param, d, f, mult, raw);
+    unsigned long long fp[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) fp[k] = f32x2_pack(f[k], f[k]);
+    const ulonglong2 *w1v = reinterpret_cast<const ulonglong2 *>(w1);
+    // ---- phase F: layer 1 and GELU; h1 into row tid of A1 and column tid of B3
+#pragma unroll 2
+    for (int kc = 0; kc < H / 8; ++kc) {
+      uint32_t pk[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int pr = 4 * kc + q;
+        unsigned long long z = *reinterpret_cast<const unsigned long long *>(b1 + 2 * pr);
+#pragma unroll
+        for (int k2 = 0; k2 < 4; ++k2) {
+          const ulonglong2 w = w1v[pr * 4 + k2];
+          if (2 * k2 < D) z = f32x2_fma(w.x, fp[2 * k2], z);
+          if (2 * k2 + 1 < D) z = f32x2_fma(w.y, fp[2 * k2 + 1], z);
+        }
+        float g0, g1;
+        f32x2_unpack(gelu2(z), g0, g1);
+        pk[q] = pack_bf16(g0, g1);
+        *reinterpret_cast<uint16_t *>(sm + L::kB3 + kmajor128_off(2 * pr, tid)) = (uint16_t)(pk[q] & 0xffffu);
+        *reinterpret_cast<uint16_t *>(sm + L::kB3 + kmajor128_off(2 * pr + 1, tid)) = (uint16_t)(pk[q] >> 16);
+      }
+      *reinterpret_cast<uint4 *>(sm + L::kA1 + kmajor_off<H>(tid, 8 * kc)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+    }
+    sync_for_umma();
+    if (tid == 0) {
+      umma_k(d12, a1, b1d, idesc_m128<H>(), H / 16, false);
+      umma_commit(bar);
+    }
+    if (__syncthreads_or(!mbar_wait_bounded(bar, parity))) {
+      failed = true;
+      break;
+    }
+    parity ^= 1u;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    // ---- phase B, pass 1: the network output and the loss derivative dy
+    unsigned long long y2 = 0ull;
+#pragma unroll
+    for (int c = 0; c < H; c += 32) {
+      float v[32];
+      tmem_ld32(d12 + lane_base + (uint32_t)c, v);
+#pragma unroll
+      for (int j = 0; j < 32; j += 2) {
+        const unsigned long long z = f32x2_add(f32x2_pack(v[j], v[j + 1]), *reinterpret_cast<const unsigned long long *>(b2 + c + j));
+        float g0, g1;
+        f32x2_unpack(gelu2(z), g0, g1);
+        const float2 hb = __bfloat1622float2(__floats2bfloat162_rn(g0, g1));
+        y2 = f32x2_fma(f32x2_pack(hb.x, hb.y), *reinterpret_cast<const unsigned long long *>(w3 + c + j), y2);
+      }
+    }
+    float ye, yo;
+    f32x2_unpack(y2, ye, yo);
+    const float y = (ye + yo) + b3;
+    float dy, e2 = 0.f;
+    if (a.gout) {
+      const float o = mult * fmaf(d.out_scale, y, d.out_shift);
+      const bool k = valid && (KIND != HPAC_REGION_EOS || o > 0.f);
+      dy = k ? a.gout[i] * mult * d.out_scale : 0.f;
+    } else {
+      // rows whose multiplier is 0 (an untouched EOS element) carry no target
+      const bool u = valid && mult != 0.f;
+      const float t = u ? (a.target[i] / mult - d.out_shift) / d.out_scale : 0.f;
+      const float e = u ? y - t : 0.f;
+      dy = 2.f * e * a.inv_n;
+      e2 = e * e;
+    }
+    {
+      float s_dy = dy, s_e2 = e2;
+      for (int off = 16; off > 0; off >>= 1) {
+        s_dy += __shfl_xor_sync(0xffffffffu, s_dy, off);
+        s_e2 += __shfl_xor_sync(0xffffffffu, s_e2, off);
+      }
+      if (lane == 0) {
+        atomicAdd(&red[1], s_dy);
+        atomicAdd(&red[0], s_e2);
+      }
+    }
+    // ---- phase B, pass 2: dz2 = dy w3 gelu'(z2) into row tid of A1 (as
+    // BF16) and column tid of A3; h2 into column tid of A4; dy into B4
+    const unsigned long long dyp = f32x2_pack(dy, dy);
+#pragma unroll
+    for (int c = 0; c < H; c += 32) {
+      float v[32];
+      tmem_ld32(d12 + lane_base + (uint32_t)c, v);
+#pragma unroll
+      for (int j = 0; j < 32; j += 8) {
+        uint32_t pk[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int u = c + j + 2 * q;
+          const unsigned long long z = f32x2_add(f32x2_pack(v[j + 2 * q], v[j + 2 * q + 1]),
+                                                 *reinterpret_cast<const unsigned long long *>(b2 + u));
+          float g0, g1;
+          f32x2_unpack(gelu2(z), g0, g1);
+          const uint32_t h2 = pack_bf16(g0, g1);
+          *reinterpret_cast<uint16_t *>(sm + L::kA4 + kmajor128_off(u, tid)) = (uint16_t)(h2 & 0xffffu);
+          *reinterpret_cast<uint16_t *>(sm + L::kA4 + kmajor128_off(u + 1, tid)) = (uint16_t)(h2 >> 16);
+          const unsigned long long dz =
+              f32x2_mul(f32x2_mul(dyp, *reinterpret_cast<const unsigned long long *>(w3 + u)), gelu_grad2(z));
+          float d0, d1;
+          f32x2_unpack(dz, d0, d1);
+          pk[q] = pack_bf16(d0, d1);
+          *reinterpret_cast<uint16_t *>(sm + L::kA3 + kmajor128_off(u, tid)) = (uint16_t)(pk[q] & 0xffffu);
+          *reinterpret_cast<uint16_t *>(sm + L::kA3 + kmajor128_off(u + 1, tid)) = (uint16_t)(pk[q] >> 16);
+        }
+        *reinterpret_cast<uint4 *>(sm + L::kA1 + kmajor_off<H>(tid, c + j)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+      }
+    }
+    {
+      const float hi = bf16r(dy);
+      st_bf16(sm + L::kB4, kmajor128_off(0, tid), hi);
+      st_bf16(sm + L::kB4, kmajor128_off(1, tid), dy - hi);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    sync_for_umma();
+    if (tid == 0) {
+      umma_k(d12, a1, b2d, idesc_m128<H>(), H / 16, false);                 // dh1 = dz2 W2
+      umma_k(d3, a3, b3d, idesc_m128<H + 16>(), kTile / 16, any);           // [dW2 | db2]
+      umma_k(d4, a4, b4d, idesc_m128<16>(), kTile / 16, any);               // dW3
+      umma_commit(bar);
+    }
+    if (__syncthreads_or(!mbar_wait_bounded(bar, parity))) {
+      failed = true;
+      break;
+    }
+    parity ^= 1u;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    // ---- phase C: dz1 = dh1 gelu'(z1) (z1 recomputed) into column tid of
+    // A3; the features and a one into column tid of B4
+#pragma unroll
+    for (int c = 0; c < H; c += 32) {
+      float v[32];
+      tmem_ld32(d12 + lane_base + (uint32_t)c, v);
+#pragma unroll
+      for (int j = 0; j < 32; j += 2) {
+        const int pr = (c + j) / 2;
+        unsigned long long z = *reinterpret_cast<const unsigned long long *>(b1 + 2 * pr);
+#pragma unroll
+        for (int k2 = 0; k2 < 4; ++k2) {
+          const ulonglong2 w = w1v[pr * 4 + k2];
+          if (2 * k2 < D) z = f32x2_fma(w.x, fp[2 * k2], z);
+          if (2 * k2 + 1 < D) z = f32x2_fma(w.y, fp[2 * k2 + 1], z);
+        }
+        const unsigned long long dz1 = f32x2_mul(f32x2_pack(v[j], v[j + 1]), gelu_grad2(z));
+        float d0, d1;
+        f32x2_unpack(dz1, d0, d1);
+        st_bf16(sm + L::kA3, kmajor128_off(c + j, tid), d0);
+        st_bf16(sm + L::kA3, kmajor128_off(c + j + 1, tid), d1);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+      if (k < D) st_bf16(sm + L::kB4, kmajor128_off(k, tid), valid ? f[k] : 0.f);
+    st_bf16(sm + L::kB4, kmajor128_off(D, tid), 1.0f);
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    sync_for_umma();
+    if (tid == 0) {
+      umma_k(d5, a3, b4d, idesc_m128<16>(), kTile / 16, any);               // [dW1 | db1]
+      umma_commit(bar);
+    }
+    if (__syncthreads_or(!mbar_wait_bounded(bar, parity))) {
+      failed = true;
+      break;
+    }
+    parity ^= 1u;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    any = true;
+    // the next tile overwrites B4's rows 0 and 1 (dy) and leaves the feature
+    // rows 2..D of this one, which only columns 2..D of product 4 read
+  }
+  if (failed) {
+    mbar_wait_bounded(bar, parity);
+    if (tid == 0 && a.counters) atomicExch(&a.counters[2], 1ull);
+  } else if (any) {
+    // accumulator row tid: unit tid of dW2 / db2, dW3, dW1 / db1
+    const int j = tid;
+#pragma unroll
+    for (int c = 0; c < H; c += 32) {
+      float v[32];
+      tmem_ld32(d3 + lane_base + (uint32_t)c, v);
+      if (j < H)
+#pragma unroll
+        for (int q = 0; q < 32; ++q) atomicAdd(&a.grad[oW2 + j * H + c + q], v[q]);
+    }
+    float v16[16];
+    tmem_ld16(d3 + lane_base + (uint32_t)H, v16);
+    if (j < H) atomicAdd(&a.grad[ob2 + j], v16[0]);
+    tmem_ld16(d4 + lane_base, v16);
+    if (j < H) atomicAdd(&a.grad[oW3 + j], v16[0] + v16[1]);
+    tmem_ld16(d5 + lane_base, v16);
+    if (j < H) {
+#pragma unroll
+      for (int k = 0; k < 8; ++k)
+        if (k < D) atomicAdd(&a.grad[oW1 + j * D + k], v16[k]);
+      atomicAdd(&a.grad[ob1 + j], v16[D < 8 ? D : 7]);
+    }
+    __syncthreads();
+    if (tid == 0) {
+      atomicAdd(&a.grad[ob3], red[1]);
+      if (a.loss) atomicAdd(a.loss, red[0]);
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(L::kCols));
+}
+
 // Sums of the features, their squares and the per-invocation targets
 // (region output / multiplier) for the normalisation statistics.
 template <int KIND>
@@ -906,11 +1105,10 @@ int n_params_of(const hpac_mlp_desc &d) {
   return H * D + H + H * H + H + H + 1;
 }
 
-template <int H, int KIND, int MODE>
-hpac_status launch_t(hpac_mlp *m, const MlpArgs &a) {
-  const size_t smem = ((sizeof(Smem<H>) + 15) & ~size_t(15)) +
-                      (MODE == MODE_GRAD ? sizeof(Stage<H>) * (H / 16) : 0);
-  auto fn = mlp_kernel<H, KIND, MODE>;
+template <int H, int KIND>
+hpac_status launch_input_grad_t(hpac_mlp *m, const MlpArgs &a) {
+  const size_t smem = (sizeof(Smem<H>) + 15) & ~size_t(15);
+  auto fn = mlp_input_grad_kernel<H, KIND>;
   HPAC_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 1;
   HPAC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, H * 2, smem));
@@ -963,6 +1161,29 @@ hpac_status launch_tc_infer(hpac_mlp *m, const MlpArgs &a) {
   return HPAC_OK;
 }
 
+// The tensor-core training gradient: one 128-thread block per SM at most
+// (its operands take most of the shared memory), one tile of 128 samples per
+// block and iteration.
+template <int H, int KIND>
+hpac_status launch_tc_grad(hpac_mlp *m, const MlpArgs &a) {
+  auto fn = mlp_tc_grad<H, KIND>;
+  const int smem = TcGradLayout<H>::kBytes;
+  HPAC_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  const int64_t tiles = (a.n + kTile - 1) / kTile;
+  int64_t blocks = sm_count(m->device);
+  if (blocks > tiles) blocks = tiles < 1 ? 1 : tiles;
+  fn<<<(unsigned)blocks, kTile, smem, m->stream>>>(a, m->d);
+  HPAC_CUDA_TRY(cudaGetLastError());
+  return HPAC_OK;
+}
+
+hpac_status launch_grad(hpac_mlp *m, const MlpArgs &a) {
+  const bool bs = m->d.kind == HPAC_REGION_BLACKSCHOLES;
+  if (m->d.hidden == 64)
+    return bs ? launch_tc_grad<64, HPAC_REGION_BLACKSCHOLES>(m, a) : launch_tc_grad<64, HPAC_REGION_EOS>(m, a);
+  return bs ? launch_tc_grad<128, HPAC_REGION_BLACKSCHOLES>(m, a) : launch_tc_grad<128, HPAC_REGION_EOS>(m, a);
+}
+
 hpac_status launch_infer(hpac_mlp *m, const MlpArgs &a) {
   const bool bs = m->d.kind == HPAC_REGION_BLACKSCHOLES;
   if (m->d.hidden == 64)
@@ -970,12 +1191,13 @@ hpac_status launch_infer(hpac_mlp *m, const MlpArgs &a) {
   return bs ? launch_tc_infer<128, HPAC_REGION_BLACKSCHOLES>(m, a) : launch_tc_infer<128, HPAC_REGION_EOS>(m, a);
 }
 
-template <int MODE>
-hpac_status launch(hpac_mlp *m, const MlpArgs &a) {
+hpac_status launch_input_grad(hpac_mlp *m, const MlpArgs &a) {
   const bool bs = m->d.kind == HPAC_REGION_BLACKSCHOLES;
   if (m->d.hidden == 64)
-    return bs ? launch_t<64, HPAC_REGION_BLACKSCHOLES, MODE>(m, a) : launch_t<64, HPAC_REGION_EOS, MODE>(m, a);
-  return bs ? launch_t<128, HPAC_REGION_BLACKSCHOLES, MODE>(m, a) : launch_t<128, HPAC_REGION_EOS, MODE>(m, a);
+    return bs ? launch_input_grad_t<64, HPAC_REGION_BLACKSCHOLES>(m, a)
+              : launch_input_grad_t<64, HPAC_REGION_EOS>(m, a);
+  return bs ? launch_input_grad_t<128, HPAC_REGION_BLACKSCHOLES>(m, a)
+            : launch_input_grad_t<128, HPAC_REGION_EOS>(m, a);
 }
 
 uint64_t sm64(uint64_t &s) {
@@ -1143,13 +1365,21 @@ extern "C" hpac_status hpac_mlp_grad(hpac_mlp *m, int64_t n, const void *d_in, i
   a.params = m->params;
   a.grad = grad;
   a.loss = m->loss;
+  a.counters = m->counters;
   a.inv_n = 1.0f / (float)n;
-  s = launch<MODE_GRAD>(m, a);
+  s = launch_grad(m, a);
   if (s != HPAC_OK) return s;
   if (h_loss) {
     float l = 0.f;
+    unsigned long long status = 0;
     HPAC_CUDA_TRY(cudaMemcpyAsync(&l, m->loss, sizeof(float), cudaMemcpyDeviceToHost, m->stream));
+    HPAC_CUDA_TRY(cudaMemcpyAsync(&status, m->counters + 2, sizeof(status), cudaMemcpyDeviceToHost, m->stream));
     HPAC_CUDA_TRY(cudaStreamSynchronize(m->stream));
+    if (status) {
+      HPAC_CUDA_TRY(cudaMemsetAsync(m->counters + 2, 0, sizeof(unsigned long long), m->stream));
+      return set_error(HPAC_ETIMEOUT, "surrogate gradient: a tensor-core product did not complete within "
+                                      "the kernel's wait limit");
+    }
     *h_loss = l / (float)n;
   }
   return HPAC_OK;
@@ -1202,7 +1432,7 @@ extern "C" hpac_status hpac_mlp_input_grad(hpac_mlp *m, int64_t n, const void *d
   MlpArgs a{};
   a.in = d_in, a.stride = in_stride, a.n = n, a.param = param, a.out = d_grad;
   a.params = m->params;
-  return launch<MODE_INPUT_GRAD>(m, a);
+  return launch_input_grad(m, a);
 }
 
 extern "C" hpac_status hpac_mlp_vjp(hpac_mlp *m, int64_t n, const void *d_in, int64_t in_stride,
@@ -1219,7 +1449,8 @@ extern "C" hpac_status hpac_mlp_vjp(hpac_mlp *m, int64_t n, const void *d_in, in
       a.in = d_in, a.stride = in_stride, a.n = n, a.param = param, a.gout = d_gout;
       a.params = m->params;
       a.grad = d_grad_params;
-      s = launch<MODE_GRAD>(m, a);
+      a.counters = m->counters;
+      s = launch_grad(m, a);
       if (s != HPAC_OK) return s;
     }
   }
@@ -1227,7 +1458,7 @@ extern "C" hpac_status hpac_mlp_vjp(hpac_mlp *m, int64_t n, const void *d_in, in
     MlpArgs a{};
     a.in = d_in, a.stride = in_stride, a.n = n, a.param = param, a.out = d_grad_in, a.gout = d_gout;
     a.params = m->params;
-    s = launch<MODE_INPUT_GRAD>(m, a);
+    s = launch_input_grad(m, a);
     if (s != HPAC_OK) return s;
   }
   return HPAC_OK;
