@@ -272,6 +272,46 @@ def test_workload_256_cubed_launch_configuration(H, orc):
     G.close()
 
 
+def test_workload_256_cubed_headline_form(H, orc):
+    """The benchmark's headline form at its full size and launch configuration:
+    the 256^3 mesh with the EOS under iACT (8 slots, one table per warp,
+    distance 1e-3 on the benchmark's input scales) with one logical thread
+    per element and the tables kept across steps. Both sides take four steps
+    from the initial mesh; at every step the masks are identical, and after
+    the last the node fields agree everywhere and the element fields on a
+    sample."""
+    n, steps = 256, 4
+    E = n ** 3
+    x, y, z, e = W.hydro_initial(n)
+    S = orc.HydroState(n, x, y, z, e)
+    G = H.Hydro(n, x, y, z, e, W.hydro_dt(n), logical_threads=E // 8, block_threads=256)
+    R = H.Region(H.HPAC_REGION_EOS, G["eos_in"], param=orc.GAMMA, logical_threads=E, block_threads=256)
+    R.set_persistent(True)
+    sc = (1.0 / W.HYDRO_E0, 1.0, 10.0, 1.0 / ((orc.GAMMA - 1.0) * W.HYDRO_E0))
+    ok = orc.eos_knobs(orc.EOS_IACT, tsize=8, tperwarp=1, thresh=1e-3, threads=E, block=256, in_scale=sc,
+                       persistent=True)
+    scale = (H.C.c_double * 4)(*sc)
+    gk = H.hpac_iact_knobs(8, 1, 1e-3, 0, 0, H.C.cast(scale, H.C.POINTER(H.C.c_double)))
+    mask = torch.full((E,), 255, dtype=torch.uint8, device="cuda")
+    dt = W.hydro_dt(n)
+    for s in range(steps):
+        _, om, _ = S.step(dt, ok)
+        H.hpac_hydro_step(G.state, R._h, H.HYDRO_IACT, gk, H.C.c_void_p(mask.data_ptr()))
+        torch.cuda.synchronize()
+        gm = mask.cpu().numpy()
+        assert np.array_equal(gm, om), (s, int((gm != om).sum()))
+    assert (gm == 1).sum() > E // 2
+    for f in NODE:
+        close(G[f].cpu(), getattr(S, f), 1e-12, f)
+    idx = np.random.default_rng(2).choice(E, 1 << 16, replace=False)
+    idx = np.concatenate([idx, np.arange(4096)])            # the corner, where the blast is
+    for f in ("p", "e", "q"):
+        close(G[f].cpu().numpy()[idx], getattr(S, f)[idx], 1e-12, f)
+    R.set_persistent(False)
+    R.close()
+    G.close()
+
+
 def test_state_arrays_checkpoint_and_resume(H, orc):
     """The library keeps no state: copying the arrays and resuming gives the
     same run bit for bit."""
