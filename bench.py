@@ -917,12 +917,12 @@ def graph_ms(torch, R, stream, f, reps):
         with torch.cuda.graph(g, stream=side):
             for _ in range(reps):
                 f()
-        g.replay()
-        torch.cuda.synchronize()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(side)
-        g.replay()
-        b.record(side)
+        with torch.cuda.stream(side):      # replay() launches on the current stream
+            g.replay()
+            a.record()
+            g.replay()
+            b.record()
         torch.cuda.synchronize()
         return a.elapsed_time(b) / reps
     except Exception:
