@@ -41,7 +41,7 @@ typedef enum {
   HPAC_EINVAL = 1,        /* bad argument: descriptor, knob, pointer or size   */
   HPAC_ENOMEM = 2,        /* a device or host allocation failed                */
   HPAC_ECUDA = 3,         /* a CUDA runtime call failed (message says which)   */
-  HPAC_ETIMEOUT = 4,      /* reserved: a bounded device-side wait gave up      */
+  HPAC_ETIMEOUT = 4,      /* a bounded device-side wait gave up                */
   HPAC_EUNSUPPORTED = 5   /* valid request this build does not implement       */
 } hpac_status;
 

@@ -120,9 +120,13 @@ static hpac_status begin_counters(hpac_region *r, const void *h_stats) {
 
 static hpac_status end_counters(hpac_region *r, hpac_stats *h, int64_t skipped_known) {
   if (!h) return HPAC_OK;
-  unsigned long long c[2] = {0, 0};
+  unsigned long long c[3] = {0, 0, 0};
   HPAC_CUDA_TRY(cudaMemcpyAsync(c, r->d_counters, sizeof(c), cudaMemcpyDeviceToHost, r->stream));
   HPAC_CUDA_TRY(cudaStreamSynchronize(r->stream));
+  if (c[2]) {  // a bounded device-side wait of an earlier call gave up
+    HPAC_CUDA_TRY(cudaMemsetAsync(r->d_counters + 2, 0, sizeof(unsigned long long), r->stream));
+    return set_error(HPAC_ETIMEOUT, "a bounded device-side wait of the region's kernels gave up");
+  }
   h->invocations = r->d.n;
   h->approximated = (int64_t)c[0];
   h->skipped = skipped_known;
@@ -177,6 +181,7 @@ hpac_status hpac_region_create(const hpac_region_desc *desc, void *cuda_stream, 
   r->stream = (cudaStream_t)cuda_stream;
   cudaError_t e = cudaGetDevice(&r->device);
   if (e == cudaSuccess) e = cudaMalloc(&r->d_counters, 4 * sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMemset(r->d_counters, 0, 4 * sizeof(unsigned long long));
   if (e != cudaSuccess) {
     free(r);
     return cuda_error(e, "hpac_region_create");
