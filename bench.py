@@ -761,6 +761,10 @@ def bench_surrogate(hpac, torch, dev, stream, n_train=1 << 22, n_cal=1 << 20, n_
         taf_stats = R.run_taf(xi, taf_out, 4, 8, 0.005, 0, stats=True)
     sur_ms = timed(lambda: S.infer(xi, out, W.BS_RATE, fallback_below=tau, mask=mask))
     nofb_ms = timed(lambda: S.infer(xi, out, W.BS_RATE))
+    # input derivatives (the input half of a vector-Jacobian product) on the same options
+    gin = torch.zeros(4, n_inf, dtype=torch.float32, device=dev)
+    igrad_ms = timed(lambda: S.input_grad(xi, gin, W.BS_RATE))
+    del gin
     S.infer(xi, out, W.BS_RATE, fallback_below=tau, mask=mask)
     ref = exact(xi, torch.float64)
     o, r, m = out.cpu().numpy().astype(np.float64), ref.cpu().numpy(), mask.cpu().numpy()
@@ -779,6 +783,8 @@ def bench_surrogate(hpac, torch, dev, stream, n_train=1 << 22, n_cal=1 << 20, n_
                       "exact_kernel_ms": exact_ms, "speedup_vs_exact": exact_ms / sur_ms,
                       "surrogate_fraction": st["approximated"] / n_inf,
                       "layer2_tensor_tflops": flops / (nofb_ms * 1e-3) / 1e12},
+        "input_gradient": {"options": n_inf, "ms": igrad_ms,
+                           "tensor_tflops": 2 * flops / (igrad_ms * 1e-3) / 1e12},
         "quality": {"nrmse": float(np.sqrt(np.mean((o - r) ** 2)) / rms),
                     "p99_rel_err_on_surrogate_outputs": float(np.quantile(rel[approx], 0.99)) if approx.any() else None,
                     "max_rel_err_on_surrogate_outputs": float(rel[approx].max()) if approx.any() else None},

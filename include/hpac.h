@@ -446,8 +446,9 @@ hpac_status hpac_region_vjp(hpac_region *region, const void *d_in, const void *d
  * Learned surrogate of a region (not from the paper): an MLP
  * n_feat -> hidden -> hidden -> 1 with GELU (tanh form), BF16 weights and
  * activations and FP32 accumulation; layer 1 on FP32 features, layer 2 (in
- * inference and training) and the training gradient's contractions over the
- * samples on the tcgen05 tensor cores with tensor-memory accumulators. Their
+ * inference, training and input derivatives), the backward product
+ * dh1 = dz2 W2 and the training gradient's contractions over the samples on
+ * the tcgen05 tensor cores with tensor-memory accumulators. Their
  * kernels bound every wait on a tensor-core product; a wait that gives up is
  * reported as HPAC_ETIMEOUT by the next call that returns statistics or a
  * loss (hpac_mlp_infer with h_stats, hpac_mlp_grad / hpac_mlp_train with
@@ -537,7 +538,10 @@ hpac_status hpac_mlp_train(hpac_mlp *mlp, int64_t n, const void *d_in, int64_t i
 
 /* Derivatives of the surrogate's region output with respect to the region
  * inputs (the surrogate's counterpart of hpac_region_adjoint): d_grad receives
- * 4 x n floats, row d at d_grad[d * n + i]. */
+ * 4 x n floats, row d at d_grad[d * n + i]. Asynchronous on the surrogate's
+ * stream. Errors: HPAC_EINVAL (NULL surrogate, inputs or d_grad with n > 0,
+ * n < 0, stride < n), HPAC_ECUDA, HPAC_EUNSUPPORTED (the kernel does not fit
+ * an SM). */
 hpac_status hpac_mlp_input_grad(hpac_mlp *mlp, int64_t n, const void *d_in, int64_t in_stride,
                                 double param, float *d_grad);
 

@@ -15,11 +15,11 @@
 //    accumulated in tensor memory across a block's tiles; the same pass with
 //    a caller's per-sample d(loss)/d(output) in place of the squared error's
 //    gives the parameter half of a vector-Jacobian product;
-//  - input derivatives (mlp_input_grad_kernel): forward and backward through
-//    the network on warp-level mma.sync m16n8k16 with the fragments kept in
-//    registers, then the chain rule from the features to the region inputs
-//    (the input half of a vector-Jacobian product scales it by the caller's
-//    per-sample derivative).
+//  - input derivatives (mlp_tc_input_grad): the forward product and the
+//    backward product dh1 = dz2 W2 on tcgen05, one invocation per thread,
+//    then the chain rule from the features to the region inputs on the CUDA
+//    cores (the input half of a vector-Jacobian product scales it by the
+//    caller's per-sample derivative).
 #include <cuda_bf16.h>
 #include <math.h>
 #include <stdlib.h>
@@ -52,31 +52,11 @@ __device__ __forceinline__ float tanh_fast(float x) {
   asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
   return y;
 }
-__device__ __forceinline__ float gelu(float z) {
-  const float th = tanh_fast(kGeluA * fmaf(kGeluB * z, z * z, z));
-  return 0.5f * z * (1.0f + th);
-}
-__device__ __forceinline__ float gelu_grad(float z) {
-  const float th = tanh_fast(kGeluA * fmaf(kGeluB * z, z * z, z));
-  return 0.5f * (1.0f + th) + 0.5f * z * (1.0f - th * th) * kGeluA * fmaf(3.0f * kGeluB, z * z, 1.0f);
-}
-
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
   const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
   return *reinterpret_cast<const uint32_t *>(&v);
 }
 __device__ __forceinline__ float bf16r(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
-
-__device__ __forceinline__ void mma16816(float (&d)[4], const uint32_t (&a)[4], uint32_t b0,
-                                         uint32_t b1) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
-      "{%8,%9}, {%0,%1,%2,%3};\n"
-      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-
-
 
 struct MlpArgs {
   const void *in;       // region inputs (SoA, in_stride)
@@ -95,6 +75,13 @@ struct MlpArgs {
                         // the gradient takes it instead of the squared error, the input
                         // gradient multiplies each input derivative by it (nullable)
 };
+
+// Feature count of a region kind (the descriptor's n_feat is checked against it
+// at creation), a compile-time constant in the kernels.
+template <int KIND>
+constexpr int n_feat_of() {
+  return KIND == HPAC_REGION_BLACKSCHOLES ? 5 : 4;
+}
 
 // Features of one invocation (FP32) and the output multiplier of the region.
 template <int KIND>
@@ -125,256 +112,7 @@ __device__ __forceinline__ void features(const void *in, int64_t stride, int64_t
     mult = u > 0.0 ? (float)((param - 1.0) * u / v1) : 0.f;
   }
 #pragma unroll
-  for (int k = 0; k < 8; ++k) f[k] = k < d.n_feat ? (f[k] - d.feat_shift[k]) * d.feat_scale[k] : 0.f;
-}
-
-template <int H>
-struct Smem {
-  static constexpr int LD = H + 8;  // padded row (bf16): conflict-free 32-bit and ldmatrix loads
-  __nv_bfloat16 w2[H * LD];         // W2[out][in]
-  __nv_bfloat16 w2t[H * LD];        // W2[out][in] transposed: [in][out]
-  float w1[H * 8];                  // W1[unit][feature], BF16-rounded values
-  float b1[H], b2[H], w3[H];
-  float b3;
-};
-
-
-template <int H>
-__device__ void load_params(Smem<H> &s, const float *p, int D) {
-  constexpr int LD = Smem<H>::LD;
-  const int oW1 = 0, ob1 = H * D, oW2 = ob1 + H, ob2 = oW2 + H * H, oW3 = ob2 + H, ob3 = oW3 + H;
-  for (int j = threadIdx.x; j < H * H; j += blockDim.x) {
-    const int o = j / H, k = j % H;
-    const __nv_bfloat16 w = __float2bfloat16_rn(p[oW2 + j]);
-    s.w2[o * LD + k] = w;
-    s.w2t[k * LD + o] = w;
-  }
-  for (int j = threadIdx.x; j < H * 8; j += blockDim.x) {
-    const int u = j / 8, k = j % 8;
-    s.w1[j] = k < D ? bf16r(p[oW1 + u * D + k]) : 0.f;
-  }
-  for (int j = threadIdx.x; j < H; j += blockDim.x) {
-    s.b1[j] = p[ob1 + j];
-    s.b2[j] = p[ob2 + j];
-    s.w3[j] = bf16r(p[oW3 + j]);
-  }
-  if (threadIdx.x == 0) s.b3 = p[ob3];
-}
-
-// Layer-1 pre-activations of n-tile j in the m16n8 accumulator layout of lane
-// (g, t): rows g and g + 8 (features f0, f1), units 8j + 2t and 8j + 2t + 1.
-template <int H>
-__device__ __forceinline__ void layer1_tile(const Smem<H> &s, int j, int t, int D, const float (&f0)[8],
-                                            const float (&f1)[8], float (&z)[4]) {
-  const int u0 = 8 * j + 2 * t, u1 = u0 + 1;
-  float s00 = s.b1[u0], s01 = s.b1[u1], s10 = s.b1[u0], s11 = s.b1[u1];
-#pragma unroll
-  for (int k = 0; k < 8; ++k) {
-    if (k < D) {
-      s00 = fmaf(s.w1[u0 * 8 + k], f0[k], s00);
-      s01 = fmaf(s.w1[u1 * 8 + k], f0[k], s01);
-      s10 = fmaf(s.w1[u0 * 8 + k], f1[k], s10);
-      s11 = fmaf(s.w1[u1 * 8 + k], f1[k], s11);
-    }
-  }
-  z[0] = s00, z[1] = s01, z[2] = s10, z[3] = s11;
-}
-
-// Derivatives of the surrogate's output with respect to the region inputs
-// (hpac_mlp_input_grad and the input half of hpac_mlp_vjp) on warp-level
-// mma.sync: a warp owns 16 samples at a time; its layer-1 outputs land in the
-// accumulator layout of the m16n8 tiles, so GELU and BF16 packing turn them
-// into the A fragments of layer 2 in registers, and the backward product
-// dh1 = dz2 W2 reads B from the transposed copy of W2.
-template <int H, int KIND>
-__global__ void __launch_bounds__(H * 2) mlp_input_grad_kernel(MlpArgs a, hpac_mlp_desc d) {
-  constexpr int NT = H / 8;    // n-tiles of 8 hidden units
-  constexpr int KS = H / 16;   // k-steps of 16 hidden units
-  constexpr int W = H / 16;    // warps per block
-  constexpr int LD = Smem<H>::LD;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  Smem<H> &s = *reinterpret_cast<Smem<H> *>(smem_raw);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int g = lane >> 2, t = lane & 3;
-  load_params<H>(s, a.params, d.n_feat);
-  __syncthreads();
-
-  const int64_t chunk = 16 * W;
-  const int64_t n_chunks = (a.n + chunk - 1) / chunk;
-  for (int64_t c = blockIdx.x; c < n_chunks; c += gridDim.x) {
-    const int64_t base = c * chunk + warp * 16;
-    const int64_t r0 = base + g, r1 = base + g + 8;
-    const bool v0 = r0 < a.n, v1 = r1 < a.n;
-    // ---- features of rows g and g + 8
-    float f0[8], f1[8], m0 = 0.f, m1 = 0.f, raw0[4], raw1[4];
-    features<KIND>(a.in, a.stride, v0 ? r0 : 0, a.param, d, f0, m0, raw0);
-    features<KIND>(a.in, a.stride, v1 ? r1 : 0, a.param, d, f1, m1, raw1);
-    // ---- layer 1 (FP32, CUDA cores) straight into the accumulator layout of
-    // n-tile j, then GELU and BF16 packing into the A fragments of layer 2
-    uint32_t a2[KS][4];
-#pragma unroll
-    for (int kk = 0; kk < KS; ++kk) {
-      float z[2][4];
-#pragma unroll
-      for (int h = 0; h < 2; ++h) layer1_tile(s, 2 * kk + h, t, d.n_feat, f0, f1, z[h]);
-      a2[kk][0] = pack_bf16(gelu(z[0][0]), gelu(z[0][1]));
-      a2[kk][1] = pack_bf16(gelu(z[0][2]), gelu(z[0][3]));
-      a2[kk][2] = pack_bf16(gelu(z[1][0]), gelu(z[1][1]));
-      a2[kk][3] = pack_bf16(gelu(z[1][2]), gelu(z[1][3]));
-    }
-    // ---- layer 2 (tensor cores)
-    float z2[NT][4];
-#pragma unroll
-    for (int j = 0; j < NT; ++j) {
-      const float bb0 = s.b2[8 * j + 2 * t], bb1 = s.b2[8 * j + 2 * t + 1];
-      z2[j][0] = bb0, z2[j][1] = bb1, z2[j][2] = bb0, z2[j][3] = bb1;
-      const __nv_bfloat16 *wrow = s.w2 + (8 * j + g) * LD + 2 * t;
-#pragma unroll
-      for (int kk = 0; kk < KS; ++kk) {
-        const uint32_t b0 = *reinterpret_cast<const uint32_t *>(wrow + 16 * kk);
-        const uint32_t b1 = *reinterpret_cast<const uint32_t *>(wrow + 16 * kk + 8);
-        mma16816(z2[j], a2[kk], b0, b1);
-      }
-    }
-    // ---- GELU, BF16 h2, layer 3 (h2 is recomputed where the backward needs it)
-    float y0 = 0.f, y1 = 0.f;
-#pragma unroll
-    for (int j = 0; j < NT; ++j) {
-      const float w0 = s.w3[8 * j + 2 * t], w1 = s.w3[8 * j + 2 * t + 1];
-      y0 = fmaf(bf16r(gelu(z2[j][0])), w0, fmaf(bf16r(gelu(z2[j][1])), w1, y0));
-      y1 = fmaf(bf16r(gelu(z2[j][2])), w0, fmaf(bf16r(gelu(z2[j][3])), w1, y1));
-    }
-    y0 += __shfl_xor_sync(0xffffffffu, y0, 1);
-    y0 += __shfl_xor_sync(0xffffffffu, y0, 2);
-    y1 += __shfl_xor_sync(0xffffffffu, y1, 1);
-    y1 += __shfl_xor_sync(0xffffffffu, y1, 2);
-    y0 += s.b3;
-    y1 += s.b3;
-
-    // ---- backward: dy per row
-    float dy0, dy1;
-    // d(region output)/d(net) of each row, for the vector-Jacobian products:
-    // mult out_scale, and 0 where the EOS output is clamped at zero
-    float go0 = 0.f, go1 = 0.f;
-    if (a.gout) {
-      const float o0 = m0 * fmaf(d.out_scale, y0, d.out_shift);
-      const float o1 = m1 * fmaf(d.out_scale, y1, d.out_shift);
-      const bool k0 = v0 && (KIND != HPAC_REGION_EOS || o0 > 0.f);
-      const bool k1 = v1 && (KIND != HPAC_REGION_EOS || o1 > 0.f);
-      go0 = k0 ? a.gout[r0] : 0.f;
-      go1 = k1 ? a.gout[r1] : 0.f;
-    }
-    dy0 = v0 ? 1.f : 0.f;  // d(net)/d(inputs)
-    dy1 = v1 ? 1.f : 0.f;
-    // dz2 = dy W3 gelu'(z2), packed as BF16 A fragments for dh1 = dz2 W2
-    uint32_t ad[KS][4];
-#pragma unroll
-    for (int kk = 0; kk < KS; ++kk) {
-      float dz[2][4];
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int j = 2 * kk + h;
-        const float w0 = s.w3[8 * j + 2 * t], w1 = s.w3[8 * j + 2 * t + 1];
-        dz[h][0] = dy0 * w0 * gelu_grad(z2[j][0]);
-        dz[h][1] = dy0 * w1 * gelu_grad(z2[j][1]);
-        dz[h][2] = dy1 * w0 * gelu_grad(z2[j][2]);
-        dz[h][3] = dy1 * w1 * gelu_grad(z2[j][3]);
-      }
-      ad[kk][0] = pack_bf16(dz[0][0], dz[0][1]);
-      ad[kk][1] = pack_bf16(dz[0][2], dz[0][3]);
-      ad[kk][2] = pack_bf16(dz[1][0], dz[1][1]);
-      ad[kk][3] = pack_bf16(dz[1][2], dz[1][3]);
-    }
-    // dh1 = dz2 W2 (tensor cores, B from the transposed copy); dz1 = dh1 gelu'(z1)
-    // with z1 recomputed from the features
-    float df0[8], df1[8];
-#pragma unroll
-    for (int k = 0; k < 8; ++k) df0[k] = df1[k] = 0.f;
-#pragma unroll
-    for (int j = 0; j < NT; ++j) {
-      float acc[4] = {0.f, 0.f, 0.f, 0.f};
-      const __nv_bfloat16 *wrow = s.w2t + (8 * j + g) * LD + 2 * t;
-#pragma unroll
-      for (int kk = 0; kk < KS; ++kk) {
-        const uint32_t b0 = *reinterpret_cast<const uint32_t *>(wrow + 16 * kk);
-        const uint32_t b1 = *reinterpret_cast<const uint32_t *>(wrow + 16 * kk + 8);
-        mma16816(acc, ad[kk], b0, b1);
-      }
-      float z1[4];
-      layer1_tile(s, j, t, d.n_feat, f0, f1, z1);
-      float dz1[4];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) dz1[q] = acc[q] * gelu_grad(z1[q]);
-      const int u0 = 8 * j + 2 * t, u1 = u0 + 1;
-      // d(net)/d(features) = dz1 W1
-#pragma unroll
-      for (int k = 0; k < 8; ++k) {
-        df0[k] = fmaf(dz1[0], s.w1[u0 * 8 + k], fmaf(dz1[1], s.w1[u1 * 8 + k], df0[k]));
-        df1[k] = fmaf(dz1[2], s.w1[u0 * 8 + k], fmaf(dz1[3], s.w1[u1 * 8 + k], df1[k]));
-      }
-    }
-
-    {
-      // the chain rule from the features to the region inputs
-#pragma unroll
-      for (int k = 0; k < 8; ++k) {
-        df0[k] += __shfl_xor_sync(0xffffffffu, df0[k], 1);
-        df0[k] += __shfl_xor_sync(0xffffffffu, df0[k], 2);
-        df1[k] += __shfl_xor_sync(0xffffffffu, df1[k], 1);
-        df1[k] += __shfl_xor_sync(0xffffffffu, df1[k], 2);
-      }
-      if (t == 0) {
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          if (!(h ? v1 : v0)) continue;
-          const int64_t i = h ? r1 : r0;
-          float df[8], raw[4];
-#pragma unroll
-          for (int k = 0; k < 8; ++k) df[k] = (h ? df1[k] : df0[k]) * d.feat_scale[k];
-#pragma unroll
-          for (int k = 0; k < 4; ++k) raw[k] = h ? raw1[k] : raw0[k];
-          const float net = h ? y1 : y0;
-          float gin[4];
-          if (KIND == HPAC_REGION_BLACKSCHOLES) {
-            // region output C = S (shift + scale net); features ln(S/K),
-            // sigma sqrt(T), r T, d1 (clamped to [-10, 10]), sigma
-            const float S = raw[0], K = raw[1], Tm = raw[2], sig = raw[3];
-            const float sc = d.out_scale, sq = sqrtf(Tm), r = (float)a.param;
-            const float sst = sig * sq;
-            const float d1 = (logf(S / K) + (r + 0.5f * sig * sig) * Tm) / sst;
-            const float g3 = (d1 > -10.f && d1 < 10.f) ? df[3] : 0.f;  // clamp
-            const float dnet_dS = df[0] / S + g3 / (S * sst);
-            const float dnet_dK = -df[0] / K - g3 / (K * sst);
-            const float dnet_dT = df[1] * sig * 0.5f / sq + df[2] * r +
-                                  g3 * ((r + 0.5f * sig * sig) / sst - 0.5f * d1 / Tm);
-            const float dnet_dsig = df[1] * sq + df[4] + g3 * (sq - d1 / sig);
-            gin[0] = fmaf(sc, net, d.out_shift) + S * sc * dnet_dS;
-            gin[1] = S * sc * dnet_dK;
-            gin[2] = S * sc * dnet_dT;
-            gin[3] = S * sc * dnet_dsig;
-          } else {
-            // p = mult (shift + scale net), mult = (g - 1) (e - dv q) / v1 where positive
-            const float v1 = raw[1], dv = raw[2], q = raw[3];
-            const float g1 = (float)a.param - 1.f;
-            const float m = h ? m1 : m0;
-            const float ratio = fmaf(d.out_scale, net, d.out_shift);
-            const bool on = m > 0.f;
-            const float dm[4] = {on ? g1 / v1 : 0.f, on ? -m / v1 : 0.f, on ? -g1 * q / v1 : 0.f,
-                                 on ? -g1 * dv / v1 : 0.f};
-#pragma unroll
-            for (int k = 0; k < 4; ++k) gin[k] = ratio * dm[k] + m * d.out_scale * df[k];
-          }
-          if (a.gout) {
-            const float go = h ? go1 : go0;
-#pragma unroll
-            for (int k = 0; k < 4; ++k) gin[k] *= go;
-          }
-#pragma unroll
-          for (int k = 0; k < 4; ++k) a.out[k * a.n + i] = gin[k];
-        }
-      }
-    }
-  }
+  for (int k = 0; k < 8; ++k) f[k] = k < n_feat_of<KIND>() ? (f[k] - d.feat_shift[k]) * d.feat_scale[k] : 0.f;
 }
 
 // ---------------------------------------------------------------------------
@@ -485,9 +223,9 @@ __device__ __forceinline__ int kmajor_off(int r, int k) {
   return (r >> 3) * (16 * H) + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2;
 }
 
-// GELU of two values in packed single-precision pairs: the operations and
-// their order are those of gelu() per half (one IEEE rounding each), the
-// hyperbolic tangent per value.
+// GELU of two values in packed single-precision pairs,
+// 0.5 z (1 + tanh(sqrt(2/pi) (z + 0.044715 z^3))), one IEEE rounding per
+// operation and half, the hyperbolic tangent per value.
 __device__ __forceinline__ unsigned long long gelu2(unsigned long long z) {
   const unsigned long long kA2 = f32x2_pack(kGeluA, kGeluA), kB2 = f32x2_pack(kGeluB, kGeluB);
   const unsigned long long half2 = f32x2_pack(0.5f, 0.5f), one2 = f32x2_pack(1.0f, 1.0f);
@@ -511,7 +249,7 @@ __global__ void __launch_bounds__(kTile) mlp_tc_infer(MlpArgs a, hpac_mlp_desc d
   uint32_t *slot = reinterpret_cast<uint32_t *>(sm + L::kSlot);
   __shared__ unsigned long long fallbacks;
   const int tid = threadIdx.x, warp = tid >> 5;
-  const int D = d.n_feat;
+  constexpr int D = n_feat_of<KIND>();
   {
     const float *p = a.params;
     const int oW1 = 0, ob1 = H * D, oW2 = ob1 + H, ob2 = oW2 + H * H, oW3 = ob2 + H, ob3 = oW3 + H;
@@ -737,6 +475,28 @@ __device__ __forceinline__ unsigned long long gelu_grad2(unsigned long long z) {
   return f32x2_add(t1, t2);
 }
 
+// GELU and its derivative of two values in packed pairs from one hyperbolic
+// tangent per value: the same operations, in the same order, as gelu2 and
+// gelu_grad2 (bit-identical results).
+__device__ __forceinline__ void gelu_both2(unsigned long long z, unsigned long long &g,
+                                           unsigned long long &dg) {
+  const unsigned long long kA2 = f32x2_pack(kGeluA, kGeluA), kB2 = f32x2_pack(kGeluB, kGeluB);
+  const unsigned long long k3B2 = f32x2_pack(3.0f * kGeluB, 3.0f * kGeluB);
+  const unsigned long long half2 = f32x2_pack(0.5f, 0.5f), one2 = f32x2_pack(1.0f, 1.0f);
+  const unsigned long long zz = f32x2_mul(z, z);
+  const unsigned long long arg = f32x2_mul(kA2, f32x2_fma(f32x2_mul(kB2, z), zz, z));
+  float a0, a1;
+  f32x2_unpack(arg, a0, a1);
+  const unsigned long long th = f32x2_pack(tanh_fast(a0), tanh_fast(a1));
+  const unsigned long long hz = f32x2_mul(half2, z);
+  const unsigned long long opt = f32x2_add(one2, th);
+  g = f32x2_mul(hz, opt);
+  const unsigned long long t1 = f32x2_mul(half2, opt);
+  const unsigned long long sech2 = f32x2_sub(one2, f32x2_mul(th, th));
+  const unsigned long long t2 = f32x2_mul(f32x2_mul(f32x2_mul(hz, sech2), kA2), f32x2_fma(k3B2, zz, one2));
+  dg = f32x2_add(t1, t2);
+}
+
 __device__ __forceinline__ void st_bf16(unsigned char *base, int off, float v) {
   *reinterpret_cast<__nv_bfloat16 *>(base + off) = __float2bfloat16_rn(v);
 }
@@ -773,7 +533,7 @@ __global__ void __launch_bounds__(kTile) mlp_tc_grad(MlpArgs a, hpac_mlp_desc d)
   const uint32_t bar = smem_u32(sm + L::kBar);
   uint32_t *slot = reinterpret_cast<uint32_t *>(sm + L::kSlot);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int D = d.n_feat;
+  constexpr int D = n_feat_of<KIND>();
   const float *p = a.params;
   const int oW1 = 0, ob1 = H * D, oW2 = ob1 + H, ob2 = oW2 + H * H, oW3 = ob2 + H, ob3 = oW3 + H;
   // operands: W2 and its transpose, zeroed sample-major operands, the row of
@@ -931,13 +691,15 @@ __global__ void __launch_bounds__(kTile) mlp_tc_grad(MlpArgs a, hpac_mlp_desc d)
           const int u = c + j + 2 * q;
           const unsigned long long z = f32x2_add(f32x2_pack(v[j + 2 * q], v[j + 2 * q + 1]),
                                                  *reinterpret_cast<const unsigned long long *>(b2 + u));
+          unsigned long long gz, dgz;
+          gelu_both2(z, gz, dgz);
           float g0, g1;
-          f32x2_unpack(gelu2(z), g0, g1);
+          f32x2_unpack(gz, g0, g1);
           const uint32_t h2 = pack_bf16(g0, g1);
           *reinterpret_cast<uint16_t *>(sm + L::kA4 + kmajor128_off(u, tid)) = (uint16_t)(h2 & 0xffffu);
           *reinterpret_cast<uint16_t *>(sm + L::kA4 + kmajor128_off(u + 1, tid)) = (uint16_t)(h2 >> 16);
           const unsigned long long dz =
-              f32x2_mul(f32x2_mul(dyp, *reinterpret_cast<const unsigned long long *>(w3 + u)), gelu_grad2(z));
+              f32x2_mul(f32x2_mul(dyp, *reinterpret_cast<const unsigned long long *>(w3 + u)), dgz);
           float d0, d1;
           f32x2_unpack(dz, d0, d1);
           pk[q] = pack_bf16(d0, d1);
@@ -1048,6 +810,248 @@ __global__ void __launch_bounds__(kTile) mlp_tc_grad(MlpArgs a, hpac_mlp_desc d)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(L::kCols));
 }
 
+// ---------------------------------------------------------------------------
+// Input derivatives on tcgen05 (hpac_mlp_input_grad, the input half of
+// hpac_mlp_vjp): per 128-sample tile the forward product z2 = h1 W2^T and the
+// backward product dh1 = dz2 W2 (dz2 = w3 gelu'(z2), the derivative of the
+// network output), each into the same H tensor-memory columns; then per
+// thread dz1 = dh1 gelu'(z1), d(net)/d(features) = dz1 W1 and the chain rule
+// from the features to the region inputs, scaled by the caller's per-sample
+// derivative when one is given.
+// ---------------------------------------------------------------------------
+template <int H>
+struct TcIgLayout {
+  static constexpr int kA1 = 0;                      // 128 x H: h1, then dz2
+  static constexpr int kB1 = kA1 + kTile * H * 2;    // W2 [out][in]
+  static constexpr int kB2 = kB1 + H * H * 2;        // W2^T [in][out]
+  static constexpr int kW1 = kB2 + H * H * 2;        // unit pairs x 8 features (float pairs)
+  static constexpr int kB1v = kW1 + H * 8 * 4;
+  static constexpr int kB2v = kB1v + H * 4;
+  static constexpr int kW3 = kB2v + H * 4;
+  static constexpr int kBar = (kW3 + H * 4 + 7) & ~7;
+  static constexpr int kSlot = kBar + 8;
+  static constexpr int kBytes = kSlot + 8;
+};
+
+template <int H, int KIND>
+__global__ void __launch_bounds__(kTile) mlp_tc_input_grad(MlpArgs a, hpac_mlp_desc d) {
+  using L = TcIgLayout<H>;
+  extern __shared__ __align__(1024) unsigned char sm[];
+  float *w1 = reinterpret_cast<float *>(sm + L::kW1);
+  float *b1 = reinterpret_cast<float *>(sm + L::kB1v);
+  float *b2 = reinterpret_cast<float *>(sm + L::kB2v);
+  float *w3 = reinterpret_cast<float *>(sm + L::kW3);
+  const uint32_t bar = smem_u32(sm + L::kBar);
+  uint32_t *slot = reinterpret_cast<uint32_t *>(sm + L::kSlot);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  constexpr int D = n_feat_of<KIND>();
+  const float *p = a.params;
+  const int oW1 = 0, ob1 = H * D, oW2 = ob1 + H, ob2 = oW2 + H * H, oW3 = ob2 + H, ob3 = oW3 + H;
+  for (int j = tid; j < H * H; j += kTile) {
+    const int o = j / H, k = j % H;
+    const __nv_bfloat16 w = __float2bfloat16_rn(p[oW2 + j]);
+    *reinterpret_cast<__nv_bfloat16 *>(sm + L::kB1 + kmajor_off<H>(o, k)) = w;
+    *reinterpret_cast<__nv_bfloat16 *>(sm + L::kB2 + kmajor_off<H>(k, o)) = w;
+  }
+  for (int j = tid; j < H * 8; j += kTile) {
+    const int pr = j / 16, k = (j / 2) % 8, h = j % 2;
+    w1[j] = k < D ? bf16r(p[oW1 + (2 * pr + h) * D + k]) : 0.f;
+  }
+  for (int j = tid; j < H; j += kTile) {
+    b1[j] = p[ob1 + j];
+    b2[j] = p[ob2 + j];
+    w3[j] = bf16r(p[oW3 + j]);
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)),
+                 "r"(H));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  sync_for_umma();
+  const uint32_t tmem = *slot;
+  const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+  const uint64_t a1 = umma_desc(smem_u32(sm + L::kA1), 128, 16 * H);
+  const uint64_t b1d = umma_desc(smem_u32(sm + L::kB1), 128, 16 * H);
+  const uint64_t b2d = umma_desc(smem_u32(sm + L::kB2), 128, 16 * H);
+  const float b3 = p[ob3];
+  const ulonglong2 *w1v = reinterpret_cast<const ulonglong2 *>(w1);
+  uint32_t parity = 0;
+  bool failed = false;
+  const int64_t tiles = (a.n + kTile - 1) / kTile;
+  for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+    const int64_t i = tile * kTile + tid;
+    const bool valid = i < a.n;
+    float f[8], mult = 0.f, raw[4];
+    features<KIND>(a.in, a.stride, valid ? i : 0, a.param, d, f, mult, raw);
+    unsigned long long fp[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) fp[k] = f32x2_pack(f[k], f[k]);
+    // layer 1 and GELU into row tid of A1
+#pragma unroll 2
+    for (int kc = 0; kc < H / 8; ++kc) {
+      uint32_t pk[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int pr = 4 * kc + q;
+        unsigned long long z = *reinterpret_cast<const unsigned long long *>(b1 + 2 * pr);
+#pragma unroll
+        for (int k2 = 0; k2 < 4; ++k2) {
+          const ulonglong2 w = w1v[pr * 4 + k2];
+          if (2 * k2 < D) z = f32x2_fma(w.x, fp[2 * k2], z);
+          if (2 * k2 + 1 < D) z = f32x2_fma(w.y, fp[2 * k2 + 1], z);
+        }
+        float g0, g1;
+        f32x2_unpack(gelu2(z), g0, g1);
+        pk[q] = pack_bf16(g0, g1);
+      }
+      *reinterpret_cast<uint4 *>(sm + L::kA1 + kmajor_off<H>(tid, 8 * kc)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+    }
+    sync_for_umma();
+    if (tid == 0) {
+      umma_k(tmem, a1, b1d, idesc_m128<H>(), H / 16, false);
+      umma_commit(bar);
+    }
+    if (__syncthreads_or(!mbar_wait_bounded(bar, parity))) {
+      failed = true;
+      break;
+    }
+    parity ^= 1u;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    // the network output, then dz2 = w3 gelu'(z2) into row tid of A1
+    unsigned long long y2 = 0ull;
+#pragma unroll
+    for (int c = 0; c < H; c += 32) {
+      float v[32];
+      tmem_ld32(tmem + lane_base + (uint32_t)c, v);
+#pragma unroll
+      for (int j = 0; j < 32; j += 8) {
+        uint32_t pk[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int u = c + j + 2 * q;
+          const unsigned long long z = f32x2_add(f32x2_pack(v[j + 2 * q], v[j + 2 * q + 1]),
+                                                 *reinterpret_cast<const unsigned long long *>(b2 + u));
+          const unsigned long long w3p = *reinterpret_cast<const unsigned long long *>(w3 + u);
+          unsigned long long gz, dgz;
+          gelu_both2(z, gz, dgz);
+          float g0, g1;
+          f32x2_unpack(gz, g0, g1);
+          const float2 hb = __bfloat1622float2(__floats2bfloat162_rn(g0, g1));
+          y2 = f32x2_fma(f32x2_pack(hb.x, hb.y), w3p, y2);
+          float d0, d1;
+          f32x2_unpack(f32x2_mul(w3p, dgz), d0, d1);
+          pk[q] = pack_bf16(valid ? d0 : 0.f, valid ? d1 : 0.f);
+        }
+        *reinterpret_cast<uint4 *>(sm + L::kA1 + kmajor_off<H>(tid, c + j)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+      }
+    }
+    float ye, yo;
+    f32x2_unpack(y2, ye, yo);
+    const float net = (ye + yo) + b3;
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    sync_for_umma();
+    if (tid == 0) {
+      umma_k(tmem, a1, b2d, idesc_m128<H>(), H / 16, false);  // dh1 = dz2 W2
+      umma_commit(bar);
+    }
+    if (__syncthreads_or(!mbar_wait_bounded(bar, parity))) {
+      failed = true;
+      break;
+    }
+    parity ^= 1u;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    // dz1 = dh1 gelu'(z1) (z1 recomputed) and d(net)/d(features) = dz1 W1,
+    // two units per packed pair, the halves summed at the end
+    unsigned long long df2[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) df2[k] = 0ull;
+#pragma unroll
+    for (int c = 0; c < H; c += 32) {
+      float v[32];
+      tmem_ld32(tmem + lane_base + (uint32_t)c, v);
+#pragma unroll
+      for (int j = 0; j < 32; j += 2) {
+        const int pr = (c + j) / 2;
+        unsigned long long z = *reinterpret_cast<const unsigned long long *>(b1 + 2 * pr);
+        ulonglong2 w[4];
+#pragma unroll
+        for (int k2 = 0; k2 < 4; ++k2) {
+          w[k2] = w1v[pr * 4 + k2];
+          if (2 * k2 < D) z = f32x2_fma(w[k2].x, fp[2 * k2], z);
+          if (2 * k2 + 1 < D) z = f32x2_fma(w[k2].y, fp[2 * k2 + 1], z);
+        }
+        const unsigned long long dz1 = f32x2_mul(f32x2_pack(v[j], v[j + 1]), gelu_grad2(z));
+#pragma unroll
+        for (int k2 = 0; k2 < 4; ++k2) {
+          if (2 * k2 < D) df2[2 * k2] = f32x2_fma(dz1, w[k2].x, df2[2 * k2]);
+          if (2 * k2 + 1 < D) df2[2 * k2 + 1] = f32x2_fma(dz1, w[k2].y, df2[2 * k2 + 1]);
+        }
+      }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    if (valid) {
+      float df[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        float lo, hi;
+        f32x2_unpack(df2[k], lo, hi);
+        df[k] = (lo + hi) * d.feat_scale[k];
+      }
+      float gin[4];
+      if (KIND == HPAC_REGION_BLACKSCHOLES) {
+        // region output C = S (shift + scale net); features ln(S/K),
+        // sigma sqrt(T), r T, d1 (clamped to [-10, 10]), sigma
+        const float S = raw[0], K = raw[1], Tm = raw[2], sig = raw[3];
+        const float sc = d.out_scale, sq = sqrtf(Tm), r = (float)a.param;
+        const float sst = sig * sq;
+        const float d1 = (logf(S / K) + (r + 0.5f * sig * sig) * Tm) / sst;
+        const float g3 = (d1 > -10.f && d1 < 10.f) ? df[3] : 0.f;  // clamp
+        const float dnet_dS = df[0] / S + g3 / (S * sst);
+        const float dnet_dK = -df[0] / K - g3 / (K * sst);
+        const float dnet_dT = df[1] * sig * 0.5f / sq + df[2] * r +
+                              g3 * ((r + 0.5f * sig * sig) / sst - 0.5f * d1 / Tm);
+        const float dnet_dsig = df[1] * sq + df[4] + g3 * (sq - d1 / sig);
+        gin[0] = fmaf(sc, net, d.out_shift) + S * sc * dnet_dS;
+        gin[1] = S * sc * dnet_dK;
+        gin[2] = S * sc * dnet_dT;
+        gin[3] = S * sc * dnet_dsig;
+      } else {
+        // p = mult (shift + scale net), mult = (g - 1) (e - dv q) / v1 where positive
+        const float v1 = raw[1], dv = raw[2], q = raw[3];
+        const float g1 = (float)a.param - 1.f;
+        const float ratio = fmaf(d.out_scale, net, d.out_shift);
+        const bool on = mult > 0.f;
+        const float dm[4] = {on ? g1 / v1 : 0.f, on ? -mult / v1 : 0.f, on ? -g1 * q / v1 : 0.f,
+                             on ? -g1 * dv / v1 : 0.f};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) gin[k] = ratio * dm[k] + mult * d.out_scale * df[k];
+      }
+      if (a.gout) {
+        // the caller's d(loss)/d(output); zero where the EOS output is clamped
+        const float o = mult * fmaf(d.out_scale, net, d.out_shift);
+        const float go = (KIND != HPAC_REGION_EOS || o > 0.f) ? a.gout[i] : 0.f;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) gin[k] *= go;
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) a.out[k * a.n + i] = gin[k];
+    }
+  }
+  if (failed) {
+    mbar_wait_bounded(bar, parity);
+    if (tid == 0 && a.counters) atomicExch(&a.counters[2], 1ull);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(H));
+}
+
 // Sums of the features, their squares and the per-invocation targets
 // (region output / multiplier) for the normalisation statistics.
 template <int KIND>
@@ -1103,23 +1107,6 @@ __global__ void adam_kernel(float *p, const float *g, float *m, float *v, int n,
 int n_params_of(const hpac_mlp_desc &d) {
   const int H = d.hidden, D = d.n_feat;
   return H * D + H + H * H + H + H + 1;
-}
-
-template <int H, int KIND>
-hpac_status launch_input_grad_t(hpac_mlp *m, const MlpArgs &a) {
-  const size_t smem = (sizeof(Smem<H>) + 15) & ~size_t(15);
-  auto fn = mlp_input_grad_kernel<H, KIND>;
-  HPAC_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  int per_sm = 1;
-  HPAC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, H * 2, smem));
-  int sms = 148;
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, m->device);
-  const int64_t chunks = (a.n + 16 * (H / 16) - 1) / (16 * (H / 16));
-  int64_t blocks = (int64_t)sms * (per_sm < 1 ? 1 : per_sm);
-  if (blocks > chunks) blocks = chunks < 1 ? 1 : chunks;
-  fn<<<(unsigned)blocks, H * 2, smem, m->stream>>>(a, m->d);
-  HPAC_CUDA_TRY(cudaGetLastError());
-  return HPAC_OK;
 }
 
 // The tensor-core inference: persistent blocks of 128 threads, as many per
@@ -1191,13 +1178,45 @@ hpac_status launch_infer(hpac_mlp *m, const MlpArgs &a) {
   return bs ? launch_tc_infer<128, HPAC_REGION_BLACKSCHOLES>(m, a) : launch_tc_infer<128, HPAC_REGION_EOS>(m, a);
 }
 
+// The tensor-core input derivatives: residency as for the inference kernel.
+template <int H, int KIND>
+hpac_status launch_tc_input_grad(hpac_mlp *m, const MlpArgs &a) {
+  auto fn = mlp_tc_input_grad<H, KIND>;
+  cudaFuncAttributes fa;
+  HPAC_CUDA_TRY(cudaFuncGetAttributes(&fa, fn));
+  int sm_smem = 0, sm_regs = 0, sm_threads = 0, reserved = 0;
+  HPAC_CUDA_TRY(cudaDeviceGetAttribute(&sm_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, m->device));
+  HPAC_CUDA_TRY(cudaDeviceGetAttribute(&sm_regs, cudaDevAttrMaxRegistersPerMultiprocessor, m->device));
+  HPAC_CUDA_TRY(cudaDeviceGetAttribute(&sm_threads, cudaDevAttrMaxThreadsPerMultiProcessor, m->device));
+  HPAC_CUDA_TRY(cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, m->device));
+  const int regs = ((fa.numRegs + 7) / 8) * 8 * kTile;
+  int smem = TcIgLayout<H>::kBytes;
+  int per_sm = 0;
+  for (;;) {
+    const int by_smem = sm_smem / (smem + (int)fa.sharedSizeBytes + reserved);
+    const int by_regs = regs > 0 ? sm_regs / regs : 32;
+    per_sm = by_smem < by_regs ? by_smem : by_regs;
+    per_sm = per_sm < sm_threads / kTile ? per_sm : sm_threads / kTile;
+    if (per_sm * H <= 512 || per_sm <= 1) break;
+    smem += 1024;
+  }
+  if (per_sm < 1) return set_error(HPAC_EUNSUPPORTED, "surrogate input-gradient kernel does not fit an SM");
+  HPAC_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  const int64_t tiles = (a.n + kTile - 1) / kTile;
+  int64_t blocks = (int64_t)sm_count(m->device) * per_sm;
+  if (blocks > tiles) blocks = tiles < 1 ? 1 : tiles;
+  fn<<<(unsigned)blocks, kTile, smem, m->stream>>>(a, m->d);
+  HPAC_CUDA_TRY(cudaGetLastError());
+  return HPAC_OK;
+}
+
 hpac_status launch_input_grad(hpac_mlp *m, const MlpArgs &a) {
   const bool bs = m->d.kind == HPAC_REGION_BLACKSCHOLES;
   if (m->d.hidden == 64)
-    return bs ? launch_input_grad_t<64, HPAC_REGION_BLACKSCHOLES>(m, a)
-              : launch_input_grad_t<64, HPAC_REGION_EOS>(m, a);
-  return bs ? launch_input_grad_t<128, HPAC_REGION_BLACKSCHOLES>(m, a)
-            : launch_input_grad_t<128, HPAC_REGION_EOS>(m, a);
+    return bs ? launch_tc_input_grad<64, HPAC_REGION_BLACKSCHOLES>(m, a)
+              : launch_tc_input_grad<64, HPAC_REGION_EOS>(m, a);
+  return bs ? launch_tc_input_grad<128, HPAC_REGION_BLACKSCHOLES>(m, a)
+            : launch_tc_input_grad<128, HPAC_REGION_EOS>(m, a);
 }
 
 uint64_t sm64(uint64_t &s) {
@@ -1432,6 +1451,7 @@ extern "C" hpac_status hpac_mlp_input_grad(hpac_mlp *m, int64_t n, const void *d
   MlpArgs a{};
   a.in = d_in, a.stride = in_stride, a.n = n, a.param = param, a.out = d_grad;
   a.params = m->params;
+  a.counters = m->counters;
   return launch_input_grad(m, a);
 }
 
@@ -1458,6 +1478,7 @@ extern "C" hpac_status hpac_mlp_vjp(hpac_mlp *m, int64_t n, const void *d_in, in
     MlpArgs a{};
     a.in = d_in, a.stride = in_stride, a.n = n, a.param = param, a.out = d_grad_in, a.gout = d_gout;
     a.params = m->params;
+    a.counters = m->counters;
     s = launch_input_grad(m, a);
     if (s != HPAC_OK) return s;
   }

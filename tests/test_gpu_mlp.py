@@ -85,18 +85,34 @@ def test_gradient_matches_oracle(H):
     S.close()
 
 
-def test_input_gradient_matches_oracle(H):
-    desc = H.blackscholes_desc(64)
-    n = 2048
-    x = W.blackscholes_inputs(n, seed=23)
+@pytest.mark.parametrize("kind,hidden,n", [(0, 64, 2048), (0, 128, 3 * 128 + 77), (1, 64, 5 * 128 + 1),
+                                            (1, 128, 4096), (0, 64, 1)])
+def test_input_gradient_matches_oracle(H, kind, hidden, n):
+    """d(region output)/d(region inputs) of the surrogate (tcgen05 forward and
+    backward products, chain rule per thread) against the oracle's FP64
+    derivatives, within the bfloat16 rounding of the activations; sizes span
+    several 128-sample tiles with a ragged tail, and a single sample."""
+    if kind == 0:
+        desc = H.blackscholes_desc(hidden)
+        x = W.blackscholes_inputs(n, seed=23)
+        param = W.BS_RATE
+    else:
+        desc = H.eos_desc(hidden)
+        x = W.eos_inputs(n, seed=23)
+        param = 5.0 / 3.0
     S = H.Surrogate(desc, seed=7)
-    xd = torch.from_numpy(x).cuda()
-    out = torch.zeros(4, n, dtype=torch.float32, device="cuda")
-    S.input_grad(xd, out, W.BS_RATE)
-    ref = M.input_grad(S.params(), dd(desc), 0, x.astype(np.float64), W.BS_RATE)
+    xd = torch.from_numpy(np.ascontiguousarray(x)).cuda()
+    out = torch.full((4, n), np.nan, dtype=torch.float32, device="cuda")
+    S.input_grad(xd, out, param)
+    ref = M.input_grad(S.params(), dd(S.get_desc()), kind, x.astype(np.float64), param)
     g = out.cpu().numpy().astype(np.float64)
+    assert np.all(np.isfinite(g))
     for d in range(4):
-        err = np.linalg.norm(g[d] - ref[d]) / np.linalg.norm(ref[d])
+        nr = np.linalg.norm(ref[d])
+        if nr == 0:
+            assert np.all(g[d] == 0), d
+            continue
+        err = np.linalg.norm(g[d] - ref[d]) / nr
         assert err < 0.03, (d, err)
     S.close()
 
