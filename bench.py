@@ -87,10 +87,10 @@ HEAD_FORMS = [
 ]
 
 # FP64 operations of the element kernel per element, each add, multiply or FMA
-# one issue slot of the FP64 pipe: 15 shared corner-pair cross products (90),
-# their 42 scatters less 7 first assignments (105 adds), 3 single-use pairs as
-# fused multiply-adds (18), 21 relative-position subtractions, 18 corner-0
-# sums, 8 for the volume, 1 for dv, and 2 for v = V / V0 formed as a comparison
+# one issue slot of the FP64 pipe, in Grandy's three-triple-product form of the
+# trilinear volume: 39 corner differences and their sums, 9 cross products
+# (54), 10 for the volume (three dot products and the 1/12), 39 for the corner
+# sums of the gradient, 1 for dv, and 2 for v = V / V0 formed as a comparison
 # with V0 and a product with the stored 1 / V0. Its ceiling, in the same unit
 # (FP64 instructions per lane per second), is the FP64 issue rate of the part:
 # the nominal 1.25 TFLOP/s of GB300 at 152 SMs and 2070 MHz is
@@ -98,7 +98,7 @@ HEAD_FORMS = [
 # at the SM count of the device and the median SM clock sampled under load.
 # The FMA rate that the library's probe measures in the same run is reported
 # beside it.
-ELEM_OPS = 90 + 105 + 18 + 21 + 18 + 8 + 1 + 2
+ELEM_OPS = 39 + 54 + 10 + 39 + 1 + 2
 FP64_FMA_PER_SM_CLK = 2
 # EOS closed form per element: v_n, (g-1) e, the numerator N (e v_n, 2 q v_n,
 # the sum, 0.5 dv times it, the difference: 6), the denominator (3), (g-1) N

@@ -13,20 +13,31 @@
 //   EOS region      exact, TAF, iACT or perforation through the region API;
 //   finalize        e = p v / (gamma - 1), v = v_{n+1}, pq = p + q.
 //
-// Volume of a trilinear hexahedron. With corners P_c in lexicographic order
-// (c = a + 2b + 4d for offsets a, b, d), the integral of det J over the
-// reference cube is the trilinear form
-//   V = (1/12) sum over 24 corner triples (a < b < c) of s_abc det(P_a, P_b, P_c),
-// s_abc = +-1: the integral of det(grad N_a, grad N_b, grad N_c) times 12,
-// worked out symbolically. V is translation invariant, so with positions
-// relative to corner 0 the nine triples containing corner 0 vanish; the
-// gradient of a corner c > 0 is the sum over the remaining 15 triples holding c
-// of s times the cross product of the other two corners (oriented as in the
-// determinant), and corner 0 gets minus the sum of the others. The kernel
-// stores 12 dV/dP_c (the 1/12 is applied where the gradient is used).
-// Cost per element: the 15 triples share 18 corner-pair cross products, formed
-// once each and scattered to their corners (hex_grad12): 260 FP64 operations
-// with the relative positions, the bulk of the step on GB300's narrow FP64 pipe.
+// Volume of a trilinear hexahedron and its gradient. With corners P_c in
+// lexicographic order (c = a + 2b + 4d for offsets a, b, d), the integral of
+// det J over the reference cube equals Grandy's sum of three triple products
+// (J. Grandy, "Efficient computation of volume of hexahedral cells", LLNL
+// UCRL-ID-128886, 1997), one per pair of faces meeting at corner 7 and at
+// corner 0:
+//   12 V = s1 . (c1 x d1) + s2 . (c2 x d2) + s3 . (c3 x d3),
+//   s1 = (P2 - P1) + (P6 - P3), c1 = P7 - P2, d1 = P3 - P0,
+//   s2 = (P4 - P2) + (P5 - P6), c2 = P7 - P4, d2 = P6 - P0,
+//   s3 = (P1 - P4) + (P3 - P5) = -(s1 + s2), c3 = P7 - P1, d3 = P5 - P0.
+// V is a cubic polynomial of the corners, so its gradient follows by the
+// product rule: with A_i = c_i x d_i, B_i = d_i x s_i, C_i = s_i x c_i (the
+// derivatives of the i-th triple product with respect to s_i, c_i and d_i),
+// each corner collects the terms of the differences it appears in:
+//   12 dV/dP0 = -(C1 + C2 + C3)        12 dV/dP7 = B1 + B2 + B3
+//   12 dV/dP1 = (A3 - A1) - B3         12 dV/dP3 = (A3 - A1) + C1
+//   12 dV/dP2 = (A1 - A2) - B1         12 dV/dP6 = (A1 - A2) + C2
+//   12 dV/dP4 = (A2 - A3) - B2         12 dV/dP5 = (A2 - A3) + C3
+// Every difference is of two corners of one element, so it carries the
+// rounding of the element's size, not of its position. The kernel stores
+// 12 dV/dP_c (the 1/12 is applied where the gradient is used).
+// Cost per element: 39 differences and sums, 9 cross products (54), the
+// volume (9) and the corner sums (39): 141 FP64 operations, the bulk of the
+// step on GB300's narrow FP64 pipe (the plain sum over the 24 corner triples
+// of the trilinear form, with shared pair cross products, takes 260).
 #include <math.h>
 
 #include "hpac_internal.cuh"
@@ -37,40 +48,6 @@ namespace {
 constexpr double kCq = 2.0;   // quadratic viscosity coefficient
 constexpr double kCl = 0.5;   // linear viscosity coefficient
 
-// The 15 corner triples (a < b < c, all > 0) with signs s_abc hold 18
-// distinct corner pairs. Triple (a, b, c) adds s P_b x P_c to 12 dV/dP_a,
-// -s P_a x P_c to 12 dV/dP_b and s P_a x P_b to 12 dV/dP_c, so each pair's cross
-// product C_ij = P_i x P_j is formed once and scattered to the corners that use
-// it. kPairs lists the 15 pairs used two to four times (corner k, sign, and
-// whether it is the corner's first term, which assigns instead of adding), in
-// an order that touches every corner 1..7 before any single-use pair;
-// kSingle the 3 pairs used once, added with two fused multiply-adds per
-// component instead of a cross product and an add.
-struct PairUse {
-  int i, j, n;
-  int k[4], s[4], first[4];
-};
-__device__ constexpr PairUse kPairs[15] = {
-    {1, 3, 3, {2, 5, 7, 0}, {-1, 1, 1, 0}, {1, 1, 1, 0}},
-    {1, 5, 3, {3, 4, 7, 0}, {-1, 1, -1, 0}, {1, 1, 0, 0}},
-    {1, 7, 2, {3, 5, 0, 0}, {-1, 1, 0, 0}, {0, 0, 0, 0}},
-    {2, 3, 3, {1, 6, 7, 0}, {1, -1, -1, 0}, {1, 1, 0, 0}},
-    {2, 6, 3, {3, 4, 7, 0}, {1, -1, 1, 0}, {0, 0, 0, 0}},
-    {2, 7, 2, {3, 6, 0, 0}, {1, -1, 0, 0}, {0, 0, 0, 0}},
-    {3, 5, 2, {1, 7, 0, 0}, {1, -1, 0, 0}, {0, 0, 0, 0}},
-    {3, 6, 2, {2, 7, 0, 0}, {-1, 1, 0, 0}, {0, 0, 0, 0}},
-    {3, 7, 4, {1, 2, 5, 6}, {1, -1, 1, -1}, {0, 0, 0, 0}},
-    {4, 5, 3, {1, 6, 7, 0}, {-1, 1, 1, 0}, {0, 0, 0, 0}},
-    {4, 6, 3, {2, 5, 7, 0}, {1, -1, -1, 0}, {0, 0, 0, 0}},
-    {4, 7, 2, {5, 6, 0, 0}, {-1, 1, 0, 0}, {0, 0, 0, 0}},
-    {5, 6, 2, {4, 7, 0, 0}, {1, -1, 0, 0}, {0, 0, 0, 0}},
-    {5, 7, 4, {1, 3, 4, 6}, {-1, -1, 1, 1}, {0, 0, 0, 0}},
-    {6, 7, 4, {2, 3, 4, 5}, {1, 1, -1, -1}, {0, 0, 0, 0}}};
-struct SingleUse {
-  int i, j, k, s;
-};
-__device__ constexpr SingleUse kSingle[3] = {{1, 2, 3, 1}, {1, 4, 5, -1}, {2, 4, 6, 1}};
-
 __device__ __forceinline__ void cross3(double ax, double ay, double az, double bx, double by,
                                        double bz, double &cx, double &cy, double &cz) {
   cx = fma(ay, bz, -az * by);
@@ -78,54 +55,55 @@ __device__ __forceinline__ void cross3(double ax, double ay, double az, double b
   cz = fma(ax, by, -ay * bx);
 }
 
-// 12 dV/dP_c for the corners (relative to corner 0) and the volume V.
-// FP64 operations: 15 cross products (90), 42 scatters less the 7 first
-// assignments (105 adds), 3 fused single-use pairs (18), corner 0 (18), the
-// volume (8): 239, plus the 21 subtractions of the relative positions.
+// 12 dV/dP_c for the eight corners (absolute positions) and the volume V, in
+// the three-triple-product form above.
 __device__ __forceinline__ double hex_grad12(const double (&X)[8], const double (&Y)[8],
                                              const double (&Z)[8], double (&gx)[8], double (&gy)[8],
                                              double (&gz)[8]) {
-#pragma unroll
-  for (int p = 0; p < 15; ++p) {
-    const PairUse &u = kPairs[p];
-    double cx, cy, cz;
-    cross3(X[u.i], Y[u.i], Z[u.i], X[u.j], Y[u.j], Z[u.j], cx, cy, cz);
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      if (q >= u.n) break;
-      const int k = u.k[q];
-      const double sx = u.s[q] > 0 ? cx : -cx, sy = u.s[q] > 0 ? cy : -cy, sz = u.s[q] > 0 ? cz : -cz;
-      if (u.first[q]) {
-        gx[k] = sx;
-        gy[k] = sy;
-        gz[k] = sz;
-      } else {
-        gx[k] += sx;
-        gy[k] += sy;
-        gz[k] += sz;
-      }
-    }
-  }
-#pragma unroll
-  for (int p = 0; p < 3; ++p) {
-    const SingleUse &u = kSingle[p];
-    const double sg = (double)u.s;
-    // g_k += s (P_i x P_j), one component at a time in two fused steps
-    gx[u.k] = fma(-sg * Z[u.i], Y[u.j], fma(sg * Y[u.i], Z[u.j], gx[u.k]));
-    gy[u.k] = fma(-sg * X[u.i], Z[u.j], fma(sg * Z[u.i], X[u.j], gy[u.k]));
-    gz[u.k] = fma(-sg * Y[u.i], X[u.j], fma(sg * X[u.i], Y[u.j], gz[u.k]));
-  }
-  double sx = 0.0, sy = 0.0, sz = 0.0, v12 = 0.0;
-#pragma unroll
-  for (int c = 1; c < 8; ++c) {
-    sx = c == 1 ? gx[c] : sx + gx[c];
-    sy = c == 1 ? gy[c] : sy + gy[c];
-    sz = c == 1 ? gz[c] : sz + gz[c];
-    v12 = c == 1 ? X[c] * gx[c] : fma(X[c], gx[c], v12);  // V is linear in the x coordinates
-  }
-  gx[0] = -sx;
-  gy[0] = -sy;
-  gz[0] = -sz;
+  // s1, s2 and t = s1 + s2 = -s3; c_i; d_i
+  const double s1x = (X[2] - X[1]) + (X[6] - X[3]), s1y = (Y[2] - Y[1]) + (Y[6] - Y[3]),
+               s1z = (Z[2] - Z[1]) + (Z[6] - Z[3]);
+  const double s2x = (X[4] - X[2]) + (X[5] - X[6]), s2y = (Y[4] - Y[2]) + (Y[5] - Y[6]),
+               s2z = (Z[4] - Z[2]) + (Z[5] - Z[6]);
+  const double tx = s1x + s2x, ty = s1y + s2y, tz = s1z + s2z;
+  const double c1x = X[7] - X[2], c1y = Y[7] - Y[2], c1z = Z[7] - Z[2];
+  const double c2x = X[7] - X[4], c2y = Y[7] - Y[4], c2z = Z[7] - Z[4];
+  const double c3x = X[7] - X[1], c3y = Y[7] - Y[1], c3z = Z[7] - Z[1];
+  const double d1x = X[3] - X[0], d1y = Y[3] - Y[0], d1z = Z[3] - Z[0];
+  const double d2x = X[6] - X[0], d2y = Y[6] - Y[0], d2z = Z[6] - Z[0];
+  const double d3x = X[5] - X[0], d3y = Y[5] - Y[0], d3z = Z[5] - Z[0];
+  double a1x, a1y, a1z, a2x, a2y, a2z, a3x, a3y, a3z;
+  cross3(c1x, c1y, c1z, d1x, d1y, d1z, a1x, a1y, a1z);
+  cross3(c2x, c2y, c2z, d2x, d2y, d2z, a2x, a2y, a2z);
+  cross3(c3x, c3y, c3z, d3x, d3y, d3z, a3x, a3y, a3z);
+  double b1x, b1y, b1z, b2x, b2y, b2z, b3x, b3y, b3z;
+  cross3(d1x, d1y, d1z, s1x, s1y, s1z, b1x, b1y, b1z);
+  cross3(d2x, d2y, d2z, s2x, s2y, s2z, b2x, b2y, b2z);
+  cross3(tx, ty, tz, d3x, d3y, d3z, b3x, b3y, b3z);  // d3 x s3 = t x d3
+  double e1x, e1y, e1z, e2x, e2y, e2z, e3x, e3y, e3z;  // the C_i
+  cross3(s1x, s1y, s1z, c1x, c1y, c1z, e1x, e1y, e1z);
+  cross3(s2x, s2y, s2z, c2x, c2y, c2z, e2x, e2y, e2z);
+  cross3(c3x, c3y, c3z, tx, ty, tz, e3x, e3y, e3z);  // s3 x c3 = c3 x t
+  double v12 = s1x * a1x;
+  v12 = fma(s1y, a1y, v12);
+  v12 = fma(s1z, a1z, v12);
+  v12 = fma(s2x, a2x, v12);
+  v12 = fma(s2y, a2y, v12);
+  v12 = fma(s2z, a2z, v12);
+  v12 = fma(-tx, a3x, v12);
+  v12 = fma(-ty, a3y, v12);
+  v12 = fma(-tz, a3z, v12);
+  const double p31x = a3x - a1x, p31y = a3y - a1y, p31z = a3z - a1z;
+  const double p12x = a1x - a2x, p12y = a1y - a2y, p12z = a1z - a2z;
+  const double p23x = a2x - a3x, p23y = a2y - a3y, p23z = a2z - a3z;
+  gx[0] = -e1x - e2x - e3x, gy[0] = -e1y - e2y - e3y, gz[0] = -e1z - e2z - e3z;
+  gx[1] = p31x - b3x, gy[1] = p31y - b3y, gz[1] = p31z - b3z;
+  gx[2] = p12x - b1x, gy[2] = p12y - b1y, gz[2] = p12z - b1z;
+  gx[3] = p31x + e1x, gy[3] = p31y + e1y, gz[3] = p31z + e1z;
+  gx[4] = p23x - b2x, gy[4] = p23y - b2y, gz[4] = p23z - b2z;
+  gx[5] = p23x + e3x, gy[5] = p23y + e3y, gz[5] = p23z + e3z;
+  gx[6] = p12x + e2x, gy[6] = p12y + e2y, gz[6] = p12z + e2z;
+  gx[7] = b1x + b2x + b3x, gy[7] = b1y + b2y + b3y, gz[7] = b1z + b2z + b3z;
   return v12 * (1.0 / 12.0);
 }
 
@@ -156,10 +134,10 @@ __device__ __forceinline__ uint32_t fdiv(uint32_t x, const FastDiv &f) {
   return (t + ((x - t) >> f.s1)) >> f.s2;
 }
 
-__device__ __forceinline__ void gather_rel(int n, int64_t e, const double *__restrict__ x,
-                                           const double *__restrict__ y,
-                                           const double *__restrict__ z, double (&X)[8],
-                                           double (&Y)[8], double (&Z)[8]) {
+// Corner positions of element e (lexicographic corner order).
+__device__ __forceinline__ void gather(int n, int64_t e, const double *__restrict__ x,
+                                       const double *__restrict__ y, const double *__restrict__ z,
+                                       double (&X)[8], double (&Y)[8], double (&Z)[8]) {
   const int64_t n1 = n + 1;
   const int64_t i = e % n, j = (e / n) % n, k = e / ((int64_t)n * n);
   const int64_t base = (k * n1 + j) * n1 + i;
@@ -170,21 +148,13 @@ __device__ __forceinline__ void gather_rel(int n, int64_t e, const double *__res
     Y[c] = y[nd];
     Z[c] = z[nd];
   }
-#pragma unroll
-  for (int c = 1; c < 8; ++c) {
-    X[c] -= X[0];
-    Y[c] -= Y[0];
-    Z[c] -= Z[0];
-  }
-  X[0] = Y[0] = Z[0] = 0.0;
 }
 
 // The same gather for the time-step kernel: element e split by the fixed
 // divisor n, node offsets in 32 bits.
-__device__ __forceinline__ void gather_rel32(uint32_t e, const FastDiv &fn, const double *__restrict__ x,
-                                             const double *__restrict__ y,
-                                             const double *__restrict__ z, double (&X)[8],
-                                             double (&Y)[8], double (&Z)[8]) {
+__device__ __forceinline__ void gather32(uint32_t e, const FastDiv &fn, const double *__restrict__ x,
+                                         const double *__restrict__ y, const double *__restrict__ z,
+                                         double (&X)[8], double (&Y)[8], double (&Z)[8]) {
   const uint32_t n = fn.d, n1 = n + 1;
   const uint32_t jk = fdiv(e, fn), i = e - jk * n;
   const uint32_t k = fdiv(jk, fn), j = jk - k * n;
@@ -196,13 +166,6 @@ __device__ __forceinline__ void gather_rel32(uint32_t e, const FastDiv &fn, cons
     Y[c] = y[nd];
     Z[c] = z[nd];
   }
-#pragma unroll
-  for (int c = 1; c < 8; ++c) {
-    X[c] -= X[0];
-    Y[c] -= Y[0];
-    Z[c] -= Z[0];
-  }
-  X[0] = Y[0] = Z[0] = 0.0;
 }
 
 __global__ void __launch_bounds__(128) init_elem_kernel(hpac_hydro_state s) {
@@ -212,7 +175,7 @@ __global__ void __launch_bounds__(128) init_elem_kernel(hpac_hydro_state s) {
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < E;
        e += (int64_t)gridDim.x * blockDim.x) {
     double X[8], Y[8], Z[8], gx[8], gy[8], gz[8];
-    gather_rel(n, e, s.x, s.y, s.z, X, Y, Z);
+    gather(n, e, s.x, s.y, s.z, X, Y, Z);
     const double V = hex_grad12(X, Y, Z, gx, gy, gz);
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
@@ -303,7 +266,7 @@ __global__ void __launch_bounds__(96) elem_kernel(hpac_hydro_state s, FastDiv fn
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < E;
        e += (int64_t)gridDim.x * blockDim.x) {
     double X[8], Y[8], Z[8], gx[8], gy[8], gz[8];
-    gather_rel32((uint32_t)e, fn, s.x, s.y, s.z, X, Y, Z);
+    gather32((uint32_t)e, fn, s.x, s.y, s.z, X, Y, Z);
     const double V = hex_grad12(X, Y, Z, gx, gy, gz);
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
