@@ -88,17 +88,19 @@ HEAD_FORMS = [
 
 # FP64 operations of the element kernel per element, each add, multiply or FMA
 # one issue slot of the FP64 pipe, in Grandy's three-triple-product form of the
-# trilinear volume: 39 corner differences and their sums, 9 cross products
-# (54), 10 for the volume (three dot products and the 1/12), 39 for the corner
-# sums of the gradient, 1 for dv, and 2 for v = V / V0 formed as a comparison
-# with V0 and a product with the stored 1 / V0. Its ceiling, in the same unit
+# trilinear volume: 9 cross products (54), 10 for the volume (three dot
+# products and the 1/12), 39 for the corner sums of the gradient, 1 for dv, and
+# 2 for v = V / V0 formed as a comparison with V0 and a product with the stored
+# 1 / V0. The 39 corner differences and their sums run exactly on the integer
+# pipes (a fixed-point grid per element and axis) and are not counted. Its
+# ceiling, in the same unit
 # (FP64 instructions per lane per second), is the FP64 issue rate of the part:
 # the nominal 1.25 TFLOP/s of GB300 at 152 SMs and 2070 MHz is
 # 1.25e12 / (2 x 152 x 2.07e9) = 1.99, i.e. 2 FP64 FMA per SM per clock, taken
 # at the SM count of the device and the median SM clock sampled under load.
 # The FMA rate that the library's probe measures in the same run is reported
 # beside it.
-ELEM_OPS = 39 + 54 + 10 + 39 + 1 + 2
+ELEM_OPS = 54 + 10 + 39 + 1 + 2
 FP64_FMA_PER_SM_CLK = 2
 # EOS closed form per element: v_n, (g-1) e, the numerator N (e v_n, 2 q v_n,
 # the sum, 0.5 dv times it, the difference: 6), the denominator (3), (g-1) N

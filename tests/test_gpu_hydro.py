@@ -77,6 +77,64 @@ def test_init_matches_oracle(H, orc):
     G.close()
 
 
+@pytest.mark.parametrize("mesh", ["offset", "binades", "tiny_node", "scaled_down", "scaled_up", "nan_node"])
+def test_init_geometry_edge_meshes(H, orc, mesh):
+    """Volumes and volume gradients of meshes that stress the element
+    kernel's fixed-point corner differences, against the oracle: a mesh far
+    from the origin (differences of large coordinates), coordinates spanning
+    several binades within one element, a node 1e-30 from a symmetry plane
+    (rounded to the element's grid), meshes scaled by 2^-500 and 2^500, and a
+    NaN coordinate (the kernel takes the FP64 differences there)."""
+    n = 5
+    x, y, z, e = W.hydro_initial(n)
+    x, y, z = (np.array(a, dtype=np.float64) for a in (x, y, z))
+    tol = 1e-13
+    if mesh == "offset":
+        x, y, z = x - 0.37, y + 5.0, z - 1e3
+        tol = 1e-13 * 1e3 * n  # the oracle's FP64 differences lose log2(1e3 n) bits
+    elif mesh == "binades":
+        x, y, z = x ** 4, y ** 3, z ** 2
+    elif mesh == "tiny_node":
+        n1 = n + 1
+        x[1 + n1 * (2 + n1 * 3)] = 1e-30
+    elif mesh == "scaled_down":
+        x, y, z = x * 2.0 ** -500, y * 2.0 ** -500, z * 2.0 ** -500
+    elif mesh == "scaled_up":
+        x, y, z = x * 2.0 ** 500, y * 2.0 ** 500, z * 2.0 ** 500
+    elif mesh == "nan_node":
+        x[7] = np.nan
+    S = orc.HydroState(n, x, y, z, e)
+    G = H.Hydro(n, x, y, z, e, W.hydro_dt(n))
+    torch.cuda.synchronize()
+    g_ref = grad12(orc, S)
+    g = G["grad"].cpu().numpy()
+    V = G["V0"].cpu().numpy()
+    if mesh == "nan_node":
+        # node 7 = (1, 1, 0): the four elements around it have a NaN volume on
+        # both sides (V is linear in every corner); which gradient components
+        # of those elements turn NaN depends on the evaluation order (the
+        # gradient at a corner does not depend on that corner), so only the
+        # other elements are compared
+        E = n ** 3
+        el = np.arange(E)
+        i, j, k = el % n, (el // n) % n, el // (n * n)
+        touch = (i <= 1) & (j <= 1) & (k == 0)
+        assert np.all(np.isnan(V[touch])) and np.all(np.isnan(S.V0[touch]))
+        keep = np.tile(~touch, 24)
+        assert np.all(np.isfinite(g[keep]))
+        close(g[keep], g_ref[keep], tol, "grad")
+        close(V[~touch], S.V0[~touch], tol, "V0")
+    else:
+        close(g, g_ref, tol, "grad")
+        if mesh == "scaled_up":
+            # 12 V is a sum of signed triple products near 2^1500: both sides
+            # overflow (to an infinity, or NaN where infinities cancel)
+            assert not np.any(np.isfinite(V)) and not np.any(np.isfinite(S.V0))
+        else:
+            close(V, S.V0, tol, "V0")
+    G.close()
+
+
 def test_exact_steps_side_by_side(H, orc):
     n, steps = 12, 30
     S, G = pair(H, orc, n)
