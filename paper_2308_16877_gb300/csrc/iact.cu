@@ -32,6 +32,25 @@ struct IactParams {
   double thr_d;
 };
 
+// Double to single precision, rounded to nearest even, on the integer pipes
+// where the result is a normal single or a zero. GB300 executes the hardware
+// conversion on its narrow FP64 pipe (about two per SM and clock), the same
+// pipe as the product before it. Results below the normal single range,
+// overflows and non-finite inputs take the hardware conversion.
+__device__ __forceinline__ float double_to_float_rn(double x) {
+  const uint64_t u = (uint64_t)__double_as_longlong(x);
+  const uint32_t hi = (uint32_t)(u >> 32), sign = hi & 0x80000000u;
+  const uint32_t ed = (hi >> 20) & 0x7ffu;
+  if (ed == 0u) return __uint_as_float(sign);  // zero or double subnormal: a signed zero
+  const int e = (int)ed - (1023 - 127);        // single-precision biased exponent
+  if (e < 1 || e > 254) return __double2float_rn(x);
+  const uint32_t frac = (uint32_t)((u >> 29) & 0x7fffffu);  // top 23 fraction bits
+  const uint32_t rem = (uint32_t)(u & 0x1fffffffu);          // the 29 dropped bits
+  const uint32_t up = (rem > 0x10000000u) | ((rem == 0x10000000u) & (frac & 1u));
+  // a carry out of the fraction raises the exponent (to infinity from 254)
+  return __uint_as_float(sign | (((uint32_t)e << 23) + frac + up));
+}
+
 template <typename V>
 struct WarpTables {
   float *z;     // [tsize][D][g]
@@ -40,11 +59,15 @@ struct WarpTables {
   int *rr;      // [g]
 };
 
+// Bytes of one warp's tables, a multiple of 16 so that every warp's image
+// starts on a 16-byte boundary (the one-table scan reads a slot's four
+// scaled inputs as one 16-byte word).
 template <typename V>
 __host__ __device__ inline size_t warp_table_bytes(int tsize, int D, int g) {
   size_t zb = (size_t)tsize * D * g * sizeof(float);
   zb = (zb + 7) & ~(size_t)7;
-  return zb + (size_t)tsize * g * sizeof(V) + 2 * (size_t)g * sizeof(int);
+  const size_t b = zb + (size_t)tsize * g * sizeof(V) + 2 * (size_t)g * sizeof(int);
+  return (b + 15) & ~(size_t)15;
 }
 
 // DC: the number of inputs when fixed by the region (4 for Black-Scholes and
@@ -131,25 +154,47 @@ __global__ void __launch_bounds__(1024) iact_kernel(R reg, const typename R::T *
             if (sizeof(V) == 4)
               z[d] = __fmul_rn(P.scale_f[d], (float)x[d]);
             else
-              z[d] = __double2float_rn(__dmul_rn(P.scale_d[d], (double)x[d]));
+              z[d] = double_to_float_rn(__dmul_rn(P.scale_d[d], (double)x[d]));
           }
         }
         const int filled = W.filled[tab];
-        for (int j = 0; j < filled; ++j) {
-          float acc = 0.0f;
-          const float *zs = W.z + (size_t)j * D * g + tab;
-#pragma unroll
-          for (int d = 0; d < KD; ++d) {
-            if (d < D) {
-              const float df = __fsub_rn(z[d], zs[d * g]);
-              acc = __fadd_rn(acc, __fmul_rn(df, df));
+        if (DC == 4 && g == 1) {
+          // one table per warp: a slot's four scaled inputs are contiguous,
+          // read as one 16-byte word (a broadcast); differences and squares
+          // in packed pairs, the sum in dimension order as below (the same
+          // IEEE operations, so the same bits)
+          const unsigned long long z01 = f32x2_pack(z[0], z[1]), z23 = f32x2_pack(z[2], z[3]);
+          for (int j = 0; j < filled; ++j) {
+            const float4 t = *reinterpret_cast<const float4 *>(W.z + (size_t)j * 4);
+            const unsigned long long d01 = f32x2_sub(z01, f32x2_pack(t.x, t.y));
+            const unsigned long long d23 = f32x2_sub(z23, f32x2_pack(t.z, t.w));
+            float s0, s1, s2, s3;
+            f32x2_unpack(f32x2_mul(d01, d01), s0, s1);
+            f32x2_unpack(f32x2_mul(d23, d23), s2, s3);
+            const float acc = __fadd_rn(__fadd_rn(__fadd_rn(s0, s1), s2), s3);
+            if (!has || acc < best) {
+              best = acc;
+              near = j;
             }
+            has = true;
           }
-          if (!has || acc < best) {
-            best = acc;
-            near = j;
+        } else {
+          for (int j = 0; j < filled; ++j) {
+            float acc = 0.0f;
+            const float *zs = W.z + (size_t)j * D * g + tab;
+#pragma unroll
+            for (int d = 0; d < KD; ++d) {
+              if (d < D) {
+                const float df = __fsub_rn(z[d], zs[d * g]);
+                acc = __fadd_rn(acc, __fmul_rn(df, df));
+              }
+            }
+            if (!has || acc < best) {
+              best = acc;
+              near = j;
+            }
+            has = true;
           }
-          has = true;
         }
       }
       const float dmin = has ? __fsqrt_rn(best) : INFINITY;

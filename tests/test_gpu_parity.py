@@ -311,7 +311,7 @@ def test_taf_blackscholes_workload_counts(H, orc):
 @pytest.mark.parametrize("kind,dt,d", [(3, np.float32, 2), (3, np.float64, 3), (0, np.float32, 4),
                                        (1, np.float64, 4)])
 @pytest.mark.parametrize("level", [0, 1, 2])
-@pytest.mark.parametrize("g,ts", [(32, 8), (16, 4), (4, 2), (1, 1), (2, 64)])
+@pytest.mark.parametrize("g,ts", [(32, 8), (16, 4), (4, 2), (1, 1), (1, 3), (1, 8), (2, 64)])
 def test_iact(H, orc, kind, dt, d, level, g, ts):
     n, T, B = 30011, 3000, 128
     x, param = inputs(kind, n, dt, d=d, ikind="levels")
