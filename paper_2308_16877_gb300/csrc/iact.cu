@@ -70,6 +70,137 @@ __host__ __device__ inline size_t warp_table_bytes(int tsize, int D, int g) {
   return (b + 15) & ~(size_t)15;
 }
 
+// One invocation of a logical thread: read phase (scaled inputs and the
+// nearest valid slot of the lane's table), decision at the level, execution
+// (the slot's output or the exact region), and the write phase (per table
+// the farthest exactly computing lane writes the round-robin slot). Shared by
+// the launch-scoped kernel and the pipelined kept-state kernel.
+template <class R, int LEVEL, int DC, bool COUNT>
+__device__ __forceinline__ void iact_step(const R &reg, const WarpTables<typename R::T> &W,
+                                          const IactParams &P, int D, int g, int L, int tab, int lane,
+                                          bool act, int64_t i,
+                                          const typename R::T (&x)[DC > 0 ? DC : kMaxIn],
+                                          typename R::T *__restrict__ out, uint8_t *__restrict__ mask,
+                                          typename R::T *__restrict__ stat, int *s_tally, int &k3,
+                                          unsigned long long &n_apx, unsigned long long &n_border) {
+  using V = typename R::T;
+  constexpr int KD = DC > 0 ? DC : kMaxIn;
+  const int tsize = P.tsize;
+  float z[KD];
+  bool has = false;
+  float best = INFINITY;
+  int near = 0;
+  if (act) {
+#pragma unroll
+    for (int d = 0; d < KD; ++d) {
+      if (d < D) {
+        if (sizeof(V) == 4)
+          z[d] = __fmul_rn(P.scale_f[d], (float)x[d]);
+        else
+          z[d] = double_to_float_rn(__dmul_rn(P.scale_d[d], (double)x[d]));
+      }
+    }
+    const int filled = W.filled[tab];
+    if (DC == 4 && g == 1) {
+      // one table per warp: a slot's four scaled inputs are contiguous, read
+      // as one 16-byte word (a broadcast); differences and squares in packed
+      // pairs, the sum in dimension order as below (the same IEEE
+      // operations, so the same bits)
+      const unsigned long long z01 = f32x2_pack(z[0], z[1]), z23 = f32x2_pack(z[2], z[3]);
+      for (int j = 0; j < filled; ++j) {
+        const float4 t = *reinterpret_cast<const float4 *>(W.z + (size_t)j * 4);
+        const unsigned long long d01 = f32x2_sub(z01, f32x2_pack(t.x, t.y));
+        const unsigned long long d23 = f32x2_sub(z23, f32x2_pack(t.z, t.w));
+        float s0, s1, s2, s3;
+        f32x2_unpack(f32x2_mul(d01, d01), s0, s1);
+        f32x2_unpack(f32x2_mul(d23, d23), s2, s3);
+        const float acc = __fadd_rn(__fadd_rn(__fadd_rn(s0, s1), s2), s3);
+        if (!has || acc < best) {
+          best = acc;
+          near = j;
+        }
+        has = true;
+      }
+    } else {
+      for (int j = 0; j < filled; ++j) {
+        float acc = 0.0f;
+        const float *zs = W.z + (size_t)j * D * g + tab;
+#pragma unroll
+        for (int d = 0; d < KD; ++d) {
+          if (d < D) {
+            const float df = __fsub_rn(z[d], zs[d * g]);
+            acc = __fadd_rn(acc, __fmul_rn(df, df));
+          }
+        }
+        if (!has || acc < best) {
+          best = acc;
+          near = j;
+        }
+        has = true;
+      }
+    }
+  }
+  const float dmin = has ? __fsqrt_rn(best) : INFINITY;
+  const bool wants = act && has && dmin < P.thr;
+  // ---- decision
+  bool apx;
+  if (LEVEL == HPAC_LEVEL_THREAD) {
+    apx = wants;
+  } else if (LEVEL == HPAC_LEVEL_WARP) {
+    const unsigned na = __ballot_sync(0xffffffffu, act);
+    const unsigned nw = __ballot_sync(0xffffffffu, wants);
+    apx = (2 * __popc(nw) > __popc(na)) && act && has;
+  } else {
+    const unsigned na = __ballot_sync(0xffffffffu, act);
+    const unsigned nw = __ballot_sync(0xffffffffu, wants);
+    if (threadIdx.x == 0) s_tally[k3 == 2 ? 0 : k3 + 1] = 0;
+    if (lane == 0) atomicAdd(&s_tally[k3], (__popc(nw) << 16) | __popc(na));
+    __syncthreads();
+    const int tally = s_tally[k3];
+    apx = (2 * (tally >> 16) > (tally & 0xffff)) && act && has;
+    k3 = k3 == 2 ? 0 : k3 + 1;
+  }
+  // ---- execute
+  V y = (V)0;
+  if (act) {
+    if (apx) {
+      y = W.y[(size_t)near * g + tab];
+      if (mask) mask[i] = HPAC_MASK_APPROX;
+      ++n_apx;
+    } else {
+      y = reg(x);
+      if (mask) mask[i] = HPAC_MASK_EXACT;
+    }
+    out[i] = y;
+    if (stat) stat[i] = (V)dmin;
+    // diagnostic, compiled only into the counting variant: its double-precision
+    // test would otherwise be evaluated (and discarded) for every invocation
+    if (COUNT && has && borderline((double)dmin, P.thr_d)) ++n_border;
+  }
+  __syncwarp();
+  // ---- write phase: per table, the farthest exactly computing lane
+  float key = (act && !apx) ? dmin : -1.0f;
+  int who = lane;
+  for (int off = 1; off < L; off <<= 1) {
+    const float ok = __shfl_xor_sync(0xffffffffu, key, off);
+    const int ow = __shfl_xor_sync(0xffffffffu, who, off);
+    if (ok > key || (ok == key && ow < who)) {
+      key = ok;
+      who = ow;
+    }
+  }
+  if (who == lane && key >= 0.0f) {
+    const int slot = W.rr[tab];
+#pragma unroll
+    for (int d = 0; d < KD; ++d)
+      if (d < D) W.z[((size_t)slot * D + d) * g + tab] = z[d];
+    W.y[(size_t)slot * g + tab] = y;
+    W.rr[tab] = slot + 1 == tsize ? 0 : slot + 1;
+    if (W.filled[tab] < tsize) W.filled[tab] += 1;
+  }
+  __syncwarp();
+}
+
 // DC: the number of inputs when fixed by the region (4 for Black-Scholes and
 // the EOS), so that the distance loops are fully unrolled; 0 reads P.D.
 // COUNT: the caller asked for counters.
@@ -134,12 +265,7 @@ __global__ void __launch_bounds__(1024) iact_kernel(R reg, const typename R::T *
     int k3 = 0;
     for (int64_t i = t; t_lead + (i - t) < n; i += T) {
       const bool act = (t < T) && (i < n);
-      // ---- read phase
-      float z[KD];
       V x[KD];
-      bool has = false;
-      float best = INFINITY;
-      int near = 0;
       if (act) {
 #pragma unroll
         for (int d = 0; d < KD; ++d) x[d] = xn[d];
@@ -148,114 +274,9 @@ __global__ void __launch_bounds__(1024) iact_kernel(R reg, const typename R::T *
           for (int d = 0; d < KD; ++d)
             if (d < D) xn[d] = in[d * stride + i + T];
         }
-#pragma unroll
-        for (int d = 0; d < KD; ++d) {
-          if (d < D) {
-            if (sizeof(V) == 4)
-              z[d] = __fmul_rn(P.scale_f[d], (float)x[d]);
-            else
-              z[d] = double_to_float_rn(__dmul_rn(P.scale_d[d], (double)x[d]));
-          }
-        }
-        const int filled = W.filled[tab];
-        if (DC == 4 && g == 1) {
-          // one table per warp: a slot's four scaled inputs are contiguous,
-          // read as one 16-byte word (a broadcast); differences and squares
-          // in packed pairs, the sum in dimension order as below (the same
-          // IEEE operations, so the same bits)
-          const unsigned long long z01 = f32x2_pack(z[0], z[1]), z23 = f32x2_pack(z[2], z[3]);
-          for (int j = 0; j < filled; ++j) {
-            const float4 t = *reinterpret_cast<const float4 *>(W.z + (size_t)j * 4);
-            const unsigned long long d01 = f32x2_sub(z01, f32x2_pack(t.x, t.y));
-            const unsigned long long d23 = f32x2_sub(z23, f32x2_pack(t.z, t.w));
-            float s0, s1, s2, s3;
-            f32x2_unpack(f32x2_mul(d01, d01), s0, s1);
-            f32x2_unpack(f32x2_mul(d23, d23), s2, s3);
-            const float acc = __fadd_rn(__fadd_rn(__fadd_rn(s0, s1), s2), s3);
-            if (!has || acc < best) {
-              best = acc;
-              near = j;
-            }
-            has = true;
-          }
-        } else {
-          for (int j = 0; j < filled; ++j) {
-            float acc = 0.0f;
-            const float *zs = W.z + (size_t)j * D * g + tab;
-#pragma unroll
-            for (int d = 0; d < KD; ++d) {
-              if (d < D) {
-                const float df = __fsub_rn(z[d], zs[d * g]);
-                acc = __fadd_rn(acc, __fmul_rn(df, df));
-              }
-            }
-            if (!has || acc < best) {
-              best = acc;
-              near = j;
-            }
-            has = true;
-          }
-        }
       }
-      const float dmin = has ? __fsqrt_rn(best) : INFINITY;
-      const bool wants = act && has && dmin < P.thr;
-      // ---- decision
-      bool apx;
-      if (LEVEL == HPAC_LEVEL_THREAD) {
-        apx = wants;
-      } else if (LEVEL == HPAC_LEVEL_WARP) {
-        const unsigned na = __ballot_sync(0xffffffffu, act);
-        const unsigned nw = __ballot_sync(0xffffffffu, wants);
-        apx = (2 * __popc(nw) > __popc(na)) && act && has;
-      } else {
-        const unsigned na = __ballot_sync(0xffffffffu, act);
-        const unsigned nw = __ballot_sync(0xffffffffu, wants);
-        if (threadIdx.x == 0) s_tally[k3 == 2 ? 0 : k3 + 1] = 0;
-        if (lane == 0) atomicAdd(&s_tally[k3], (__popc(nw) << 16) | __popc(na));
-        __syncthreads();
-        const int tally = s_tally[k3];
-        apx = (2 * (tally >> 16) > (tally & 0xffff)) && act && has;
-        k3 = k3 == 2 ? 0 : k3 + 1;
-      }
-      // ---- execute
-      V y = (V)0;
-      if (act) {
-        if (apx) {
-          y = W.y[(size_t)near * g + tab];
-          if (mask) mask[i] = HPAC_MASK_APPROX;
-          ++n_apx;
-        } else {
-          y = reg(x);
-          if (mask) mask[i] = HPAC_MASK_EXACT;
-        }
-        out[i] = y;
-        if (stat) stat[i] = (V)dmin;
-        // diagnostic, compiled only into the counting variant: its double-precision
-        // test would otherwise be evaluated (and discarded) for every invocation
-        if (COUNT && has && borderline((double)dmin, P.thr_d)) ++n_border;
-      }
-      __syncwarp();
-      // ---- write phase: per table, the farthest exactly computing lane
-      float key = (act && !apx) ? dmin : -1.0f;
-      int who = lane;
-      for (int off = 1; off < L; off <<= 1) {
-        const float ok = __shfl_xor_sync(0xffffffffu, key, off);
-        const int ow = __shfl_xor_sync(0xffffffffu, who, off);
-        if (ok > key || (ok == key && ow < who)) {
-          key = ok;
-          who = ow;
-        }
-      }
-      if (who == lane && key >= 0.0f) {
-        const int slot = W.rr[tab];
-#pragma unroll
-        for (int d = 0; d < KD; ++d)
-          if (d < D) W.z[((size_t)slot * D + d) * g + tab] = z[d];
-        W.y[(size_t)slot * g + tab] = y;
-        W.rr[tab] = slot + 1 == tsize ? 0 : slot + 1;
-        if (W.filled[tab] < tsize) W.filled[tab] += 1;
-      }
-      __syncwarp();
+      iact_step<R, LEVEL, DC, COUNT>(reg, W, P, D, g, L, tab, lane, act, i, x, out, mask, stat, s_tally,
+                                     k3, n_apx, n_border);
     }
   }
   if (has_state) {  // save this warp's tables for the next call
@@ -263,6 +284,109 @@ __global__ void __launch_bounds__(1024) iact_kernel(R reg, const typename R::T *
     const uint32_t *src = reinterpret_cast<const uint32_t *>(base);
     for (size_t q = lane; q < wbytes / 4; q += 32) wst[q] = src[q];
   }
+  warp_count(s_cnt, n_apx, n_border);
+  __syncthreads();
+  if (counters && threadIdx.x == 0) {
+    if (s_cnt[0]) atomicAdd(&counters[0], s_cnt[0]);
+    if (s_cnt[1]) atomicAdd(&counters[1], s_cnt[1]);
+  }
+}
+
+// Kept-state iACT at thread and warp level, the call's logical warps
+// pipelined over persistent physical warps. Each physical warp works through
+// logical warps lw = first, first + stride, ... with two table buffers in
+// shared memory: while the invocations of one logical warp run on one
+// buffer, the next logical warp's table image is copied into the other by
+// cp.async (16-byte copies that hold no registers) and its first inputs are
+// loaded into registers. The decisions, outputs and saved images are those
+// of iact_kernel with one physical warp per logical warp.
+__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gmem_src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(smem_dst)),
+               "l"(gmem_src)
+               : "memory");
+}
+
+template <class R, int LEVEL, int DC, bool COUNT>
+__global__ void __launch_bounds__(256) iact_kept_kernel(R reg, const typename R::T *__restrict__ in,
+                                                        int64_t stride, typename R::T *__restrict__ out,
+                                                        uint8_t *__restrict__ mask,
+                                                        typename R::T *__restrict__ stat, int64_t n,
+                                                        int64_t T, IactParams P,
+                                                        unsigned long long *__restrict__ counters,
+                                                        uint32_t *__restrict__ st) {
+  using V = typename R::T;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ unsigned long long s_cnt[2];
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  constexpr int KD = DC > 0 ? DC : kMaxIn;
+  const int D = DC > 0 ? DC : P.D, tsize = P.tsize, g = P.g, L = P.L;
+  const int tab = lane / L;
+  const size_t wbytes = warp_table_bytes<V>(tsize, D, g);
+  const size_t zb = ((size_t)tsize * D * g * sizeof(float) + 7) & ~(size_t)7;
+  unsigned char *const buf0 = smem_raw + (size_t)warp * 2 * wbytes;  // buffers buf0 and buf0 + wbytes
+  const int64_t nlw = (T + 31) / 32;
+  const int64_t wstride = (int64_t)gridDim.x * (blockDim.x / 32);
+  const int64_t first = (int64_t)blockIdx.x * (blockDim.x / 32) + warp;
+  const int chunks = (int)(wbytes / 16);
+  const unsigned char *img = reinterpret_cast<const unsigned char *>(st);
+  if (threadIdx.x < 2) s_cnt[threadIdx.x] = 0;
+  __syncthreads();
+
+  V xn[KD];
+  auto fetch = [&](int64_t lw, unsigned char *dst) {
+    const unsigned char *src = img + (size_t)lw * wbytes;
+    for (int q = lane; q < chunks; q += 32) cp_async16(dst + 16 * q, src + 16 * q);
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    const int64_t t = lw * 32 + lane;
+    if (t < T && t < n) {
+#pragma unroll
+      for (int d = 0; d < KD; ++d)
+        if (d < D) xn[d] = in[d * stride + t];
+    }
+  };
+  if (first < nlw) fetch(first, buf0);
+
+  unsigned long long n_apx = 0, n_border = 0;
+  int cur = 0, k3 = 0;
+  for (int64_t lw = first; lw < nlw; lw += wstride) {
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    __syncwarp();
+    V xc[KD];
+#pragma unroll
+    for (int d = 0; d < KD; ++d) xc[d] = xn[d];
+    if (lw + wstride < nlw) fetch(lw + wstride, buf0 + (cur ^ 1) * wbytes);
+    unsigned char *base = buf0 + cur * wbytes;
+    WarpTables<V> W;
+    W.z = reinterpret_cast<float *>(base);
+    W.y = reinterpret_cast<V *>(base + zb);
+    W.filled = reinterpret_cast<int *>(base + zb + (size_t)tsize * g * sizeof(V));
+    W.rr = W.filled + g;
+    const int64_t t = lw * 32 + lane, t_lead = lw * 32;
+    for (int64_t i = t; t_lead + (i - t) < n; i += T) {
+      const bool act = (t < T) && (i < n);
+      V x[KD];
+      if (act) {
+#pragma unroll
+        for (int d = 0; d < KD; ++d) x[d] = xc[d];
+        if (i + T < n) {
+#pragma unroll
+          for (int d = 0; d < KD; ++d)
+            if (d < D) xc[d] = in[d * stride + i + T];
+        }
+      }
+      iact_step<R, LEVEL, DC, COUNT>(reg, W, P, D, g, L, tab, lane, act, i, x, out, mask, stat, nullptr,
+                                     k3, n_apx, n_border);
+    }
+    // save this logical warp's tables for the next call; the buffer is
+    // refilled two logical warps later, after the __syncwarp below
+    uint4 *dst = reinterpret_cast<uint4 *>(st + (size_t)lw * (wbytes / 4));
+    const uint4 *src = reinterpret_cast<const uint4 *>(base);
+    for (int q = lane; q < chunks; q += 32) dst[q] = src[q];
+    __syncwarp();
+    cur ^= 1;
+  }
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
   warp_count(s_cnt, n_apx, n_border);
   __syncthreads();
   if (counters && threadIdx.x == 0) {
@@ -315,6 +439,31 @@ hpac_status launch(hpac_region *r, R reg, const hpac_iact_knobs *k, const void *
   V *st = static_cast<V *>(stat);
   const V *x = static_cast<const V *>(in);
   constexpr int kDC = R::kReads == 4 ? 4 : 0;
+  if (st_words && k->level != HPAC_LEVEL_BLOCK) {
+    // kept state at thread or warp level: persistent warps, two buffers each
+    int Bk = 256;
+    while (Bk > 32 && (size_t)(Bk / 32) * 2 * wbytes > (size_t)limit) Bk -= 32;
+    const size_t smem_k = (size_t)(Bk / 32) * 2 * wbytes;
+    if (smem_k > (size_t)limit)
+      return set_error(HPAC_EUNSUPPORTED, "iACT tables of %zu bytes per block exceed %d", smem_k, limit);
+    auto fn = k->level == HPAC_LEVEL_THREAD
+                  ? (counters ? iact_kept_kernel<R, HPAC_LEVEL_THREAD, kDC, true>
+                              : iact_kept_kernel<R, HPAC_LEVEL_THREAD, kDC, false>)
+                  : (counters ? iact_kept_kernel<R, HPAC_LEVEL_WARP, kDC, true>
+                              : iact_kept_kernel<R, HPAC_LEVEL_WARP, kDC, false>);
+    HPAC_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_k));
+    int per_sm = 0;
+    HPAC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, Bk, smem_k));
+    if (per_sm < 1) per_sm = 1;
+    const int64_t nlw = (T + 31) / 32;
+    int64_t kb = (int64_t)sm_count(r->device) * per_sm;
+    const int64_t need = (nlw + Bk / 32 - 1) / (Bk / 32);
+    if (kb > need) kb = need;
+    fn<<<(unsigned)kb, Bk, smem_k, r->stream>>>(reg, x, d.in_stride, o, mask, st, d.n, T, P, counters,
+                                               st_words);
+    HPAC_CUDA_TRY(cudaGetLastError());
+    return HPAC_OK;
+  }
   switch (k->level) {
     case HPAC_LEVEL_THREAD: {
       auto fn = st_words ? (counters ? iact_kernel<R, HPAC_LEVEL_THREAD, kDC, true, true>
