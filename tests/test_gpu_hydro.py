@@ -330,14 +330,16 @@ def test_workload_256_cubed_launch_configuration(H, orc):
     G.close()
 
 
-def test_workload_256_cubed_headline_form(H, orc):
-    """The benchmark's headline form at its full size and launch configuration:
-    the 256^3 mesh with the EOS under iACT (8 slots, one table per warp,
-    distance 1e-3 on the benchmark's input scales) with one logical thread
-    per element and the tables kept across steps. Both sides take four steps
-    from the initial mesh; at every step the masks are identical, and after
-    the last the node fields agree everywhere and the element fields on a
-    sample."""
+@pytest.mark.parametrize("tsize,tperwarp", [(8, 1), (4, 4)])
+def test_workload_256_cubed_headline_form(H, orc, tsize, tperwarp):
+    """The benchmark's headline forms at their full size and launch
+    configuration: the 256^3 mesh with the EOS under iACT (8 slots and one
+    table per warp, or 4 slots and four tables per warp; distance 1e-3 on the
+    benchmark's input scales) with one logical thread per element and the
+    tables kept across steps (the pipelined kept-state kernel). Both sides
+    take four steps from the initial mesh; at every step the masks are
+    identical, and after the last the node fields agree everywhere and the
+    element fields on a sample."""
     n, steps = 256, 4
     E = n ** 3
     x, y, z, e = W.hydro_initial(n)
@@ -346,10 +348,10 @@ def test_workload_256_cubed_headline_form(H, orc):
     R = H.Region(H.HPAC_REGION_EOS, G["eos_in"], param=orc.GAMMA, logical_threads=E, block_threads=256)
     R.set_persistent(True)
     sc = (1.0 / W.HYDRO_E0, 1.0, 10.0, 1.0 / ((orc.GAMMA - 1.0) * W.HYDRO_E0))
-    ok = orc.eos_knobs(orc.EOS_IACT, tsize=8, tperwarp=1, thresh=1e-3, threads=E, block=256, in_scale=sc,
-                       persistent=True)
+    ok = orc.eos_knobs(orc.EOS_IACT, tsize=tsize, tperwarp=tperwarp, thresh=1e-3, threads=E, block=256,
+                       in_scale=sc, persistent=True)
     scale = (H.C.c_double * 4)(*sc)
-    gk = H.hpac_iact_knobs(8, 1, 1e-3, 0, 0, H.C.cast(scale, H.C.POINTER(H.C.c_double)))
+    gk = H.hpac_iact_knobs(tsize, tperwarp, 1e-3, 0, 0, H.C.cast(scale, H.C.POINTER(H.C.c_double)))
     mask = torch.full((E,), 255, dtype=torch.uint8, device="cuda")
     dt = W.hydro_dt(n)
     for s in range(steps):

@@ -115,6 +115,43 @@ def test_iact_persistent_tables(H, orc, kind, dt, level, ts, g):
 
 @pytest.mark.parametrize("kind,dt", [(0, np.float32), (1, np.float64)])
 @pytest.mark.parametrize("level", [0, 1])
+@pytest.mark.parametrize("ts,g", [(8, 1), (4, 4)])
+def test_iact_persistent_tables_pipelined(H, orc, kind, dt, level, ts, g):
+    """Kept tables at thread and warp level run on persistent warps that take
+    several logical warps each, the next one's table image copied in while
+    the current one runs: 7,813 logical warps (the last one ragged) outnumber
+    the resident physical warps (a few thousand on 152 SMs), so most physical
+    warps take two or more. Masks and distances equal the oracle's bit for
+    bit, call after call."""
+    T, B, calls = 250001, 256, 2
+    n = 2 * T
+    x, param = region_inputs(kind, n * calls, dt)
+    sc = W.iact_scale(x, x.shape[1])
+    thr = 0.2
+    tdt = torch.float32 if x.dtype == np.float32 else torch.float64
+    st = orc.iact_state(T, ts, g, x.shape[0])
+    with H.Region(kind, dev(x[:, :n]), param=param, logical_threads=T, block_threads=B) as R:
+        R.set_persistent(True)
+        total = 0
+        for c in range(calls):
+            xs = np.ascontiguousarray(x[:, c * n:(c + 1) * n])
+            out = torch.full((n,), float("nan"), dtype=tdt, device="cuda")
+            mask = torch.full((n,), 255, dtype=torch.uint8, device="cuda")
+            stat = torch.full((n,), -1.0, dtype=tdt, device="cuda")
+            R.run_iact(dev(xs), out, ts, g, thr, level, in_scale=sc, mask=mask, stat=stat)
+            o, m, s, cnt = orc.run_iact(kind, xs, param, ts, g, thr, level=level, in_scale=sc,
+                                        threads=T, block=B, state=st)
+            assert np.array_equal(host(mask), m), c
+            assert np.array_equal(host(stat), s), c
+            tol = output_tol(kind, x.astype(np.float64), param, x.dtype)
+            assert np.all(np.abs(host(out).astype(np.float64) - o.astype(np.float64)) <= tol.max()), c
+            total += cnt[1]
+    if level == 0:   # warp majorities are rare on the Black-Scholes stream
+        assert total > 0
+
+
+@pytest.mark.parametrize("kind,dt", [(0, np.float32), (1, np.float64)])
+@pytest.mark.parametrize("level", [0, 1])
 def test_taf_regions_persistent_replay(H, orc, kind, dt, level):
     """Black-Scholes / EOS: the masks of three persistent calls, concatenated,
     are a valid trace of one call over the concatenated inputs, checked by
