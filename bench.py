@@ -299,7 +299,7 @@ def hydro_cpu(form, n=HEAD_N, steps=4, single_steps=0):
     dt_s = timed(steps)
     label = form[0] if form is not None else "exact EOS"
     out = {"value": E * steps / dt_s, "unit": "elements/s", "cores": cores, "kind": "oracle",
-           "sample": f"{n}^3 mesh, {label}, first {steps} of the time steps", "seconds": dt_s}
+           "sample": f"{n}^3, first {steps} steps", "seconds": dt_s}
     if single_steps:
         oracle.set_threads(1)
         try:
@@ -309,6 +309,12 @@ def hydro_cpu(form, n=HEAD_N, steps=4, single_steps=0):
         out["single_thread"] = {"value": E * single_steps / t1, "unit": "elements/s",
                                 "sample": f"first {single_steps} time step(s), one core"}
     return out
+
+
+def workload_name(n, time_steps, form):
+    """The headline workload as the bench line's config names it."""
+    return (f"hydro {n}^3, {time_steps} steps, EOS under {form} (fastest within 1% loss, "
+            f">={MIN_ACTIVE_APPROX:.0%} of active calls approximated)")
 
 
 def run_reference(args):
@@ -331,9 +337,7 @@ def run_reference(args):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"hydro {args.n}^3 hex mesh, {args.time_steps} time steps, EOS region "
-                                   f"under {form[0]} (fastest form within 1% that approximates "
-                                   f">= {MIN_ACTIVE_APPROX:.0%} of active invocations)",
+            "config": {"workload": workload_name(args.n, args.time_steps, form[0]),
                        "l2": "inputs > L2 (6.5 GB state)", "parallelism": "oracle on host cores"},
             "cpu_baseline": {"value": v, "unit": "elements/s", "cores": cores, "kind": "oracle",
                              "sample": f"first time step of the {args.n}^3 run, {form[0]}"},
@@ -1504,13 +1508,11 @@ def main(argv=None):
         form = head["form"]
         rl = head["roofline"]
         line = {
-            "metric": METRIC, "value": head["value"], "unit": "elements/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms_per_step"],
+            "metric": METRIC, "value": sig(head["value"], 5), "unit": "elements/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": sig(head["ms_per_step"], 5),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": f"hydro {args.n}^3 hex mesh, {args.time_steps} time steps, EOS region "
-                                   f"under {form[0]} (fastest form within 1% that approximates "
-                                   f">= {MIN_ACTIVE_APPROX:.0%} of active invocations)",
+            "config": {"workload": workload_name(args.n, args.time_steps, form[0]),
                        "l2": "inputs > L2 (6.5 GB state)", "parallelism": f"replicas{world}"},
             "speedup_vs_exact": {"run": sig(best["speedup"]), "eos_region": sig(best["region_speedup"])},
             "quality": {"qoi_rel_err": sig(head["timed_quality"]["qoi_rel_err"], 3),
@@ -1526,15 +1528,17 @@ def main(argv=None):
             "gpu_launches": head["gpu_launches"],
             "clocks": {k: clocks.get(k) for k in ("sm_mhz", "sm_max_mhz", "reasons")},
         }
-        if kern is not None:
-            line["kernels_frac"] = {k: sig(v["frac"], 3) for k, v in kern["kernels"].items()}
+        if kern is not None:  # roofline fractions of the exact kernels (all rows in the detail file)
+            short = {"node_kernel": "node", "elem_kernel": "elem", "eos_exact": "eos", "finalize_kernel": "finalize",
+                     "bs_exact_16M": "bs16M"}
+            line["kernels_frac"] = {short[k]: sig(v["frac"], 3) for k, v in kern["kernels"].items() if k in short}
         try:
             os.makedirs(os.path.dirname(args.detail), exist_ok=True)
             with open(args.detail, "w") as f:
                 json.dump({"final": line, **detail}, f, indent=1, default=float)
         except OSError:
             pass
-        print(json.dumps(line, default=float))
+        print(json.dumps(line, default=float, separators=(",", ":")))
     if world > 1:
         dist.destroy_process_group()
     return 0
