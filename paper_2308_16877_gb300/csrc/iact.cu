@@ -60,8 +60,8 @@ struct WarpTables {
 };
 
 // Bytes of one warp's tables, a multiple of 16 so that every warp's image
-// starts on a 16-byte boundary (the one-table scan reads a slot's four
-// scaled inputs as one 16-byte word).
+// starts on a 16-byte boundary (the kept-state kernel copies images in
+// 16-byte pieces).
 template <typename V>
 __host__ __device__ inline size_t warp_table_bytes(int tsize, int D, int g) {
   size_t zb = (size_t)tsize * D * g * sizeof(float);
@@ -101,43 +101,21 @@ __device__ __forceinline__ void iact_step(const R &reg, const WarpTables<typenam
       }
     }
     const int filled = W.filled[tab];
-    if (DC == 4 && g == 1) {
-      // one table per warp: a slot's four scaled inputs are contiguous, read
-      // as one 16-byte word (a broadcast); differences and squares in packed
-      // pairs, the sum in dimension order as below (the same IEEE
-      // operations, so the same bits)
-      const unsigned long long z01 = f32x2_pack(z[0], z[1]), z23 = f32x2_pack(z[2], z[3]);
-      for (int j = 0; j < filled; ++j) {
-        const float4 t = *reinterpret_cast<const float4 *>(W.z + (size_t)j * 4);
-        const unsigned long long d01 = f32x2_sub(z01, f32x2_pack(t.x, t.y));
-        const unsigned long long d23 = f32x2_sub(z23, f32x2_pack(t.z, t.w));
-        float s0, s1, s2, s3;
-        f32x2_unpack(f32x2_mul(d01, d01), s0, s1);
-        f32x2_unpack(f32x2_mul(d23, d23), s2, s3);
-        const float acc = __fadd_rn(__fadd_rn(__fadd_rn(s0, s1), s2), s3);
-        if (!has || acc < best) {
-          best = acc;
-          near = j;
-        }
-        has = true;
-      }
-    } else {
-      for (int j = 0; j < filled; ++j) {
-        float acc = 0.0f;
-        const float *zs = W.z + (size_t)j * D * g + tab;
+    for (int j = 0; j < filled; ++j) {
+      float acc = 0.0f;
+      const float *zs = W.z + (size_t)j * D * g + tab;
 #pragma unroll
-        for (int d = 0; d < KD; ++d) {
-          if (d < D) {
-            const float df = __fsub_rn(z[d], zs[d * g]);
-            acc = __fadd_rn(acc, __fmul_rn(df, df));
-          }
+      for (int d = 0; d < KD; ++d) {
+        if (d < D) {
+          const float df = __fsub_rn(z[d], zs[d * g]);
+          acc = __fadd_rn(acc, __fmul_rn(df, df));
         }
-        if (!has || acc < best) {
-          best = acc;
-          near = j;
-        }
-        has = true;
       }
+      if (!has || acc < best) {
+        best = acc;
+        near = j;
+      }
+      has = true;
     }
   }
   const float dmin = has ? __fsqrt_rn(best) : INFINITY;
