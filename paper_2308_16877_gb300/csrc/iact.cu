@@ -16,6 +16,7 @@
 // (segmented arg-max of the distance over each table's exactly computing
 // lanes with shuffles; the winner writes its slot), __syncwarp.
 #include "hpac_internal.cuh"
+#include "convert.cuh"
 #include "regions.cuh"
 
 namespace hpac {
@@ -32,24 +33,6 @@ struct IactParams {
   double thr_d;
 };
 
-// Double to single precision, rounded to nearest even, on the integer pipes
-// where the result is a normal single or a zero. GB300 executes the hardware
-// conversion on its narrow FP64 pipe (about two per SM and clock), the same
-// pipe as the product before it. Results below the normal single range,
-// overflows and non-finite inputs take the hardware conversion.
-__device__ __forceinline__ float double_to_float_rn(double x) {
-  const uint64_t u = (uint64_t)__double_as_longlong(x);
-  const uint32_t hi = (uint32_t)(u >> 32), sign = hi & 0x80000000u;
-  const uint32_t ed = (hi >> 20) & 0x7ffu;
-  if (ed == 0u) return __uint_as_float(sign);  // zero or double subnormal: a signed zero
-  const int e = (int)ed - (1023 - 127);        // single-precision biased exponent
-  if (e < 1 || e > 254) return __double2float_rn(x);
-  const uint32_t frac = (uint32_t)((u >> 29) & 0x7fffffu);  // top 23 fraction bits
-  const uint32_t rem = (uint32_t)(u & 0x1fffffffu);          // the 29 dropped bits
-  const uint32_t up = (rem > 0x10000000u) | ((rem == 0x10000000u) & (frac & 1u));
-  // a carry out of the fraction raises the exponent (to infinity from 254)
-  return __uint_as_float(sign | (((uint32_t)e << 23) + frac + up));
-}
 
 template <typename V>
 struct WarpTables {

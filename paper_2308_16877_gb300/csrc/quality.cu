@@ -19,6 +19,7 @@
 #include <mutex>
 
 #include "hpac_internal.cuh"
+#include "convert.cuh"
 
 namespace hpac {
 namespace {
@@ -34,46 +35,60 @@ struct Partial {
   unsigned long long zbad;
 };
 
-template <typename B>
+template <typename B, int METRIC>
 __global__ void __launch_bounds__(kThreads) quality_partial(const double *__restrict__ a,
-                                                            const B *__restrict__ b, int64_t n,
-                                                            int metric, Partial *__restrict__ part) {
+                                                            const void *__restrict__ bv_, int64_t n,
+                                                            Partial *__restrict__ part) {
+  const B *__restrict__ b = static_cast<const B *>(bv_);
+  constexpr int metric = METRIC;
   __shared__ double s_sum[kThreads];
   __shared__ double s_zmax[kThreads];
   __shared__ unsigned long long s_used[kThreads], s_zeros[kThreads], s_zbad[kThreads];
-  double sum = 0.0, zmax = 0.0;
+  double sum = 0.0;
+  unsigned long long zmax = 0;  // bits of the largest |b| where a == 0 (NaN skipped, as fmax does)
   unsigned long long used = 0, zeros = 0, zbad = 0;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   // GB300 issues one double-precision warp instruction per 16 cycles per SM, so
   // the per-element work keeps a single FP64 operation (the difference a - b,
-  // exact for the single-precision approximations); the ratio or square is
-  // formed in single precision and summed in groups of 16 before entering the
-  // double-precision accumulator. Exact values outside [1e-30, 1e30] take the
-  // double-precision division.
+  // exact for the single-precision approximations; for MCR the comparison).
+  // The conversions between the precisions and the range tests of the exact
+  // value run on the integer pipes (the same bits as the hardware conversions
+  // and comparisons), the ratio or square is formed in single precision, and the
+  // terms are summed in groups of 16 before entering the double-precision
+  // accumulator. Exact values outside [1e-30, 1e30] take the double-precision
+  // division. Each thread walks its grid-stride sequence four elements at a
+  // time, the four loads issued before the first is used (the same elements
+  // in the same order as one at a time, so the same sums).
+  const uint64_t kLo = (uint64_t)__double_as_longlong(1e-30), kHi = (uint64_t)__double_as_longlong(1e30);
   float chunk = 0.0f;
   int in_chunk = 0;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-    const double ai = __ldcs(a + i);
-    const double bi = (double)__ldcs(b + i);
+  auto element = [&](double ai, B braw) {
+    double bi;
+    if (sizeof(B) == 4)
+      bi = float_to_double((float)braw);
+    else
+      bi = (double)braw;
+    const uint64_t aabs = (uint64_t)__double_as_longlong(ai) & 0x7fffffffffffffffull;
     float term;
     if (metric == HPAC_METRIC_MAPE) {
-      if (ai == 0.0) {
+      if (aabs == 0ull) {
+        const uint64_t babs = (uint64_t)__double_as_longlong(bi) & 0x7fffffffffffffffull;
         ++zeros;
-        if (bi != 0.0) ++zbad;
-        zmax = fmax(zmax, fabs(bi));
-        continue;
+        if (babs != 0ull) ++zbad;
+        if (babs <= 0x7ff0000000000000ull && babs > zmax) zmax = babs;
+        return;
       }
       const double d = ai - bi;
-      const double aa = fabs(ai);
-      if (aa >= 1e-30 && aa <= 1e30) {
-        term = __fdiv_rn(fabsf((float)d), (float)aa);
+      if (aabs >= kLo && aabs <= kHi) {
+        term = __fdiv_rn(fabsf(double_to_float_rn(d)),
+                         double_to_float_rn(__longlong_as_double((long long)aabs)));
       } else {
-        sum += fabs(d) / aa;
+        sum += fabs(d) / fabs(ai);
         ++used;
-        continue;
+        return;
       }
     } else if (metric == HPAC_METRIC_RMSE) {
-      const float d = (float)(ai - bi);
+      const float d = double_to_float_rn(ai - bi);
       term = d * d;
     } else {
       term = (ai != bi) ? 1.0f : 0.0f;
@@ -81,14 +96,29 @@ __global__ void __launch_bounds__(kThreads) quality_partial(const double *__rest
     chunk += term;
     ++used;
     if (++in_chunk == 16) {
-      sum += (double)chunk;
+      sum += float_to_double(chunk);
       chunk = 0.0f;
       in_chunk = 0;
     }
+  };
+  for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < n; i0 += 4 * stride) {
+    double av[4];
+    B bv[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int64_t i = i0 + k * stride;
+      if (i < n) {
+        av[k] = __ldcs(a + i);
+        bv[k] = __ldcs(b + i);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      if (i0 + k * stride < n) element(av[k], bv[k]);
   }
-  sum += (double)chunk;
+  sum += float_to_double(chunk);
   s_sum[threadIdx.x] = sum;
-  s_zmax[threadIdx.x] = zmax;
+  s_zmax[threadIdx.x] = __longlong_as_double((long long)zmax);
   s_used[threadIdx.x] = used;
   s_zeros[threadIdx.x] = zeros;
   s_zbad[threadIdx.x] = zbad;
@@ -106,6 +136,20 @@ __global__ void __launch_bounds__(kThreads) quality_partial(const double *__rest
   if (threadIdx.x == 0) {
     part[blockIdx.x] = Partial{s_sum[0], s_zmax[0], s_used[0], s_zeros[0], s_zbad[0]};
   }
+}
+
+// The partial-sum kernel for an approximation type and a metric (one
+// instantiation each, so a metric's unused paths are not compiled in).
+using PartialKernel = void (*)(const double *, const void *, int64_t, Partial *);
+PartialKernel partial_kernel(int32_t approx_dtype, int32_t metric) {
+  if (approx_dtype == HPAC_F32) {
+    if (metric == HPAC_METRIC_MAPE) return quality_partial<float, HPAC_METRIC_MAPE>;
+    if (metric == HPAC_METRIC_RMSE) return quality_partial<float, HPAC_METRIC_RMSE>;
+    return quality_partial<float, HPAC_METRIC_MCR>;
+  }
+  if (metric == HPAC_METRIC_MAPE) return quality_partial<double, HPAC_METRIC_MAPE>;
+  if (metric == HPAC_METRIC_RMSE) return quality_partial<double, HPAC_METRIC_RMSE>;
+  return quality_partial<double, HPAC_METRIC_MCR>;
 }
 
 __global__ void __launch_bounds__(kThreads) quality_final(const Partial *__restrict__ part, int np,
@@ -178,14 +222,17 @@ extern "C" hpac_status hpac_quality(int32_t approx_dtype, int64_t n, const doubl
   hpac_status s = scratch_for(dev, &scr);
   if (s != HPAC_OK) return s;
   cudaStream_t st = (cudaStream_t)cuda_stream;
+  // one wave of resident blocks (at most kBlocks): every thread's sequence
+  // runs to the end without a second, partly filled wave
+  const PartialKernel fn = partial_kernel(approx_dtype, metric);
+  int per_sm = 0, sms = 0;
+  HPAC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kThreads, 0));
+  HPAC_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int64_t wave = (int64_t)(per_sm > 0 ? per_sm : 1) * sms;
   int64_t blocks = (n + kThreads - 1) / kThreads;
-  blocks = blocks > kBlocks ? kBlocks : blocks;
-  if (approx_dtype == HPAC_F32)
-    quality_partial<float><<<(unsigned)blocks, kThreads, 0, st>>>(
-        d_exact, static_cast<const float *>(d_approx), n, metric, scr);
-  else
-    quality_partial<double><<<(unsigned)blocks, kThreads, 0, st>>>(
-        d_exact, static_cast<const double *>(d_approx), n, metric, scr);
+  if (blocks > wave) blocks = wave;
+  if (blocks > kBlocks) blocks = kBlocks;
+  fn<<<(unsigned)blocks, kThreads, 0, st>>>(d_exact, d_approx, n, scr);
   HPAC_CUDA_TRY(cudaGetLastError());
   quality_final<<<1, kThreads, 0, st>>>(scr, (int)blocks, scr + kBlocks);
   HPAC_CUDA_TRY(cudaGetLastError());
@@ -266,11 +313,12 @@ extern "C" hpac_status hpac_quality_noalloc(int32_t approx_dtype, int64_t n, con
   if (s != HPAC_OK) return s;
   if (n == 0) {
     // The warm-up call: besides the address lookup above, make the runtime
-    // load the three kernels now (with lazy module loading they would load,
-    // and allocate device memory for their code, at their first launch).
+    // load the kernels now (with lazy module loading they would load, and
+    // allocate device memory for their code, at their first launch).
     cudaFuncAttributes fa;
-    HPAC_CUDA_TRY(cudaFuncGetAttributes(&fa, quality_partial<float>));
-    HPAC_CUDA_TRY(cudaFuncGetAttributes(&fa, quality_partial<double>));
+    for (int32_t dt : {HPAC_F32, HPAC_F64})
+      for (int32_t m : {HPAC_METRIC_MAPE, HPAC_METRIC_RMSE, HPAC_METRIC_MCR})
+        HPAC_CUDA_TRY(cudaFuncGetAttributes(&fa, partial_kernel(dt, m)));
     HPAC_CUDA_TRY(cudaFuncGetAttributes(&fa, quality_final));
     return HPAC_OK;
   }
@@ -278,12 +326,7 @@ extern "C" hpac_status hpac_quality_noalloc(int32_t approx_dtype, int64_t n, con
   // Every partial slot the final kernel reads is written earlier in this call,
   // so nothing left in the shared array by a previous call is used.
   const int64_t blocks = (n + kStaticTile - 1) / kStaticTile;
-  if (approx_dtype == HPAC_F32)
-    quality_partial<float><<<(unsigned)blocks, kThreads, 0, st>>>(
-        d_exact, static_cast<const float *>(d_approx), n, metric, scr);
-  else
-    quality_partial<double><<<(unsigned)blocks, kThreads, 0, st>>>(
-        d_exact, static_cast<const double *>(d_approx), n, metric, scr);
+  partial_kernel(approx_dtype, metric)<<<(unsigned)blocks, kThreads, 0, st>>>(d_exact, d_approx, n, scr);
   HPAC_CUDA_TRY(cudaGetLastError());
   quality_final<<<1, kThreads, 0, st>>>(scr, (int)blocks, scr + kStaticPartials);
   HPAC_CUDA_TRY(cudaGetLastError());
