@@ -55,11 +55,13 @@ __global__ void __launch_bounds__(kThreads) quality_partial(const double *__rest
   // value run on the integer pipes (the same bits as the hardware conversions
   // and comparisons), the ratio or square is formed in single precision, and the
   // terms are summed in groups of 16 before entering the double-precision
-  // accumulator. Exact values outside [1e-30, 1e30] take the double-precision
-  // division. Each thread walks its grid-stride sequence four elements at a
+  // accumulator. For MAPE the exact value and the difference are first scaled
+  // by the same power of two (an exact change of their exponent fields), so
+  // the single-precision ratio covers every finite exact value; only ratios
+  // above 2^126 and subnormal operands take the double-precision division.
+  // Each thread walks its grid-stride sequence four elements at a
   // time, the four loads issued before the first is used (the same elements
   // in the same order as one at a time, so the same sums).
-  const uint64_t kLo = (uint64_t)__double_as_longlong(1e-30), kHi = (uint64_t)__double_as_longlong(1e30);
   float chunk = 0.0f;
   int in_chunk = 0;
   auto element = [&](double ai, B braw) {
@@ -78,17 +80,34 @@ __global__ void __launch_bounds__(kThreads) quality_partial(const double *__rest
         if (babs <= 0x7ff0000000000000ull && babs > zmax) zmax = babs;
         return;
       }
-      const double d = ai - bi;
-      if (aabs >= kLo && aabs <= kHi) {
-        term = __fdiv_rn(fabsf(double_to_float_rn(d)),
-                         double_to_float_rn(__longlong_as_double((long long)aabs)));
+      // |d| / |a| with both scaled by the power of two that puts |a| in
+      // [1, 2) (exact, on the exponent fields), then rounded to single
+      // precision and divided there; a ratio below 2^-1021 rounds to zero
+      // the one FP64 operation; the opaque move keeps the compiler from
+      // recomputing it where d is used again
+      uint64_t dbits;
+      asm volatile("mov.b64 %0, %1;" : "=l"(dbits) : "d"(ai - bi));
+      const double d = __longlong_as_double((long long)dbits);
+      const uint64_t dabs = dbits & 0x7fffffffffffffffull;
+      const int ea = (int)(aabs >> 52), ed = (int)(dabs >> 52), rel = ed - ea;
+      if (ea != 0 && ea != 0x7ff && ed != 0x7ff && (ed != 0 || dabs == 0ull) && rel <= 126) {
+        float fd = 0.0f;
+        if (dabs != 0ull && rel >= -1022)
+          fd = double_to_float_rn(__longlong_as_double(
+              (long long)((dabs & 0xfffffffffffffull) | ((uint64_t)(rel + 1023) << 52))));
+        const uint32_t fa_frac = (uint32_t)((aabs >> 29) & 0x7fffffu), fa_rem = (uint32_t)(aabs & 0x1fffffffu);
+        const float fa = __uint_as_float((127u << 23) + fa_frac +
+                                         ((fa_rem > 0x10000000u) | ((fa_rem == 0x10000000u) & (fa_frac & 1u))));
+        term = __fdiv_rn(fd, fa);
       } else {
         sum += fabs(d) / fabs(ai);
         ++used;
         return;
       }
     } else if (metric == HPAC_METRIC_RMSE) {
-      const float d = double_to_float_rn(ai - bi);
+      uint64_t dbits;
+      asm volatile("mov.b64 %0, %1;" : "=l"(dbits) : "d"(ai - bi));
+      const float d = double_to_float_rn(__longlong_as_double((long long)dbits));
       term = d * d;
     } else {
       term = (ai != bi) ? 1.0f : 0.0f;

@@ -452,6 +452,32 @@ def test_quality(H, orc, metric, dt, n):
         assert r["zero_max_abs"] == info["zero_max_abs"]
 
 
+@pytest.mark.parametrize("far_ratios", [False, True])
+@pytest.mark.parametrize("dt", [np.float32, np.float64])
+def test_quality_mape_whole_exponent_range(H, orc, dt, far_ratios):
+    """MAPE over exact values from the subnormal range to the largest normal
+    ones: each ratio is scaled by the exact value's power of two and formed in
+    single precision, and ratios above 2^126 or subnormal operands take the
+    double-precision division. 1e-6 relative against the oracle's FP64 sum."""
+    n = 1 << 18
+    rng = np.random.default_rng(7)
+    lo, hi = (-44.0, 38.0) if dt == np.float32 else (-310.0, 307.0)
+    a = 10.0 ** rng.uniform(lo, hi, n) * rng.choice([-1.0, 1.0], n)
+    b = a * (1 + rng.normal(0, 0.01, n))
+    if far_ratios:                            # ratios far above 2^126 (they dominate the mean)
+        far = np.arange(0, n, 97)
+        far = far[np.abs(a[far]) < 1e-3]
+        b[far] = a[far] * 1e40
+    b[1::89] = a[1::89]                       # exact: zero terms
+    b = b.astype(dt)
+    a[2::101] = 0.0
+    v, info = orc.quality(a, b.astype(np.float64), 0)
+    r = H.quality(dev(a), dev(b), 0)
+    assert np.isfinite(v)
+    assert r["value"] == pytest.approx(v, rel=1e-6, abs=1e-300)
+    assert r["zeros"] == info["zeros"] and r["zeros_mismatch"] == info["zeros_mismatch"]
+
+
 # ---------------------------------------------------------------- errors
 
 def test_invalid_arguments_are_rejected(H):
