@@ -1,9 +1,10 @@
 // Conversions between double and single precision on the integer pipes.
 // GB300 executes the hardware conversions (and double comparisons) on its
 // narrow FP64 pipe, about two per SM and clock; these give the same bits with
-// integer operations only, for every input (normal, subnormal, zero, infinite
-// and NaN), so no FP64 instruction is issued for them, not even a predicated
-// one.
+// integer operations, for every input (normal, subnormal, zero, infinite and
+// NaN). The common cases take a few instructions; a warp with a rare input
+// takes the full integer conversion for it, so no FP64 instruction is issued,
+// not even a predicated one.
 #pragma once
 
 #include <stdint.h>
@@ -87,6 +88,24 @@ __device__ __forceinline__ double float_to_double(float f) {
     if (rare) r = (uint64_t)__double_as_longlong(float_to_double_full(f));
   }
   return __longlong_as_double((long long)r);
+}
+
+// Double to single precision, rounded to nearest even: the integer fast path
+// for normal-single results and zeros, the hardware conversion for the rest,
+// without a warp vote. The compiler may issue that conversion predicated in
+// every warp; in a kernel with slack on its FP64 pipe this costs less than
+// the vote (the kept-state iACT kernel is bound by issue and latency).
+__device__ __forceinline__ float double_to_float_rn_novote(double x) {
+  const uint64_t u = (uint64_t)__double_as_longlong(x);
+  const uint32_t hi = (uint32_t)(u >> 32), sign = hi & 0x80000000u;
+  const uint32_t ed = (hi >> 20) & 0x7ffu;
+  if (ed == 0u) return __uint_as_float(sign);
+  const int e = (int)ed - (1023 - 127);
+  if (e < 1 || e > 254) return __double2float_rn(x);
+  const uint32_t frac = (uint32_t)((u >> 29) & 0x7fffffu);
+  const uint32_t rem = (uint32_t)(u & 0x1fffffffu);
+  const uint32_t up = (rem > 0x10000000u) | ((rem == 0x10000000u) & (frac & 1u));
+  return __uint_as_float(sign | (((uint32_t)e << 23) + frac + up));
 }
 
 }  // namespace hpac

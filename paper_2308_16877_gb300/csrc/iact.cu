@@ -80,7 +80,7 @@ __device__ __forceinline__ void iact_step(const R &reg, const WarpTables<typenam
         if (sizeof(V) == 4)
           z[d] = __fmul_rn(P.scale_f[d], (float)x[d]);
         else
-          z[d] = double_to_float_rn(__dmul_rn(P.scale_d[d], (double)x[d]));
+          z[d] = double_to_float_rn_novote(__dmul_rn(P.scale_d[d], (double)x[d]));
       }
     }
     const int filled = W.filled[tab];

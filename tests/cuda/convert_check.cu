@@ -1,5 +1,5 @@
-// Bit-exactness of the integer-pipe precision conversions (convert.cuh)
-// against the hardware conversions: every single-precision input, and 2^30
+// Bit-exactness of the integer-pipe precision conversions (convert.cuh, both
+// double-to-single variants) against the hardware conversions: every single-precision input, and 2^30
 // doubles of each of five kinds over the whole range. Prints one line per
 // case and exits non-zero on any mismatch.
 #include <cstdio>
@@ -29,8 +29,8 @@ __global__ void d2f(int kind, unsigned long long *bad, unsigned long long *first
     else if (kind == 3) u = (r & 0x8000000000000000ull) | ((uint64_t)(1023 - 127 - (r >> 52) % 30) << 52) | (r & 0xfffffffffffffull);  // single subnormal range
     else { const uint64_t e = 1023 - 127 - (r >> 52) % 30; u = (r & 0x8000000000000000ull) | (e << 52) | (r & 0xfffffe0000000ull) | ((r & 1) << 28); }  // subnormal ties
     const double x = __longlong_as_double((long long)u);
-    const float a = double_to_float_rn(x), b = __double2float_rn(x);
-    if (__float_as_uint(a) != __float_as_uint(b)) {
+    const float a = double_to_float_rn(x), b = __double2float_rn(x), c = double_to_float_rn_novote(x);
+    if (__float_as_uint(a) != __float_as_uint(b) || __float_as_uint(c) != __float_as_uint(b)) {
       if (atomicAdd(bad, 1ull) == 0) { first[0] = u; first[1] = __float_as_uint(a); first[2] = __float_as_uint(b); }
     }
   }
