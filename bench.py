@@ -24,9 +24,11 @@ against the exact run on the same GPU; `roofline` covers the dominant kernel
 (the FP64-bound element kernel) and `kernels` every exact kernel's roofline
 fraction; `cpu_baseline` is the CPU oracle on a bounded sample of the same run.
 Every other configuration (Black-Scholes at 65,536 and 2^24 options, the
-64^3 hydro run, the batched knob sweep, the surrogate, the NEXT rows) is a
-section printed on its own line before the final one, and the whole record is
-written to gpurun_out/bench_detail.json.
+64^3 hydro run, the batched knob sweep, the surrogate, Binomial Options,
+K-Means and the other added workloads) is a section printed on its own line
+before the final one, and the whole record is written to the --detail file
+(by default _build/bench_detail.json at the repository root, which git
+ignores).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
@@ -1434,7 +1436,7 @@ def main(argv=None):
     ap.add_argument("--sections", default="all",
                     help="comma-separated sections after the headline, 'all' or 'none'")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--detail", default=os.path.join(ROOT, "gpurun_out", "bench_detail.json"))
+    ap.add_argument("--detail", default=os.path.join(ROOT, "_build", "bench_detail.json"))
     args = ap.parse_args(argv)
     if args.impl == "reference":
         return run_reference(args)
