@@ -1501,7 +1501,7 @@ def main(argv=None):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = hydro_cpu(head["form"], n=args.n, steps=4)
+        cpu = hydro_cpu(head["form"], n=args.n, steps=4, single_steps=1)
         cpu.pop("seconds", None)
         emit(detail, "cpu_baseline", cpu)
 
