@@ -138,11 +138,15 @@ def test_iact_persistent_tables_pipelined(H, orc, kind, dt, level, ts, g):
             out = torch.full((n,), float("nan"), dtype=tdt, device="cuda")
             mask = torch.full((n,), 255, dtype=torch.uint8, device="cuda")
             stat = torch.full((n,), -1.0, dtype=tdt, device="cuda")
-            R.run_iact(dev(xs), out, ts, g, thr, level, in_scale=sc, mask=mask, stat=stat)
+            # the second call asks for counters (the counting instantiation)
+            r = R.run_iact(dev(xs), out, ts, g, thr, level, in_scale=sc, mask=mask, stat=stat,
+                           stats=c == 1)
             o, m, s, cnt = orc.run_iact(kind, xs, param, ts, g, thr, level=level, in_scale=sc,
                                         threads=T, block=B, state=st)
             assert np.array_equal(host(mask), m), c
             assert np.array_equal(host(stat), s), c
+            if c == 1:
+                assert r["approximated"] == cnt[1] and r["borderline"] == cnt[3]
             tol = output_tol(kind, x.astype(np.float64), param, x.dtype)
             assert np.all(np.abs(host(out).astype(np.float64) - o.astype(np.float64)) <= tol.max()), c
             total += cnt[1]
