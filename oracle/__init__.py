@@ -62,6 +62,8 @@ def lib() -> C.CDLL:
                   "orc_quality", "orc_run_taf_persist", "orc_run_iact_persist"):
             getattr(L, f).restype = C.c_int
         _hydro_bind(L)
+        L.orc_lavamd.argtypes = [I32, I32, D, P, P, I32, I32, I32, I32, D, I32, I32, I32, P, P, P]
+        L.orc_lavamd.restype = C.c_int
         _lib = L
     return _lib
 
@@ -380,3 +382,29 @@ def eos_knobs(mode, hsize=4, psize=8, tsize=8, tperwarp=32, level=THREAD, thresh
 
 
 __all__ = [k for k in dir() if not k.startswith("_")] + ["math"]
+
+
+# ------------------------------------------------------------- LavaMD region
+
+LAVAMD_EXACT, LAVAMD_TAF, LAVAMD_IACT = 0, 1, 2
+
+
+def lavamd(boxes1d, par_per_box, a2, rq, technique=LAVAMD_EXACT, level=THREAD, hsize=4, psize=8,
+           thresh=0.0, reset=0, tsize=8, tperwarp=32, in_scale=None, mask=False):
+    """LavaMD-style neighbour-box forces (lavamd_oracle.c): rq is (4, P) float64
+    (x, y, z, charge), P = boxes1d^3 par_per_box. Returns (fv (4, P), counters
+    [invocations, approximated, 0, borderline], mask (27 P bytes, 255 where no
+    invocation) or None)."""
+    B, NP = int(boxes1d), int(par_per_box)
+    P = B ** 3 * NP
+    rq = np.ascontiguousarray(rq, dtype=np.float64).reshape(4, P)
+    fv = np.zeros((4, P), dtype=np.float64)
+    cnt = np.zeros(4, dtype=np.int64)
+    m = np.full(27 * P, 255, dtype=np.uint8) if mask else None
+    sc = None if in_scale is None else np.ascontiguousarray(in_scale, dtype=np.float64)
+    rc = lib().orc_lavamd(B, NP, float(a2), _ptr(rq), _ptr(fv), int(technique), int(level), int(hsize),
+                          int(psize), float(thresh), int(reset), int(tsize), int(tperwarp),
+                          None if sc is None else _ptr(sc), None if m is None else _ptr(m), _ptr(cnt))
+    if rc != 0:
+        raise ValueError("orc_lavamd rejected its arguments")
+    return fv, cnt, m

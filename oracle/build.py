@@ -12,7 +12,7 @@ import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["hpac_oracle.c", "hydro_oracle.c"]
+SOURCES = ["hpac_oracle.c", "hydro_oracle.c", "lavamd_oracle.c"]
 LIB = os.path.join(BUILD, "liboracle.so")
 
 

@@ -1,0 +1,228 @@
+"""Pins of the LavaMD-style neighbour-box force oracle (oracle/lavamd_oracle.c)
+against results fixed independently of it: a numpy brute force over all pairs
+of particles whose boxes touch, closed forms for one and two particles, the
+invocation count (3B - 2)^3 NP, and the TAF / iACT limits thr = 0 and
+thr = +inf, where every decision is known in advance."""
+import numpy as np
+import pytest
+
+import oracle
+
+A2 = 0.5
+
+
+def inputs(B, NP, seed):
+    rng = np.random.default_rng(seed)
+    return rng.uniform(0.1, 1.0, (4, B ** 3 * NP))
+
+
+def brute_force(B, NP, rq, a2=A2):
+    """fv by all pairs (p, j) whose boxes differ by at most one in every
+    coordinate: a different formulation from the oracle's neighbour list."""
+    P = B ** 3 * NP
+    box = np.arange(P) // NP
+    bc = np.stack([box % B, (box // B) % B, box // (B * B)])
+    near = np.all(np.abs(bc[:, :, None] - bc[:, None, :]) <= 1, axis=0)
+    d = rq[:3, :, None] - rq[:3, None, :]
+    v = np.exp(-a2 * np.sum(d * d, axis=0)) * near
+    q = rq[3][None, :]
+    return np.concatenate([np.sum(q * v, axis=1)[None], np.sum(q[None] * 2 * v[None] * d, axis=2)])
+
+
+def per_invocation(B, NP, rq, a2=A2):
+    """y[p][k]: box k's contribution (4 values) in the oracle's neighbour order,
+    formed by numpy from the pair terms."""
+    P = B ** 3 * NP
+    out = []
+    for p in range(P):
+        h = p // NP
+        hx, hy, hz = h % B, (h // B) % B, h // (B * B)
+        seq = [h] + [((hz + dz) * B + hy + dy) * B + hx + dx
+                     for dz in (-1, 0, 1) for dy in (-1, 0, 1) for dx in (-1, 0, 1)
+                     if (dx, dy, dz) != (0, 0, 0) and 0 <= hx + dx < B and 0 <= hy + dy < B
+                     and 0 <= hz + dz < B]
+        ys = []
+        for b in seq:
+            j = np.arange(b * NP, (b + 1) * NP)
+            d = rq[:3, p][:, None] - rq[:3, j]
+            v = np.exp(-a2 * np.sum(d * d, axis=0))
+            ys.append(np.concatenate([[np.sum(rq[3, j] * v)], np.sum(rq[3, j] * 2 * v * d, axis=1)]))
+        out.append(ys)
+    return out
+
+
+@pytest.mark.parametrize("B,NP", [(1, 5), (2, 3), (3, 7), (4, 2)])
+def test_exact_equals_the_pairwise_brute_force(B, NP):
+    rq = inputs(B, NP, 10 * B + NP)
+    fv, cnt, _ = oracle.lavamd(B, NP, A2, rq)
+    ref = brute_force(B, NP, rq)
+    scale = np.abs(ref).max()
+    assert np.abs(fv - ref).max() <= 1e-13 * scale
+    assert cnt[0] == (3 * B - 2) ** 3 * NP if B >= 2 else cnt[0] == NP
+
+
+def test_one_particle_feels_only_itself():
+    rq = np.array([[0.3], [0.6], [0.2], [0.7]])
+    fv, cnt, _ = oracle.lavamd(1, 1, A2, rq)
+    assert fv[:, 0].tolist() == [0.7, 0.0, 0.0, 0.0]
+    assert cnt.tolist() == [1, 0, 0, 0]
+
+
+def test_two_particles_closed_form():
+    r0, r1, q0, q1 = np.array([0.2, 0.5, 0.9]), np.array([0.7, 0.1, 0.4]), 0.3, 0.8
+    rq = np.array([[r0[0], r1[0]], [r0[1], r1[1]], [r0[2], r1[2]], [q0, q1]])
+    fv, _, _ = oracle.lavamd(1, 2, A2, rq)
+    e = np.exp(-A2 * np.sum((r0 - r1) ** 2))
+    assert fv[0, 0] == pytest.approx(q0 + q1 * e, rel=1e-15)
+    assert fv[1:, 0] == pytest.approx(q1 * 2 * e * (r0 - r1), rel=1e-15)
+    assert fv[1:, 1] == pytest.approx(q0 * 2 * e * (r1 - r0), rel=1e-15)
+
+
+def test_boxes_that_do_not_touch_do_not_interact():
+    # one particle in each of 27 boxes: the corner boxes (0,0,0) and (2,2,2) are
+    # two boxes apart; every particle feels exactly the boxes that touch its own
+    B = 3
+    rq = inputs(B, 1, 3)
+    fv, _, _ = oracle.lavamd(B, 1, A2, rq)
+    ref = brute_force(B, 1, rq)
+    assert np.abs(fv - ref).max() <= 1e-14 * np.abs(ref).max()
+    corner = 0
+    far = 26
+    d = rq[:3, corner] - rq[:3, far]
+    alone = brute_force(B, 1, rq)[0, corner]
+    with_far = alone + rq[3, far] * np.exp(-A2 * d @ d)
+    assert fv[0, corner] == pytest.approx(alone, rel=1e-14) and fv[0, corner] != pytest.approx(with_far, rel=1e-9)
+
+
+@pytest.mark.parametrize("technique", [oracle.LAVAMD_TAF, oracle.LAVAMD_IACT])
+@pytest.mark.parametrize("level", [oracle.THREAD, oracle.WARP, oracle.BLOCK])
+def test_threshold_zero_is_exact(technique, level):
+    B, NP = 3, 40
+    rq = inputs(B, NP, 5)
+    ex, _, mex = oracle.lavamd(B, NP, A2, rq, mask=True)
+    fv, cnt, m = oracle.lavamd(B, NP, A2, rq, technique=technique, level=level, thresh=0.0,
+                               tperwarp=4, mask=True)
+    assert np.array_equal(fv, ex)
+    assert cnt[1] == 0 and np.array_equal(m, mex)
+
+
+def taf_inf_count(nn, h, p):
+    """Approximated invocations of one particle under TAF with thr = +inf:
+    h accurate outputs fill the window, then p predictions and one accurate
+    output alternate."""
+    if nn <= h:
+        return 0
+    r = nn - h
+    return (r // (p + 1)) * p + min(r % (p + 1), p)
+
+
+@pytest.mark.parametrize("h,p", [(1, 1), (2, 3), (4, 8), (5, 0), (30, 2)])
+def test_taf_infinite_threshold_closed_form(h, p):
+    B, NP = 3, 6
+    rq = inputs(B, NP, 7)
+    fv, cnt, m = oracle.lavamd(B, NP, A2, rq, technique=oracle.LAVAMD_TAF, hsize=h, psize=p,
+                               thresh=np.inf, mask=True)
+    ys = per_invocation(B, NP, rq)
+    P = B ** 3 * NP
+    expect_fv = np.zeros((4, P))
+    total = 0
+    for q in range(P):
+        nn = len(ys[q])
+        total += taf_inf_count(nn, h, p)
+        acc, newest, k = np.zeros(4), None, 0
+        pattern = []
+        while k < nn:
+            if k < h:
+                pattern.append(0)
+                k += 1
+                continue
+            run = min(p, nn - k)
+            pattern += [1] * run
+            k += run
+            if k < nn:
+                pattern.append(0)
+                k += 1
+        for k, apx in enumerate(pattern):
+            if not apx:
+                newest = ys[q][k]
+            acc = acc + newest
+            assert m[k * P + q] == apx
+        expect_fv[:, q] = acc
+        assert all(m[k * P + q] == 255 for k in range(nn, 27))
+    assert cnt[0] == (3 * B - 2) ** 3 * NP and cnt[1] == total
+    assert np.abs(fv - expect_fv).max() <= 1e-13 * np.abs(expect_fv).max()
+
+
+def test_iact_infinite_threshold_private_tables_repeat_the_home_box():
+    B, NP = 3, 9
+    rq = inputs(B, NP, 8)
+    fv, cnt, m = oracle.lavamd(B, NP, A2, rq, technique=oracle.LAVAMD_IACT, tsize=4, tperwarp=32,
+                               thresh=np.inf, mask=True)
+    ys = per_invocation(B, NP, rq)
+    P = B ** 3 * NP
+    expect = np.stack([len(ys[q]) * ys[q][0] for q in range(P)], axis=1)
+    assert cnt[1] == cnt[0] - P
+    assert np.abs(fv - expect).max() <= 1e-13 * np.abs(expect).max()
+    assert all(m[q] == 0 for q in range(P))
+    assert all(m[k * P + q] == 1 for q in range(P) for k in range(1, len(ys[q])))
+
+
+@pytest.mark.parametrize("technique,knobs", [
+    (oracle.LAVAMD_TAF, dict(hsize=3, psize=4, thresh=0.05)),
+    (oracle.LAVAMD_IACT, dict(tsize=4, tperwarp=1, thresh=0.3)),
+])
+def test_one_lane_groups_make_warp_and_block_level_the_thread_level(technique, knobs):
+    # one particle per box: every warp and block has one active lane, so the
+    # majority of its deciding lanes is that lane's own decision
+    B = 4
+    rq = inputs(B, 1, 9)
+    res = [oracle.lavamd(B, 1, A2, rq, technique=technique, level=lv, mask=True, **knobs)
+           for lv in (oracle.THREAD, oracle.WARP, oracle.BLOCK)]
+    assert res[0][1][1] > 0
+    for fv, cnt, m in res[1:]:
+        assert np.array_equal(fv, res[0][0]) and np.array_equal(m, res[0][2])
+        assert cnt.tolist() == res[0][1].tolist()
+
+
+def test_rejects_bad_arguments():
+    rq = inputs(2, 3, 1)
+    with pytest.raises(ValueError):
+        oracle.lavamd(2, 3, A2, rq, technique=oracle.LAVAMD_TAF, hsize=0)
+    with pytest.raises(ValueError):
+        oracle.lavamd(2, 3, A2, rq, technique=oracle.LAVAMD_IACT, tperwarp=3)
+    with pytest.raises(ValueError):
+        oracle.lavamd(2, 0, A2, rq[:, :0])
+
+
+@pytest.mark.parametrize("h,p,thr", [(3, 2, 0.05), (4, 8, 0.08), (2, 1, 0.02)])
+def test_taf_thread_level_decisions_follow_numpy_rsd(h, p, thr):
+    """Thread level, a threshold that some windows pass: every decision
+    replayed from the per-invocation potentials with numpy's population
+    standard deviation over |mean|."""
+    B, NP = 3, 8
+    rq = inputs(B, NP, 11)
+    fv, cnt, m = oracle.lavamd(B, NP, A2, rq, technique=oracle.LAVAMD_TAF, hsize=h, psize=p,
+                               thresh=thr, mask=True)
+    ys = per_invocation(B, NP, rq)
+    P = B ** 3 * NP
+    n_apx = 0
+    for q in range(P):
+        win, pred, acc = [], 0, np.zeros(4)
+        for k, y in enumerate(ys[q]):
+            if pred > 0:
+                assert m[k * P + q] == 1
+                acc = acc + win[-1]
+                pred -= 1
+                n_apx += 1
+                continue
+            assert m[k * P + q] == 0
+            acc = acc + y
+            win = (win + [y])[-h:]
+            if len(win) == h:
+                pots = np.array([w[0] for w in win])
+                s = np.std(pots) / abs(np.mean(pots))
+                assert abs(s - thr) > 1e-9 * thr
+                if s < thr:
+                    pred = p
+        assert np.abs(fv[:, q] - acc).max() <= 1e-12 * np.abs(acc).max()
+    assert cnt[1] == n_apx and n_apx > 0
