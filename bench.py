@@ -718,6 +718,72 @@ def bench_levels(hpac, torch, dev, stream, n=1 << 22, clusters=64, reps=5):
             "exact_ms": exact_ms, "table": rows}
 
 
+# FP64 operations of one LavaMD pair term outside the exponential: three
+# differences, r^2 (a multiply and two FMAs), the exponent's scaling, q v,
+# 2 q v, the potential's add and three force FMAs.
+LAVAMD_PAIR_FP64_OPS = 13
+
+
+def bench_lavamd(hpac, torch, dev, stream, boxes1d=16, reps=3):
+    """LavaMD-style neighbour-box forces (Table 1; Section 5 approximates the
+    force calculation for a neighbouring box, Figure 9): 16^3 boxes of 100
+    particles, FP64. The exact run, TAF (h4 p8) and iACT (8 slots, tables shared
+    by 32 or 8 lanes) at thread, warp and block level: time, share of the
+    invocations approximated, potential MAPE and force NRMSE against the exact
+    run. Warp- and block-level decisions keep a warp (or the box's block) on
+    one path, where thread-level decisions leave the warp running the pair loop
+    for any lane that computes."""
+    B, NP = boxes1d, W.LAVAMD_PAR_PER_BOX
+    rq = torch.from_numpy(W.lavamd_inputs(B, NP)).to(dev)
+    P = rq.shape[1]
+    ex = torch.empty_like(rq)
+    out = torch.empty_like(rq)
+
+    def timed(f):
+        f()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            f()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    def run(**kn):
+        return hpac.lavamd(rq, B, NP, W.LAVAMD_A2, fv=out, stream=stream, **kn)
+
+    exact_ms = timed(lambda: hpac.lavamd(rq, B, NP, W.LAVAMD_A2, fv=ex, stream=stream))
+    _, st = hpac.lavamd(rq, B, NP, W.LAVAMD_A2, fv=ex, stats=True, stream=stream)
+    inv = st["invocations"]
+    pairs = inv * NP
+    f_ex = ex[1:].contiguous()
+    f_rms = float(torch.sqrt(torch.mean(f_ex * f_ex)).item())
+    fp64 = hpac.hpac_device_fp64_rate(stream.cuda_stream)
+    rows = []
+    forms = [("taf", dict(technique=hpac.LAVAMD_TAF, hsize=4, psize=8, thresh=t), f"h4 p8 {t}") for t in (0.02, 0.04)]
+    forms += [("iact", dict(technique=hpac.LAVAMD_IACT, tsize=8, tperwarp=g, thresh=0.05), f"t8 g{g} 0.05")
+              for g in (1, 4)]
+    for tech, kn, label in forms:
+        for level in (hpac.HPAC_LEVEL_THREAD, hpac.HPAC_LEVEL_WARP, hpac.HPAC_LEVEL_BLOCK):
+            _, st = run(level=level, stats=True, **kn)
+            mape = hpac.quality(ex[0].contiguous(), out[0].contiguous(), hpac.HPAC_METRIC_MAPE,
+                                stream=stream)["value"]
+            rmse = hpac.quality(f_ex, out[1:].contiguous(), hpac.HPAC_METRIC_RMSE, stream=stream)["value"]
+            ms = timed(lambda: run(level=level, **kn))
+            rows.append({"technique": tech, "knobs": label, "level": ["thread", "warp", "block"][level],
+                         "ms": ms, "speedup_vs_exact": exact_ms / ms,
+                         "approximated": st["approximated"] / inv,
+                         "potential_mape": mape, "force_nrmse": rmse / f_rms})
+    within = [r for r in rows if r["potential_mape"] <= QUALITY_BOUND]
+    best = max(within, key=lambda r: r["speedup_vs_exact"]) if within else None
+    ops = LAVAMD_PAIR_FP64_OPS * pairs / (exact_ms * 1e-3)
+    return {"boxes": f"{B}^3", "particles": P, "par_per_box": NP, "invocations": inv,
+            "pair_terms": pairs, "exact_ms": exact_ms, "exact_pairs_per_s": pairs / (exact_ms * 1e-3),
+            "exact_fp64_ops_outside_exp_per_s": ops,
+            "exact_fp64_outside_exp_frac_of_measured_fma_rate": ops / (fp64 / 2.0 * 1e12),
+            "table": rows, "fastest_within_1pct_potential_mape": best}
+
+
 def bench_surrogate(hpac, torch, dev, stream, n_train=1 << 22, n_cal=1 << 20, n_inf=1 << 24,
                     epochs=24, batch=8192, lr=3e-3):
     """The learned surrogate of the Black-Scholes region: trained by the
@@ -1455,7 +1521,7 @@ def main(argv=None):
     hpac.load()
     stream = torch.cuda.current_stream(dev)
     all_sections = ["kernels", "cfg4_extras", "hydro64", "blackscholes_65536", "blackscholes_16M", "sweep",
-                    "search", "binomial", "kmeans", "levels", "surrogate", "persistent_state"]
+                    "search", "binomial", "kmeans", "levels", "lavamd", "surrogate", "persistent_state"]
     want = all_sections if args.sections == "all" else ([] if args.sections == "none"
                                                          else args.sections.split(","))
     detail = {}
@@ -1496,6 +1562,7 @@ def main(argv=None):
     section("binomial", lambda: bench_binomial(hpac, torch, dev, stream))
     section("kmeans", lambda: bench_kmeans(hpac, torch, dev, stream))
     section("levels", lambda: bench_levels(hpac, torch, dev, stream))
+    section("lavamd", lambda: bench_lavamd(hpac, torch, dev, stream))
     section("surrogate", lambda: bench_surrogate(hpac, torch, dev, stream))
     section("persistent_state", lambda: bench_persistent(hpac, torch, dev, stream))
 

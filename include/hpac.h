@@ -356,6 +356,51 @@ hpac_status hpac_hydro_run(const hpac_hydro_state *s, hpac_region *eos, int32_t 
                            int32_t technique, const void *knobs);
 
 /* ------------------------------------------------------------------------
+ * LavaMD-style neighbour-box forces (Table 1, LavaMD: the potential and force
+ * on each particle from the particles of the boxes that touch its own).
+ * Section 5 approximates the force calculation for a neighbouring box with
+ * TAF and iACT and compares thread- and warp-level decisions (Figure 9).
+ *
+ * Space: boxes1d^3 boxes, box b = (bz B + by) B + bx, par_per_box (NP)
+ * particles per box, particle p = b NP + m, P = boxes1d^3 NP. d_rq: 4 rows of
+ * P doubles (x, y, z, charge q; row stride P), device, 8-byte aligned, read
+ * only. d_fv: 4 rows of P doubles (potential, force x, y, z), device, written.
+ * One invocation is the contribution of one box b to one particle p:
+ *   sum over b's particles j of (q_j v, 2 q_j v d), d = r_p - r_j,
+ *   v = exp(-a2 |d|^2),
+ * and fv_p sums the invocations of p's neighbour sequence: its own box, then
+ * the touching boxes inside the grid at offsets (dx, dy, dz) != 0 in the
+ * order dz, dy, dx (dx fastest); (3 boxes1d - 2)^3 NP invocations in all.
+ *
+ * The block of a home box holds its NP particles on ceil(NP/32) warps; its
+ * lanes advance through the sequence together. technique 0: exact. 1: TAF
+ * (hpac_taf_knobs): per particle a window of the last hsize accurate outputs,
+ * the RSD of their potentials against thresh, a prediction repeating all four
+ * components of the newest output. 2: iACT (hpac_iact_knobs): the inputs are
+ * the particle's coordinates (in_scale: 3 doubles or NULL), tables shared by
+ * 32 / tperwarp lanes hold scaled coordinates and the four outputs; with one
+ * table per lane every invocation after a particle's first hits (its own entry
+ * is at distance 0) for any thresh > 0. Decision levels as for the regions
+ * (level BLOCK: the home box). Shared memory per block: 32 NP bytes plus, for
+ * TAF, 32 hsize ceil(NP/32)*32 or, for iACT, about 44 tsize bytes per table;
+ * HPAC_EINVAL above the device's limit. d_mask (nullable, 27 P bytes): at
+ * k P + p, for the k-th invocation of particle p, HPAC_MASK_EXACT or
+ * HPAC_MASK_APPROX; the bytes of invocations that do not exist are left as
+ * they are. h_stats (nullable) makes the call synchronous and returns the
+ * counts. Errors: HPAC_EINVAL (descriptor, knobs, NULL or misaligned
+ * pointers when P > 0), HPAC_ECUDA. Asynchronous on cuda_stream otherwise.
+ * ------------------------------------------------------------------------ */
+typedef struct {
+  int32_t boxes1d;      /* B, 0..1290                                           */
+  int32_t par_per_box;  /* NP, 1..1024                                          */
+  double a2;            /* pair potential exp(-a2 r^2): a2 = 2 alpha^2, >= 0    */
+} hpac_lavamd_desc;
+
+hpac_status hpac_lavamd_run(const hpac_lavamd_desc *desc, int32_t technique, const void *knobs,
+                            const double *d_rq, double *d_fv, uint8_t *d_mask,
+                            hpac_stats *h_stats, void *cuda_stream);
+
+/* ------------------------------------------------------------------------
  * Batched knob sweep (the paper's design-space exploration, Section 2.4 and
  * Section 4 / Table 2, which builds and runs each configuration separately):
  * every configuration over every Black-Scholes region (single precision) in

@@ -52,6 +52,10 @@ class hpac_stats(C.Structure):
         return {f: int(getattr(self, f)) for f, _ in self._fields_}
 
 
+class hpac_lavamd_desc(C.Structure):
+    _fields_ = [("boxes1d", C.c_int32), ("par_per_box", C.c_int32), ("a2", C.c_double)]
+
+
 class hpac_quality_result(C.Structure):
     _fields_ = [("value", C.c_double), ("zero_max_abs", C.c_double), ("used", C.c_int64),
                 ("zeros", C.c_int64), ("zeros_mismatch", C.c_int64)]
@@ -123,6 +127,8 @@ SIGNATURES = {
     "hpac_hydro_finalize": (C.c_int, [C.POINTER(hpac_hydro_state), _P]),
     "hpac_hydro_run": (C.c_int, [C.POINTER(hpac_hydro_state), _P, C.c_int32, C.c_int32, _P]),
     "hpac_device_fp64_rate": (C.c_int, [C.POINTER(C.c_double), _P]),
+    "hpac_lavamd_run": (C.c_int, [C.POINTER(hpac_lavamd_desc), C.c_int32, _P, _P, _P, _P,
+                                  C.POINTER(hpac_stats), _P]),
     "hpac_sweep_create": (C.c_int, [C.c_int32, C.POINTER(hpac_sweep_config), C.c_int32,
                                     C.POINTER(hpac_sweep_region), _P, C.c_int64, _P, C.c_double,
                                     C.c_int32, C.c_int32, C.c_int32, _P, C.POINTER(_P)]),
@@ -312,6 +318,14 @@ def hpac_hydro_run(state, eos, steps, technique, knobs=None):
                                  C.byref(knobs) if knobs is not None else None), "hpac_hydro_run")
 
 
+def hpac_lavamd_run(desc, technique, knobs, d_rq, d_fv, d_mask=None, want_stats=False, stream=None):
+    st = hpac_stats() if want_stats else None
+    _check(load().hpac_lavamd_run(C.byref(desc), technique, C.byref(knobs) if knobs is not None else None,
+                                  d_rq, d_fv, d_mask, C.byref(st) if st is not None else None,
+                                  stream or None), "hpac_lavamd_run")
+    return st
+
+
 def hpac_device_fp64_rate(stream=None) -> float:
     v = C.c_double()
     _check(load().hpac_device_fp64_rate(C.byref(v), stream or None), "hpac_device_fp64_rate")
@@ -452,6 +466,42 @@ def kmeans_update(x, assign, cent, work, prev=None, stream=None, changed=True):
                                      C.byref(ch) if changed else None, _stream_handle(stream)),
            "hpac_kmeans_update")
     return int(ch.value) if changed else None
+
+
+LAVAMD_EXACT, LAVAMD_TAF, LAVAMD_IACT = 0, 1, 2
+
+
+def lavamd(rq, boxes1d, par_per_box, a2=0.5, technique=LAVAMD_EXACT, level=HPAC_LEVEL_THREAD,
+           hsize=4, psize=8, thresh=0.0, reset_on_exit=False, tsize=8, tperwarp=32, in_scale=None,
+           fv=None, mask=None, stats=False, stream=None):
+    """LavaMD-style neighbour-box forces (hpac_lavamd_run) on CUDA tensors: rq
+    (4, P) float64 (x, y, z, charge), P = boxes1d^3 par_per_box. Returns fv
+    (4, P) float64 (potential, force x, y, z) and, with stats, the counts.
+    mask: an optional uint8 tensor of 27 P bytes."""
+    import torch
+    P = int(boxes1d) ** 3 * int(par_per_box)
+    if tuple(rq.shape) != (4, P) or rq.dtype != torch.float64 or not rq.is_contiguous():
+        raise ValueError("rq must be a contiguous (4, boxes1d^3 par_per_box) float64 tensor")
+    if fv is None:
+        fv = torch.empty_like(rq)
+    if mask is not None and mask.numel() < 27 * P:
+        raise ValueError("mask needs 27 P bytes")
+    desc = hpac_lavamd_desc(int(boxes1d), int(par_per_box), float(a2))
+    knobs = None
+    if technique == LAVAMD_TAF:
+        knobs = hpac_taf_knobs(int(hsize), int(psize), float(thresh), int(level), int(bool(reset_on_exit)))
+    elif technique == LAVAMD_IACT:
+        sc = None
+        if in_scale is not None:
+            vals = [float(v) for v in in_scale]
+            if len(vals) != 3:
+                raise ValueError("in_scale needs three values (x, y, z)")
+            sc = (C.c_double * 3)(*vals)
+        knobs = hpac_iact_knobs(int(tsize), int(tperwarp), float(thresh), int(level), 0,
+                                C.cast(sc, C.POINTER(C.c_double)) if sc is not None else None)
+    st = hpac_lavamd_run(desc, int(technique), knobs, _ptr(rq), _ptr(fv), _ptr(mask), stats,
+                         _stream_handle(stream))
+    return (fv, st.as_dict()) if st is not None else fv
 
 
 def kmeans_workspace(clusters, device=None):

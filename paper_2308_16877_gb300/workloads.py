@@ -329,3 +329,18 @@ def sweep_inputs(sizes, seed: int = DEFAULT_SEED, ipt: int = 8):
         regions.append((int(n), off, max(1, int(n) // ipt)))
         off += n
     return x, regions
+
+
+# LavaMD-style particles: coordinates and charges uniform in [0.1, 1.0), drawn
+# independently of the particle's box (the boxes only decide which particles
+# interact), so every box is a statistically alike sample of the same cloud.
+LAVAMD_A2 = 0.5          # exp(-a2 r^2) with a2 = 2 alpha^2, alpha = 0.5
+LAVAMD_PAR_PER_BOX = 100
+
+
+def lavamd_inputs(boxes1d: int, par_per_box: int = LAVAMD_PAR_PER_BOX,
+                  seed: int = DEFAULT_SEED) -> np.ndarray:
+    """(4, boxes1d^3 par_per_box) float64: x, y, z, charge of particle
+    b * par_per_box + m (box b = (bz B + by) B + bx)."""
+    P = int(boxes1d) ** 3 * int(par_per_box)
+    return _rng(seed, 9).uniform(0.1, 1.0, (4, P))
