@@ -722,6 +722,10 @@ def bench_levels(hpac, torch, dev, stream, n=1 << 22, clusters=64, reps=5):
 # differences, r^2 (a multiply and two FMAs), the exponent's scaling, q v,
 # 2 q v, the potential's add and three force FMAs.
 LAVAMD_PAIR_FP64_OPS = 13
+# FP64 instructions the exact kernel executes per pair term, the exponential
+# included, as counted by ncu at 8^3 boxes (smsp__sass_thread_inst_executed_op_
+# {dadd,dmul,dfma}_pred_on: 4.05 + 3.00 + 21.00 per pair).
+LAVAMD_PAIR_FP64_INSTR = 28.05
 
 
 def bench_lavamd(hpac, torch, dev, stream, boxes1d=16, reps=3):
@@ -777,10 +781,17 @@ def bench_lavamd(hpac, torch, dev, stream, boxes1d=16, reps=3):
     within = [r for r in rows if r["potential_mape"] <= QUALITY_BOUND]
     best = max(within, key=lambda r: r["speedup_vs_exact"]) if within else None
     ops = LAVAMD_PAIR_FP64_OPS * pairs / (exact_ms * 1e-3)
+    instr = LAVAMD_PAIR_FP64_INSTR * pairs / (exact_ms * 1e-3)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak = FP64_FMA_PER_SM_CLK * sms * 2070e6
     return {"boxes": f"{B}^3", "particles": P, "par_per_box": NP, "invocations": inv,
             "pair_terms": pairs, "exact_ms": exact_ms, "exact_pairs_per_s": pairs / (exact_ms * 1e-3),
             "exact_fp64_ops_outside_exp_per_s": ops,
-            "exact_fp64_outside_exp_frac_of_measured_fma_rate": ops / (fp64 / 2.0 * 1e12),
+            "roofline": {"bound": "alu", "unit": "T FP64-instr/s", "achieved": instr / 1e12,
+                         "peak": peak / 1e12, "frac": instr / peak,
+                         "peak_source": f"derived: {FP64_FMA_PER_SM_CLK} FP64 FMA/SM/clk x {sms} SMs x 2070 MHz",
+                         "frac_of_measured_fma": instr / (fp64 / 2.0 * 1e12),
+                         "instr_per_pair": LAVAMD_PAIR_FP64_INSTR},
             "table": rows, "fastest_within_1pct_potential_mape": best}
 
 
