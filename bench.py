@@ -724,8 +724,8 @@ def bench_levels(hpac, torch, dev, stream, n=1 << 22, clusters=64, reps=5):
 LAVAMD_PAIR_FP64_OPS = 13
 # FP64 instructions the exact kernel executes per pair term, the exponential
 # included, as counted by ncu at 8^3 boxes (smsp__sass_thread_inst_executed_op_
-# {dadd,dmul,dfma}_pred_on: 4.05 + 3.00 + 21.00 per pair).
-LAVAMD_PAIR_FP64_INSTR = 28.05
+# {dadd,dmul,dfma}_pred_on: 5.05 + 4.00 + 15.00 per pair).
+LAVAMD_PAIR_FP64_INSTR = 24.05
 
 
 def bench_lavamd(hpac, torch, dev, stream, boxes1d=16, reps=3):
