@@ -7,11 +7,11 @@
 // ceil(NP / 32) * 32 threads). The block walks the box's neighbour sequence
 // (the home box, then the touching boxes in the order dz, dy, dx); at each
 // step the neighbour's NP particles are staged in shared memory once for the
-// whole block, and every thread that computes exactly sums its NP pair terms
-// from there (broadcast reads). A step in which no thread of the block
-// computes stages nothing, so decisions taken per block drop the step's
-// loads as well as its arithmetic, and per-warp decisions drop whole warps'
-// arithmetic (Section 3.3: warp-uniform decisions remove divergence).
+// whole block. Each warp then sums the pair terms of its computing lanes'
+// particles, four lanes to a particle (box_force), so its cost follows the
+// number of particles it computes rather than the slowest lane. A step in
+// which no thread of the block computes stages nothing, so decisions taken
+// per block drop the step's loads as well as its arithmetic.
 //
 // TAF: per particle, a window of the last hsize accurate outputs (four
 // components) in shared memory, column per thread; the statistic is the RSD
@@ -67,38 +67,80 @@ __host__ __device__ inline size_t lmd_smem(int tech, int NP, int NL, int h, int 
   return b;
 }
 
-// The contribution of the staged box to the particle at (xp, yp, zp). The
-// exponential is Tang's table-driven one (10 FP64 operations against 15 for
-// the library's) while every active lane's argument lies within +-700, the
-// library's otherwise.
+// The contribution of the staged box to every computing lane's particle,
+// computed by the whole warp. The computing lanes' particles go in groups of
+// eight; within a group four lanes share a particle, each sums the pair terms
+// j = quarter + 4 t, and the four partial sums meet by two shuffle levels. So
+// c computing lanes cost the warp ceil(c / 8) ceil(NP / 4) rounds of the pair
+// loop, where one lane per particle would cost NP rounds whatever c is: a
+// warp with a few computing lanes (thread-level decisions, or the last,
+// partly filled warp of a box) is not held for a full pass. The exponential
+// is Tang's table-driven one (10 FP64 operations against 15 for the
+// library's) while every active lane's argument lies within +-700, the
+// library's otherwise. Called by all lanes of the warp; y is written on the
+// computing lanes only.
 __device__ __forceinline__ void box_force(const double *__restrict__ sx, const double *__restrict__ sy,
                                           const double *__restrict__ sz, const double *__restrict__ sq,
-                                          int NP, double na2, double xp, double yp, double zp,
-                                          const double *__restrict__ etab, double inv_l, double l1,
-                                          double l2, double (&y)[4]) {
-  double pot = 0.0, fx = 0.0, fy = 0.0, fz = 0.0;
+                                          int NP, double na2, bool compute, double xp, double yp,
+                                          double zp, const double *__restrict__ etab, double inv_l,
+                                          double l1, double l2, double (&y)[4]) {
+  constexpr unsigned kAll = 0xffffffffu;
+  const int lane = threadIdx.x & 31, sub = lane >> 2, quarter = lane & 3;
+  unsigned rest = __ballot_sync(kAll, compute);
+  while (rest) {
+    // this group: the next (up to) eight computing lanes, the s-th on sub-group s
+    unsigned group = 0;
+    int src = -1;
+#pragma unroll
+    for (int s = 0; s < 8; ++s) {
+      const unsigned low = rest & (0u - rest);
+      if (s == sub && low) src = __ffs(low) - 1;
+      group |= low;
+      rest ^= low;
+    }
+    const int from = src >= 0 ? src : lane;
+    const double px = __shfl_sync(kAll, xp, from), py = __shfl_sync(kAll, yp, from),
+                 pz = __shfl_sync(kAll, zp, from);
+    double pot = 0.0, fx = 0.0, fy = 0.0, fz = 0.0;
+    if (src >= 0) {
 #pragma unroll 4
-  for (int m = 0; m < NP; ++m) {
-    const double dx = xp - sx[m], dy = yp - sy[m], dz = zp - sz[m];
-    const double r2 = fma(dz, dz, fma(dy, dy, dx * dx));
-    const double u = na2 * r2;
-    const bool fast = exp_tang_in_range(u);
-    double v;
-    if (__all_sync(__activemask(), fast))
-      v = exp_tang(u, etab, inv_l, l1, l2);
-    else
-      v = fast ? exp_tang(u, etab, inv_l, l1, l2) : exp(u);
-    const double qv = sq[m] * v;
-    const double t = qv + qv;  // q fs with fs = 2 v
-    pot += qv;
-    fx = fma(t, dx, fx);
-    fy = fma(t, dy, fy);
-    fz = fma(t, dz, fz);
+      for (int m = quarter; m < NP; m += 4) {
+        const double dx = px - sx[m], dy = py - sy[m], dz = pz - sz[m];
+        const double r2 = fma(dz, dz, fma(dy, dy, dx * dx));
+        const double u = na2 * r2;
+        const bool fast = exp_tang_in_range(u);
+        double v;
+        if (__all_sync(__activemask(), fast))
+          v = exp_tang(u, etab, inv_l, l1, l2);
+        else
+          v = fast ? exp_tang(u, etab, inv_l, l1, l2) : exp(u);
+        const double qv = sq[m] * v;
+        const double t = qv + qv;  // q fs with fs = 2 v
+        pot += qv;
+        fx = fma(t, dx, fx);
+        fy = fma(t, dy, fy);
+        fz = fma(t, dz, fz);
+      }
+    }
+#pragma unroll
+    for (int off = 1; off < 4; off <<= 1) {
+      pot += __shfl_xor_sync(kAll, pot, off);
+      fx += __shfl_xor_sync(kAll, fx, off);
+      fy += __shfl_xor_sync(kAll, fy, off);
+      fz += __shfl_xor_sync(kAll, fz, off);
+    }
+    // each computing lane of the group takes its sub-group's sums
+    const bool mine = (group >> lane) & 1u;
+    const int at = mine ? 4 * __popc(group & ((1u << lane) - 1u)) : lane;
+    const double r0 = __shfl_sync(kAll, pot, at), r1 = __shfl_sync(kAll, fx, at),
+                 r2 = __shfl_sync(kAll, fy, at), r3 = __shfl_sync(kAll, fz, at);
+    if (mine) {
+      y[0] = r0;
+      y[1] = r1;
+      y[2] = r2;
+      y[3] = r3;
+    }
   }
-  y[0] = pot;
-  y[1] = fx;
-  y[2] = fy;
-  y[3] = fz;
 }
 
 template <int TECH, int LEVEL, int MAXT>
@@ -224,9 +266,9 @@ __global__ void __launch_bounds__(MAXT) lavamd_kernel(LmdArgs a) {
       }
       __syncthreads();
     }
+    box_force(sx, sy, sz, sq, NP, a.na2, compute, xp, yp, zp, s_exp, a.ex.inv_l, a.ex.l1, a.ex.l2, y);
     bool decided = false, wants = false;
     if (compute) {
-      box_force(sx, sy, sz, sq, NP, a.na2, xp, yp, zp, s_exp, a.ex.inv_l, a.ex.l1, a.ex.l2, y);
       if (a.mask) a.mask[(int64_t)k * P + pidx] = HPAC_MASK_EXACT;
       if (TECH == LMD_TAF) {
         int slot;
