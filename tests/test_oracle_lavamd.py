@@ -226,3 +226,94 @@ def test_taf_thread_level_decisions_follow_numpy_rsd(h, p, thr):
                     pred = p
         assert np.abs(fv[:, q] - acc).max() <= 1e-12 * np.abs(acc).max()
     assert cnt[1] == n_apx and n_apx > 0
+
+
+def line_of_four(B, xs, charges=None):
+    """NP = 4 particles per box at x = xs (y = z = 0.5) in every box; charges
+    [box][particle] or all 0.5."""
+    NP = len(xs)
+    nbox = B ** 3
+    rq = np.zeros((4, nbox * NP))
+    for b in range(nbox):
+        for j, x in enumerate(xs):
+            p = b * NP + j
+            rq[:, p] = [x, 0.5, 0.5, 0.5 if charges is None else charges[b][j]]
+    return rq
+
+
+@pytest.mark.parametrize("level", [oracle.THREAD, oracle.WARP, oracle.BLOCK])
+def test_iact_shared_table_writes_the_farthest_exact_lane(level):
+    """Four particles on a line (x = 0.10, 0.11, 0.60, 0.90) in each of the 8
+    boxes of a 2^3 grid, one table for the warp, threshold 0.2. The entries
+    each rule stores, worked out by hand:
+      k = 0: the table is empty, all compute; the writer is lane 0 (all
+             distances +inf, lowest lane) -> entry A (x = 0.10).
+      thread level: k = 1: lanes 0, 1 hit A; lanes 2, 3 compute; the writer is
+             lane 3 (0.8 from A against 0.5) -> entry D. k = 2: lane 3 hits D,
+             lane 2 (0.3 from D) computes and writes C. Later every lane hits.
+      warp or block level (the block is the one warp): k = 1: 2 of 4 lanes
+             want, no majority, all compute, lane 3 writes D. k = 2: lanes 0,
+             1, 3 want; the majority makes lane 2 take its nearest entry, D.
+    """
+    B, xs = 2, [0.10, 0.11, 0.60, 0.90]
+    rq = line_of_four(B, xs)
+    fv, cnt, m = oracle.lavamd(B, 4, A2, rq, technique=oracle.LAVAMD_IACT, level=level, tsize=4,
+                               tperwarp=1, thresh=0.2, mask=True)
+    ys = per_invocation(B, 4, rq)
+    P = 8 * 4
+    for h in range(8):
+        y = [ys[h * 4 + j] for j in range(4)]
+        if level == oracle.THREAD:
+            expect = [8 * y[0][0],
+                      y[1][0] + 7 * y[0][0],
+                      y[2][0] + y[2][1] + 6 * y[2][2],
+                      y[3][0] + 7 * y[3][1]]
+            apx = [[0] + [1] * 7, [0] + [1] * 7, [0, 0, 0] + [1] * 5, [0, 0] + [1] * 6]
+        else:
+            expect = [7 * y[0][0] + y[0][1],
+                      y[1][0] + y[1][1] + 6 * y[0][0],
+                      y[2][0] + y[2][1] + 6 * y[3][1],
+                      y[3][0] + 7 * y[3][1]]
+            apx = [[0, 0] + [1] * 6] * 4
+        for j in range(4):
+            p = h * 4 + j
+            assert np.abs(fv[:, p] - expect[j]).max() <= 1e-13 * np.abs(expect[j]).max()
+            assert [int(m[k * P + p]) for k in range(8)] == apx[j]
+
+
+@pytest.mark.parametrize("steady", [3, 2])
+@pytest.mark.parametrize("level", [oracle.THREAD, oracle.WARP, oracle.BLOCK])
+def test_taf_majority_forces_the_minority(level, steady):
+    """Four particles 0.2 apart with a2 = 1000, so each feels only its own
+    index in every box (cross terms e^-40). Particle j's potential from box b
+    is then its charge c[b][j]: 1 for j = 0, 1, 2 (window RSD ~ 0) and 2^b for
+    j = 3 (any two boxes differ twofold: RSD >= 1/3). h = 2, p = 2, threshold
+    0.1, 8 invocations each. Lanes 0-2 want to predict whenever their window
+    is full: exact, exact, 2 predicted, exact, 2 predicted, exact. Lane 3
+    never wants: at thread level it computes all 8; at warp and block level
+    the 3-of-4 majority makes it follow the same pattern, repeating its
+    newest exact output. With two steady lanes (2 of 4 is no majority) warp
+    and block level predict nothing."""
+    B, xs = 2, [0.1, 0.3, 0.5, 0.7]
+    ch = [[1.0 if j < steady else 2.0 ** b for j in range(4)] for b in range(8)]
+    rq = line_of_four(B, xs, ch)
+    fv, cnt, m = oracle.lavamd(B, 4, 1000.0, rq, technique=oracle.LAVAMD_TAF, level=level, hsize=2, psize=2,
+                               thresh=0.1, mask=True)
+    ys = per_invocation(B, 4, rq, a2=1000.0)
+    P = 32
+    pattern = [0, 0, 1, 1, 0, 1, 1, 0]
+    for h in range(8):
+        for j in range(4):
+            p = h * 4 + j
+            if level == oracle.THREAD:
+                pat = pattern if j < steady else [0] * 8
+            else:
+                pat = pattern if steady == 3 else [0] * 8
+            acc, newest = np.zeros(4), None
+            for k, a in enumerate(pat):
+                if not a:
+                    newest = ys[p][k]
+                acc = acc + newest
+            assert [int(m[k * P + p]) for k in range(8)] == pat
+            assert np.abs(fv[:, p] - acc).max() <= 1e-13 * np.abs(acc).max()
+    assert cnt[3] == 0
