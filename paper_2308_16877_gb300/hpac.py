@@ -480,12 +480,17 @@ def lavamd(rq, boxes1d, par_per_box, a2=0.5, technique=LAVAMD_EXACT, level=HPAC_
     mask: an optional uint8 tensor of 27 P bytes."""
     import torch
     P = int(boxes1d) ** 3 * int(par_per_box)
-    if tuple(rq.shape) != (4, P) or rq.dtype != torch.float64 or not rq.is_contiguous():
-        raise ValueError("rq must be a contiguous (4, boxes1d^3 par_per_box) float64 tensor")
+    if (tuple(rq.shape) != (4, P) or rq.dtype != torch.float64 or not rq.is_contiguous()
+            or not rq.is_cuda):
+        raise ValueError("rq must be a contiguous (4, boxes1d^3 par_per_box) float64 CUDA tensor")
     if fv is None:
         fv = torch.empty_like(rq)
-    if mask is not None and mask.numel() < 27 * P:
-        raise ValueError("mask needs 27 P bytes")
+    if (tuple(fv.shape) != (4, P) or fv.dtype != torch.float64 or not fv.is_contiguous()
+            or fv.device != rq.device):
+        raise ValueError("fv must be a contiguous (4, P) float64 tensor on rq's device")
+    if mask is not None and (mask.dtype != torch.uint8 or not mask.is_contiguous()
+                             or mask.device != rq.device or mask.numel() < 27 * P):
+        raise ValueError("mask must be a contiguous uint8 tensor of 27 P bytes on rq's device")
     desc = hpac_lavamd_desc(int(boxes1d), int(par_per_box), float(a2))
     knobs = None
     if technique == LAVAMD_TAF:

@@ -49,7 +49,7 @@ def test_struct_layouts_match_header(tmp_path):
     probe = tmp_path / "probe.c"
     structs = ["hpac_region_desc", "hpac_perfo_knobs", "hpac_taf_knobs", "hpac_iact_knobs",
                "hpac_stats", "hpac_quality_result", "hpac_hydro_state", "hpac_sweep_config",
-               "hpac_sweep_region", "hpac_sweep_stats", "hpac_mlp_desc"]
+               "hpac_sweep_region", "hpac_sweep_stats", "hpac_mlp_desc", "hpac_lavamd_desc"]
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "hpac.h"', "int main(void){"]
     for s in structs:
         lines.append(f'printf("{s} %zu\\n", sizeof({s}));')
@@ -98,3 +98,36 @@ def test_invalid_arguments_are_rejected_before_any_device_work():
         assert hpac.hpac_last_error(), name
     # destroying NULL is a no-op, as free(NULL)
     assert L.hpac_region_destroy(None) == hpac.HPAC_OK
+    # LavaMD: descriptor, technique, knobs and pointers are checked first; an
+    # empty grid is a no-op
+    D = hpac.hpac_lavamd_desc
+    taf = hpac.hpac_taf_knobs(4, 8, 0.01, 0, 0)
+    bad_taf = hpac.hpac_taf_knobs(0, 8, 0.01, 0, 0)
+    bad_iact = hpac.hpac_iact_knobs(8, 3, 0.01, 0, 0, None)
+    lavamd_calls = [
+        (None, 0, None, None, None),
+        (C.byref(D(2, 0, 0.5)), 0, None, None, None),
+        (C.byref(D(2, 1025, 0.5)), 0, None, None, None),
+        (C.byref(D(2, 4, -1.0)), 0, None, None, None),
+        (C.byref(D(2, 4, 0.5)), 3, None, None, None),
+        (C.byref(D(2, 4, 0.5)), 1, None, None, None),
+        (C.byref(D(2, 4, 0.5)), 1, C.byref(bad_taf), None, None),
+        (C.byref(D(2, 4, 0.5)), 2, C.byref(bad_iact), None, None),
+        (C.byref(D(2, 4, 0.5)), 1, C.byref(taf), None, None),       # NULL arrays
+        (C.byref(D(2, 4, 0.5)), 0, None, 8 + 4, 16),                 # misaligned
+    ]
+    for desc, tech, kn, rq, fv in lavamd_calls:
+        status = L.hpac_lavamd_run(desc, tech, kn, rq, fv, None, None, None)
+        assert status == EINVAL, (tech, status)
+    st = hpac.hpac_stats(7, 7, 7, 7)
+    assert L.hpac_lavamd_run(C.byref(D(0, 4, 0.5)), 0, None, None, None, None, C.byref(st), None) == hpac.HPAC_OK
+    assert (st.invocations, st.approximated) == (0, 0)
+
+
+def test_lavamd_binding_rejects_host_tensors():
+    torch = pytest.importorskip("torch")
+    from paper_2308_16877_gb300 import hpac
+    with pytest.raises(ValueError):
+        hpac.lavamd(torch.zeros(4, 8, dtype=torch.float64), 1, 8)
+    with pytest.raises(ValueError):
+        hpac.lavamd(torch.zeros(4, 9, dtype=torch.float64), 1, 8)
