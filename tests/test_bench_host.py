@@ -36,3 +36,65 @@ def test_headline_forms_and_oracle_knobs():
     for f in bench.HEAD_FORMS:
         k = bench.form_oracle_knobs(oracle, f, 8)
         assert k.mode == f[1] and (k.st[0] is not None) == f[2]
+
+
+def test_lavamd_section_plumbing(monkeypatch):
+    """The LavaMD section's bookkeeping on a 3^3 grid, with the library
+    replaced by the oracle and CUDA events by a fixed clock: every form is
+    timed at every level and scored against the exact run, and the roofline
+    counts the pair terms the oracle reports."""
+    import types
+
+    import torch
+
+    import oracle
+
+    class Event:
+        def __init__(self, enable_timing=False):
+            pass
+
+        def record(self, stream=None):
+            pass
+
+        def elapsed_time(self, other):
+            return 12.0
+
+    monkeypatch.setattr(torch.cuda, "Event", Event)
+    monkeypatch.setattr(torch.cuda, "synchronize", lambda *a, **k: None)
+    monkeypatch.setattr(torch.cuda, "get_device_properties",
+                        lambda d: types.SimpleNamespace(multi_processor_count=152))
+
+    class Lib:
+        LAVAMD_TAF, LAVAMD_IACT = oracle.LAVAMD_TAF, oracle.LAVAMD_IACT
+        HPAC_LEVEL_THREAD, HPAC_LEVEL_WARP, HPAC_LEVEL_BLOCK = oracle.THREAD, oracle.WARP, oracle.BLOCK
+        HPAC_METRIC_MAPE, HPAC_METRIC_RMSE = oracle.MAPE, oracle.RMSE
+
+        @staticmethod
+        def lavamd(rq, B, NP, a2, technique=0, fv=None, stats=False, stream=None, level=0, **kn):
+            kn = {k: v for k, v in kn.items() if k != "reset_on_exit"}
+            out, cnt, _ = oracle.lavamd(B, NP, a2, rq.numpy(), technique=technique, level=level, **kn)
+            fv.copy_(torch.from_numpy(out))
+            st = {"invocations": int(cnt[0]), "approximated": int(cnt[1]), "skipped": 0,
+                  "borderline": int(cnt[3])}
+            return (fv, st) if stats else fv
+
+        @staticmethod
+        def quality(a, b, metric, stream=None):
+            return {"value": oracle.quality(a.numpy(), b.numpy(), metric)[0]}
+
+        @staticmethod
+        def hpac_device_fp64_rate(stream=None):
+            return 1.0
+
+    r = bench.bench_lavamd(Lib, torch, torch.device("cpu"), types.SimpleNamespace(cuda_stream=None),
+                           boxes1d=3)
+    assert r["invocations"] == 7 ** 3 * 100 and r["pair_terms"] == r["invocations"] * 100
+    assert len(r["table"]) == 12
+    assert {(t["technique"], t["level"]) for t in r["table"]} == {
+        (t, lv) for t in ("taf", "iact") for lv in ("thread", "warp", "block")}
+    for t in r["table"]:
+        assert t["speedup_vs_exact"] == 1.0 and 0.0 <= t["approximated"] <= 1.0
+        assert t["potential_mape"] >= 0.0 and t["force_nrmse"] >= 0.0
+    rl = r["roofline"]
+    assert abs(rl["frac"] - rl["achieved"] / rl["peak"]) <= 1e-12
+    assert abs(rl["achieved"] * 1e12 - bench.LAVAMD_PAIR_FP64_INSTR * r["pair_terms"] / 12e-3) < 1.0
