@@ -97,4 +97,6 @@ def test_lavamd_section_plumbing(monkeypatch):
         assert t["potential_mape"] >= 0.0 and t["force_nrmse"] >= 0.0
     rl = r["roofline"]
     assert abs(rl["frac"] - rl["achieved"] / rl["peak"]) <= 1e-12
-    assert abs(rl["achieved"] * 1e12 - bench.LAVAMD_PAIR_FP64_INSTR * r["pair_terms"] / 12e-3) < 1.0
+    assert r["exact_ms"] == 12.0 / 3       # three timed repetitions in 12 ms
+    expect = bench.LAVAMD_PAIR_FP64_INSTR * r["pair_terms"] / (r["exact_ms"] * 1e-3)
+    assert abs(rl["achieved"] * 1e12 - expect) <= 1e-9 * expect
