@@ -25,7 +25,8 @@ against the exact run on the same GPU; `roofline` covers the dominant kernel
 fraction; `cpu_baseline` is the CPU oracle on a bounded sample of the same run.
 Every other configuration (Black-Scholes at 65,536 and 2^24 options, the
 64^3 hydro run, the batched knob sweep, the surrogate, Binomial Options,
-K-Means and the other added workloads) is a section printed on its own line
+K-Means, the LavaMD-style forces and the other added workloads) is a section
+printed on its own line
 before the final one, and the whole record is written to the --detail file
 (by default _build/bench_detail.json at the repository root, which git
 ignores).
