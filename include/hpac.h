@@ -371,6 +371,9 @@ hpac_status hpac_hydro_run(const hpac_hydro_state *s, hpac_region *eos, int32_t 
  * and fv_p sums the invocations of p's neighbour sequence: its own box, then
  * the touching boxes inside the grid at offsets (dx, dy, dz) != 0 in the
  * order dz, dy, dx (dx fastest); (3 boxes1d - 2)^3 NP invocations in all.
+ * Arithmetic: FP64 with fused multiply-adds; the exponential within two ulps
+ * (a table-driven method for |a2 r^2| <= 700, CUDA's exp beyond); each
+ * invocation's NP terms summed in four interleaved partial sums.
  *
  * The block of a home box holds its NP particles on ceil(NP/32) warps; its
  * lanes advance through the sequence together. technique 0: exact. 1: TAF
