@@ -317,3 +317,29 @@ def test_taf_majority_forces_the_minority(level, steady):
             assert [int(m[k * P + p]) for k in range(8)] == pat
             assert np.abs(fv[:, p] - acc).max() <= 1e-13 * np.abs(acc).max()
     assert cnt[3] == 0
+
+
+@pytest.mark.parametrize("h,p", [(1, 1), (2, 3), (3, 2), (4, 8)])
+def test_taf_infinite_threshold_with_the_window_emptied_after_a_run(h, p):
+    """The reset-on-exit reading: after p predictions the window is emptied,
+    so h accurate outputs refill it before the next run. With thr = +inf the
+    pattern is (h exact, p predicted) repeated."""
+    B, NP = 3, 5
+    rq = inputs(B, NP, 12)
+    fv, cnt, m = oracle.lavamd(B, NP, A2, rq, technique=oracle.LAVAMD_TAF, hsize=h, psize=p,
+                               thresh=np.inf, reset=1, mask=True)
+    ys = per_invocation(B, NP, rq)
+    P = B ** 3 * NP
+    total = 0
+    for q in range(P):
+        nn = len(ys[q])
+        pat = [0 if k % (h + p) < h else 1 for k in range(nn)]
+        total += sum(pat)
+        acc, newest = np.zeros(4), None
+        for k, a in enumerate(pat):
+            if not a:
+                newest = ys[q][k]
+            acc = acc + newest
+            assert m[k * P + q] == a
+        assert np.abs(fv[:, q] - acc).max() <= 1e-13 * np.abs(acc).max()
+    assert cnt[1] == total
