@@ -343,3 +343,25 @@ def test_taf_infinite_threshold_with_the_window_emptied_after_a_run(h, p):
             assert m[k * P + q] == a
         assert np.abs(fv[:, q] - acc).max() <= 1e-13 * np.abs(acc).max()
     assert cnt[1] == total
+
+
+@pytest.mark.parametrize("level", [oracle.THREAD, oracle.WARP, oracle.BLOCK])
+def test_iact_infinite_threshold_one_table_per_warp(level):
+    """One table per warp and thr = +inf: at the first step the table is empty,
+    every lane computes and the lowest lane writes (all distances +inf); from
+    then on every lane hits that single entry, so nothing is written again and
+    every later invocation repeats the warp's first lane's home-box output.
+    40 particles per box: warps of 32 and 8 lanes."""
+    B, NP = 3, 40
+    rq = inputs(B, NP, 13)
+    fv, cnt, m = oracle.lavamd(B, NP, A2, rq, technique=oracle.LAVAMD_IACT, level=level, tsize=4,
+                               tperwarp=1, thresh=np.inf, mask=True)
+    ys = per_invocation(B, NP, rq)
+    P = B ** 3 * NP
+    for q in range(P):
+        lead = (q // NP) * NP + ((q % NP) // 32) * 32
+        nn = len(ys[q])
+        expect = ys[q][0] + (nn - 1) * ys[lead][0]
+        assert np.abs(fv[:, q] - expect).max() <= 1e-13 * np.abs(expect).max()
+        assert [int(m[k * P + q]) for k in range(nn)] == [0] + [1] * (nn - 1)
+    assert cnt[1] == cnt[0] - P
